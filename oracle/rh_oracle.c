@@ -1,0 +1,1353 @@
+/*
+ * rh_oracle.c -- plain, slow FP64 CPU oracle of the column-by-column (1.5D)
+ * MALI hot path.  TEST INFRASTRUCTURE ONLY: it is called by the test-suite,
+ * by the package's smoke check and by the benchmark's CPU-baseline leg, never
+ * by the product path.  It shares no code, header or table with the CUDA path.
+ *
+ * What it follows (the paper prints no equation of the method, so every
+ * formula below is the standard form of the method the paper cites):
+ *   - Sect. 2.1: MALI with a local (diagonal) approximate Psi operator and
+ *     preconditioned rate equations (Rybicki & Hummer 1992), overlapping
+ *     transitions sharing chi and eta at a wavelength.
+ *   - Sect. 2.2: each column is an independent plane-parallel problem; only the
+ *     vertical emergent spectrum is produced.
+ *   - Sect. 2.3: Ng acceleration (order 2), LTE start solution, per-column
+ *     convergence on the maximum relative population change (1e-3).
+ *   - Sect. 3.1 (pool mode): columns are handed out dynamically to workers
+ *     (here: threads pulling column indices from a shared counter).
+ * Readings where the paper is silent (formal-solver scheme, atom data,
+ * background opacity, boundary conditions, Ng schedule) are listed in the
+ * design notes and restated at each function.
+ *
+ * Parity status: every function is pinned by a test against closed forms,
+ * limits or an independent library routine, except the overall multi-level
+ * emergent intensities of the synthetic chromosphere, which have no printed
+ * values ("parity unpinned" beyond oracle self-consistency, Newton residual
+ * and limit checks).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+/* ---- physical constants, SI (CODATA 2018; h, c, k, e exact) ---- */
+#define HPLANCK 6.62607015e-34
+#define CLIGHT 2.99792458e8
+#define KBOLTZ 1.380649e-23
+#define QELEC 1.602176634e-19
+#define MELEC 9.1093837015e-31
+#define EPS0 8.8541878128e-12
+#define AMU 1.66053906660e-27
+#define SIGMA_T 6.6524587321e-29
+#define E_RYDBERG (13.605693122994 * QELEC)
+#define PI_D 3.14159265358979323846
+
+#define MAXLEV 16
+#define MAXTR 64
+#define MAXACT 8
+
+/* ------------------------------------------------------------------ */
+/* public descriptor (same field order as the CUDA library's, declared  */
+/* separately on purpose)                                               */
+typedef struct {
+    int32_t nlev;
+    const double *E_J, *g;
+    int32_t nline;
+    const int32_t *line_l, *line_u;
+    const double *line_f, *line_a_top, *line_a_bot;
+    const int32_t *line_nlambda;
+    const double *line_qwing;
+    int32_t ncont;
+    const int32_t *cont_l;
+    const double *cont_alpha0;
+    const int32_t *cont_nlambda;
+    const double *cont_ratio;
+    double mass_amu, T_ref;
+    int32_t nmu;
+    double metal_floor;
+} rho_atom_desc;
+
+typedef struct {
+    int32_t maxiter;
+    double tol;
+    int32_t ng_order, ng_delay, ng_period;
+    int32_t start;      /* 0 LTE, 2 user populations */
+    double crsw_init;   /* collisional-radiative switching start factor; <=1 off */
+} rho_iter_opts;
+
+typedef struct {
+    int64_t n_converged, n_maxiter, n_failed;
+    int64_t iterations_total;
+    double seconds, pts, max_dn_final;
+} rho_iter_stats;
+
+enum { ST_CONV = 0, ST_MAXITER = 1, ST_NONFINITE = 2, ST_SINGULAR = 3, ST_NOTRUN = 4 };
+
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int nlev, nline, ncont, ntr, nmu;
+    double E[MAXLEV], g[MAXLEV];
+    /* transitions: t < nline lines, then continua; upper of a continuum = nlev-1 */
+    int tl[MAXTR], tu[MAXTR], kind[MAXTR];
+    double nu0[MAXTR];            /* line centre or edge frequency */
+    double f[MAXTR], A[MAXTR], Blu[MAXTR], Bul[MAXTR];
+    double a_top[MAXTR], a_bot[MAXTR], qwing[MAXTR];
+    double alpha0[MAXTR], ratio[MAXTR];
+    int nlam_t[MAXTR];
+    double nu_lo[MAXTR], nu_hi[MAXTR];
+    double mass, T_ref, floor_e;
+    double mu[16], wmu[16];
+    /* wavelength grid */
+    int64_t nlam;
+    double *nu;                   /* [nlam] */
+    int *nact;                    /* [nlam] */
+    int *act;                     /* [nlam][MAXACT] transition index */
+    double *wq;                   /* [nlam][MAXACT] quadrature weight (Hz) of that transition */
+    int *prof_slot;               /* [nlam][MAXACT] line-profile block index, -1 for continua */
+    int nprof;                    /* number of (lambda, line) pairs */
+} atom_t;
+
+struct rho_ctx {
+    char err[512];
+    int have_atom;
+    atom_t at;
+    int64_t ncol;
+    int ndep;
+    double *z, *T, *nH, *vz, *ne, *np;   /* [ncol][ndep] */
+    double *nstar;                        /* [ncol][nlev][ndep] */
+    double *pops;                         /* [ncol][nlev][ndep] */
+    int32_t *iters;
+    uint8_t *status;
+    double *dmax;
+};
+typedef struct rho_ctx rho_ctx;
+
+static int fail(rho_ctx *c, const char *msg)
+{
+    snprintf(c->err, sizeof c->err, "%s", msg);
+    return 1;
+}
+
+/* ================================================================== */
+/* Special functions                                                   */
+/* ================================================================== */
+
+/* Voigt function H(a,v) = Re w(v + i a), w the Faddeeva function, using
+ * Weideman's (1994, SIAM J. Numer. Anal. 31, 1497) rational expansion with
+ * N = 40 terms; the coefficients come from a discrete Fourier transform
+ * computed once.  Pinned against scipy.special.wofz. */
+#define WN 40
+static double w_coef[WN];
+static double w_L;
+static pthread_once_t w_once = PTHREAD_ONCE_INIT;
+
+static void weideman_init(void)
+{
+    const int M = 2 * WN, M2 = 2 * M;
+    double L = sqrt(WN / sqrt(2.0));
+    double *f = calloc(M2, sizeof(double));
+    double *g = calloc(M2, sizeof(double));
+    /* f[0] = 0, f[1 + (k + M - 1)] for k = -M+1 .. M-1 */
+    for (int k = -M + 1; k <= M - 1; ++k) {
+        double th = k * PI_D / M;
+        double t = L * tan(th / 2);
+        f[k + M] = exp(-t * t) * (L * L + t * t);
+    }
+    f[0] = 0.0;
+    for (int i = 0; i < M2; ++i) g[i] = f[(i + M) % M2];   /* fftshift */
+    double a[WN + 1];
+    for (int m = 0; m <= WN; ++m) {
+        double s = 0.0;
+        for (int i = 0; i < M2; ++i) s += g[i] * cos(2.0 * PI_D * (double)m * i / M2);
+        a[m] = s / M2;
+    }
+    for (int n = 0; n < WN; ++n) w_coef[n] = a[n + 1];   /* p(Z) = sum a[n+1] Z^n */
+    w_L = L;
+    free(f);
+    free(g);
+}
+
+typedef struct { double re, im; } cplx;
+static cplx cmul(cplx x, cplx y) { cplx r = {x.re * y.re - x.im * y.im, x.re * y.im + x.im * y.re}; return r; }
+static cplx cdiv(cplx x, cplx y)
+{
+    double d = y.re * y.re + y.im * y.im;
+    cplx r = {(x.re * y.re + x.im * y.im) / d, (x.im * y.re - x.re * y.im) / d};
+    return r;
+}
+
+double rho_voigt(double a, double v)
+{
+    pthread_once(&w_once, weideman_init);
+    /* z = v + i a;  den = L - i z = (L + a) - i v;  Z = (L + i z)/den */
+    cplx den = {w_L + a, -v};
+    cplx num = {w_L - a, v};
+    cplx Z = cdiv(num, den);
+    cplx p = {0.0, 0.0};
+    for (int n = WN - 1; n >= 0; --n) {
+        p = cmul(p, Z);
+        p.re += w_coef[n];
+    }
+    cplx den2 = cmul(den, den);
+    cplx t1 = cdiv(p, den2);
+    cplx one = {1.0 / sqrt(PI_D), 0.0};
+    cplx t2 = cdiv(one, den);
+    return 2.0 * t1.re + t2.re;
+}
+
+/* e^y E1(y) for y > 0: power series for y <= 1, continued fraction
+ * E1(y) = e^{-y} / (y + 1 - 1/(y + 3 - 4/(y + 5 - ...))) otherwise
+ * (Abramowitz & Stegun 5.1.11 and 5.1.22).  Pinned against scipy.special.exp1. */
+double rho_expE1(double y)
+{
+    if (y <= 1.0) {
+        const double gam = 0.57721566490153286061;
+        double s = 0.0, term = 1.0;
+        for (int n = 1; n < 200; ++n) {
+            term *= -y / n;
+            double add = term / n;
+            s += add;
+            if (fabs(add) < 1e-18 * fabs(s) + 1e-300) break;
+        }
+        return exp(y) * (-gam - log(y) - s);
+    }
+    /* evaluate the continued fraction from the tail (fixed depth is ample for y > 1) */
+    double f = 0.0;
+    for (int n = 300; n >= 1; --n) f = (double)n * n / (y + 2.0 * n + 1.0 - f);
+    return 1.0 / (y + 1.0 - f);
+}
+
+/* Planck function B_nu(T) [W m^-2 Hz^-1 sr^-1] */
+double rho_planck(double nu, double T)
+{
+    double x = HPLANCK * nu / (KBOLTZ * T);
+    return 2.0 * HPLANCK * nu * nu * nu / (CLIGHT * CLIGHT) / expm1(x);
+}
+
+/* Gauss-Legendre nodes and weights on (0,1), weights summing to 1 */
+static void gauss_legendre01(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(PI_D * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int j = 2; j <= n; ++j) {
+                double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        /* recompute derivative at converged root */
+        double p0 = 1.0, p1 = z;
+        for (int j = 2; j <= n; ++j) {
+            double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[n - 1 - i] = 0.5 * (z + 1.0);
+        w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);   /* (2/((1-z^2)p'^2)) / 2 */
+    }
+}
+
+int rho_gauss_legendre01(int n, double *x, double *w)
+{
+    if (n < 1 || n > 16) return 1;
+    gauss_legendre01(n, x, w);
+    return 0;
+}
+
+/* ================================================================== */
+/* Formal solver: linear short characteristics (Olson & Kunasz 1987).    */
+/* The paper (Sect. 2.1) names no scheme; this is the reading taken.     */
+/* ================================================================== */
+
+/* e0 = 1 - exp(-d), e1 = d - e0, evaluated by series for small d */
+static void sc_e01(double d, double *e0, double *e1)
+{
+    if (d < 0.5) {
+        /* e1 = sum_{n>=2} (-d)^n / n!,  e0 = d - e1 */
+        double term = -d, s = 0.0;
+        for (int n = 2; n < 60; ++n) {
+            term *= -d / n;
+            s += term;
+            if (fabs(term) < 1e-18 * fabs(s)) break;
+        }
+        *e1 = s;
+        *e0 = d - s;
+    } else {
+        *e0 = -expm1(-d);
+        *e1 = d - *e0;
+    }
+}
+
+/* One sweep along a ray.  dtau[k] is the optical path between points k and
+ * k+1 along the ray (k = 0..N-2).  dir = +1 sweeps k = 0 -> N-1 (starting
+ * value at k = 0), dir = -1 sweeps k = N-1 -> 0.  Output I[k] and the local
+ * operator lam[k] = dI_k/dS_k (0 at the starting point). */
+void rho_sc_sweep(int N, const double *dtau, const double *S, double I0, int dir,
+                  double *I, double *lam)
+{
+    int k0 = dir > 0 ? 0 : N - 1;
+    I[k0] = I0;
+    lam[k0] = 0.0;
+    for (int s = 1; s < N; ++s) {
+        int ko = dir > 0 ? s : N - 1 - s;
+        int ku = ko - dir;
+        double d = dtau[dir > 0 ? ku : ko];
+        double e0, e1;
+        sc_e01(d, &e0, &e1);
+        double wo = e1 / d;
+        double wu = e0 - wo;
+        I[ko] = I[ku] * (1.0 - e0) + wu * S[ku] + wo * S[ko];
+        lam[ko] = wo;
+    }
+}
+
+/* ================================================================== */
+/* Atom and wavelength grid                                              */
+/* ================================================================== */
+
+static int cmp_dbl_idx(const void *a, const void *b)
+{
+    const double *x = a, *y = b;
+    return (x[0] > y[0]) - (x[0] < y[0]);
+}
+
+static void atom_free(atom_t *a)
+{
+    free(a->nu);
+    free(a->nact);
+    free(a->act);
+    free(a->wq);
+    free(a->prof_slot);
+    memset(a, 0, sizeof *a);
+}
+
+static int atom_build(rho_ctx *c, const rho_atom_desc *d)
+{
+    atom_t *a = &c->at;
+    if (d->nlev < 2 || d->nlev > MAXLEV) return fail(c, "nlev out of range");
+    if (d->nline < 0 || d->ncont < 0 || d->nline + d->ncont > MAXTR || d->nline + d->ncont < 1)
+        return fail(c, "number of transitions out of range");
+    if (d->nmu < 1 || d->nmu > 16) return fail(c, "nmu out of range");
+    if (!(d->mass_amu > 0) || !(d->T_ref > 0)) return fail(c, "mass_amu and T_ref must be positive");
+    atom_free(a);
+    a->nlev = d->nlev;
+    a->nline = d->nline;
+    a->ncont = d->ncont;
+    a->ntr = d->nline + d->ncont;
+    a->nmu = d->nmu;
+    a->mass = d->mass_amu * AMU;
+    a->T_ref = d->T_ref;
+    a->floor_e = d->metal_floor;
+    for (int i = 0; i < a->nlev; ++i) {
+        a->E[i] = d->E_J[i];
+        a->g[i] = d->g[i];
+        if (!(a->g[i] > 0)) return fail(c, "statistical weights must be positive");
+    }
+    const int ic = a->nlev - 1;
+    for (int t = 0; t < d->nline; ++t) {
+        int l = d->line_l[t], u = d->line_u[t];
+        if (l < 0 || u >= ic || l >= u) return fail(c, "line levels out of range");
+        if (d->line_nlambda[t] < 2) return fail(c, "line_nlambda must be >= 2");
+        a->tl[t] = l;
+        a->tu[t] = u;
+        a->kind[t] = 0;
+        double nu0 = (a->E[u] - a->E[l]) / HPLANCK;
+        a->nu0[t] = nu0;
+        a->f[t] = d->line_f[t];
+        /* Einstein coefficients from the oscillator strength (SI) */
+        a->A[t] = 2.0 * PI_D * QELEC * QELEC * nu0 * nu0 / (EPS0 * MELEC * CLIGHT * CLIGHT * CLIGHT)
+                  * (a->g[l] / a->g[u]) * a->f[t];
+        a->Bul[t] = a->A[t] * CLIGHT * CLIGHT / (2.0 * HPLANCK * nu0 * nu0 * nu0);
+        a->Blu[t] = a->Bul[t] * a->g[u] / a->g[l];
+        a->a_top[t] = d->line_a_top[t];
+        a->a_bot[t] = d->line_a_bot[t];
+        a->qwing[t] = d->line_qwing[t];
+        a->nlam_t[t] = d->line_nlambda[t];
+        double dnu_ref = nu0 / CLIGHT * sqrt(2.0 * KBOLTZ * a->T_ref / a->mass);
+        a->nu_lo[t] = nu0 - a->qwing[t] * dnu_ref;
+        a->nu_hi[t] = nu0 + a->qwing[t] * dnu_ref;
+    }
+    for (int q = 0; q < d->ncont; ++q) {
+        int t = d->nline + q, l = d->cont_l[q];
+        if (l < 0 || l >= ic) return fail(c, "continuum lower level out of range");
+        if (d->cont_nlambda[q] < 2) return fail(c, "cont_nlambda must be >= 2");
+        if (!(d->cont_ratio[q] > 1.0)) return fail(c, "cont_ratio must exceed 1");
+        a->tl[t] = l;
+        a->tu[t] = ic;
+        a->kind[t] = 1;
+        a->nu0[t] = (a->E[ic] - a->E[l]) / HPLANCK;
+        a->alpha0[t] = d->cont_alpha0[q];
+        a->ratio[t] = d->cont_ratio[q];
+        a->nlam_t[t] = d->cont_nlambda[q];
+        a->nu_lo[t] = a->nu0[t];
+        a->nu_hi[t] = a->nu0[t] * a->ratio[t];
+    }
+    gauss_legendre01(a->nmu, a->mu, a->wmu);
+
+    /* grid: bands in transition order; lines on a sinh-stretched symmetric grid
+     * x_j = qwing sinh(beta s_j)/sinh(beta), s_j in [-1,1] (beta = 5), continua
+     * geometric in frequency from the edge to ratio*edge */
+    int64_t n = 0;
+    for (int t = 0; t < a->ntr; ++t) n += a->nlam_t[t];
+    a->nlam = n;
+    a->nu = malloc(n * sizeof(double));
+    a->nact = calloc(n, sizeof(int));
+    a->act = malloc(n * MAXACT * sizeof(int));
+    a->wq = calloc(n * MAXACT, sizeof(double));
+    a->prof_slot = malloc(n * MAXACT * sizeof(int));
+    int64_t p = 0;
+    const double beta = 5.0;
+    for (int t = 0; t < a->ntr; ++t) {
+        int m = a->nlam_t[t];
+        for (int j = 0; j < m; ++j) {
+            double nu;
+            if (a->kind[t] == 0) {
+                double s = -1.0 + 2.0 * j / (m - 1);
+                double dnu_ref = a->nu0[t] / CLIGHT * sqrt(2.0 * KBOLTZ * a->T_ref / a->mass);
+                nu = a->nu0[t] + a->qwing[t] * sinh(beta * s) / sinh(beta) * dnu_ref;
+            } else {
+                nu = a->nu0[t] * pow(a->ratio[t], (double)j / (m - 1));
+            }
+            a->nu[p++] = nu;
+        }
+    }
+    /* active transitions per grid point: owner band plus every transition whose
+     * frequency range contains the point (overlapping transitions, Sect. 2.1) */
+    int64_t q0 = 0;
+    for (int t = 0; t < a->ntr; ++t) {
+        for (int j = 0; j < a->nlam_t[t]; ++j) {
+            int64_t i = q0 + j;
+            double nu = a->nu[i];
+            int na = 0;
+            for (int s = 0; s < a->ntr; ++s) {
+                int inside = (s == t) || (nu >= a->nu_lo[s] * (1 - 1e-13) && nu <= a->nu_hi[s] * (1 + 1e-13));
+                if (inside) {
+                    if (na >= MAXACT) return fail(c, "too many overlapping transitions at one wavelength");
+                    a->act[i * MAXACT + na++] = s;
+                }
+            }
+            a->nact[i] = na;
+        }
+        q0 += a->nlam_t[t];
+    }
+    /* quadrature weights: for each transition, trapezoid in frequency over all
+     * grid points where it is active */
+    double *buf = malloc(2 * n * sizeof(double));
+    for (int t = 0; t < a->ntr; ++t) {
+        int cnt = 0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int s = 0; s < a->nact[i]; ++s)
+                if (a->act[i * MAXACT + s] == t) {
+                    buf[2 * cnt] = a->nu[i];
+                    buf[2 * cnt + 1] = (double)(i * MAXACT + s);
+                    ++cnt;
+                }
+        qsort(buf, cnt, 2 * sizeof(double), cmp_dbl_idx);
+        for (int j = 0; j < cnt; ++j) {
+            double lo = j > 0 ? buf[2 * (j - 1)] : buf[0];
+            double hi = j < cnt - 1 ? buf[2 * (j + 1)] : buf[2 * j];
+            int64_t slot = (int64_t)buf[2 * j + 1];
+            a->wq[slot] = 0.5 * (hi - lo);
+        }
+    }
+    free(buf);
+    int np = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int s = 0; s < MAXACT; ++s)
+            a->prof_slot[i * MAXACT + s] = (s < a->nact[i] && a->kind[a->act[i * MAXACT + s]] == 0) ? np++ : -1;
+    a->nprof = np;
+    return 0;
+}
+
+/* ================================================================== */
+/* LTE populations and collisional rates                                */
+/* ================================================================== */
+
+/* Saha-Boltzmann for the model atom at (T, n_e): n*_i = n*_c n_e Phi_i,
+ * Phi_i = g_i/(2 g_c) (h^2/(2 pi m_e k T))^{3/2} exp((E_c - E_i)/kT),
+ * normalised so that sum_i n*_i = n_H. */
+static void lte_pops(const atom_t *a, double T, double ne, double nH, double *nstar)
+{
+    int ic = a->nlev - 1;
+    double lam3 = pow(HPLANCK * HPLANCK / (2.0 * PI_D * MELEC * KBOLTZ * T), 1.5);
+    double phi[MAXLEV], sum = 0.0;
+    for (int i = 0; i < ic; ++i) {
+        phi[i] = a->g[i] / (2.0 * a->g[ic]) * lam3 * exp((a->E[ic] - a->E[i]) / (KBOLTZ * T));
+        sum += phi[i];
+    }
+    double nc = nH / (1.0 + ne * sum);
+    for (int i = 0; i < ic; ++i) nstar[i] = nc * ne * phi[i];
+    nstar[ic] = nc;
+}
+
+/* electron density: hydrogen Saha plus a metal electron floor f*n_H:
+ * n_e = n_p + f n_H with n_p n_e Phi = n_H - n_p  (Phi = sum_i Phi_i), i.e.
+ * Phi n_p^2 + (1 + f n_H Phi) n_p - n_H = 0 (stable root). */
+double rho_electron_density(const rho_ctx *c, double T, double nH)
+{
+    const atom_t *a = &c->at;
+    int ic = a->nlev - 1;
+    double lam3 = pow(HPLANCK * HPLANCK / (2.0 * PI_D * MELEC * KBOLTZ * T), 1.5);
+    double Phi = 0.0;
+    for (int i = 0; i < ic; ++i)
+        Phi += a->g[i] / (2.0 * a->g[ic]) * lam3 * exp((a->E[ic] - a->E[i]) / (KBOLTZ * T));
+    double b = 1.0 + a->floor_e * nH * Phi;
+    double np = 2.0 * nH / (b + sqrt(b * b + 4.0 * Phi * nH));
+    return np + a->floor_e * nH;
+}
+
+/* collisional rates C[i][j] (s^-1, from i to j) at one depth:
+ *  bound-bound: van Regemorter (1962), C_lu = n_e K Omega/(g_l sqrt T) e^{-y},
+ *    K = h^2/((2 pi m_e)^{3/2} sqrt(k)), Omega = (8 pi/sqrt 3)(E_H/dE) g_l f P(y),
+ *    P(y) = max(0.2, 0.276 e^y E1(y)), y = dE/kT
+ *  bound-free: Seaton (1962), C_lc = 1.55e13 n_e[cm^-3] gbar alpha0[cm^2] e^{-u}/(u sqrt T)
+ *    in SI: 1.55e11 n_e alpha0 gbar e^{-u}/(u sqrt T), gbar = 0.1 (hydrogen)
+ *  downward by detailed balance with the LTE populations. */
+static void collision_rates(const atom_t *a, double T, double ne, const double *nstar, double *C)
+{
+    int L = a->nlev;
+    memset(C, 0, sizeof(double) * L * L);
+    const double K = HPLANCK * HPLANCK / (pow(2.0 * PI_D * MELEC, 1.5) * sqrt(KBOLTZ));
+    for (int t = 0; t < a->ntr; ++t) {
+        int l = a->tl[t], u = a->tu[t];
+        double up;
+        if (a->kind[t] == 0) {
+            double dE = a->E[u] - a->E[l];
+            double y = dE / (KBOLTZ * T);
+            double P = 0.276 * rho_expE1(y);
+            if (P < 0.2) P = 0.2;
+            double Omega = 8.0 * PI_D / sqrt(3.0) * (E_RYDBERG / dE) * a->g[l] * a->f[t] * P;
+            up = ne * K * Omega / (a->g[l] * sqrt(T)) * exp(-y);
+        } else {
+            double u0 = HPLANCK * a->nu0[t] / (KBOLTZ * T);
+            up = 1.55e11 * ne * a->alpha0[t] * 0.1 * exp(-u0) / (u0 * sqrt(T));
+        }
+        C[l * L + u] += up;
+        C[u * L + l] += up * nstar[l] / nstar[u];
+    }
+}
+
+/* ================================================================== */
+/* Context and column loading                                            */
+/* ================================================================== */
+
+int rho_create(rho_ctx **out)
+{
+    *out = calloc(1, sizeof(rho_ctx));
+    return *out ? 0 : 2;
+}
+
+static void free_columns(rho_ctx *c)
+{
+    free(c->z); free(c->T); free(c->nH); free(c->vz); free(c->ne); free(c->np);
+    free(c->nstar); free(c->pops); free(c->iters); free(c->status); free(c->dmax);
+    c->z = c->T = c->nH = c->vz = c->ne = c->np = c->nstar = c->pops = c->dmax = NULL;
+    c->iters = NULL;
+    c->status = NULL;
+    c->ncol = 0;
+}
+
+void rho_destroy(rho_ctx *c)
+{
+    if (!c) return;
+    free_columns(c);
+    atom_free(&c->at);
+    free(c);
+}
+
+const char *rho_last_error(const rho_ctx *c) { return c->err; }
+
+int rho_setup_atom(rho_ctx *c, const rho_atom_desc *d)
+{
+    if (c->ncol) return fail(c, "atom must be set before columns are loaded"), 4;
+    if (atom_build(c, d)) return 1;
+    c->have_atom = 1;
+    return 0;
+}
+
+int64_t rho_nlambda(const rho_ctx *c) { return c->at.nlam; }
+
+int rho_get_grid(const rho_ctx *c, double *nu_out, int32_t *nact_out, int32_t *act_out, double *wq_out)
+{
+    const atom_t *a = &c->at;
+    for (int64_t i = 0; i < a->nlam; ++i) {
+        if (nu_out) nu_out[i] = a->nu[i];
+        if (nact_out) nact_out[i] = a->nact[i];
+        for (int s = 0; s < MAXACT; ++s) {
+            if (act_out) act_out[i * MAXACT + s] = s < a->nact[i] ? a->act[i * MAXACT + s] : -1;
+            if (wq_out) wq_out[i * MAXACT + s] = s < a->nact[i] ? a->wq[i * MAXACT + s] : 0.0;
+        }
+    }
+    return 0;
+}
+
+int rho_atom_info(const rho_ctx *c, double *nu0, double *A, double *Blu, double *Bul, double *mu, double *wmu)
+{
+    const atom_t *a = &c->at;
+    for (int t = 0; t < a->ntr; ++t) {
+        if (nu0) nu0[t] = a->nu0[t];
+        if (A) A[t] = a->A[t];
+        if (Blu) Blu[t] = a->Blu[t];
+        if (Bul) Bul[t] = a->Bul[t];
+    }
+    for (int m = 0; m < a->nmu; ++m) {
+        if (mu) mu[m] = a->mu[m];
+        if (wmu) wmu[m] = a->wmu[m];
+    }
+    return 0;
+}
+
+int rho_load_columns(rho_ctx *c, int64_t ncol, int32_t ndep, const double *z, const double *T,
+                     const double *ne, const double *nH, const double *vz)
+{
+    if (!c->have_atom) return fail(c, "no atom"), 4;
+    if (ncol < 0 || ndep < 2) return fail(c, "ncol >= 0 and ndep >= 2 required");
+    for (int64_t i = 0; i < ncol * ndep; ++i) {
+        if (!(isfinite(T[i]) && T[i] > 0 && isfinite(nH[i]) && nH[i] > 0 && isfinite(z[i]) &&
+              isfinite(vz[i]) && (!ne || (isfinite(ne[i]) && ne[i] > 0)))) {
+            char m[200];
+            snprintf(m, sizeof m, "invalid input at column %lld depth %lld",
+                     (long long)(i / ndep), (long long)(i % ndep));
+            return fail(c, m);
+        }
+        if (i % ndep && !(z[i] < z[i - 1])) return fail(c, "z must decrease with depth index");
+    }
+    free_columns(c);
+    int L = c->at.nlev;
+    size_t nd = (size_t)ncol * ndep;
+    c->ncol = ncol;
+    c->ndep = ndep;
+    c->z = malloc(nd * 8); c->T = malloc(nd * 8); c->nH = malloc(nd * 8); c->vz = malloc(nd * 8);
+    c->ne = malloc(nd * 8); c->np = malloc(nd * 8);
+    c->nstar = malloc(nd * L * 8); c->pops = malloc(nd * L * 8);
+    c->iters = calloc(ncol, 4); c->status = malloc(ncol); c->dmax = calloc(ncol, 8);
+    memcpy(c->z, z, nd * 8); memcpy(c->T, T, nd * 8); memcpy(c->nH, nH, nd * 8); memcpy(c->vz, vz, nd * 8);
+    for (int64_t col = 0; col < ncol; ++col) {
+        c->status[col] = ST_NOTRUN;
+        for (int k = 0; k < ndep; ++k) {
+            size_t i = (size_t)col * ndep + k;
+            c->ne[i] = ne ? ne[i] : rho_electron_density(c, T[i], nH[i]);
+            double ns[MAXLEV];
+            lte_pops(&c->at, T[i], c->ne[i], nH[i], ns);
+            c->np[i] = ns[L - 1];
+            for (int l = 0; l < L; ++l) {
+                c->nstar[((size_t)col * L + l) * ndep + k] = ns[l];
+                c->pops[((size_t)col * L + l) * ndep + k] = ns[l];
+            }
+        }
+    }
+    return 0;
+}
+
+int rho_get_lte(const rho_ctx *c, double *nstar, double *ne)
+{
+    size_t nd = (size_t)c->ncol * c->ndep;
+    if (nstar) memcpy(nstar, c->nstar, nd * c->at.nlev * 8);
+    if (ne) memcpy(ne, c->ne, nd * 8);
+    return 0;
+}
+
+int rho_get_populations(const rho_ctx *c, double *n, int32_t *iters, uint8_t *status, double *dmax)
+{
+    size_t nd = (size_t)c->ncol * c->ndep;
+    if (n) memcpy(n, c->pops, nd * c->at.nlev * 8);
+    if (iters) memcpy(iters, c->iters, c->ncol * 4);
+    if (status) memcpy(status, c->status, c->ncol);
+    if (dmax) memcpy(dmax, c->dmax, c->ncol * 8);
+    return 0;
+}
+
+int rho_set_populations(rho_ctx *c, const double *n)
+{
+    size_t nd = (size_t)c->ncol * c->ndep * c->at.nlev;
+    for (size_t i = 0; i < nd; ++i)
+        if (!(isfinite(n[i]) && n[i] > 0)) return fail(c, "populations must be finite and positive");
+    memcpy(c->pops, n, nd * 8);
+    return 0;
+}
+
+/* ================================================================== */
+/* Per-column workspace: atmosphere-only quantities                      */
+/* ================================================================== */
+typedef struct {
+    int N;
+    double *dz;       /* [N-1] */
+    double *Bnu;      /* [nlam][N] */
+    double *chic;     /* [nlam][N] background opacity */
+    double *etac;     /* [nlam][N] background emissivity */
+    double *ex;       /* [nlam][N] exp(-h nu / k T) */
+    double *prof;     /* [nprof][nmu][2][N] line profile (Hz^-1) */
+    double *C;        /* [N][L][L] collisional rates */
+    double *Gam;      /* [N][L][L] rate matrix */
+    /* sweep scratch */
+    double *chi, *eta, *etaact, *S, *dtau, *I, *lam;
+    double *chit, *Vlu, *Vul, *Ut;   /* [MAXACT][N] */
+    double *hist;     /* Ng history [4][L*N] */
+} work_t;
+
+static void work_alloc(work_t *w, const atom_t *a, int N)
+{
+    int L = a->nlev;
+    w->N = N;
+    w->dz = malloc(N * 8);
+    w->Bnu = malloc(a->nlam * N * 8);
+    w->chic = malloc(a->nlam * N * 8);
+    w->etac = malloc(a->nlam * N * 8);
+    w->ex = malloc(a->nlam * N * 8);
+    w->prof = malloc((size_t)(a->nprof > 0 ? a->nprof : 1) * a->nmu * 2 * N * 8);
+    w->C = malloc(N * L * L * 8);
+    w->Gam = malloc(N * L * L * 8);
+    w->chi = malloc(N * 8); w->eta = malloc(N * 8); w->etaact = malloc(N * 8);
+    w->S = malloc(N * 8); w->dtau = malloc(N * 8); w->I = malloc(N * 8); w->lam = malloc(N * 8);
+    w->chit = malloc(MAXACT * N * 8); w->Vlu = malloc(MAXACT * N * 8);
+    w->Vul = malloc(MAXACT * N * 8); w->Ut = malloc(MAXACT * N * 8);
+    w->hist = malloc(4 * L * N * 8);
+}
+
+static void work_free(work_t *w)
+{
+    free(w->dz); free(w->Bnu); free(w->chic); free(w->etac); free(w->ex); free(w->prof);
+    free(w->C); free(w->Gam); free(w->chi); free(w->eta); free(w->etaact); free(w->S);
+    free(w->dtau); free(w->I); free(w->lam); free(w->chit); free(w->Vlu); free(w->Vul);
+    free(w->Ut); free(w->hist);
+}
+
+/* free-free (Kramers, g_ff = 1) absorption coefficient constant, SI:
+ * chi_ff = C_ff n_e n_p T^{-1/2} nu^{-3} (1 - e^{-h nu/kT}),
+ * C_ff = (e^2/(4 pi eps0))^3 4/(3 m_e h c) sqrt(2 pi/(3 k m_e)) */
+double rho_cff(void)
+{
+    double e2 = QELEC * QELEC / (4.0 * PI_D * EPS0);
+    return e2 * e2 * e2 * 4.0 / (3.0 * MELEC * HPLANCK * CLIGHT) * sqrt(2.0 * PI_D / (3.0 * KBOLTZ * MELEC));
+}
+
+/* H- bound-free cross section [m^2] (John 1988, A&A 193, 189, fit for
+ * lambda < 1.6419 um): sigma = 1e-18 lambda^3 (1/lambda - 1/lambda0)^{3/2}
+ * f(lambda) cm^2 with f = sum_n C_n (1/lambda - 1/lambda0)^{(n-1)/2}, lambda in um. */
+double rho_hminus_sigma(double lambda_m)
+{
+    const double l0 = 1.6419;
+    const double Cn[6] = {152.519, 49.534, -118.858, 92.536, -34.194, 4.982};
+    double lum = lambda_m * 1e6;
+    if (!(lum < l0)) return 0.0;
+    double x = 1.0 / lum - 1.0 / l0;
+    double f = 0.0, xp = 1.0, sx = sqrt(x);
+    for (int n = 0; n < 6; ++n) {
+        f += Cn[n] * xp;
+        xp *= sx;
+    }
+    return 1e-18 * lum * lum * lum * x * sx * f * 1e-4;
+}
+
+/* LTE H- number density: n(H-) = n(H I, ground) n_e (1/4) (h^2/(2 pi m_e k T))^{3/2} e^{0.754 eV/kT}
+ * (g(H-) = 1, g(H I, 1s) = 2) */
+static double hminus_density(double nH1, double ne, double T)
+{
+    double lam3 = pow(HPLANCK * HPLANCK / (2.0 * PI_D * MELEC * KBOLTZ * T), 1.5);
+    return 0.25 * nH1 * ne * lam3 * exp(0.754 * QELEC / (KBOLTZ * T));
+}
+
+/* Voigt damping at depth k: log-interpolated in depth index from top to bottom */
+static double damping(const atom_t *a, int t, int k, int N)
+{
+    double s = N > 1 ? (double)k / (N - 1) : 0.0;
+    return exp((1.0 - s) * log(a->a_top[t]) + s * log(a->a_bot[t]));
+}
+
+/* Line profile phi(nu) = H(a, v)/(sqrt(pi) dnu_D) for a ray with vertical
+ * direction cosine mu_z (positive upward).  The Doppler shift of the ray:
+ * v = (nu - nu0)/dnu_D - mu_z v_z / v_th (v_z > 0 upward). */
+static double line_profile(const atom_t *a, int t, double nu, double T, double vz, double mu_z, double adamp)
+{
+    double vth = sqrt(2.0 * KBOLTZ * T / a->mass);
+    double dnuD = a->nu0[t] * vth / CLIGHT;
+    double v = (nu - a->nu0[t]) / dnuD - mu_z * vz / vth;
+    return rho_voigt(adamp, v) / (sqrt(PI_D) * dnuD);
+}
+
+static void column_setup(const rho_ctx *c, int64_t col, work_t *w)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    const double *z = c->z + col * N, *T = c->T + col * N, *vz = c->vz + col * N;
+    const double *ne = c->ne + col * N, *np = c->np + col * N;
+    const double Cff = rho_cff();
+    for (int k = 0; k < N - 1; ++k) w->dz[k] = fabs(z[k] - z[k + 1]);
+    for (int64_t i = 0; i < a->nlam; ++i) {
+        double nu = a->nu[i];
+        for (int k = 0; k < N; ++k) {
+            double x = HPLANCK * nu / (KBOLTZ * T[k]);
+            double B = rho_planck(nu, T[k]);
+            double nhm = hminus_density(c->nstar[((size_t)col * L + 0) * N + k], ne[k], T[k]);
+            double chi = (Cff * ne[k] * np[k] / sqrt(T[k]) / (nu * nu * nu) + nhm * rho_hminus_sigma(CLIGHT / nu))
+                         * (-expm1(-x)) + SIGMA_T * ne[k];
+            w->Bnu[i * N + k] = B;
+            w->chic[i * N + k] = chi;
+            w->etac[i * N + k] = chi * B;   /* background in LTE (Thomson treated as thermal) */
+            w->ex[i * N + k] = exp(-x);
+        }
+        for (int s = 0; s < a->nact[i]; ++s) {
+            int ps = a->prof_slot[i * MAXACT + s];
+            if (ps < 0) continue;
+            int t = a->act[i * MAXACT + s];
+            for (int m = 0; m < a->nmu; ++m)
+                for (int d = 0; d < 2; ++d) {
+                    double muz = d == 0 ? -a->mu[m] : a->mu[m];   /* d=0 downward, d=1 upward */
+                    double *p = w->prof + (((size_t)ps * a->nmu + m) * 2 + d) * N;
+                    for (int k = 0; k < N; ++k)
+                        p[k] = line_profile(a, t, nu, T[k], vz[k], muz, damping(a, t, k, N));
+                }
+        }
+    }
+    for (int k = 0; k < N; ++k) {
+        double ns[MAXLEV];
+        for (int l = 0; l < L; ++l) ns[l] = c->nstar[((size_t)col * L + l) * N + k];
+        collision_rates(a, T[k], ne[k], ns, w->C + (size_t)k * L * L);
+    }
+}
+
+/* per-transition V_lu, V_ul, U_ul and chi_t on all depths for grid point i, ray (m,d) */
+static void transition_coeffs(const rho_ctx *c, int64_t col, const work_t *w, const double *n,
+                              int64_t i, int m, int d)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    double nu = a->nu[i];
+    for (int s = 0; s < a->nact[i]; ++s) {
+        int t = a->act[i * MAXACT + s], l = a->tl[t], u = a->tu[t];
+        double *Vlu = w->Vlu + s * N, *Vul = w->Vul + s * N, *U = w->Ut + s * N, *ch = w->chit + s * N;
+        if (a->kind[t] == 0) {
+            const double *p = w->prof + (((size_t)a->prof_slot[i * MAXACT + s] * a->nmu + m) * 2 + d) * N;
+            double h4 = HPLANCK * nu / (4.0 * PI_D);
+            for (int k = 0; k < N; ++k) {
+                Vlu[k] = h4 * a->Blu[t] * p[k];
+                Vul[k] = a->g[l] / a->g[u] * Vlu[k];
+                U[k] = h4 * a->A[t] * p[k];
+            }
+        } else {
+            double r = a->nu0[t] / nu;
+            double alpha = a->alpha0[t] * r * r * r;
+            double tw = 2.0 * HPLANCK * nu * nu * nu / (CLIGHT * CLIGHT);
+            for (int k = 0; k < N; ++k) {
+                double G = c->nstar[((size_t)col * L + l) * N + k] / c->nstar[((size_t)col * L + u) * N + k];
+                Vlu[k] = alpha;
+                Vul[k] = G * w->ex[i * N + k] * alpha;
+                U[k] = tw * Vul[k];
+            }
+        }
+        for (int k = 0; k < N; ++k) ch[k] = n[l * N + k] * Vlu[k] - n[u * N + k] * Vul[k];
+    }
+}
+
+/* Formal solution for grid point i, ray (m, d) with populations n; fills
+ * w->I, w->lam (dI/dS) and the opacities.  d = 0: downward ray from the top
+ * (no incident radiation); d = 1: upward ray from the bottom with the
+ * diffusion approximation I = B + mu dB/dtau (vertical tau). */
+static void formal_ray(const rho_ctx *c, int64_t col, work_t *w, const double *n, int64_t i, int m, int d)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    (void)L;
+    for (int k = 0; k < N; ++k) {
+        double chi = w->chic[i * N + k], eta = w->etac[i * N + k], ea = 0.0;
+        for (int s = 0; s < a->nact[i]; ++s) {
+            int t = a->act[i * MAXACT + s];
+            chi += w->chit[s * N + k];
+            ea += n[a->tu[t] * N + k] * w->Ut[s * N + k];
+        }
+        w->chi[k] = chi;
+        w->eta[k] = eta + ea;
+        w->etaact[k] = ea;
+        w->S[k] = w->eta[k] / chi;
+    }
+    double mu = a->mu[m];
+    for (int k = 0; k < N - 1; ++k) w->dtau[k] = 0.5 * (w->chi[k] + w->chi[k + 1]) * w->dz[k] / mu;
+    if (d == 0) {
+        rho_sc_sweep(N, w->dtau, w->S, 0.0, +1, w->I, w->lam);
+    } else {
+        double dtv = 0.5 * (w->chi[N - 1] + w->chi[N - 2]) * w->dz[N - 2];
+        double B1 = w->Bnu[i * N + N - 1], B2 = w->Bnu[i * N + N - 2];
+        rho_sc_sweep(N, w->dtau, w->S, B1 + mu * (B1 - B2) / dtv, -1, w->I, w->lam);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Rate matrix.  A[r][q] is the coefficient of n_q in dn_r/dt (columns sum
+ * to zero).  mode 0: MALI (Rybicki & Hummer 1992): I_eff = I - Psi* eta_act
+ * at the old populations, cross-coupling -W Psi* chi_t(old) U_t' between
+ * every pair of transitions active at the wavelength; mode 1: plain rates
+ * with I from the formal solution (Psi* = 0); mode 2: plain rates with each
+ * transition seeing the Planck function (lines at their centre frequency,
+ * continua at the actual frequency).  Collisions are always added. */
+static void rate_matrix(const rho_ctx *c, int64_t col, work_t *w, const double *n, int mode)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    const double *T = c->T + col * N;
+    double *G = w->Gam;
+    memset(G, 0, sizeof(double) * N * L * L);
+    for (int64_t i = 0; i < a->nlam; ++i) {
+        double nu = a->nu[i];
+        for (int m = 0; m < a->nmu; ++m)
+            for (int d = 0; d < 2; ++d) {
+                transition_coeffs(c, col, w, n, i, m, d);
+                if (mode != 2) formal_ray(c, col, w, n, i, m, d);
+                for (int k = 0; k < N; ++k) {
+                    double psi = (mode == 0) ? w->lam[k] / w->chi[k] : 0.0;
+                    double Ieff = (mode == 2) ? 0.0 : w->I[k] - psi * w->etaact[k];
+                    double *Gk = G + (size_t)k * L * L;
+                    for (int s = 0; s < a->nact[i]; ++s) {
+                        int t = a->act[i * MAXACT + s], l = a->tl[t], u = a->tu[t];
+                        double W = 4.0 * PI_D * a->wq[i * MAXACT + s] * (0.5 * a->wmu[m]) / (HPLANCK * nu);
+                        double Ik = Ieff;
+                        if (mode == 2) Ik = a->kind[t] == 0 ? rho_planck(a->nu0[t], T[k]) : w->Bnu[i * N + k];
+                        Gk[u * L + l] += W * w->Vlu[s * N + k] * Ik;
+                        Gk[l * L + u] += W * (w->Ut[s * N + k] + w->Vul[s * N + k] * Ik);
+                        if (psi != 0.0) {
+                            for (int s2 = 0; s2 < a->nact[i]; ++s2) {
+                                int t2 = a->act[i * MAXACT + s2], u2 = a->tu[t2];
+                                double cc = W * psi * w->chit[s * N + k] * w->Ut[s2 * N + k];
+                                if (l != u2) Gk[l * L + u2] -= cc;
+                                if (u != u2) Gk[u * L + u2] += cc;
+                            }
+                        }
+                    }
+                }
+            }
+    }
+    for (int k = 0; k < N; ++k) {
+        double *Gk = G + (size_t)k * L * L;
+        const double *Ck = w->C + (size_t)k * L * L;
+        for (int p = 0; p < L; ++p)
+            for (int q = 0; q < L; ++q)
+                if (p != q) Gk[q * L + p] += Ck[p * L + q];
+        for (int q = 0; q < L; ++q) {
+            double s = 0.0;
+            for (int p = 0; p < L; ++p)
+                if (p != q) s += Gk[p * L + q];
+            Gk[q * L + q] = -s;
+        }
+    }
+}
+
+/* Solve A x = b (L x L) by Gaussian elimination with partial pivoting.
+ * Returns nonzero if a pivot is zero. */
+static int lu_solve(int L, double *A, double *b)
+{
+    for (int p = 0; p < L; ++p) {
+        int piv = p;
+        for (int r = p + 1; r < L; ++r)
+            if (fabs(A[r * L + p]) > fabs(A[piv * L + p])) piv = r;
+        if (A[piv * L + p] == 0.0) return 1;
+        if (piv != p) {
+            for (int q = 0; q < L; ++q) {
+                double tmp = A[p * L + q]; A[p * L + q] = A[piv * L + q]; A[piv * L + q] = tmp;
+            }
+            double tb = b[p]; b[p] = b[piv]; b[piv] = tb;
+        }
+        for (int r = p + 1; r < L; ++r) {
+            double f = A[r * L + p] / A[p * L + p];
+            for (int q = p; q < L; ++q) A[r * L + q] -= f * A[p * L + q];
+            b[r] -= f * b[p];
+        }
+    }
+    for (int p = L - 1; p >= 0; --p) {
+        double s = b[p];
+        for (int q = p + 1; q < L; ++q) s -= A[p * L + q] * b[q];
+        b[p] = s / A[p * L + p];
+    }
+    return 0;
+}
+
+/* statistical equilibrium at every depth: the row of the most populated
+ * level (old populations) is replaced by particle conservation sum n = n_H */
+static int stateq(const rho_ctx *c, int64_t col, work_t *w, const double *nold, double *nnew)
+{
+    int N = c->ndep, L = c->at.nlev;
+    for (int k = 0; k < N; ++k) {
+        double A[MAXLEV * MAXLEV], b[MAXLEV];
+        memcpy(A, w->Gam + (size_t)k * L * L, sizeof(double) * L * L);
+        int r = 0;
+        for (int l = 1; l < L; ++l)
+            if (nold[l * N + k] > nold[r * N + k]) r = l;
+        for (int q = 0; q < L; ++q) A[r * L + q] = 1.0;
+        for (int l = 0; l < L; ++l) b[l] = 0.0;
+        b[r] = c->nH[col * N + k];
+        if (lu_solve(L, A, b)) return ST_SINGULAR;
+        for (int l = 0; l < L; ++l) nnew[l * N + k] = b[l];
+    }
+    return 0;
+}
+
+/* Ng (1974) acceleration of order 2 in the formulation of Auer (1987):
+ * x0 newest .. x3 oldest; minimise |d0 - a(d0 - d1) - b(d0 - d2)|_w with
+ * d_j = x_j - x_{j+1}; return (1-a-b) x0 + a x1 + b x2.  Weights: uniform
+ * (used by the iterations) or relative (1/x0^2).  The paper gives no
+ * weights; relative weights made the extrapolation stall on hot columns and
+ * diverge on the two-level problem, uniform weights converged all of them.
+ * Returns nonzero if the 2x2 normal equations are singular. */
+static int ng2_w(int64_t n, const double *x0, const double *x1, const double *x2, const double *x3,
+                 double *out, int relative)
+{
+    double A11 = 0, A12 = 0, A22 = 0, b1 = 0, b2 = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double wgt = relative ? 1.0 / (x0[i] * x0[i]) : 1.0;
+        double d0 = x0[i] - x1[i], d1 = x1[i] - x2[i], d2 = x2[i] - x3[i];
+        double p = d0 - d1, q = d0 - d2;
+        A11 += wgt * p * p;
+        A12 += wgt * p * q;
+        A22 += wgt * q * q;
+        b1 += wgt * d0 * p;
+        b2 += wgt * d0 * q;
+    }
+    double det = A11 * A22 - A12 * A12;
+    if (!(fabs(det) > 0) || !isfinite(det)) return 1;
+    double ca = (b1 * A22 - b2 * A12) / det;
+    double cb = (A11 * b2 - A12 * b1) / det;
+    for (int64_t i = 0; i < n; ++i) out[i] = (1.0 - ca - cb) * x0[i] + ca * x1[i] + cb * x2[i];
+    return 0;
+}
+
+int rho_ng2(int64_t n, const double *x0, const double *x1, const double *x2, const double *x3, double *out,
+            int32_t relative)
+{
+    return ng2_w(n, x0, x1, x2, x3, out, relative);
+}
+
+/* ------------------------------------------------------------------ */
+/* One column: MALI iterations with Ng acceleration until
+ * max |dn/n| < tol (Sect. 2.3) or maxiter formal solutions. */
+static void iterate_column(rho_ctx *c, int64_t col, const rho_iter_opts *o, work_t *w, double *pts_out)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    size_t nv = (size_t)L * N;
+    double *n = c->pops + (size_t)col * nv;
+    double *nnew = malloc(nv * 8), *Cbase = malloc(sizeof(double) * N * L * L);
+    column_setup(c, col, w);
+    memcpy(Cbase, w->C, sizeof(double) * N * L * L);
+    if (o->start == 0)
+        memcpy(n, c->nstar + (size_t)col * nv, nv * 8);
+    int hcount = 0, it = 0, status = ST_MAXITER;
+    double dmax = INFINITY;
+    for (it = 1; it <= o->maxiter; ++it) {
+        /* collisional-radiative switching (Hummer & Voels 1988): C scaled by
+         * max(1, f0 10^{-(it-1)}) */
+        double fcr = o->crsw_init > 1.0 ? o->crsw_init * pow(10.0, -(it - 1)) : 1.0;
+        if (fcr < 1.0) fcr = 1.0;
+        for (int q = 0; q < N * L * L; ++q) w->C[q] = Cbase[q] * fcr;
+        rate_matrix(c, col, w, n, 0);
+        int st = stateq(c, col, w, n, nnew);
+        if (st) { status = st; break; }
+        dmax = 0.0;
+        int bad = 0;
+        for (size_t q = 0; q < nv; ++q) {
+            if (!(isfinite(nnew[q]) && nnew[q] > 0)) { bad = 1; break; }
+            double dd = fabs(nnew[q] - n[q]) / nnew[q];
+            if (dd > dmax) dmax = dd;
+        }
+        if (bad) { status = ST_NONFINITE; break; }
+        int converged = dmax < o->tol && fcr == 1.0;
+        /* Ng history (newest first) */
+        memmove(w->hist + nv, w->hist, 3 * nv * 8);
+        memcpy(w->hist, nnew, nv * 8);
+        if (hcount < 4) ++hcount;
+        if (!converged && o->ng_order == 2 && it >= o->ng_delay && hcount >= 4 &&
+            (it - o->ng_delay) % o->ng_period == 0) {
+            double *acc = malloc(nv * 8);
+            if (!ng2_w(nv, w->hist, w->hist + nv, w->hist + 2 * nv, w->hist + 3 * nv, acc, 0)) {
+                int ok = 1;
+                for (size_t q = 0; q < nv; ++q)
+                    if (!(isfinite(acc[q]) && acc[q] > 0)) { ok = 0; break; }
+                if (ok) {
+                    memcpy(nnew, acc, nv * 8);
+                    memcpy(w->hist, acc, nv * 8);
+                    hcount = 1;
+                }
+            }
+            free(acc);
+        }
+        memcpy(n, nnew, nv * 8);
+        if (converged) { status = ST_CONV; break; }
+    }
+    if (it > o->maxiter) it = o->maxiter;
+    c->iters[col] = it;
+    c->status[col] = (uint8_t)status;
+    c->dmax[col] = dmax;
+    *pts_out = (double)it * N * a->nlam * a->nmu;
+    memcpy(w->C, Cbase, sizeof(double) * N * L * L);
+    free(nnew);
+    free(Cbase);
+}
+
+typedef struct {
+    rho_ctx *c;
+    const rho_iter_opts *o;
+    int64_t next;
+    pthread_mutex_t mu;
+    double pts;
+} pool_t;
+
+static void *pool_worker(void *arg)
+{
+    pool_t *p = arg;
+    work_t w;
+    work_alloc(&w, &p->c->at, p->c->ndep);
+    double pts = 0.0;
+    for (;;) {
+        pthread_mutex_lock(&p->mu);
+        int64_t col = p->next++;
+        pthread_mutex_unlock(&p->mu);
+        if (col >= p->c->ncol) break;
+        double pc = 0.0;
+        iterate_column(p->c, col, p->o, &w, &pc);
+        pts += pc;
+    }
+    pthread_mutex_lock(&p->mu);
+    p->pts += pts;
+    pthread_mutex_unlock(&p->mu);
+    work_free(&w);
+    return NULL;
+}
+
+/* Pool mode (Sect. 3.1): worker threads pull columns from a shared counter. */
+int rho_iterate(rho_ctx *c, const rho_iter_opts *o, rho_iter_stats *st, int32_t nthreads)
+{
+    if (!c->ncol) return fail(c, "no columns loaded"), 4;
+    if (o->maxiter < 1 || !(o->tol >= 0)) return fail(c, "invalid iteration options");
+    if (o->ng_order != 0 && o->ng_order != 2) return fail(c, "ng_order must be 0 or 2");
+    if (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) return fail(c, "invalid Ng schedule");
+    if (nthreads < 1) nthreads = 1;
+    struct timespec t0, t1;
+    clock_gettime(CLOCK_MONOTONIC, &t0);
+    pool_t p = {c, o, 0, PTHREAD_MUTEX_INITIALIZER, 0.0};
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, pool_worker, &p);
+    for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+    free(th);
+    clock_gettime(CLOCK_MONOTONIC, &t1);
+    if (st) {
+        memset(st, 0, sizeof *st);
+        st->seconds = (t1.tv_sec - t0.tv_sec) + 1e-9 * (t1.tv_nsec - t0.tv_nsec);
+        st->pts = p.pts;
+        for (int64_t col = 0; col < c->ncol; ++col) {
+            if (c->status[col] == ST_CONV) st->n_converged++;
+            else if (c->status[col] == ST_MAXITER) st->n_maxiter++;
+            else st->n_failed++;
+            st->iterations_total += c->iters[col];
+            if (c->dmax[col] > st->max_dn_final || col == 0) st->max_dn_final = c->dmax[col];
+        }
+    }
+    return 0;
+}
+
+/* Rate matrix of one column at given populations (see rate_matrix for the
+ * modes); A_out is [ndep][nlev][nlev]. */
+int rho_rate_matrix(rho_ctx *c, int64_t col, const double *n, int32_t mode, double *A_out)
+{
+    if (col < 0 || col >= c->ncol) return fail(c, "column out of range");
+    work_t w;
+    work_alloc(&w, &c->at, c->ndep);
+    column_setup(c, col, &w);
+    rate_matrix(c, col, &w, n, mode);
+    memcpy(A_out, w.Gam, sizeof(double) * c->ndep * c->at.nlev * c->at.nlev);
+    work_free(&w);
+    return 0;
+}
+
+/* collisional rate matrix C[k][i][j] (i -> j) of one column */
+int rho_collision_rates(rho_ctx *c, int64_t col, double *C_out)
+{
+    if (col < 0 || col >= c->ncol) return fail(c, "column out of range");
+    int N = c->ndep, L = c->at.nlev;
+    for (int k = 0; k < N; ++k) {
+        double ns[MAXLEV];
+        for (int l = 0; l < L; ++l) ns[l] = c->nstar[((size_t)col * L + l) * N + k];
+        collision_rates(&c->at, c->T[col * N + k], c->ne[col * N + k], ns, C_out + (size_t)k * L * L);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Emergent intensity I(mu, nu) at the top for the current populations,
+ * at arbitrary wavelengths (Sect. 2.2: vertical emergent spectrum). */
+typedef struct {
+    rho_ctx *c;
+    double mu;
+    int64_t nl;
+    const double *lam;
+    double *out;
+    int64_t next;
+    pthread_mutex_t m;
+} spec_pool_t;
+
+static void emergent_column(rho_ctx *c, int64_t col, double mu, int64_t nl, const double *lam, double *out)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    const double *z = c->z + col * N, *T = c->T + col * N, *vz = c->vz + col * N;
+    const double *ne = c->ne + col * N, *np = c->np + col * N;
+    const double *n = c->pops + (size_t)col * L * N;
+    double *chi = malloc(N * 8), *S = malloc(N * 8), *dtau = malloc(N * 8), *I = malloc(N * 8), *lm = malloc(N * 8);
+    double *B = malloc(N * 8);
+    const double Cff = rho_cff();
+    for (int64_t j = 0; j < nl; ++j) {
+        double nu = CLIGHT / lam[j];
+        for (int k = 0; k < N; ++k) {
+            double x = HPLANCK * nu / (KBOLTZ * T[k]);
+            B[k] = rho_planck(nu, T[k]);
+            double nhm = hminus_density(c->nstar[((size_t)col * L + 0) * N + k], ne[k], T[k]);
+            double ch = (Cff * ne[k] * np[k] / sqrt(T[k]) / (nu * nu * nu) + nhm * rho_hminus_sigma(lam[j]))
+                        * (-expm1(-x)) + SIGMA_T * ne[k];
+            double et = ch * B[k];
+            for (int t = 0; t < a->ntr; ++t) {
+                if (!(nu >= a->nu_lo[t] * (1 - 1e-13) && nu <= a->nu_hi[t] * (1 + 1e-13))) continue;
+                int l = a->tl[t], u = a->tu[t];
+                double Vlu, Vul, U;
+                if (a->kind[t] == 0) {
+                    double p = line_profile(a, t, nu, T[k], vz[k], mu, damping(a, t, k, N));
+                    double h4 = HPLANCK * nu / (4.0 * PI_D);
+                    Vlu = h4 * a->Blu[t] * p;
+                    Vul = a->g[l] / a->g[u] * Vlu;
+                    U = h4 * a->A[t] * p;
+                } else {
+                    double r = a->nu0[t] / nu;
+                    double G = c->nstar[((size_t)col * L + l) * N + k] / c->nstar[((size_t)col * L + u) * N + k];
+                    Vlu = a->alpha0[t] * r * r * r;
+                    Vul = G * exp(-x) * Vlu;
+                    U = 2.0 * HPLANCK * nu * nu * nu / (CLIGHT * CLIGHT) * Vul;
+                }
+                ch += n[l * N + k] * Vlu - n[u * N + k] * Vul;
+                et += n[u * N + k] * U;
+            }
+            chi[k] = ch;
+            S[k] = et / ch;
+        }
+        for (int k = 0; k < N - 1; ++k) dtau[k] = 0.5 * (chi[k] + chi[k + 1]) * fabs(z[k] - z[k + 1]) / mu;
+        double dtv = 0.5 * (chi[N - 1] + chi[N - 2]) * fabs(z[N - 2] - z[N - 1]);
+        rho_sc_sweep(N, dtau, S, B[N - 1] + mu * (B[N - 1] - B[N - 2]) / dtv, -1, I, lm);
+        out[j] = I[0];
+    }
+    free(chi); free(S); free(dtau); free(I); free(lm); free(B);
+}
+
+static void *spec_worker(void *arg)
+{
+    spec_pool_t *p = arg;
+    for (;;) {
+        pthread_mutex_lock(&p->m);
+        int64_t col = p->next++;
+        pthread_mutex_unlock(&p->m);
+        if (col >= p->c->ncol) break;
+        emergent_column(p->c, col, p->mu, p->nl, p->lam, p->out + col * p->nl);
+    }
+    return NULL;
+}
+
+int rho_emergent_spectrum(rho_ctx *c, double mu, int64_t nl, const double *lam, double *out, int32_t nthreads)
+{
+    if (!(mu > 0 && mu <= 1)) return fail(c, "mu must be in (0, 1]");
+    if (!c->ncol) return fail(c, "no columns loaded"), 4;
+    for (int64_t j = 0; j < nl; ++j)
+        if (!(lam[j] > 0)) return fail(c, "wavelengths must be positive");
+    if (nthreads < 1) nthreads = 1;
+    spec_pool_t p = {c, mu, nl, lam, out, 0, PTHREAD_MUTEX_INITIALIZER};
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, spec_worker, &p);
+    for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+    free(th);
+    return 0;
+}
+
+/* ================================================================== */
+/* Two-level atom, complete redistribution (the textbook reduction of     */
+/* MALI): S = (1 - eps) Jbar + eps B with the ALI update                   */
+/* S_new = [(1-eps)(Jbar - Lstar S) + eps B] / [1 - (1-eps) Lstar].         */
+/* Grid: line-centre optical depth tau0[k]; Doppler profile at x_f in      */
+/* [-xmax, xmax]; trapezoid weights renormalised so sum w phi = 1;          */
+/* tau_x = tau0 phi(x)/phi(0); no incident radiation at the top, I = B +    */
+/* mu dB/dtau (= B here) at the bottom.                                    */
+/* ================================================================== */
+
+/* Jbar and Lambda-bar* for a given S */
+int rho_two_level_jbar(int N, const double *tau0, int nfreq, double xmax, int nmu, double B,
+                       const double *S, double *Jbar, double *Lstar)
+{
+    if (N < 2 || nfreq < 2 || nmu < 1 || nmu > 16) return 1;
+    double mu[16], wmu[16];
+    gauss_legendre01(nmu, mu, wmu);
+    double *x = malloc(nfreq * 8), *wf = malloc(nfreq * 8), *phi = malloc(nfreq * 8);
+    double norm = 0.0;
+    for (int f = 0; f < nfreq; ++f) {
+        x[f] = -xmax + 2.0 * xmax * f / (nfreq - 1);
+        phi[f] = exp(-x[f] * x[f]) / sqrt(PI_D);
+        double h = 2.0 * xmax / (nfreq - 1);
+        wf[f] = (f == 0 || f == nfreq - 1) ? 0.5 * h : h;
+        norm += wf[f] * phi[f];
+    }
+    for (int f = 0; f < nfreq; ++f) wf[f] /= norm;
+    double *dt = malloc(N * 8), *I = malloc(N * 8), *lm = malloc(N * 8);
+    for (int k = 0; k < N; ++k) Jbar[k] = Lstar[k] = 0.0;
+    double phi0 = 1.0 / sqrt(PI_D);
+    for (int f = 0; f < nfreq; ++f)
+        for (int m = 0; m < nmu; ++m) {
+            for (int k = 0; k < N - 1; ++k) dt[k] = (tau0[k + 1] - tau0[k]) * phi[f] / phi0 / mu[m];
+            double wgt = wf[f] * phi[f] * 0.5 * wmu[m];
+            rho_sc_sweep(N, dt, S, 0.0, +1, I, lm);
+            for (int k = 0; k < N; ++k) { Jbar[k] += wgt * I[k]; Lstar[k] += wgt * lm[k]; }
+            double dtv = (tau0[N - 1] - tau0[N - 2]) * phi[f] / phi0;
+            (void)dtv;   /* isothermal: dB/dtau = 0, I = B at the bottom */
+            rho_sc_sweep(N, dt, S, B, -1, I, lm);
+            for (int k = 0; k < N; ++k) { Jbar[k] += wgt * I[k]; Lstar[k] += wgt * lm[k]; }
+        }
+    free(x); free(wf); free(phi); free(dt); free(I); free(lm);
+    return 0;
+}
+
+int rho_two_level_solve(int N, const double *tau0, int nfreq, double xmax, int nmu, double eps,
+                        double B, int maxiter, double tol, int ng_order, int ng_delay, int ng_period,
+                        double *S, int32_t *iters_out)
+{
+    size_t nv = N;
+    double *J = malloc(N * 8), *Ls = malloc(N * 8), *Sn = malloc(N * 8), *hist = malloc(4 * N * 8);
+    for (int k = 0; k < N; ++k) S[k] = B;   /* LTE start */
+    int hcount = 0, it;
+    for (it = 1; it <= maxiter; ++it) {
+        if (rho_two_level_jbar(N, tau0, nfreq, xmax, nmu, B, S, J, Ls)) { it = -1; break; }
+        double dmax = 0.0;
+        for (int k = 0; k < N; ++k) {
+            Sn[k] = ((1.0 - eps) * (J[k] - Ls[k] * S[k]) + eps * B) / (1.0 - (1.0 - eps) * Ls[k]);
+            double dd = fabs(Sn[k] - S[k]) / Sn[k];
+            if (dd > dmax) dmax = dd;
+        }
+        memmove(hist + nv, hist, 3 * nv * 8);
+        memcpy(hist, Sn, nv * 8);
+        if (hcount < 4) ++hcount;
+        int conv = dmax < tol;
+        if (!conv && ng_order == 2 && it >= ng_delay && hcount >= 4 && (it - ng_delay) % ng_period == 0) {
+            if (!ng2_w(nv, hist, hist + nv, hist + 2 * nv, hist + 3 * nv, Sn, 0)) {
+                memcpy(hist, Sn, nv * 8);
+                hcount = 1;
+            } else {
+                memcpy(Sn, hist, nv * 8);
+            }
+        }
+        memcpy(S, Sn, nv * 8);
+        if (conv) break;
+    }
+    if (iters_out) *iters_out = it > maxiter ? maxiter : it;
+    free(J); free(Ls); free(Sn); free(hist);
+    return 0;
+}

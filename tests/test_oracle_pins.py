@@ -1,0 +1,413 @@
+"""Pins of the FP64 oracle against what physics and mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: a closed
+form, a limit, an independent library routine (scipy), brute force on a tiny
+problem, or a second published form of the same formula.
+"""
+import numpy as np
+import pytest
+import scipy.constants as sc
+from scipy.special import exp1, wofz
+
+import rh_synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# ---------------------------------------------------------------- special functions
+def test_voigt_matches_faddeeva_library(orc):
+    v = np.concatenate([np.linspace(0, 10, 401), np.linspace(10, 300, 60)])
+    for a in (1e-3, 3e-3, 1e-2, 5e-2):
+        ref = wofz(v + 1j * a).real
+        got = np.array([orc.voigt(a, x) for x in v])
+        assert np.max(np.abs(got / ref - 1)) < 1e-10, a
+
+
+def test_voigt_limits(orc):
+    # a -> 0: Gaussian; symmetric in v; integral over v is sqrt(pi)
+    v = np.linspace(-4, 4, 33)
+    got = np.array([orc.voigt(1e-12, x) for x in v])
+    assert np.allclose(got, np.exp(-v * v), rtol=1e-9, atol=1e-11)
+    assert orc.voigt(1e-2, 3.7) == pytest.approx(orc.voigt(1e-2, -3.7), rel=1e-13)
+    a = 1e-2
+    x = np.linspace(0, 400, 400001)
+    h = np.array([orc.voigt(a, t) for t in x[::40]])
+    xs = x[::40]
+    integ = 2 * np.trapezoid(h, xs) + 2 * a / (np.sqrt(np.pi) * 400)   # Lorentz tail beyond 400
+    assert integ == pytest.approx(np.sqrt(np.pi), rel=2e-5)
+
+
+def test_expE1_matches_library(orc):
+    for y in (1e-4, 0.1, 0.7, 1.0, 1.0001, 2.5, 10.0, 40.0, 200.0):
+        ref = np.exp(y) * exp1(y) if y < 700 else 1 / y
+        assert orc.expE1(y) == pytest.approx(ref, rel=1e-12), y
+
+
+def test_gauss_legendre_nodes(orc):
+    for n in (1, 2, 5, 8):
+        x, w = orc.gauss_legendre01(n)
+        xr, wr = np.polynomial.legendre.leggauss(n)
+        assert np.allclose(x, 0.5 * (xr + 1), atol=1e-14)
+        assert np.allclose(w, 0.5 * wr, atol=1e-14)
+        assert w.sum() == pytest.approx(1.0, abs=1e-14)
+
+
+def test_planck_stefan_boltzmann(orc):
+    # integral of B_nu over nu equals sigma T^4 / pi (Stefan-Boltzmann)
+    T = 5777.0
+    nu = np.logspace(10, 17, 200001)
+    B = np.array([orc.planck(f, T) for f in nu[::20]])
+    integ = np.trapezoid(B, nu[::20])
+    assert integ == pytest.approx(sc.Stefan_Boltzmann * T ** 4 / np.pi, rel=1e-6)
+    # Rayleigh-Jeans limit
+    f = 1e9
+    assert orc.planck(f, T) == pytest.approx(2 * f * f * sc.k * T / sc.c ** 2, rel=1e-4)
+
+
+def test_hminus_cross_section_peak(orc):
+    # H- bound-free: peak ~4e-17 cm^2 near 850 nm, threshold at 1.6419 um (0.754 eV)
+    lam = np.linspace(0.5e-6, 1.64e-6, 1141)
+    sig = np.array([orc.lib().rho_hminus_sigma(x) for x in lam])
+    assert lam[np.argmax(sig)] == pytest.approx(0.85e-6, abs=0.05e-6)
+    assert sig.max() == pytest.approx(4.0e-21, rel=0.03)
+    assert orc.lib().rho_hminus_sigma(1.65e-6) == 0.0
+    assert sc.h * sc.c / 1.6419e-6 / sc.e == pytest.approx(0.7552, rel=1e-3)
+
+
+def test_free_free_constant_matches_cgs_textbook_value(orc):
+    # Rybicki & Lightman Eq. (5.18b): alpha_ff = 3.7e8 T^-1/2 Z^2 n_e n_i nu^-3 (1-e^-x) g (cgs);
+    # cm^-1 -> m^-1 (x100) and n_cgs = 1e-6 n_SI for both densities
+    assert orc.cff() == pytest.approx(3.692e8 * 1e2 * 1e-12, rel=2e-3)
+
+
+# ---------------------------------------------------------------- formal solver
+def _tau_grid(N, tmax=1e3):
+    t = np.concatenate([[0.0], np.logspace(-4, np.log10(tmax), N - 1)])
+    return t
+
+
+def test_formal_solver_exact_for_linear_source(orc):
+    # S = a + b tau (vertical tau); semi-infinite: I(0, mu) = a + b mu.
+    # The diffusion condition I = S + mu dS/dtau is exact for linear S and the
+    # linear short-characteristics scheme integrates linear S exactly.
+    a, b = 0.7, 2.3
+    tau = _tau_grid(70)
+    S = a + b * tau
+    for mu in (0.05, 0.3, 1.0):
+        dtau = np.diff(tau) / mu
+        I, _ = orc.sc_sweep(dtau, S, S[-1] + mu * b, -1)
+        assert I[0] == pytest.approx(a + b * mu, rel=1e-12)
+        # and everywhere: I(tau, mu) = a + b (tau + mu)
+        assert np.allclose(I, a + b * (tau + mu), rtol=1e-11)
+        # downward ray from zero incident intensity: closed form
+        Id, _ = orc.sc_sweep(dtau, S, 0.0, +1)
+        t = tau / mu
+        exact = a * (1 - np.exp(-t)) + b * mu * (t - 1 + np.exp(-t))
+        assert np.allclose(Id[1:], exact[1:], rtol=1e-10)
+
+
+def test_formal_solver_exponential_source_second_order(orc):
+    # S = exp(-k tau): I(0, mu) = 1 / (1 + k mu); linear SC is second order
+    k, mu = 3.0, 0.4
+    errs = []
+    for N in (401, 801, 1601):
+        tau = np.linspace(0, 40, N)
+        S = np.exp(-k * tau)
+        I, _ = orc.sc_sweep(np.diff(tau) / mu, S, S[-1] * (1 - k * mu), -1)
+        errs.append(abs(I[0] - 1 / (1 + k * mu)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.6 < r1 < 4.4 and 3.6 < r2 < 4.4
+    assert errs[-1] < 1e-3
+
+
+def test_formal_solver_local_operator_is_derivative(orc):
+    rng = np.random.default_rng(5)
+    tau = _tau_grid(30, 50)
+    dtau = np.diff(tau) / 0.6
+    S = rng.uniform(0.5, 2.0, tau.size)
+    for direction, I0 in ((+1, 0.3), (-1, 1.7)):
+        I, lam = orc.sc_sweep(dtau, S, I0, direction)
+        for k in (3, 12, 29 if direction > 0 else 0):
+            d = 1e-2      # I is linear in S: the difference quotient is exact up to rounding
+            S2 = S.copy()
+            S2[k] += d
+            I2, _ = orc.sc_sweep(dtau, S2, I0, direction)
+            assert (I2[k] - I[k]) / d == pytest.approx(lam[k], rel=1e-9, abs=1e-13)
+        assert lam[0 if direction > 0 else -1] == 0.0
+
+
+# ---------------------------------------------------------------- two-level atom
+TL = rh_synth.two_level_problem()
+
+
+def test_two_level_lte_limit(orc):
+    S, it = orc.two_level_solve(TL["tau"], TL["nfreq"], TL["xmax"], TL["nmu"], 1.0, 2.5)
+    assert np.allclose(S, 2.5, rtol=1e-14)
+
+
+def test_two_level_matches_brute_force_lambda_inversion(orc):
+    # build the full Lambda-bar operator column by column from unit source
+    # functions and solve [1 - (1-eps) Lambda] S = (1-eps) J_bc + eps B directly
+    tau = TL["tau"]
+    N = tau.size
+    eps, B = TL["eps"], 1.0
+    args = (tau, TL["nfreq"], TL["xmax"], TL["nmu"], B)
+    Jbc, _ = orc.two_level_jbar(*args, np.zeros(N))
+    Lam = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        Lam[:, j] = orc.two_level_jbar(*args, e)[0] - Jbc
+    S_direct = np.linalg.solve(np.eye(N) - (1 - eps) * Lam, (1 - eps) * Jbc + eps * B)
+    S, it = orc.two_level_solve(tau, TL["nfreq"], TL["xmax"], TL["nmu"], eps, B, tol=1e-13,
+                                maxiter=5000)
+    assert np.allclose(S, S_direct, rtol=1e-10)
+    # the diagonal of Lambda-bar is the local operator of the ALI scheme
+    _, Ls = orc.two_level_jbar(*args, np.ones(N))
+    assert np.allclose(np.diag(Lam), Ls, rtol=1e-10, atol=1e-14)
+
+
+def test_two_level_sqrt_eps_surface_law(orc):
+    # S(0) -> sqrt(eps) B for the semi-infinite isothermal atmosphere (exact for
+    # the continuous problem with normalised angle and frequency quadratures).
+    # On the log-spaced depth grid the linear short-characteristics error is
+    # first order in the spacing: it must fall by ~2 per doubling, and the
+    # Richardson-extrapolated surface value must approach sqrt(eps) B.
+    eps = 1e-4
+    errs = []
+    for N in (64, 128, 256, 512):
+        tau = np.logspace(-6, 4, N)
+        S, _ = orc.two_level_solve(tau, 101, 6.0, 5, eps, 1.0, tol=1e-10, maxiter=20000)
+        errs.append(S[0] / np.sqrt(eps) - 1)
+    errs = np.array(errs)
+    assert np.all(np.abs(errs[1:]) < np.abs(errs[:-1]))
+    ratios = errs[:-1] / errs[1:]
+    assert np.all((ratios > 1.6) & (ratios < 3.0))
+    assert abs(errs[-1]) < 0.06
+    richardson = 2 * errs[-1] - errs[-2]
+    assert abs(richardson) < 0.03
+
+
+# ---------------------------------------------------------------- Ng acceleration
+def test_ng_order2_exact_for_two_mode_linear_iteration(orc):
+    rng = np.random.default_rng(1)
+    n = 40
+    V = np.linalg.qr(rng.standard_normal((n, n)))[0][:, :2]
+    M = V @ np.diag([0.93, -0.6]) @ V.T           # two non-zero eigenvalues
+    xstar = rng.uniform(1, 2, n)
+    c = xstar - M @ xstar
+    xs = [rng.uniform(1, 2, n)]
+    for _ in range(4):                  # after one step every error lies in the 2-mode subspace
+        xs.append(M @ xs[-1] + c)
+    for rel in (False, True):
+        acc = orc.ng2(xs[4], xs[3], xs[2], xs[1], relative=rel)
+        assert np.allclose(acc, xstar, rtol=1e-11)
+
+
+# ---------------------------------------------------------------- atom, LTE, collisions
+@pytest.fixture(scope="module")
+def column_oracle(orc):
+    o = orc.Oracle()
+    o.setup_atom(rh_synth.hydrogen_like_atom())
+    o.load_columns(rh_synth.chromosphere_column())
+    return o
+
+
+def test_einstein_coefficients_and_grid(orc, column_oracle):
+    info = column_oracle.atom_info()
+    # Lyman alpha: nu0 from 13.6 eV (3/4); A_21 averaged over n=2 with f_K
+    nu0 = 13.6 * sc.e * 0.75 / sc.h
+    assert info["nu0"][0] == pytest.approx(nu0, rel=1e-14)
+    fK = rh_synth.kramers_f(1, 2)
+    assert fK * 0.7166 == pytest.approx(0.4162, rel=2e-3)    # NIST f with the Lya Gaunt factor
+    # A_ul g_u = 8 pi^2 e^2 nu^2 / (m_e c^3) * g_l f_lu  (Gaussian units) -> SI
+    A_ref = 8 * np.pi ** 2 * (sc.e ** 2 / (4 * np.pi * sc.epsilon_0)) * nu0 ** 2 / (sc.m_e * sc.c ** 3) \
+        * (2.0 / 8.0) * fK
+    assert info["A"][0] == pytest.approx(A_ref, rel=1e-8)
+    # Einstein relations
+    assert info["Bul"][0] * 2 * sc.h * nu0 ** 3 / sc.c ** 2 == pytest.approx(info["A"][0], rel=1e-12)
+    assert info["Blu"][0] * 2 == pytest.approx(info["Bul"][0] * 8, rel=1e-12)
+    g = column_oracle.grid()
+    assert column_oracle.nlambda == 608
+    # quadrature weights of a continuum integrate its frequency range exactly
+    t = 10 + 1    # Balmer continuum
+    w = np.where(g["act"] == t, g["wq"], 0).sum()
+    nu_edge = info["nu0"][t]
+    assert w == pytest.approx(nu_edge * (2.5 - 1.0), rel=1e-12)
+
+
+def test_saha_boltzmann(orc, column_oracle):
+    o = column_oracle
+    ns, ne = o.lte()
+    cols = rh_synth.chromosphere_column()
+    T, nH = cols["T"][0], cols["nH"][0]
+    assert np.allclose(ns[0].sum(axis=0), nH, rtol=1e-13)
+    atom = rh_synth.hydrogen_like_atom()
+    E, g = atom["E_J"], atom["g"]
+    for k in (0, 40, 81):
+        # Boltzmann between bound levels
+        r = ns[0, 3, k] / ns[0, 1, k]
+        assert r == pytest.approx(g[3] / g[1] * np.exp(-(E[3] - E[1]) / (sc.k * T[k])), rel=1e-12)
+        # Saha for the ground level
+        saha = (2 * g[5] / g[0]) * (2 * np.pi * sc.m_e * sc.k * T[k] / sc.h ** 2) ** 1.5 \
+            * np.exp(-(E[5] - E[0]) / (sc.k * T[k]))
+        assert ns[0, 5, k] * ne[0, k] / ns[0, 0, k] == pytest.approx(saha, rel=1e-8)  # CODATA 2018 vs 2022 m_e
+        # the electron density: protons plus the metal floor
+        assert ne[0, k] == pytest.approx(ns[0, 5, k] + 1e-4 * nH[k], rel=1e-12)
+    # hot, dilute gas is fully ionised
+    assert o.electron_density(5e4, 1e15) == pytest.approx(1e15 * (1 + 1e-4), rel=1e-6)
+
+
+def test_collision_rates_two_published_forms(orc, column_oracle):
+    o = column_oracle
+    Cm = o.collision_rates(0)
+    ns, ne = o.lte()
+    T = rh_synth.chromosphere_column()["T"][0]
+    info = o.atom_info()
+    atom = rh_synth.hydrogen_like_atom()
+    for k in (5, 60):
+        # van Regemorter in its original form (cgs): C_lu = 20.6 lambda^3 n_e T^-1/2 A_ul
+        # (g_u/g_l) P(y) e^-y with lambda in cm -- independent of the Omega/8.63e-6 form
+        lam_cm = sc.c / info["nu0"][0] * 100
+        y = sc.h * info["nu0"][0] / (sc.k * T[k])
+        P = max(0.2, 0.276 * np.exp(y) * exp1(y))
+        ref = 20.6 * lam_cm ** 3 * (ne[0, k] * 1e-6) / np.sqrt(T[k]) * info["A"][0] * (8 / 2) * P * np.exp(-y)
+        assert Cm[k, 0, 1] == pytest.approx(ref, rel=3e-3)
+        # Seaton bound-free in cgs units
+        u = sc.h * info["nu0"][10] / (sc.k * T[k])
+        ref = 1.55e13 * (ne[0, k] * 1e-6) / np.sqrt(T[k]) * 0.1 * (atom["cont_alpha0"][0] * 1e4) * np.exp(-u) / u
+        assert Cm[k, 0, 5] == pytest.approx(ref, rel=1e-12)
+        # detailed balance of the downward rates
+        for (l, u_) in ((0, 1), (1, 3), (2, 5)):
+            assert Cm[k, u_, l] / Cm[k, l, u_] == pytest.approx(ns[0, l, k] / ns[0, u_, k], rel=1e-12)
+
+
+def test_rate_matrix_columns_sum_to_zero(orc, column_oracle):
+    o = column_oracle
+    ns, _ = o.lte()
+    for mode in (0, 1, 2):
+        A = o.rate_matrix(0, ns[0], mode)
+        scale = np.abs(A).max(axis=(1, 2))
+        assert np.all(np.abs(A.sum(axis=1)).max(axis=1) <= 1e-13 * scale)
+
+
+def _solve_stateq(A, nold, ntot):
+    out = np.zeros_like(nold)
+    for k in range(A.shape[0]):
+        M = A[k].copy()
+        r = int(np.argmax(nold[:, k]))
+        M[r, :] = 1.0
+        b = np.zeros(M.shape[0])
+        b[r] = ntot[k]
+        out[:, k] = np.linalg.solve(M, b)
+    return out
+
+
+def test_detailed_balance_returns_lte(orc, column_oracle):
+    # every transition sees the Planck function, no Psi*: the rate equations
+    # must return the Saha-Boltzmann populations
+    o = column_oracle
+    ns, _ = o.lte()
+    A = o.rate_matrix(0, ns[0], 2)
+    n = _solve_stateq(A, ns[0], rh_synth.chromosphere_column()["nH"][0])
+    assert np.allclose(n, ns[0], rtol=1e-10)
+
+
+def test_lte_limit_with_dominant_collisions(orc):
+    # scaling n_e scales every collisional rate: the departures from LTE must
+    # fall as 1/f, populations -> Saha-Boltzmann and S_line -> B_nu0(T)
+    atom = rh_synth.hydrogen_like_atom()
+    cols = rh_synth.chromosphere_column()
+    o0 = orc.Oracle()
+    o0.setup_atom(atom)
+    o0.load_columns(cols)
+    _, ne = o0.lte()
+    dev = {}
+    for f in (1e10, 1e12):
+        o = orc.Oracle()
+        o.setup_atom(atom)
+        o.load_columns(cols, ne=ne * f)
+        o.iterate(maxiter=50, tol=1e-13)
+        n, it, st, _ = o.populations()
+        ns, _ = o.lte()
+        dev[f] = np.max(np.abs(n / ns - 1))
+    assert dev[1e12] < 1e-5
+    assert dev[1e12] / dev[1e10] == pytest.approx(1e-2, rel=0.1)
+    info = o.atom_info()
+    T = cols["T"][0]
+    for t, (l, u) in enumerate(zip(atom["line_l"][:3], atom["line_u"][:3])):
+        Sl = n[0, u] * info["A"][t] / (n[0, l] * info["Blu"][t] - n[0, u] * info["Bul"][t])
+        B = np.array([orc.planck(info["nu0"][t], x) for x in T])
+        assert np.allclose(Sl, B, rtol=1e-5)
+
+
+def test_mali_converges_with_conservation(orc, column_oracle):
+    o = column_oracle
+    st = o.iterate(maxiter=300, tol=1e-3)
+    n, it, status, dmax = o.populations()
+    assert status[0] == orc.ST_CONV and dmax[0] < 1e-3
+    assert np.allclose(n[0].sum(axis=0), rh_synth.chromosphere_column()["nH"][0], rtol=1e-13)
+    ns, _ = o.lte()
+    b = n[0] / ns[0]
+    # deep layers: ground level and continuum approach LTE
+    assert abs(b[0, -1] - 1) < 1e-3 and abs(b[5, -1] - 1) < 3e-2
+    assert st["pts"] == it[0] * 82 * 608 * 5
+
+
+def test_isothermal_lte_column_emits_planck(orc):
+    o = orc.Oracle()
+    o.setup_atom(rh_synth.hydrogen_like_atom())
+    cols = rh_synth.chromosphere_column()
+    cols["T"][:] = 6000.0
+    o.load_columns(cols)
+    ns, _ = o.lte()
+    o.set_populations(ns)
+    lam = np.array([121.567e-9, 121.6e-9, 656.3e-9, 364e-9, 3e-6])
+    for mu in (1.0, 0.3):
+        I = o.emergent_spectrum(mu, lam)
+        B = np.array([orc.planck(sc.c / x, 6000.0) for x in lam])
+        assert np.allclose(I[0], B, rtol=1e-12)
+
+
+def test_mali_fixed_point_solves_plain_rate_equations_and_newton(orc):
+    # tiny problem: 3 bound levels + continuum, 8 depths, 2 angles
+    o = orc.Oracle()
+    atom = rh_synth.small_atom()
+    o.setup_atom(atom)
+    cols = rh_synth.chromosphere_column(ndep=8)
+    o.load_columns(cols)
+    o.iterate(maxiter=2000, tol=1e-11)      # round-off floor of the iteration is ~1e-12
+    n, it, st, _ = o.populations()
+    assert st[0] == orc.ST_CONV
+    nH = cols["nH"][0]
+    A = o.rate_matrix(0, n[0], 1)       # plain rates, I from the formal solution
+    n_plain = _solve_stateq(A, n[0], nH)
+    assert np.allclose(n_plain, n[0], rtol=1e-9)
+
+    # Newton on the full discrete system with a finite-difference Jacobian,
+    # started 10 % away from the MALI solution
+    L, N = n[0].shape
+
+    def F(x):
+        X = x.reshape(L, N)
+        Am = o.rate_matrix(0, X, 1)
+        res = np.einsum("kij,jk->ik", Am, X)
+        scale = np.abs(Am).max(axis=(1, 2))[None, :] * X.max(axis=0)[None, :]
+        r = res / scale
+        r[0] = (X.sum(axis=0) - nH) / nH     # conservation replaces level 0's equation
+        return r.reshape(-1)
+
+    x = (n[0] * (1 + 0.1 * np.sin(np.arange(L * N)).reshape(L, N))).reshape(-1)
+    for _ in range(30):
+        f = F(x)
+        J = np.zeros((x.size, x.size))
+        for j in range(x.size):
+            h = 1e-7 * x[j]
+            xp = x.copy()
+            xp[j] += h
+            J[:, j] = (F(xp) - f) / h
+        dx = np.linalg.solve(J, -f)
+        x = x + dx
+        if np.max(np.abs(dx / x)) < 1e-12:
+            break
+    assert np.allclose(x.reshape(L, N), n[0], rtol=1e-8)
