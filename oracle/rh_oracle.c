@@ -972,21 +972,37 @@ static int lu_solve(int L, double *A, double *b)
 }
 
 /* statistical equilibrium at every depth: the row of the most populated
- * level (old populations) is replaced by particle conservation sum n = n_H */
+ * level (old populations) is replaced by particle conservation sum n = n_H.
+ * The unknowns are scaled by the old populations (y = n / n_old) and every
+ * row by its largest entry before elimination: populations of one depth span
+ * up to ~20 decades, and the scaling keeps the small ones accurate (it does
+ * not change the exact solution). */
 static int stateq(const rho_ctx *c, int64_t col, work_t *w, const double *nold, double *nnew)
 {
     int N = c->ndep, L = c->at.nlev;
     for (int k = 0; k < N; ++k) {
-        double A[MAXLEV * MAXLEV], b[MAXLEV];
+        double A[MAXLEV * MAXLEV], b[MAXLEV], s[MAXLEV];
         memcpy(A, w->Gam + (size_t)k * L * L, sizeof(double) * L * L);
         int r = 0;
-        for (int l = 1; l < L; ++l)
-            if (nold[l * N + k] > nold[r * N + k]) r = l;
+        for (int l = 0; l < L; ++l) {
+            s[l] = nold[l * N + k];
+            if (s[l] > s[r]) r = l;
+        }
         for (int q = 0; q < L; ++q) A[r * L + q] = 1.0;
         for (int l = 0; l < L; ++l) b[l] = 0.0;
         b[r] = c->nH[col * N + k];
+        for (int p = 0; p < L; ++p) {
+            double mx = 0.0;
+            for (int q = 0; q < L; ++q) {
+                A[p * L + q] *= s[q];
+                if (fabs(A[p * L + q]) > mx) mx = fabs(A[p * L + q]);
+            }
+            if (!(mx > 0)) return ST_SINGULAR;
+            for (int q = 0; q < L; ++q) A[p * L + q] /= mx;
+            b[p] /= mx;
+        }
         if (lu_solve(L, A, b)) return ST_SINGULAR;
-        for (int l = 0; l < L; ++l) nnew[l * N + k] = b[l];
+        for (int l = 0; l < L; ++l) nnew[l * N + k] = b[l] * s[l];
     }
     return 0;
 }
