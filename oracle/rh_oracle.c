@@ -271,8 +271,14 @@ int rho_gauss_legendre01(int n, double *x, double *w)
 /* The paper (Sect. 2.1) names no scheme; this is the reading taken.     */
 /* ================================================================== */
 
-/* e0 = 1 - exp(-d), e1 = d - e0, evaluated by series for small d */
-static void sc_e01(double d, double *e0, double *e1)
+/* Weights of the linear short-characteristics step over optical path d:
+ * e0 = 1 - exp(-d), e1 = d - e0, w_o = e1/d, w_u = e0 - w_o.  For d < 0.5
+ * e1 comes from its power series; otherwise 1 - w_o = e0/d and
+ * w_u = e0/d - exp(-d) are evaluated directly, because w_u ~ 1/d and
+ * 1 - w_o ~ 1/d at large d would otherwise be differences of two numbers
+ * close to one (relative error ~ 1e-16 d, and d reaches 1e8 in the Lyman
+ * line cores). */
+static void sc_step_weights(double d, double *ex, double *wu, double *wo, double *omwo)
 {
     if (d < 0.5) {
         /* e1 = sum_{n>=2} (-d)^n / n!,  e0 = d - e1 */
@@ -282,35 +288,53 @@ static void sc_e01(double d, double *e0, double *e1)
             s += term;
             if (fabs(term) < 1e-18 * fabs(s)) break;
         }
-        *e1 = s;
-        *e0 = d - s;
+        double e0 = d - s;
+        *wo = s / d;
+        *wu = e0 - *wo;
+        *omwo = 1.0 - *wo;
+        *ex = 1.0 - e0;
     } else {
-        *e0 = -expm1(-d);
-        *e1 = d - *e0;
+        double e0 = -expm1(-d);
+        *ex = exp(-d);
+        *omwo = e0 / d;
+        *wo = 1.0 - *omwo;
+        *wu = *omwo - *ex;
     }
 }
 
 /* One sweep along a ray.  dtau[k] is the optical path between points k and
  * k+1 along the ray (k = 0..N-2).  dir = +1 sweeps k = 0 -> N-1 (starting
  * value at k = 0), dir = -1 sweeps k = N-1 -> 0.  Output I[k] and the local
- * operator lam[k] = dI_k/dS_k (0 at the starting point). */
-void rho_sc_sweep(int N, const double *dtau, const double *S, double I0, int dir,
-                  double *I, double *lam)
+ * operator lam[k] = dI_k/dS_k (0 at the starting point).  Optional outputs
+ * (NULL to skip): Ieff[k], the intensity at k with the local source S[k]
+ * replaced by Sloc[k] (for the preconditioned rates, Sloc is the background
+ * part of the source function, so Ieff = I - Psi* eta_active), and
+ * omlam[k] = 1 - lam[k]. */
+static void sc_sweep_full(int N, const double *dtau, const double *S, const double *Sloc, double I0, int dir,
+                          double *I, double *lam, double *Ieff, double *omlam)
 {
     int k0 = dir > 0 ? 0 : N - 1;
     I[k0] = I0;
     lam[k0] = 0.0;
+    if (Ieff) Ieff[k0] = I0;
+    if (omlam) omlam[k0] = 1.0;
     for (int s = 1; s < N; ++s) {
         int ko = dir > 0 ? s : N - 1 - s;
         int ku = ko - dir;
         double d = dtau[dir > 0 ? ku : ko];
-        double e0, e1;
-        sc_e01(d, &e0, &e1);
-        double wo = e1 / d;
-        double wu = e0 - wo;
-        I[ko] = I[ku] * (1.0 - e0) + wu * S[ku] + wo * S[ko];
+        double ex, wu, wo, omwo;
+        sc_step_weights(d, &ex, &wu, &wo, &omwo);
+        double base = I[ku] * ex + wu * S[ku];
+        I[ko] = base + wo * S[ko];
         lam[ko] = wo;
+        if (Ieff) Ieff[ko] = base + wo * Sloc[ko];
+        if (omlam) omlam[ko] = omwo;
     }
+}
+
+void rho_sc_sweep(int N, const double *dtau, const double *S, double I0, int dir, double *I, double *lam)
+{
+    sc_sweep_full(N, dtau, S, NULL, I0, dir, I, lam, NULL, NULL);
 }
 
 /* ================================================================== */
@@ -692,7 +716,7 @@ typedef struct {
     double *C;        /* [N][L][L] collisional rates */
     double *Gam;      /* [N][L][L] rate matrix */
     /* sweep scratch */
-    double *chi, *eta, *etaact, *S, *dtau, *I, *lam;
+    double *chi, *eta, *etaact, *S, *dtau, *I, *lam, *Ieff, *omlam, *Sbg;
     double *chit, *Vlu, *Vul, *Ut;   /* [MAXACT][N] */
     double *hist;     /* Ng history [4][L*N] */
 } work_t;
@@ -711,6 +735,7 @@ static void work_alloc(work_t *w, const atom_t *a, int N)
     w->Gam = malloc(N * L * L * 8);
     w->chi = malloc(N * 8); w->eta = malloc(N * 8); w->etaact = malloc(N * 8);
     w->S = malloc(N * 8); w->dtau = malloc(N * 8); w->I = malloc(N * 8); w->lam = malloc(N * 8);
+    w->Ieff = malloc(N * 8); w->omlam = malloc(N * 8); w->Sbg = malloc(N * 8);
     w->chit = malloc(MAXACT * N * 8); w->Vlu = malloc(MAXACT * N * 8);
     w->Vul = malloc(MAXACT * N * 8); w->Ut = malloc(MAXACT * N * 8);
     w->hist = malloc(4 * L * N * 8);
@@ -721,6 +746,7 @@ static void work_free(work_t *w)
     free(w->dz); free(w->Bnu); free(w->chic); free(w->etac); free(w->ex); free(w->prof);
     free(w->C); free(w->Gam); free(w->chi); free(w->eta); free(w->etaact); free(w->S);
     free(w->dtau); free(w->I); free(w->lam); free(w->chit); free(w->Vlu); free(w->Vul);
+    free(w->Ieff); free(w->omlam); free(w->Sbg);
     free(w->Ut); free(w->hist);
 }
 
@@ -871,26 +897,34 @@ static void formal_ray(const rho_ctx *c, int64_t col, work_t *w, const double *n
         w->eta[k] = eta + ea;
         w->etaact[k] = ea;
         w->S[k] = w->eta[k] / chi;
+        w->Sbg[k] = eta / chi;
     }
     double mu = a->mu[m];
     for (int k = 0; k < N - 1; ++k) w->dtau[k] = 0.5 * (w->chi[k] + w->chi[k + 1]) * w->dz[k] / mu;
     if (d == 0) {
-        rho_sc_sweep(N, w->dtau, w->S, 0.0, +1, w->I, w->lam);
+        sc_sweep_full(N, w->dtau, w->S, w->Sbg, 0.0, +1, w->I, w->lam, w->Ieff, w->omlam);
     } else {
         double dtv = 0.5 * (w->chi[N - 1] + w->chi[N - 2]) * w->dz[N - 2];
         double B1 = w->Bnu[i * N + N - 1], B2 = w->Bnu[i * N + N - 2];
-        rho_sc_sweep(N, w->dtau, w->S, B1 + mu * (B1 - B2) / dtv, -1, w->I, w->lam);
+        sc_sweep_full(N, w->dtau, w->S, w->Sbg, B1 + mu * (B1 - B2) / dtv, -1, w->I, w->lam, w->Ieff, w->omlam);
     }
 }
 
 /* ------------------------------------------------------------------ */
 /* Rate matrix.  A[r][q] is the coefficient of n_q in dn_r/dt (columns sum
- * to zero).  mode 0: MALI (Rybicki & Hummer 1992): I_eff = I - Psi* eta_act
- * at the old populations, cross-coupling -W Psi* chi_t(old) U_t' between
- * every pair of transitions active at the wavelength; mode 1: plain rates
- * with I from the formal solution (Psi* = 0); mode 2: plain rates with each
- * transition seeing the Planck function (lines at their centre frequency,
- * continua at the actual frequency).  Collisions are always added. */
+ * to zero).  mode 0: MALI (Rybicki & Hummer 1992): the radiative terms use
+ * I_eff = I - Psi* eta_act (the intensity without the local emission of the
+ * active atom, at the old populations), the downward rate of transition t
+ * gets the preconditioning term -W Psi* chi_t(old) U_t, and every other
+ * transition t' active at the wavelength couples through -W Psi* chi_t U_t'.
+ * I_eff comes from the sweep with the local source replaced by its
+ * background part, and U_t - Psi* chi_t U_t = U_t [(1 - Lambda*) +
+ * Lambda* (chi - chi_t)/chi] with chi - chi_t summed from the other
+ * contributions: the same quantities without subtracting nearly equal
+ * numbers in optically thick layers.  mode 1: plain rates with I from the
+ * formal solution (Psi* = 0); mode 2: plain rates with each transition seeing
+ * the Planck function (lines at their centre frequency, continua at the
+ * actual frequency).  Collisions are always added. */
 static void rate_matrix(const rho_ctx *c, int64_t col, work_t *w, const double *n, int mode)
 {
     const atom_t *a = &c->at;
@@ -906,17 +940,26 @@ static void rate_matrix(const rho_ctx *c, int64_t col, work_t *w, const double *
                 if (mode != 2) formal_ray(c, col, w, n, i, m, d);
                 for (int k = 0; k < N; ++k) {
                     double psi = (mode == 0) ? w->lam[k] / w->chi[k] : 0.0;
-                    double Ieff = (mode == 2) ? 0.0 : w->I[k] - psi * w->etaact[k];
+                    double Ieff = (mode == 2) ? 0.0 : (mode == 0 ? w->Ieff[k] : w->I[k]);
                     double *Gk = G + (size_t)k * L * L;
                     for (int s = 0; s < a->nact[i]; ++s) {
                         int t = a->act[i * MAXACT + s], l = a->tl[t], u = a->tu[t];
                         double W = 4.0 * PI_D * a->wq[i * MAXACT + s] * (0.5 * a->wmu[m]) / (HPLANCK * nu);
                         double Ik = Ieff;
                         if (mode == 2) Ik = a->kind[t] == 0 ? rho_planck(a->nu0[t], T[k]) : w->Bnu[i * N + k];
+                        double Ut = w->Ut[s * N + k];
+                        double spont = Ut;
+                        if (mode == 0) {
+                            double other = w->chic[i * N + k];
+                            for (int s2 = 0; s2 < a->nact[i]; ++s2)
+                                if (s2 != s) other += w->chit[s2 * N + k];
+                            spont = Ut * (w->omlam[k] + w->lam[k] * other / w->chi[k]);
+                        }
                         Gk[u * L + l] += W * w->Vlu[s * N + k] * Ik;
-                        Gk[l * L + u] += W * (w->Ut[s * N + k] + w->Vul[s * N + k] * Ik);
+                        Gk[l * L + u] += W * (spont + w->Vul[s * N + k] * Ik);
                         if (psi != 0.0) {
                             for (int s2 = 0; s2 < a->nact[i]; ++s2) {
+                                if (s2 == s) continue;
                                 int t2 = a->act[i * MAXACT + s2], u2 = a->tu[t2];
                                 double cc = W * psi * w->chit[s * N + k] * w->Ut[s2 * N + k];
                                 if (l != u2) Gk[l * L + u2] -= cc;
