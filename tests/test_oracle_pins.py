@@ -20,7 +20,7 @@ def test_voigt_matches_faddeeva_library(orc):
     for a in (1e-3, 3e-3, 1e-2, 5e-2):
         ref = wofz(v + 1j * a).real
         got = np.array([orc.voigt(a, x) for x in v])
-        assert np.max(np.abs(got / ref - 1)) < 1e-10, a
+        assert np.max(np.abs(got / ref - 1)) < 1e-13, a
 
 
 def test_voigt_limits(orc):
