@@ -1,0 +1,348 @@
+"""Benchmark: converged columns/s of the 1.5D MALI hot path on GB300.
+
+Workload: 256x256 = 65536 synthetic chromospheric columns of 82 heights
+(seeded; a stand-in for the paper's 3D MHD snapshot), hydrogen-like 5-level +
+continuum atom, 608 wavelengths, 5 angles; every column iterated from LTE to
+max|dn/n| < 1e-3 with Ng acceleration; FP32 formal solution and rates, FP64
+rate equations and Ng; device work queue over resident blocks.
+One step = one rh_iterate over all columns (inputs resident in HBM).
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import rh_synth  # noqa: E402
+
+NX = NY = 256
+NDEP = 82
+TOL = 1e-3
+MAXITER = 500
+METRIC = "converged columns/s to max|dn/n|<1e-3"
+# FP32 operations per formal-solver point (one depth x lambda x mu, both
+# sweep directions), counted from the kernel source (see the design notes)
+FLOP_PER_PT = 264
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, p in rows:
+            for nm, val in zip(names, p[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(cube, seconds_target=15.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample."""
+    import oracle
+    atom = rh_synth.hydrogen_like_atom()
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle()
+    o.setup_atom(atom)
+    rng = np.random.default_rng(99)
+    n0 = 2 * cores
+    idx = rng.choice(cube["T"].shape[0], n0, replace=False)
+    o.load_columns(rh_synth.subset(cube, idx))
+    t0 = time.perf_counter()
+    o.iterate(maxiter=MAXITER, tol=TOL, nthreads=cores)
+    dt0 = time.perf_counter() - t0
+    n1 = int(max(n0, min(4096, n0 * seconds_target / max(dt0, 1e-3))))
+    idx = rng.choice(cube["T"].shape[0], n1, replace=False)
+    t0 = time.perf_counter()
+    conv = oracle_two_pass(o, rh_synth.subset(cube, idx), cores)
+    dt = time.perf_counter() - t0
+    return {"value": n1 / dt, "unit": "columns/s", "cores": cores, "kind": "oracle",
+            "sample": "%d random columns of the 256x256 cube (seed 99), LTE start, tol 1e-3, same re-run "
+                      "strategy, %d threads, %.1f s; %d converged" % (n1, cores, dt, conv)}
+
+
+def oracle_two_pass(o, cols, cores):
+    """The oracle with the same two passes as the GPU run; returns converged count."""
+    import oracle
+    o.load_columns(cols)
+    o.iterate(maxiter=MAXITER, tol=TOL, nthreads=cores)
+    n, it, st, _ = o.populations()
+    conv = int((st == oracle.ST_CONV).sum())
+    for f0 in (1e3, 1e5):
+        bad = np.where(st != oracle.ST_CONV)[0]
+        if not bad.size:
+            break
+        o2 = oracle.Oracle()
+        o2.setup_atom(rh_synth.hydrogen_like_atom())
+        cols = rh_synth.subset(cols, bad)
+        o2.load_columns(cols)
+        o2.iterate(maxiter=MAXITER, tol=TOL, ng_order=0, crsw_init=f0, nthreads=cores)
+        st = o2.populations()[2]
+        conv += int((st == oracle.ST_CONV).sum())
+    return conv
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    cube = rh_synth.chromosphere_cube(NX, NY, NDEP, seed=1234)
+    import oracle
+    cores = os.cpu_count() or 1
+    atom = rh_synth.hydrogen_like_atom()
+    o = oracle.Oracle()
+    o.setup_atom(atom)
+    ncol = 2 * cores
+    rng = np.random.default_rng(7)
+    times = []
+    for step in range(args.warmup + args.steps):
+        idx = rng.choice(NX * NY, ncol, replace=False)
+        t0 = time.perf_counter()
+        oracle_two_pass(o, rh_synth.subset(cube, idx), cores)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = ncol * len(times) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": "columns/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "256x256 synthetic chromosphere cube, 82 heights, H-like 5+1 atom, "
+                                   "608 wavelengths, 5 mu; each step a random sample of %d columns" % ncol,
+                       "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": "columns/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d random columns per step, %d threads" % (ncol, cores)},
+            "e2e": {"value": value, "unit": "columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1411_1079_gb300 as rh
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cube = rh_synth.chromosphere_cube(NX, NY, NDEP, seed=1234 + rank)
+    ncol = NX * NY
+    stream = torch.cuda.current_stream()
+    ctx = rh.Context(local, stream=stream.cuda_stream)
+    atom = rh_synth.hydrogen_like_atom()
+    ctx.setup_atom(atom)
+    dev = {k: torch.from_numpy(v).to("cuda") for k, v in cube.items()}
+    ctx.load_columns(dev, on_device=True)
+    opts = dict(maxiter=MAXITER, tol=TOL, precision=1, persistent=1)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        s = ctx.solve(**opts)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    kern_s = 0.0
+    pts = 0.0
+    iters = 0
+    conv = 0
+    launches = 0
+    rescued = 0
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            s = ctx.solve(**opts)
+            kern_s += s["seconds"]
+            pts += s["pts"]
+            iters += s["iterations_total"]
+            conv += s["n_converged"]
+            launches += s["launches"]
+            rescued += s["rerun_columns"]
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    value = ws * ncol * args.steps / (ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    pin = {k: torch.from_numpy(v).pin_memory() for k, v in cube.items()}
+    out = torch.empty((ncol, atom["nlev"], NDEP), dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * 8 for v in pin.values())
+    d2h = out.numel() * 8
+    ctx.load_columns(pin)
+    ctx.solve(**opts)
+    ctx.populations(out=out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.load_columns(pin)
+        ctx.solve(**opts)
+        ctx.populations(out=out)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * ncol * args.steps / e2e_s, "unit": "columns/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h + ncol * (4 + 1 + 8)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = _peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # FP32 lanes x 2 flop per FMA x clock (152 SMs, 128 FP32 lanes each)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tflops = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = pts * FLOP_PER_PT / kern_s / 1e12
+    pts_s = pts / kern_s
+    line = {
+        "metric": METRIC, "value": value, "unit": "columns/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "256x256 synthetic chromosphere cube (65536 columns), 82 heights, "
+                               "H-like 5-level+continuum atom, 608 wavelengths, 5 mu, tol 1e-3, LTE start",
+                   "ncol_per_gpu": ncol, "ndep": NDEP, "nlambda": ctx.nlambda, "nmu": atom["nmu"],
+                   "precision": "fp32 formal solution/rates, fp64 rate equations/Ng",
+                   "scheduling": "device work queue (pool mode); columns not converged are re-run "
+                                 "from LTE with collisional-radiative switching x1e3, no Ng",
+                   "l2": "working set 2 GB > L2 (inputs larger than L2)",
+                   "parallelism": "dp%d (independent columns)" % ws},
+        "formal_solver_pts_per_s": pts_s,
+        "iterations_per_column": iters / (ncol * args.steps),
+        "converged_fraction": conv / (ncol * args.steps),
+        "rerun_columns_per_step": rescued / args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "mali_kernel<float,5>",
+                     "peak_note": "FP32 FMA peak = %d SMs x 128 lanes x 2 x %.0f MHz (median SM clock "
+                                  "sampled during the timed region)" % (nsm, sm_mhz)},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cube)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_ncu_case(args):
+    """Small fixed case for ncu captures: 608 columns of the cube, 3 iterations."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1411_1079_gb300 as rh
+    cube = rh_synth.chromosphere_cube(NX, NY, NDEP, seed=1234)
+    ctx = rh.Context(0)
+    ctx.setup_atom(rh_synth.hydrogen_like_atom())
+    ctx.load_columns(rh_synth.subset(cube, slice(0, args.ncu_columns)))
+    s = ctx.iterate(maxiter=3, tol=0.0, precision=args.ncu_precision)
+    print(json.dumps({"ncu_case": True, "columns": args.ncu_columns, "seconds": s["seconds"]}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profiler captures")
+    ap.add_argument("--ncu-columns", type=int, default=608)
+    ap.add_argument("--ncu-precision", type=int, default=1)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.ncu_case:
+        run_ncu_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * rh15d.h -- C ABI of librh15d_gpu.so: the column-by-column (1.5D) multi-level
+ * accelerated Lambda iteration (MALI) on one NVIDIA GB300 (sm_103a).
+ *
+ * The problem (Pereira & Uitenbroek, RH 1.5D, Sect. 2): a model atom and many
+ * atmosphere columns go in; every column is an independent plane-parallel NLTE
+ * problem (Sect. 2.2) iterated to its own convergence (Sect. 2.3); converged
+ * level populations and the vertical emergent spectrum (Sect. 2.2) come out.
+ * The method (Sect. 2.1): MALI with a local (diagonal) approximate Psi
+ * operator and preconditioned rate equations, overlapping transitions sharing
+ * opacity and emissivity, Ng acceleration (Sect. 2.3), LTE start (Sect. 2.3).
+ *
+ * Conventions (all functions):
+ *   - return an rh_status; no exception or abort crosses the ABI;
+ *   - host pointers are read (inputs) or written (outputs) during the call
+ *     only, the library keeps no reference to them; the library copies;
+ *   - the context owns all device memory it allocates and frees it in
+ *     rh_destroy;
+ *   - calls on one context are not thread-safe; distinct contexts are
+ *     independent;
+ *   - all arrays are C-contiguous, SI units, depth index k = 0 at the TOP;
+ *   - after an error, rh_last_error() returns a message naming the first bad
+ *     argument (e.g. the first bad column and depth).
+ * Nothing here needs PyTorch; the Python binding passes plain pointers.
+ */
+#ifndef RH15D_H
+#define RH15D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rh_ctx rh_ctx;
+
+typedef enum {
+    RH_OK = 0,
+    RH_EINVAL = 1,     /* invalid argument or input value */
+    RH_ENOMEM = 2,     /* device or host allocation failed */
+    RH_ECUDA = 3,      /* a CUDA runtime call or kernel failed */
+    RH_ESTATE = 4,     /* call out of order (e.g. iterate before load) */
+    RH_ETIMEOUT = 5,   /* a bounded device wait gave up */
+    RH_ENOTCONV = 6    /* informational: some columns did not converge */
+} rh_status;
+
+/* per-column status codes written by rh_iterate */
+enum { RH_COL_CONVERGED = 0, RH_COL_MAXITER = 1, RH_COL_NONFINITE = 2, RH_COL_SINGULAR = 3,
+       RH_COL_NOTRUN = 4 };
+
+/* Create a context on CUDA device `cuda_device`.  `cuda_stream` is a
+ * cudaStream_t to launch on (NULL: the context creates its own stream).
+ * The caller keeps ownership of a stream it passes. */
+int rh_create(rh_ctx **out, int cuda_device, void *cuda_stream);
+void rh_destroy(rh_ctx *ctx);
+/* Message of the last failed call on this context (never NULL; valid until
+ * the next call on the context). */
+const char *rh_last_error(const rh_ctx *ctx);
+
+/* ---------------------------------------------------------------------- */
+/* Model atom (Sect. 2.1: multi-level atom with bound-bound and bound-free  */
+/* transitions).  Levels are indexed from the ground level; the last level  */
+/* is the continuum (ionised stage).  Every bound-free transition goes from  */
+/* cont_l[q] to the last level.                                              */
+typedef struct {
+    int32_t nlev;                  /* levels including the continuum, 2..8 */
+    const double *E_J;             /* [nlev] energy above the ground level, J */
+    const double *g;               /* [nlev] statistical weights (> 0) */
+    int32_t nline;                 /* bound-bound transitions */
+    const int32_t *line_l, *line_u;/* [nline] lower < upper < nlev-1 */
+    const double *line_f;          /* [nline] absorption oscillator strength */
+    const double *line_a_top;      /* [nline] Voigt damping at k = 0 */
+    const double *line_a_bot;      /* [nline] Voigt damping at k = ndep-1 (log-interpolated in k) */
+    const int32_t *line_nlambda;   /* [nline] wavelength points of the line (>= 2) */
+    const double *line_qwing;      /* [nline] half-width of the line grid, Doppler widths at T_ref */
+    int32_t ncont;                 /* bound-free transitions */
+    const int32_t *cont_l;         /* [ncont] lower level */
+    const double *cont_alpha0;     /* [ncont] cross section at the edge, m^2 (Kramers nu^-3 law) */
+    const int32_t *cont_nlambda;   /* [ncont] wavelength points (>= 2) */
+    const double *cont_ratio;      /* [ncont] range: edge frequency .. ratio * edge (> 1) */
+    double mass_amu;               /* atomic mass, amu */
+    double T_ref;                  /* K, reference temperature of the line grids */
+    int32_t nmu;                   /* Gauss-Legendre angles on (0,1], 1..8 */
+    double metal_floor;            /* electrons per hydrogen atom from metals */
+} rh_atom_desc;
+
+/* Copy the atom, build the wavelength grid (line bands on a sinh-stretched
+ * symmetric grid, continua geometric in frequency), the per-wavelength lists
+ * of overlapping transitions (Sect. 2.1), quadrature weights, and upload the
+ * tables.  RH_ESTATE if columns are loaded.  RH_EINVAL for a descriptor out
+ * of range (more than 3 transitions overlapping at one wavelength, more
+ * than 32 transitions, nlev > 8, nmu > 8, Voigt damping above 0.05). */
+int rh_setup_atom(rh_ctx *ctx, const rh_atom_desc *desc);
+
+/* Number of wavelength points of the grid (0 before rh_setup_atom). */
+int64_t rh_nlambda(const rh_ctx *ctx);
+/* Copy the grid frequencies [nlambda] (Hz) into nu_out (host). */
+int rh_get_grid(const rh_ctx *ctx, double *nu_out);
+
+/* ---------------------------------------------------------------------- */
+/* Load ncol columns of ndep depth points (Sect. 2.2: one column = one       */
+/* independent 1D problem).  Layout [ncol][ndep], k = 0 at the top, z        */
+/* strictly decreasing with k.  ne_m3 may be NULL: n_e then comes from       */
+/* hydrogen Saha ionisation plus metal_floor * n_H electrons.  on_device = 0: */
+/* host pointers, copied; on_device = 1: device pointers, copied on the       */
+/* context's stream (the caller keeps ownership).  Computes the LTE           */
+/* populations n*, collisional rates and the LTE start.  RH_EINVAL names the  */
+/* first non-finite or non-positive T, n_H (n_e), or non-decreasing z.        */
+int rh_load_columns(rh_ctx *ctx, int64_t ncol, int32_t ndep, const double *z_m,
+                    const double *T_K, const double *ne_m3, const double *nH_m3,
+                    const double *vz_ms, int32_t on_device);
+
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t maxiter;      /* formal solutions per column (default 500) */
+    double tol;           /* stop when max_{i,k} |dn/n| < tol (Sect. 2.3: 1e-3) */
+    int32_t ng_order;     /* 0 (off) or 2 (Ng 1974, Sect. 2.3) */
+    int32_t ng_delay;     /* first acceleration at this iteration */
+    int32_t ng_period;    /* iterations between accelerations */
+    int32_t start;        /* 0: LTE populations; 2: populations set by rh_set_populations
+                             or left by the previous rh_iterate */
+    int32_t precision;    /* 0: all FP64; 1: FP32 formal solution and rates, FP64 solve and Ng */
+    int32_t persistent;   /* 0: static split of columns over resident blocks (normal mode,
+                             Sect. 3.1); 1: device work queue (pool mode, Sect. 3.1) */
+    int32_t block_warps;  /* warps per block (0: library default) */
+    double crsw_init;     /* collisional-radiative switching (Hummer & Voels 1988, Sect. 2.3):
+                             collisional rates scaled by max(1, crsw_init 10^-(it-1)); <= 1: off */
+    int32_t only_unconverged; /* 1: iterate only the columns whose status is not RH_COL_CONVERGED
+                             (Sect. 2.3: re-run the columns that did not converge with other
+                             options); converged columns are left untouched */
+} rh_iter_opts;
+
+typedef struct {
+    int64_t n_converged, n_maxiter, n_failed;   /* over all loaded columns, after the call */
+    int64_t n_processed;           /* columns iterated by this call */
+    int64_t iterations_total;      /* sum over the processed columns of formal solutions */
+    double seconds;                /* device time of the iteration kernel */
+    double pts;                    /* depth x lambda x mu points solved */
+    double max_dn_final;           /* max over columns of the last max |dn/n| */
+} rh_iter_stats;
+
+/* Iterate every loaded column to convergence or maxiter.  Writes per-column
+ * populations, iteration counts, status and last max|dn/n| (read them with
+ * rh_get_populations).  Returns RH_OK, or RH_ENOTCONV if any column did not
+ * converge (results are still valid for the converged ones). */
+int rh_iterate(rh_ctx *ctx, const rh_iter_opts *opts, rh_iter_stats *stats_out);
+
+/* Copy results to host arrays (any pointer may be NULL):
+ * n_out [ncol][nlev][ndep] m^-3, iters [ncol], status [ncol] (RH_COL_*),
+ * dmax [ncol].  n_out may also be a device pointer when on_device = 1. */
+int rh_get_populations(rh_ctx *ctx, double *n_out, int32_t *iters, uint8_t *status,
+                       double *dmax, int32_t on_device);
+/* LTE populations [ncol][nlev][ndep] and electron densities [ncol][ndep] (host). */
+int rh_get_lte(rh_ctx *ctx, double *nstar_out, double *ne_out);
+/* Set the current populations (host [ncol][nlev][ndep], finite, > 0): the
+ * checkpoint / restart path (rh_iterate with start = 2). */
+int rh_set_populations(rh_ctx *ctx, const double *n_in);
+
+/* Emergent intensity I(mu, lambda) at the top of every column for the current
+ * populations (Sect. 2.2: vertical emergent spectrum; mu = 1 is vertical),
+ * at arbitrary wavelengths lambda_m [nlambda] (m, > 0).  I_out [ncol][nlambda]
+ * in W m^-2 Hz^-1 sr^-1, host memory (on_device = 0) or device (1).
+ * precision as in rh_iter_opts. */
+int rh_emergent_spectrum(rh_ctx *ctx, double mu, int64_t nlambda, const double *lambda_m,
+                         double *I_out, int32_t precision, int32_t on_device);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RH15D_H */

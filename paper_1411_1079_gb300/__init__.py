@@ -1,0 +1,241 @@
+"""Python binding of librh15d_gpu.so (the C ABI in include/rh15d.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Arrays are numpy (host) or torch CUDA tensors (device, passed by
+pointer with ``on_device=True``).  There is no CPU fallback: if the library
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._build import LIB, build
+
+RH_OK, RH_EINVAL, RH_ENOMEM, RH_ECUDA, RH_ESTATE, RH_ETIMEOUT, RH_ENOTCONV = range(7)
+COL_CONVERGED, COL_MAXITER, COL_NONFINITE, COL_SINGULAR, COL_NOTRUN = range(5)
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lib = None
+
+EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlambda", "rh_get_grid",
+           "rh_load_columns", "rh_iterate", "rh_get_populations", "rh_get_lte", "rh_set_populations",
+           "rh_emergent_spectrum")
+
+
+class AtomDesc(C.Structure):
+    _fields_ = [("nlev", C.c_int32), ("E_J", _dp), ("g", _dp),
+                ("nline", C.c_int32), ("line_l", _ip), ("line_u", _ip),
+                ("line_f", _dp), ("line_a_top", _dp), ("line_a_bot", _dp),
+                ("line_nlambda", _ip), ("line_qwing", _dp),
+                ("ncont", C.c_int32), ("cont_l", _ip), ("cont_alpha0", _dp),
+                ("cont_nlambda", _ip), ("cont_ratio", _dp),
+                ("mass_amu", C.c_double), ("T_ref", C.c_double), ("nmu", C.c_int32),
+                ("metal_floor", C.c_double)]
+
+
+class IterOpts(C.Structure):
+    _fields_ = [("maxiter", C.c_int32), ("tol", C.c_double), ("ng_order", C.c_int32),
+                ("ng_delay", C.c_int32), ("ng_period", C.c_int32), ("start", C.c_int32),
+                ("precision", C.c_int32), ("persistent", C.c_int32), ("block_warps", C.c_int32),
+                ("crsw_init", C.c_double), ("only_unconverged", C.c_int32)]
+
+
+class IterStats(C.Structure):
+    _fields_ = [("n_converged", C.c_int64), ("n_maxiter", C.c_int64), ("n_failed", C.c_int64),
+                ("n_processed", C.c_int64), ("iterations_total", C.c_int64), ("seconds", C.c_double),
+                ("pts", C.c_double), ("max_dn_final", C.c_double)]
+
+
+def lib(path: str | None = None):
+    """Load the CUDA library (raises if it is missing or fails to load)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB
+        if not os.path.exists(p):
+            raise RuntimeError("librh15d_gpu.so is not built (run paper_1411_1079_gb300._build.build())")
+        L = C.CDLL(p)
+        vp = C.c_void_p
+        L.rh_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+        L.rh_destroy.argtypes = [vp]
+        L.rh_destroy.restype = None
+        L.rh_last_error.argtypes = [vp]
+        L.rh_last_error.restype = C.c_char_p
+        L.rh_setup_atom.argtypes = [vp, C.POINTER(AtomDesc)]
+        L.rh_nlambda.argtypes = [vp]
+        L.rh_nlambda.restype = C.c_int64
+        L.rh_get_grid.argtypes = [vp, _dp]
+        L.rh_load_columns.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp, vp, vp, C.c_int32]
+        L.rh_iterate.argtypes = [vp, C.POINTER(IterOpts), C.POINTER(IterStats)]
+        L.rh_get_populations.argtypes = [vp, vp, _ip, C.POINTER(C.c_uint8), _dp, C.c_int32]
+        L.rh_get_lte.argtypes = [vp, _dp, _dp]
+        L.rh_set_populations.argtypes = [vp, _dp]
+        L.rh_emergent_spectrum.argtypes = [vp, C.c_double, C.c_int64, _dp, vp, C.c_int32, C.c_int32]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+def _ptr(x):
+    """Pointer of a numpy array or a torch tensor (device)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+class RhError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("rh error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Context:
+    """One rh_ctx: an atom, a set of columns and their MALI state on one GPU."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = lib()
+        p = C.c_void_p()
+        rc = self._lib.rh_create(C.byref(p), device, C.c_void_p(stream) if stream else None)
+        self._p = p
+        if rc:
+            msg = self._lib.rh_last_error(p).decode() if p else "rh_create failed"
+            raise RhError(rc, msg)
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self._lib.rh_destroy(self._p)
+            self._p = None
+
+    __del__ = close
+
+    def _check(self, rc, allow=()):
+        if rc and rc not in allow:
+            raise RhError(rc, self._lib.rh_last_error(self._p).decode())
+        return rc
+
+    def setup_atom(self, atom: dict):
+        a = {k: (np.ascontiguousarray(v) if isinstance(v, np.ndarray) else v) for k, v in atom.items()}
+        self._keep = a
+        d = AtomDesc(nlev=a["nlev"], E_J=_d(a["E_J"]), g=_d(a["g"]), nline=len(a["line_l"]),
+                     line_l=_i(a["line_l"]), line_u=_i(a["line_u"]), line_f=_d(a["line_f"]),
+                     line_a_top=_d(a["line_a_top"]), line_a_bot=_d(a["line_a_bot"]),
+                     line_nlambda=_i(a["line_nlambda"]), line_qwing=_d(a["line_qwing"]),
+                     ncont=len(a["cont_l"]), cont_l=_i(a["cont_l"]), cont_alpha0=_d(a["cont_alpha0"]),
+                     cont_nlambda=_i(a["cont_nlambda"]), cont_ratio=_d(a["cont_ratio"]),
+                     mass_amu=a["mass_amu"], T_ref=a["T_ref"], nmu=a["nmu"],
+                     metal_floor=a["metal_floor"])
+        self._check(self._lib.rh_setup_atom(self._p, C.byref(d)))
+        self.nlev = a["nlev"]
+        self.nmu = a["nmu"]
+
+    @property
+    def nlambda(self) -> int:
+        return int(self._lib.rh_nlambda(self._p))
+
+    def grid(self):
+        nu = np.zeros(self.nlambda)
+        self._check(self._lib.rh_get_grid(self._p, _d(nu)))
+        return nu
+
+    def load_columns(self, cols: dict, ne=None, on_device: bool = False):
+        """``cols``: z, T, nH, vz arrays [ncol][ndep] (numpy; or torch tensors,
+        CUDA with on_device=True, or CPU/pinned with on_device=False)."""
+        if on_device or hasattr(cols["T"], "data_ptr"):
+            arrs = [cols["z"], cols["T"], ne, cols["nH"], cols["vz"]]
+            ncol, ndep = cols["T"].shape
+        else:
+            arrs = [None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+                    for x in (cols["z"], cols["T"], ne, cols["nH"], cols["vz"])]
+            ncol, ndep = arrs[1].shape
+        self._cols_keep = arrs
+        self._check(self._lib.rh_load_columns(self._p, ncol, ndep, *[_ptr(x) for x in arrs], int(on_device)))
+        self.ncol, self.ndep = int(ncol), int(ndep)
+
+    def iterate(self, maxiter=500, tol=1e-3, ng_order=2, ng_delay=5, ng_period=3, start=0,
+                precision=1, persistent=1, block_warps=0, crsw_init=1.0, only_unconverged=0) -> dict:
+        o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
+                     ng_period=ng_period, start=start, precision=precision, persistent=persistent,
+                     block_warps=block_warps, crsw_init=crsw_init, only_unconverged=only_unconverged)
+        s = IterStats()
+        rc = self._check(self._lib.rh_iterate(self._p, C.byref(o), C.byref(s)), allow=(RH_ENOTCONV,))
+        out = {f: getattr(s, f) for f, _ in IterStats._fields_}
+        out["rc"] = rc
+        return out
+
+    # Sect. 2.3: run all columns with an aggressive choice of options, then
+    # re-run the columns that did not converge with other options.
+    RESCUE_PASSES = (dict(ng_order=0, crsw_init=1e3), dict(ng_order=0, crsw_init=1e5))
+
+    def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True):
+        """All columns from LTE with Ng acceleration, then the columns that did
+        not converge again from LTE with collisional-radiative switching
+        (x1e3, then x1e5) and without Ng (the paper's two-stage strategy)."""
+        s = self.iterate(maxiter=maxiter, tol=tol, precision=precision, persistent=persistent,
+                         block_warps=block_warps)
+        passes = [s]
+        if rescue:
+            for kw in self.RESCUE_PASSES:
+                if not (s["n_maxiter"] or s["n_failed"]):
+                    break
+                s = self.iterate(maxiter=maxiter, tol=tol, precision=precision, persistent=persistent,
+                                 block_warps=block_warps, only_unconverged=1, **kw)
+                passes.append(s)
+        return {"passes": passes, "n_converged": s["n_converged"], "n_maxiter": s["n_maxiter"],
+                "n_failed": s["n_failed"], "seconds": sum(p["seconds"] for p in passes),
+                "pts": sum(p["pts"] for p in passes),
+                "iterations_total": sum(p["iterations_total"] for p in passes),
+                "rerun_columns": sum(p["n_processed"] for p in passes[1:]),
+                "launches": sum(1 for p in passes if p["n_processed"] > 0)}
+
+    def populations(self, out=None):
+        """(n [ncol][nlev][ndep], iters, status, dmax).  ``out`` may be a torch
+        tensor (CUDA: device copy; CPU, e.g. pinned: host copy)."""
+        it = np.zeros(self.ncol, np.int32)
+        st = np.zeros(self.ncol, np.uint8)
+        dm = np.zeros(self.ncol)
+        if out is not None:
+            dev = int(bool(getattr(out, "is_cuda", False)))
+            self._check(self._lib.rh_get_populations(self._p, _ptr(out), _i(it),
+                                                     st.ctypes.data_as(C.POINTER(C.c_uint8)), _d(dm), dev))
+            return out, it, st, dm
+        n = np.zeros((self.ncol, self.nlev, self.ndep))
+        self._check(self._lib.rh_get_populations(self._p, _ptr(n), _i(it),
+                                                 st.ctypes.data_as(C.POINTER(C.c_uint8)), _d(dm), 0))
+        return n, it, st, dm
+
+    def lte(self):
+        ns = np.zeros((self.ncol, self.nlev, self.ndep))
+        ne = np.zeros((self.ncol, self.ndep))
+        self._check(self._lib.rh_get_lte(self._p, _d(ns), _d(ne)))
+        return ns, ne
+
+    def set_populations(self, n):
+        n = np.ascontiguousarray(n, dtype=np.float64)
+        self._check(self._lib.rh_set_populations(self._p, _d(n)))
+
+    def emergent_spectrum(self, mu, lam_m, precision=0, out=None):
+        lam_m = np.ascontiguousarray(lam_m, dtype=np.float64)
+        if out is not None:
+            self._check(self._lib.rh_emergent_spectrum(self._p, float(mu), lam_m.size, _d(lam_m), _ptr(out),
+                                                       precision, 1))
+            return out
+        I = np.zeros((self.ncol, lam_m.size))
+        self._check(self._lib.rh_emergent_spectrum(self._p, float(mu), lam_m.size, _d(lam_m), _ptr(I),
+                                                   precision, 0))
+        return I
+
+
+__all__ = ["Context", "RhError", "build", "lib", "EXPORTS"]

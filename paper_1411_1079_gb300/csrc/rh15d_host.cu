@@ -1,0 +1,819 @@
+// rh15d_host.cu -- the C ABI (include/rh15d.h): context, atom tables,
+// wavelength grid, column storage, launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rh15d_internal.h"
+
+using namespace rh;
+
+namespace {
+
+struct HostTrans {
+    int l, u, kind, sub;
+    double nu0, f, A, Blu, Bul, a_top, a_bot, qwing, alpha0, ratio, nu_lo, nu_hi;
+    int nlam;
+};
+
+struct HostAtom {
+    int nlev = 0, nline = 0, ncont = 0, ntr = 0, nmu = 0;
+    double E[RH_MAXLEV], g[RH_MAXLEV];
+    double mass = 0, T_ref = 0, floor_e = 0;
+    std::vector<HostTrans> tr;
+    std::vector<double> nu;                 // grid, band order
+    std::vector<int> owner;                 // band transition of each point
+    std::vector<std::vector<int>> act;      // active transitions per point
+    std::vector<std::vector<double>> wq;    // quadrature weight of each active transition
+    // tiles
+    int ntile = 0, npad = 0;
+    std::vector<int> lane_point;            // grid index of each padded lane, -1 padding
+    std::vector<std::vector<int>> tile_union;
+    double mu[RH_MAXMU], wmu[RH_MAXMU];
+};
+
+}  // namespace
+
+struct rh_ctx {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int nsm = 0;
+    std::string err;
+    bool have_atom = false;
+    HostAtom ha;
+    DevAtom da;
+    std::vector<double> lane_master;        // unscaled lane table, [kLaneFields][npad]
+    void *lane_d = nullptr;                 // device lane table in the current precision/scale
+    int lane_prec = -1;
+    double lane_nref = 0;
+    float *daw_d = nullptr;
+    // columns
+    int64_t ncol = 0;
+    int ndep = 0;
+    double nref = 1.0;
+    ColumnArrays ca{};
+    double *nghist = nullptr;
+    size_t nghist_cap = 0;
+    int *queue = nullptr;
+    long long *badidx = nullptr;
+    int *colidx = nullptr;
+    int64_t colidx_cap = 0;
+};
+
+namespace {
+
+int fail(rh_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(c, RH_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void free_columns(rh_ctx *c)
+{
+    dfree(c->ca.z);
+    dfree(c->ca.T);
+    dfree(c->ca.nH);
+    dfree(c->ca.vz);
+    dfree(c->ca.ne);
+    dfree(c->ca.np);
+    dfree(c->ca.nstar);
+    dfree(c->ca.pops);
+    dfree(c->ca.Crate);
+    dfree(c->ca.dmax);
+    dfree(c->ca.iters);
+    dfree(c->ca.status);
+    c->ncol = 0;
+    c->ca.ncol = 0;
+}
+
+// Gauss-Legendre nodes/weights on (0,1) (weights sum to 1), Newton on P_n.
+void gauss_legendre_unit(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int iter = 0; iter < 100; ++iter) {
+            double p0 = 1.0, p1 = z;
+            for (int j = 2; j <= n; ++j) {
+                double p2 = ((2 * j - 1) * z * p1 - (j - 1) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            double pn = n == 1 ? z : p1;
+            double pm = n == 1 ? 1.0 : p0;
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+            double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-15) {
+                // one more evaluation of the derivative at the root
+                p0 = 1.0;
+                p1 = z;
+                for (int j = 2; j <= n; ++j) {
+                    double p2 = ((2 * j - 1) * z * p1 - (j - 1) * p0) / j;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                pn = n == 1 ? z : p1;
+                pm = n == 1 ? 1.0 : p0;
+                dp = n * (z * pn - pm) / (z * z - 1.0);
+                break;
+            }
+        }
+        x[n - 1 - i] = 0.5 * (1.0 + z);
+        w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+int build_atom(rh_ctx *c, const rh_atom_desc *d)
+{
+    HostAtom a;
+    if (!d) return fail(c, RH_EINVAL, "desc is NULL");
+    if (d->nlev < 2 || d->nlev > RH_MAXLEV) return fail(c, RH_EINVAL, "nlev must be in 2..%d", RH_MAXLEV);
+    if (d->nline < 0 || d->ncont < 0 || d->nline + d->ncont < 1 || d->nline + d->ncont > RH_MAXTR)
+        return fail(c, RH_EINVAL, "nline + ncont must be in 1..%d", RH_MAXTR);
+    if (d->nmu < 1 || d->nmu > 8) return fail(c, RH_EINVAL, "nmu must be in 1..8");
+    if (!(d->mass_amu > 0) || !(d->T_ref > 0) || !(d->metal_floor >= 0))
+        return fail(c, RH_EINVAL, "mass_amu, T_ref must be > 0 and metal_floor >= 0");
+    a.nlev = d->nlev;
+    a.nline = d->nline;
+    a.ncont = d->ncont;
+    a.ntr = d->nline + d->ncont;
+    a.nmu = d->nmu;
+    a.mass = d->mass_amu * kAmu;
+    a.T_ref = d->T_ref;
+    a.floor_e = d->metal_floor;
+    for (int i = 0; i < a.nlev; ++i) {
+        a.E[i] = d->E_J[i];
+        a.g[i] = d->g[i];
+        if (!(a.g[i] > 0) || !std::isfinite(a.E[i])) return fail(c, RH_EINVAL, "level %d: bad E or g", i);
+    }
+    const int ic = a.nlev - 1;
+    for (int i = 0; i < ic; ++i)
+        if (!(a.E[ic] > a.E[i])) return fail(c, RH_EINVAL, "level %d lies above the continuum", i);
+    for (int t = 0; t < d->nline; ++t) {
+        HostTrans h{};
+        h.l = d->line_l[t];
+        h.u = d->line_u[t];
+        if (h.l < 0 || h.u >= ic || h.l >= h.u) return fail(c, RH_EINVAL, "line %d: levels out of range", t);
+        if (d->line_nlambda[t] < 2) return fail(c, RH_EINVAL, "line %d: line_nlambda < 2", t);
+        if (!(d->line_f[t] > 0) || !(d->line_qwing[t] > 0) || !(d->line_a_top[t] > 0) || !(d->line_a_bot[t] > 0) ||
+            d->line_a_top[t] > 0.05 || d->line_a_bot[t] > 0.05)
+            return fail(c, RH_EINVAL, "line %d: f, qwing must be > 0 and damping in (0, 0.05]", t);
+        h.kind = 0;
+        h.sub = t;
+        h.nu0 = (a.E[h.u] - a.E[h.l]) / kH;
+        if (!(h.nu0 > 0)) return fail(c, RH_EINVAL, "line %d: upper level not above lower", t);
+        h.f = d->line_f[t];
+        h.A = 2.0 * kPi * kQ * kQ * h.nu0 * h.nu0 / (kEps0 * kMe * kC * kC * kC) * (a.g[h.l] / a.g[h.u]) * h.f;
+        h.Bul = h.A * kC * kC / (2.0 * kH * h.nu0 * h.nu0 * h.nu0);
+        h.Blu = h.Bul * a.g[h.u] / a.g[h.l];
+        h.a_top = d->line_a_top[t];
+        h.a_bot = d->line_a_bot[t];
+        h.qwing = d->line_qwing[t];
+        h.nlam = d->line_nlambda[t];
+        double dnu = h.nu0 / kC * std::sqrt(2.0 * kK * a.T_ref / a.mass);
+        h.nu_lo = h.nu0 - h.qwing * dnu;
+        h.nu_hi = h.nu0 + h.qwing * dnu;
+        a.tr.push_back(h);
+    }
+    for (int q = 0; q < d->ncont; ++q) {
+        HostTrans h{};
+        h.l = d->cont_l[q];
+        h.u = ic;
+        if (h.l < 0 || h.l >= ic) return fail(c, RH_EINVAL, "continuum %d: lower level out of range", q);
+        if (d->cont_nlambda[q] < 2) return fail(c, RH_EINVAL, "continuum %d: cont_nlambda < 2", q);
+        if (!(d->cont_ratio[q] > 1.0) || !(d->cont_alpha0[q] > 0))
+            return fail(c, RH_EINVAL, "continuum %d: ratio must exceed 1 and alpha0 be > 0", q);
+        h.kind = 1;
+        h.sub = q;
+        h.nu0 = (a.E[ic] - a.E[h.l]) / kH;
+        h.alpha0 = d->cont_alpha0[q];
+        h.ratio = d->cont_ratio[q];
+        h.nlam = d->cont_nlambda[q];
+        h.nu_lo = h.nu0;
+        h.nu_hi = h.nu0 * h.ratio;
+        a.tr.push_back(h);
+    }
+    gauss_legendre_unit(a.nmu, a.mu, a.wmu);
+    // grid: bands in transition order
+    const double beta = 5.0;
+    for (int t = 0; t < a.ntr; ++t) {
+        const HostTrans &h = a.tr[t];
+        for (int j = 0; j < h.nlam; ++j) {
+            double nu;
+            if (h.kind == 0) {
+                double s = -1.0 + 2.0 * j / (h.nlam - 1);
+                double dnu = h.nu0 / kC * std::sqrt(2.0 * kK * a.T_ref / a.mass);
+                nu = h.nu0 + h.qwing * std::sinh(beta * s) / std::sinh(beta) * dnu;
+            } else {
+                nu = h.nu0 * std::pow(h.ratio, (double)j / (h.nlam - 1));
+            }
+            a.nu.push_back(nu);
+            a.owner.push_back(t);
+        }
+    }
+    const size_t np = a.nu.size();
+    a.act.resize(np);
+    a.wq.resize(np);
+    for (size_t i = 0; i < np; ++i) {
+        for (int t = 0; t < a.ntr; ++t) {
+            const HostTrans &h = a.tr[t];
+            bool in = t == a.owner[i] ||
+                      (a.nu[i] >= h.nu_lo * (1 - 1e-13) && a.nu[i] <= h.nu_hi * (1 + 1e-13));
+            if (in) a.act[i].push_back(t);
+        }
+        a.wq[i].assign(a.act[i].size(), 0.0);
+    }
+    // trapezoid weights in frequency per transition over its active points
+    for (int t = 0; t < a.ntr; ++t) {
+        std::vector<std::pair<double, std::pair<size_t, size_t>>> pts;
+        for (size_t i = 0; i < np; ++i)
+            for (size_t s = 0; s < a.act[i].size(); ++s)
+                if (a.act[i][s] == t) pts.push_back({a.nu[i], {i, s}});
+        std::sort(pts.begin(), pts.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+        for (size_t j = 0; j < pts.size(); ++j) {
+            double lo = j > 0 ? pts[j - 1].first : pts[j].first;
+            double hi = j + 1 < pts.size() ? pts[j + 1].first : pts[j].first;
+            a.wq[pts[j].second.first][pts[j].second.second] = 0.5 * (hi - lo);
+        }
+    }
+    // tiles of 32 lanes within each band; a tile is closed (and padded) when it
+    // is full or when the next point would bring more than RH_KMAX transitions
+    // into the tile's union
+    size_t p0 = 0;
+    for (int t = 0; t < a.ntr; ++t) {
+        int n = a.tr[t].nlam;
+        std::vector<int> lanes, un;
+        auto flush = [&]() {
+            if (lanes.empty()) return;
+            for (int l = 0; l < 32; ++l) a.lane_point.push_back(l < (int)lanes.size() ? lanes[l] : -1);
+            std::sort(un.begin(), un.end());
+            a.tile_union.push_back(un);
+            lanes.clear();
+            un.clear();
+        };
+        for (int j = 0; j < n; ++j) {
+            const int gi = (int)(p0 + j);
+            if ((int)a.act[gi].size() > RH_KMAX)
+                return fail(c, RH_EINVAL, "%zu transitions overlap at one wavelength (max %d)", a.act[gi].size(),
+                            RH_KMAX);
+            std::vector<int> nu2 = un;
+            for (int tt : a.act[gi])
+                if (std::find(nu2.begin(), nu2.end(), tt) == nu2.end()) nu2.push_back(tt);
+            if ((int)nu2.size() > RH_KMAX || lanes.size() == 32) {
+                flush();
+                nu2 = a.act[gi];
+            }
+            lanes.push_back(gi);
+            un = nu2;
+        }
+        flush();
+        p0 += n;
+    }
+    a.ntile = (int)a.tile_union.size();
+    a.npad = a.ntile * 32;
+    if (a.ntile > RH_MAXTILE) return fail(c, RH_EINVAL, "grid needs %d tiles (max %d)", a.ntile, RH_MAXTILE);
+
+    // device atom
+    DevAtom &da = c->da;
+    memset(&da, 0, sizeof da);
+    da.nlev = a.nlev;
+    da.ntr = a.ntr;
+    da.nline = a.nline;
+    da.ncont = a.ncont;
+    da.ntile = a.ntile;
+    da.nmu = a.nmu;
+    da.mass = a.mass;
+    da.metal_floor = a.floor_e;
+    for (int i = 0; i < ic; ++i) {
+        da.lev_chi[i] = a.E[ic] - a.E[i];
+        da.lev_g2[i] = a.g[i] / (2.0 * a.g[ic]);
+    }
+    for (int m = 0; m < a.nmu; ++m) {
+        da.mu[m] = a.mu[m];
+        da.wmu[m] = a.wmu[m];
+        da.muf[m] = (float)a.mu[m];
+        da.wm2f[m] = (float)(0.5 * a.wmu[m]);
+    }
+    for (int t = 0; t < a.ntr; ++t) {
+        const HostTrans &h = a.tr[t];
+        DevTrans &dt = da.tr[t];
+        dt.l = h.l;
+        dt.u = h.u;
+        dt.kind = h.kind;
+        dt.sub = h.sub;
+        dt.nu0 = h.nu0;
+        dt.A = h.A;
+        dt.Blu = h.Blu;
+        dt.Bul = h.Bul;
+        dt.alpha0 = h.alpha0;
+        dt.f = h.f;
+        dt.ln_atop = h.kind == 0 ? std::log(h.a_top) : 0.0;
+        dt.ln_abot = h.kind == 0 ? std::log(h.a_bot) : 0.0;
+    }
+    int acc = 0, nmap = 0;
+    for (int b = 0; b < a.ntile; ++b) {
+        const std::vector<int> &un = a.tile_union[b];
+        int K = (int)un.size();
+        DevTile &tl = da.tile[b];
+        tl.K = K;
+        for (int j = 0; j < K; ++j) tl.t[j] = un[j];
+        tl.acc_off = acc;
+        tl.m = K * (K + 1);
+        auto add = [&](int accj, int row, int col, int sign) -> bool {
+            if (row == col) return true;
+            if (nmap >= RH_MAXMAP) return false;
+            da.map_acc[nmap] = (int16_t)(acc + accj);
+            da.map_row[nmap] = (int8_t)row;
+            da.map_col[nmap] = (int8_t)col;
+            da.map_sign[nmap] = (int8_t)sign;
+            ++nmap;
+            return true;
+        };
+        bool ok = true;
+        for (int j = 0; j < K; ++j) {
+            const HostTrans &h = a.tr[un[j]];
+            ok &= add(j, h.u, h.l, +1);        // upward rate l -> u
+            ok &= add(K + j, h.l, h.u, +1);    // downward rate u -> l (with the self cross term)
+        }
+        int idx = 2 * K;
+        for (int j = 0; j < K; ++j)
+            for (int j2 = 0; j2 < K; ++j2) {
+                if (j2 == j) continue;
+                const HostTrans &h = a.tr[un[j]], &h2 = a.tr[un[j2]];
+                ok &= add(idx, h.l, h2.u, -1);
+                ok &= add(idx, h.u, h2.u, +1);
+                ++idx;
+            }
+        if (!ok) return fail(c, RH_EINVAL, "rate-matrix map exceeds %d entries", RH_MAXMAP);
+        acc += tl.m;
+    }
+    da.macc = acc;
+    da.nmap = nmap;
+
+    // lane master table (unscaled)
+    const int F = kLaneFields;
+    c->lane_master.assign((size_t)F * a.npad, 0.0);
+    auto LM = [&](int f, int p) -> double & { return c->lane_master[(size_t)f * a.npad + p]; };
+    for (int b = 0; b < a.ntile; ++b) {
+        const std::vector<int> &un = a.tile_union[b];
+        int first = -1;
+        for (int l = 0; l < 32; ++l)
+            if (a.lane_point[b * 32 + l] >= 0) {
+                first = a.lane_point[b * 32 + l];
+                break;
+            }
+        for (int l = 0; l < 32; ++l) {
+            int p = b * 32 + l;
+            int gi = a.lane_point[p];
+            double nu = a.nu[gi >= 0 ? gi : first];
+            LM(kLaneNu, p) = nu;
+            LM(kLaneHm, p) = hminus_sigma(kC / nu);
+            LM(kLaneNu3, p) = std::pow(1e15 / nu, 3);
+            LM(kLaneTw, p) = 2.0 * kH * nu * nu * nu / (kC * kC);
+            if (gi < 0) continue;
+            for (size_t j = 0; j < un.size(); ++j) {
+                int t = un[j];
+                auto it = std::find(a.act[gi].begin(), a.act[gi].end(), t);
+                if (it == a.act[gi].end()) continue;
+                double w = a.wq[gi][it - a.act[gi].begin()];
+                const HostTrans &h = a.tr[t];
+                int f0 = RH_NLANEF * (int)j;
+                if (h.kind == 0) {
+                    double h4 = kH * nu / (4.0 * kPi);
+                    LM(f0 + 0, p) = w * h.Blu;
+                    LM(f0 + 1, p) = h4 * h.Blu;
+                    LM(f0 + 2, p) = h4 * h.A;
+                    LM(f0 + 3, p) = 2.0 * kH * h.nu0 * h.nu0 * h.nu0 / (kC * kC);
+                    LM(f0 + 4, p) = kC * ((nu - h.nu0) / h.nu0);   // nu - nu0 is exact (Sterbenz)
+                    LM(f0 + 5, p) = kC / (kSqrtPi * h.nu0);
+                    LM(f0 + 6, p) = a.g[h.l] / a.g[h.u];
+                } else {
+                    double r = h.nu0 / nu;
+                    double alpha = h.alpha0 * r * r * r;
+                    double tw = 2.0 * kH * nu * nu * nu / (kC * kC);
+                    LM(f0 + 0, p) = 4.0 * kPi * w * alpha / (kH * nu);
+                    LM(f0 + 1, p) = alpha;
+                    LM(f0 + 2, p) = tw * alpha;
+                    LM(f0 + 3, p) = tw;
+                }
+            }
+        }
+    }
+    c->ha = std::move(a);
+    return RH_OK;
+}
+
+// upload the lane table in precision prec with populations scaled by 1/nref
+int ensure_lane(rh_ctx *c, int prec)
+{
+    if (c->lane_d && c->lane_prec == prec && c->lane_nref == c->nref) return RH_OK;
+    dfree(c->lane_d);
+    const int F = kLaneFields, np = c->ha.npad;
+    std::vector<double> v = c->lane_master;
+    for (int j = 0; j < RH_KMAX; ++j)
+        for (int f : {1, 2})
+            for (int p = 0; p < np; ++p) v[(size_t)(RH_NLANEF * j + f) * np + p] *= c->nref;
+    size_t n = (size_t)F * np;
+    if (prec == 1) {
+        std::vector<float> h(n);
+        for (size_t i = 0; i < n; ++i) h[i] = (float)v[i];
+        CK(cudaMalloc(&c->lane_d, n * sizeof(float)));
+        CK(cudaMemcpy(c->lane_d, h.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        CK(cudaMalloc(&c->lane_d, n * sizeof(double)));
+        CK(cudaMemcpy(c->lane_d, v.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    c->lane_prec = prec;
+    c->lane_nref = c->nref;
+    return RH_OK;
+}
+
+__global__ void validate_kernel(int64_t ncol, int ndep, const double *z, const double *T, const double *ne,
+                                const double *nH, const double *vz, unsigned long long *bad)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncol * ndep) return;
+    int k = (int)(i % ndep);
+    bool ok = isfinite(T[i]) && T[i] > 0 && isfinite(nH[i]) && nH[i] > 0 && isfinite(z[i]) && isfinite(vz[i]) &&
+              (!ne || (isfinite(ne[i]) && ne[i] > 0));
+    if (ok && k > 0) ok = z[i] < z[i - 1];
+    if (!ok) atomicMin(bad, (unsigned long long)i);
+}
+
+__global__ void max_kernel(int64_t n, const double *x, unsigned long long *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // positive doubles order like their bit patterns
+    atomicMax(out, (unsigned long long)__double_as_longlong(x[i]));
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+int rh_create(rh_ctx **out, int cuda_device, void *cuda_stream)
+{
+    if (!out) return RH_EINVAL;
+    *out = nullptr;
+    rh_ctx *c = new (std::nothrow) rh_ctx();
+    if (!c) return RH_ENOMEM;
+    c->dev = cuda_device;
+    cudaError_t e = cudaSetDevice(cuda_device);
+    if (e == cudaSuccess && cuda_stream) {
+        c->st = (cudaStream_t)cuda_stream;
+    } else if (e == cudaSuccess) {
+        e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+        c->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, cuda_device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->badidx, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        *out = c;
+        c->err = std::string("rh_create: ") + cudaGetErrorString(e);
+        return RH_ECUDA;
+    }
+    // Dawson's integral table for the FP32 Voigt function
+    std::vector<float> daw(RH_DAW_N);
+    for (int i = 0; i < RH_DAW_N; ++i) daw[i] = (float)dawson_series(i * RH_DAW_H);
+    e = cudaMalloc(&c->daw_d, RH_DAW_N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(c->daw_d, daw.data(), RH_DAW_N * sizeof(float), cudaMemcpyHostToDevice);
+    *out = c;
+    if (e != cudaSuccess) {
+        c->err = std::string("rh_create: ") + cudaGetErrorString(e);
+        return RH_ECUDA;
+    }
+    return RH_OK;
+}
+
+void rh_destroy(rh_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    if (c->st) cudaStreamSynchronize(c->st);
+    free_columns(c);
+    dfree(c->lane_d);
+    dfree(c->daw_d);
+    dfree(c->nghist);
+    dfree(c->queue);
+    dfree(c->badidx);
+    dfree(c->colidx);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+const char *rh_last_error(const rh_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int rh_setup_atom(rh_ctx *c, const rh_atom_desc *d)
+{
+    if (!c) return RH_EINVAL;
+    if (c->ncol) return fail(c, RH_ESTATE, "rh_setup_atom: columns are loaded; set the atom first");
+    cudaSetDevice(c->dev);
+    c->have_atom = false;
+    int r = build_atom(c, d);
+    if (r) return r;
+    dfree(c->lane_d);
+    c->lane_prec = -1;
+    c->have_atom = true;
+    return RH_OK;
+}
+
+int64_t rh_nlambda(const rh_ctx *c) { return (c && c->have_atom) ? (int64_t)c->ha.nu.size() : 0; }
+
+int rh_get_grid(const rh_ctx *c, double *nu_out)
+{
+    if (!c || !c->have_atom || !nu_out) return RH_EINVAL;
+    memcpy(nu_out, c->ha.nu.data(), c->ha.nu.size() * sizeof(double));
+    return RH_OK;
+}
+
+int rh_load_columns(rh_ctx *c, int64_t ncol, int32_t ndep, const double *z_m, const double *T_K,
+                    const double *ne_m3, const double *nH_m3, const double *vz_ms, int32_t on_device)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->have_atom) return fail(c, RH_ESTATE, "rh_load_columns: no atom");
+    if (ncol < 1 || ndep < 2 || ndep > 4096) return fail(c, RH_EINVAL, "need ncol >= 1 and 2 <= ndep <= 4096");
+    if (!z_m || !T_K || !nH_m3 || !vz_ms) return fail(c, RH_EINVAL, "z, T, nH, vz must not be NULL");
+    cudaSetDevice(c->dev);
+    free_columns(c);
+    const int L = c->da.nlev;
+    const size_t nd = (size_t)ncol * ndep;
+    ColumnArrays &a = c->ca;
+    a.ncol = ncol;
+    a.ndep = ndep;
+    CK(cudaMalloc(&a.z, nd * 8));
+    CK(cudaMalloc(&a.T, nd * 8));
+    CK(cudaMalloc(&a.nH, nd * 8));
+    CK(cudaMalloc(&a.vz, nd * 8));
+    CK(cudaMalloc(&a.ne, nd * 8));
+    CK(cudaMalloc(&a.np, nd * 8));
+    CK(cudaMalloc(&a.nstar, nd * L * 8));
+    CK(cudaMalloc(&a.pops, nd * L * 8));
+    CK(cudaMalloc(&a.Crate, nd * 2 * c->da.ntr * 8));
+    CK(cudaMalloc(&a.dmax, ncol * 8));
+    CK(cudaMalloc(&a.iters, ncol * 4));
+    CK(cudaMalloc(&a.status, ncol));
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(a.z, z_m, nd * 8, kind, c->st));
+    CK(cudaMemcpyAsync(a.T, T_K, nd * 8, kind, c->st));
+    CK(cudaMemcpyAsync(a.nH, nH_m3, nd * 8, kind, c->st));
+    CK(cudaMemcpyAsync(a.vz, vz_ms, nd * 8, kind, c->st));
+    if (ne_m3) CK(cudaMemcpyAsync(a.ne, ne_m3, nd * 8, kind, c->st));
+    CK(cudaMemsetAsync(a.iters, 0, ncol * 4, c->st));
+    CK(cudaMemsetAsync(a.status, RH_COL_NOTRUN, ncol, c->st));
+    CK(cudaMemsetAsync(a.dmax, 0, ncol * 8, c->st));
+    unsigned long long bad0 = ~0ull;
+    CK(cudaMemcpyAsync(c->badidx, &bad0, 8, cudaMemcpyHostToDevice, c->st));
+    validate_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, c->st>>>(ncol, ndep, a.z, a.T, ne_m3 ? a.ne : nullptr,
+                                                                   a.nH, a.vz, (unsigned long long *)c->badidx);
+    CK(cudaGetLastError());
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, c->badidx, 8, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (bad != ~0ull) {
+        long long col = (long long)(bad / ndep), k = (long long)(bad % ndep);
+        free_columns(c);
+        return fail(c, RH_EINVAL,
+                    "invalid input at column %lld depth %lld (need finite T, n_H, n_e > 0, finite v_z, z decreasing)",
+                    col, k);
+    }
+    c->ncol = ncol;
+    c->ndep = ndep;
+    CK(launch_lte_setup(c->da, a, ne_m3 ? 1 : 0, c->st));
+    // reference density for the FP32 population scaling: max n_H / 1e3
+    unsigned long long mx = 0;
+    CK(cudaMemcpyAsync(c->badidx, &mx, 8, cudaMemcpyHostToDevice, c->st));
+    max_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, c->st>>>((int64_t)nd, a.nH, (unsigned long long *)c->badidx);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&mx, c->badidx, 8, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double mxd;
+    memcpy(&mxd, &mx, 8);
+    c->nref = mxd > 0 ? mxd / 1e3 : 1.0;
+    return RH_OK;
+}
+
+int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "rh_iterate: no columns loaded");
+    if (!o) return fail(c, RH_EINVAL, "opts is NULL");
+    if (o->maxiter < 1 || !(o->tol >= 0) || (o->ng_order != 0 && o->ng_order != 2) ||
+        (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) || (o->precision != 0 && o->precision != 1) ||
+        (o->start != 0 && o->start != 2) || o->block_warps < 0 || o->block_warps > 8 ||
+        (o->only_unconverged != 0 && o->only_unconverged != 1))
+        return fail(c, RH_EINVAL, "rh_iterate: invalid options");
+    cudaSetDevice(c->dev);
+    // work list: every column, or the columns not converged so far
+    int64_t nwork = c->ncol;
+    const int *colidx_d = nullptr;
+    if (o->only_unconverged) {
+        std::vector<uint8_t> st0(c->ncol);
+        CK(cudaMemcpy(st0.data(), c->ca.status, c->ncol, cudaMemcpyDeviceToHost));
+        std::vector<int> idx;
+        for (int64_t i = 0; i < c->ncol; ++i)
+            if (st0[i] != RH_COL_CONVERGED) idx.push_back((int)i);
+        nwork = (int64_t)idx.size();
+        if (nwork > c->colidx_cap) {
+            dfree(c->colidx);
+            CK(cudaMalloc(&c->colidx, nwork * sizeof(int)));
+            c->colidx_cap = nwork;
+        }
+        if (nwork) CK(cudaMemcpy(c->colidx, idx.data(), nwork * sizeof(int), cudaMemcpyHostToDevice));
+        colidx_d = c->colidx;
+    }
+    int r = ensure_lane(c, o->precision);
+    if (r) return r;
+    size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
+    size_t want = per_block * (size_t)c->nsm * 4;
+    if (c->nghist_cap < want) {
+        dfree(c->nghist);
+        CK(cudaMalloc(&c->nghist, want));
+        c->nghist_cap = want;
+    }
+    IterLaunch il;
+    il.precision = o->precision;
+    il.persistent = o->persistent;
+    il.block_warps = o->block_warps;
+    il.maxiter = o->maxiter;
+    il.ng_order = o->ng_order;
+    il.ng_delay = o->ng_delay;
+    il.ng_period = o->ng_period;
+    il.start = o->start;
+    il.tol = o->tol;
+    il.crsw = o->crsw_init;
+    il.nsm = c->nsm;
+    il.colidx = colidx_d;
+    il.nwork = nwork;
+    float ms = 0;
+    int grid = 0;
+    char ebuf[256] = {0};
+    if (nwork > 0) {
+        cudaError_t e = launch_mali(c->da, c->ca, c->lane_d, c->ha.npad, c->daw_d, c->nref, c->nghist,
+                                    c->nghist_cap, c->queue, il, c->st, &ms, &grid, ebuf, sizeof ebuf);
+        if (e != cudaSuccess)
+            return fail(c, RH_ECUDA, "rh_iterate: %s%s%s", cudaGetErrorString(e), ebuf[0] ? ": " : "", ebuf);
+    }
+    std::vector<int32_t> it(c->ncol);
+    std::vector<uint8_t> s(c->ncol);
+    std::vector<double> dm(c->ncol);
+    CK(cudaMemcpy(it.data(), c->ca.iters, c->ncol * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s.data(), c->ca.status, c->ncol, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(dm.data(), c->ca.dmax, c->ncol * 8, cudaMemcpyDeviceToHost));
+    rh_iter_stats S{};
+    S.seconds = ms * 1e-3;
+    S.n_processed = nwork;
+    std::vector<char> done(c->ncol, o->only_unconverged ? 0 : 1);
+    if (o->only_unconverged) {
+        std::vector<int> idx(nwork);
+        if (nwork) CK(cudaMemcpy(idx.data(), c->colidx, nwork * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int i : idx) done[i] = 1;
+    }
+    for (int64_t i = 0; i < c->ncol; ++i) {
+        if (s[i] == RH_COL_CONVERGED) S.n_converged++;
+        else if (s[i] == RH_COL_MAXITER) S.n_maxiter++;
+        else S.n_failed++;
+        if (done[i]) S.iterations_total += it[i];
+        if (i == 0 || dm[i] > S.max_dn_final) S.max_dn_final = dm[i];
+    }
+    S.pts = (double)S.iterations_total * c->ndep * (double)c->ha.nu.size() * c->ha.nmu;
+    if (st) *st = S;
+    return (S.n_maxiter || S.n_failed) ? RH_ENOTCONV : RH_OK;
+}
+
+int rh_get_populations(rh_ctx *c, double *n_out, int32_t *iters, uint8_t *status, double *dmax, int32_t on_device)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "no columns loaded");
+    cudaSetDevice(c->dev);
+    CK(cudaStreamSynchronize(c->st));
+    size_t nv = (size_t)c->ncol * c->ndep * c->da.nlev;
+    if (n_out) CK(cudaMemcpy(n_out, c->ca.pops, nv * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    if (iters) CK(cudaMemcpy(iters, c->ca.iters, c->ncol * 4, cudaMemcpyDeviceToHost));
+    if (status) CK(cudaMemcpy(status, c->ca.status, c->ncol, cudaMemcpyDeviceToHost));
+    if (dmax) CK(cudaMemcpy(dmax, c->ca.dmax, c->ncol * 8, cudaMemcpyDeviceToHost));
+    return RH_OK;
+}
+
+int rh_get_lte(rh_ctx *c, double *nstar_out, double *ne_out)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "no columns loaded");
+    cudaSetDevice(c->dev);
+    CK(cudaStreamSynchronize(c->st));
+    size_t nd = (size_t)c->ncol * c->ndep;
+    if (nstar_out) CK(cudaMemcpy(nstar_out, c->ca.nstar, nd * c->da.nlev * 8, cudaMemcpyDeviceToHost));
+    if (ne_out) CK(cudaMemcpy(ne_out, c->ca.ne, nd * 8, cudaMemcpyDeviceToHost));
+    return RH_OK;
+}
+
+int rh_set_populations(rh_ctx *c, const double *n_in)
+{
+    if (!c || !n_in) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "no columns loaded");
+    size_t nv = (size_t)c->ncol * c->ndep * c->da.nlev;
+    for (size_t i = 0; i < nv; ++i)
+        if (!(std::isfinite(n_in[i]) && n_in[i] > 0))
+            return fail(c, RH_EINVAL, "populations must be finite and > 0 (first bad flat index %zu)", i);
+    cudaSetDevice(c->dev);
+    CK(cudaMemcpy(c->ca.pops, n_in, nv * 8, cudaMemcpyHostToDevice));
+    return RH_OK;
+}
+
+int rh_emergent_spectrum(rh_ctx *c, double mu, int64_t nlambda, const double *lambda_m, double *I_out,
+                         int32_t precision, int32_t on_device)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "no columns loaded");
+    if (!(mu > 0 && mu <= 1)) return fail(c, RH_EINVAL, "mu must be in (0, 1]");
+    if (nlambda < 1 || !lambda_m || !I_out) return fail(c, RH_EINVAL, "need nlambda >= 1 and buffers");
+    if (precision != 0 && precision != 1) return fail(c, RH_EINVAL, "precision must be 0 or 1");
+    cudaSetDevice(c->dev);
+    const HostAtom &a = c->ha;
+    std::vector<double> nu(nlambda), spec((size_t)nlambda * RH_SPEC_ACT * RH_SPEC_F, 0.0);
+    std::vector<int> nact(nlambda, 0), act((size_t)nlambda * RH_SPEC_ACT, 0);
+    for (int64_t j = 0; j < nlambda; ++j) {
+        if (!(lambda_m[j] > 0) || !std::isfinite(lambda_m[j]))
+            return fail(c, RH_EINVAL, "wavelength %lld is not positive", (long long)j);
+        double f = kC / lambda_m[j];
+        nu[j] = f;
+        for (int t = 0; t < a.ntr; ++t) {
+            const HostTrans &h = a.tr[t];
+            if (!(f >= h.nu_lo * (1 - 1e-13) && f <= h.nu_hi * (1 + 1e-13))) continue;
+            if (nact[j] >= RH_SPEC_ACT) return fail(c, RH_EINVAL, "more than %d transitions at one wavelength", RH_SPEC_ACT);
+            int s = nact[j]++;
+            act[j * RH_SPEC_ACT + s] = t;
+            double *p = &spec[((size_t)j * RH_SPEC_ACT + s) * RH_SPEC_F];
+            if (h.kind == 0) {
+                double h4 = kH * f / (4.0 * kPi);
+                p[0] = h4 * h.Blu;
+                p[1] = h4 * h.A;
+                p[2] = a.g[h.l] / a.g[h.u];
+                p[3] = kC * ((f - h.nu0) / h.nu0);
+                p[4] = kC / (kSqrtPi * h.nu0);
+            } else {
+                double r = h.nu0 / f;
+                double alpha = h.alpha0 * r * r * r;
+                p[0] = alpha;
+                p[1] = 2.0 * kH * f * f * f / (kC * kC) * alpha;
+            }
+        }
+    }
+    double *nu_d = nullptr, *spec_d = nullptr, *out_d = nullptr;
+    int *nact_d = nullptr, *act_d = nullptr;
+    int rc = RH_OK;
+    auto cleanup = [&]() {
+        dfree(nu_d);
+        dfree(spec_d);
+        dfree(nact_d);
+        dfree(act_d);
+        if (!on_device) dfree(out_d);
+    };
+    cudaError_t e = cudaMalloc(&nu_d, nlambda * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&spec_d, spec.size() * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&nact_d, nlambda * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&act_d, act.size() * 4);
+    if (e == cudaSuccess) {
+        if (on_device) out_d = I_out;
+        else e = cudaMalloc(&out_d, (size_t)c->ncol * nlambda * 8);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nu_d, nu.data(), nlambda * 8, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(spec_d, spec.data(), spec.size() * 8, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nact_d, nact.data(), nlambda * 4, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(act_d, act.data(), act.size() * 4, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = launch_spectrum(c->da, c->ca, mu, nlambda, nu_d, nact_d, act_d, spec_d, out_d, precision, c->st);
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(I_out, out_d, (size_t)c->ncol * nlambda * 8, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) rc = fail(c, RH_ECUDA, "rh_emergent_spectrum: %s", cudaGetErrorString(e));
+    cleanup();
+    return rc;
+}
+
+}  // extern "C"

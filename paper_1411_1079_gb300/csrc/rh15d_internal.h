@@ -1,0 +1,320 @@
+// rh15d_internal.h -- tables and device math shared by the translation units
+// of librh15d_gpu.so (not part of the public ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rh15d.h"
+
+#define RH_MAXLEV 8
+#define RH_MAXTR 32
+#define RH_KMAX 3          // transitions active in one 32-wavelength tile (union)
+#define RH_MAXTILE 96      // 32-wavelength tiles of the grid
+#define RH_MAXMU 16
+#define RH_MAXMAP 2048
+#define RH_NLANEF 7        // per-slot lane fields
+#define RH_DAW_N 321       // Dawson table on [0, 5] with spacing 1/64
+#define RH_DAW_H (1.0 / 64.0)
+
+namespace rh {
+
+// SI constants (CODATA 2018; h, c, k, e exact)
+constexpr double kH = 6.62607015e-34;
+constexpr double kC = 2.99792458e8;
+constexpr double kK = 1.380649e-23;
+constexpr double kQ = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kSigmaT = 6.6524587321e-29;
+constexpr double kERyd = 13.605693122994 * 1.602176634e-19;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kSqrtPi = 1.77245385090551602730;
+
+struct DevTrans {
+    int l, u, kind, sub;          // kind 0 line (sub = line index), 1 continuum (sub = continuum index)
+    double nu0, A, Blu, Bul, alpha0, ln_atop, ln_abot, f;
+};
+
+struct DevTile {
+    int K;                        // transitions in the union of the tile
+    int t[RH_KMAX];
+    int acc_off;                  // first accumulator of the tile (per depth)
+    int m;                        // accumulators of the tile = K (K + 1)
+};
+
+// Everything the column kernel needs about the atom, passed by value as a
+// __grid_constant__ kernel parameter (read through the constant bank).
+struct DevAtom {
+    int nlev, ntr, nline, ncont, ntile, nmu, macc, nmap;
+    double mass, metal_floor;
+    double lev_chi[RH_MAXLEV];    // E_continuum - E_i, J (bound levels)
+    double lev_g2[RH_MAXLEV];     // g_i / (2 g_continuum)
+    double mu[RH_MAXMU], wmu[RH_MAXMU];
+    float muf[RH_MAXMU], wm2f[RH_MAXMU];   // mu and w_mu / 2 for the FP32 sweep
+    DevTrans tr[RH_MAXTR];
+    DevTile tile[RH_MAXTILE];
+    // accumulator -> rate-matrix entry map: A[row][col] += sign * acc
+    int16_t map_acc[RH_MAXMAP];
+    int8_t map_row[RH_MAXMAP], map_col[RH_MAXMAP], map_sign[RH_MAXMAP];
+};
+
+// Lane-table fields (structure of arrays, [field][npad]); per-slot fields are
+// [RH_NLANEF * s + f].  Population-proportional quantities are scaled so that
+// they stay inside the FP32 range: populations enter the sweep divided by
+// n_ref, hence V and U carry a factor n_ref.
+//   f = 0 c   : up-rate coefficient  (lines w B_lu; continua 4 pi w alpha / (h nu))
+//   f = 1 Vc  : n_ref * V_lu without profile (lines h nu/4pi B_lu; continua alpha)
+//   f = 2 Uc  : n_ref * U without profile / depth factor (lines h nu/4pi A;
+//               continua 2 h nu^3/c^2 alpha)
+//   f = 3 E   : A/B_ul-type constant (lines 2 h nu0^3/c^2; continua 2 h nu^3/c^2)
+//   f = 4 q   : Doppler offset c (nu/nu0 - 1) [m/s] (lines)
+//   f = 5 pn  : profile normalisation c / (sqrt(pi) nu0) (lines)
+//   f = 6 grat: g_l/g_u (lines) -- the continua use G(k) exp(-h nu/kT)
+// then four per-lane fields: nu, sigma(H-), (1e15/nu)^3, 2 h nu^3/c^2.
+constexpr int kLaneSlotFields = RH_NLANEF;
+constexpr int kLaneNu = RH_NLANEF * RH_KMAX;
+constexpr int kLaneHm = kLaneNu + 1;
+constexpr int kLaneNu3 = kLaneNu + 2;
+constexpr int kLaneTw = kLaneNu + 3;
+constexpr int kLaneFields = kLaneNu + 4;
+constexpr double kNuRef3 = 1e45;   // (1e15 Hz)^3: free-free coefficient scale
+
+// ----------------------------------------------------------------------------
+// Voigt function H(a, v), FP64 (FP64 path and table set-up).
+// |v| < 6: Taylor expansion of w(v + i a) in the damping a about the real
+// axis, w(v) = exp(-v^2) + (2i/sqrt(pi)) F(v) with Dawson's integral F from
+// its positive power series F(v) = exp(-v^2) sum v^{2n+1} / (n! (2n+1)), and
+// the derivatives from w' = -2 z w + 2i/sqrt(pi), w^{(n+1)} = -2 z w^{(n)} -
+// 2 n w^{(n-1)} (order 9; a <= 0.05).  |v| >= 6: w(z) ~ exp(-z^2) +
+// (i / (sqrt(pi) z)) sum_k (2k-1)!! / (2 z^2)^k, 36 terms.  ~1e-13 relative.
+__host__ __device__ inline double dawson_series(double x)
+{
+    double s = 0.0, term = x, x2 = x * x;
+    for (int n = 0; n < 400; ++n) {
+        double t = term / (2 * n + 1);
+        s += t;
+        if (t <= 1e-17 * s) break;
+        term *= x2 / (n + 1);
+    }
+    return exp(-x2) * s;
+}
+
+__host__ __device__ inline double voigt_f64(double a, double v)
+{
+    double av = fabs(v);
+    if (av < 6.0) {
+        // w and derivatives at the real point v (complex as re/im pairs)
+        double e = exp(-av * av);
+        double F = dawson_series(av);
+        double wr[10], wi[10];
+        wr[0] = e;
+        wi[0] = 2.0 / kSqrtPi * F;
+        wr[1] = -2.0 * av * wr[0];
+        wi[1] = -2.0 * av * wi[0] + 2.0 / kSqrtPi;
+        for (int n = 1; n < 9; ++n) {
+            wr[n + 1] = -2.0 * (av * wr[n] + n * wr[n - 1]);
+            wi[n + 1] = -2.0 * (av * wi[n] + n * wi[n - 1]);
+        }
+        // sum_n (i a)^n / n! w^{(n)}: real part
+        double h = 0.0, pw = 1.0;
+        for (int n = 0; n <= 9; ++n) {
+            switch (n & 3) {
+            case 0: h += pw * wr[n]; break;
+            case 1: h -= pw * wi[n]; break;
+            case 2: h -= pw * wr[n]; break;
+            default: h += pw * wi[n]; break;
+            }
+            pw *= a / (n + 1);
+        }
+        return h;
+    }
+    // asymptotic: z = av + i a; w = exp(-z^2) + (i/(sqrt(pi) z)) S,
+    // S = sum t_k, t_{k+1} = t_k (2k+1)/(2 z^2)
+    double zr = av, zi = a;
+    double z2r = 2.0 * (zr * zr - zi * zi), z2i = 2.0 * (2.0 * zr * zi);
+    double d = z2r * z2r + z2i * z2i;
+    double ir = z2r / d, ii = -z2i / d;   // 1/(2 z^2)
+    double sr = 0.0, si = 0.0, tr = 1.0, ti = 0.0;
+    for (int k = 0; k <= 36; ++k) {
+        sr += tr;
+        si += ti;
+        double nr = (tr * ir - ti * ii) * (2 * k + 1), ni = (tr * ii + ti * ir) * (2 * k + 1);
+        tr = nr;
+        ti = ni;
+    }
+    // Re[i S conj(z)] / (sqrt(pi)|z|^2) with i S = (-si) + i sr
+    double mz = zr * zr + zi * zi;
+    return (-si * zr + sr * zi) / (kSqrtPi * mz) + exp(zi * zi - zr * zr) * cos(2.0 * zr * zi);
+}
+
+// Voigt function, FP32 (mixed-precision formal solution).  |v| < 5:
+// H = e^{-v^2}(1 + a^2 (1 - 2 v^2)) - a (2/sqrt pi)(1 - 2 v F) +
+//     a^3 (4/(3 sqrt pi)) (v^2 - 1 + v F (3 - 2 v^2)), the expansion in a to
+// third order, with F from a cubic-Hermite table of Dawson's integral
+// (F' = 1 - 2 v F).  |v| >= 5: e^{-v^2}(1 + a^2(1-2v^2)) +
+// (a / (sqrt pi v^2)) sum_k (2k+1)!! (2 v^2)^{-k} (12 terms).
+__device__ __forceinline__ float voigt_f32(float a, float v, const float *__restrict__ daw)
+{
+    float av = fabsf(v);
+    float v2 = av * av;
+    float g = __expf(-v2) * (1.0f + a * a * (1.0f - 2.0f * v2));
+    if (av < 5.0f) {
+        float x = av * 64.0f;
+        int i = min((int)x, RH_DAW_N - 2);
+        float t = x - (float)i;
+        float v0 = i * (1.0f / 64.0f), v1 = v0 + (1.0f / 64.0f);
+        float F0 = daw[i], F1 = daw[i + 1];
+        float d0 = (1.0f / 64.0f) * (1.0f - 2.0f * v0 * F0);
+        float d1 = (1.0f / 64.0f) * (1.0f - 2.0f * v1 * F1);
+        float t2 = t * t, t3 = t2 * t;
+        float F = (2.0f * t3 - 3.0f * t2 + 1.0f) * F0 + (t3 - 2.0f * t2 + t) * d0 +
+                  (-2.0f * t3 + 3.0f * t2) * F1 + (t3 - t2) * d1;
+        float vF = av * F;
+        return g - a * 1.1283791670955126f * (1.0f - 2.0f * vF) +
+               a * a * a * 0.75225277806367511f * (v2 - 1.0f + vF * (3.0f - 2.0f * v2));
+    }
+    float u = 0.5f / v2;
+    // sum_k (2k+1)!! u^k, Horner over k = 0..11
+    float s = 1.0f;
+#pragma unroll
+    for (int k = 11; k >= 1; --k) s = 1.0f + (2 * k + 1) * u * s;
+    return g + a * 0.56418958354775628f / v2 * s;
+}
+
+// ----------------------------------------------------------------------------
+// Linear short characteristics weights: e0 = 1 - exp(-d), e1 = d - e0,
+// w_o = e1/d, w_u = e0 - w_o; also 1 - w_o = e0/d, formed without
+// cancellation (it carries the preconditioned rates in optically thick
+// layers, where w_o -> 1).
+__device__ __forceinline__ void sc_weights(double d, double &one_m_e0, double &wu, double &wo, double &omwo)
+{
+    double e0 = -expm1(-d);
+    if (d < 0.1) {
+        // w_o = sum_{n>=2} (-1)^n d^{n-1}/n!  (13 terms: truncation < 1e-20 relative)
+        double t = d * 0.5, s = 0.0;
+#pragma unroll
+        for (int n = 3; n <= 15; ++n) {
+            s += t;
+            t *= -d / n;
+        }
+        wo = s;
+        wu = e0 - wo;          // ~ d/2: no cancellation
+        omwo = 1.0 - wo;
+        one_m_e0 = 1.0 - e0;
+    } else {
+        // 1 - w_o = e0/d and w_u = e0/d - e^{-d}: w_u ~ 1/d at large d is formed
+        // without subtracting two numbers close to one
+        double ex = exp(-d);
+        omwo = e0 / d;
+        wo = 1.0 - omwo;
+        wu = omwo - ex;
+        one_m_e0 = ex;
+    }
+}
+
+__device__ __forceinline__ void sc_weights(float d, float &one_m_e0, float &wu, float &wo, float &omwo)
+{
+    if (d < 0.5f) {
+        // w_o = sum_{n>=2} (-1)^n d^{n-1}/n!,  e0 = sum_{n>=1} (-1)^{n+1} d^n/n!  (Horner, 9 terms)
+        float wo_ = 0.5f + d * (-1.0f / 6 + d * (1.0f / 24 + d * (-1.0f / 120 + d * (1.0f / 720 +
+                    d * (-1.0f / 5040 + d * (1.0f / 40320 + d * (-1.0f / 362880)))))));
+        wo_ *= d;
+        float e0 = d * (1.0f + d * (-0.5f + d * (1.0f / 6 + d * (-1.0f / 24 + d * (1.0f / 120 +
+                   d * (-1.0f / 720 + d * (1.0f / 5040 + d * (-1.0f / 40320))))))));
+        wo = wo_;
+        wu = e0 - wo_;
+        omwo = 1.0f - wo_;
+        one_m_e0 = 1.0f - e0;
+    } else {
+        float ex = __expf(-d);
+        float inv = __frcp_rn(d);
+        omwo = (1.0f - ex) * inv;
+        wo = 1.0f - omwo;
+        wu = omwo - ex;
+        one_m_e0 = ex;
+    }
+}
+
+// spectrum sweeps need no 1 - w_o
+template <typename R>
+__device__ __forceinline__ void sc_weights(R d, R &one_m_e0, R &wu, R &wo)
+{
+    R omwo;
+    sc_weights(d, one_m_e0, wu, wo, omwo);
+}
+
+// e^y E1(y), y > 0: series (y <= 1) or the continued fraction
+// E1(y) = e^{-y} / (y + 1 - 1^2/(y + 3 - 2^2/(y + 5 - ...))) evaluated with
+// the modified Lentz algorithm.
+__host__ __device__ inline double exp_e1(double y)
+{
+    if (y <= 1.0) {
+        const double gam = 0.57721566490153286061;
+        double s = 0.0, t = 1.0;
+        for (int n = 1; n < 100; ++n) {
+            t *= -y / n;
+            double a = t / n;
+            s += a;
+            if (fabs(a) < 1e-18 * fabs(s) + 1e-300) break;
+        }
+        return exp(y) * (-gam - log(y) - s);
+    }
+    const double tiny = 1e-300;
+    double f = y + 1.0, C = f, D = 0.0;
+    for (int n = 1; n < 500; ++n) {
+        double an = -(double)n * n, bn = y + 2.0 * n + 1.0;
+        D = bn + an * D;
+        if (fabs(D) < tiny) D = tiny;
+        C = bn + an / C;
+        if (fabs(C) < tiny) C = tiny;
+        D = 1.0 / D;
+        double delta = C * D;
+        f *= delta;
+        if (fabs(delta - 1.0) < 1e-16) break;
+    }
+    return 1.0 / f;
+}
+
+// H- bound-free cross section (John 1988 fit), m^2; lambda in m.
+__host__ __device__ inline double hminus_sigma(double lambda_m)
+{
+    const double l0 = 1.6419;
+    double lum = lambda_m * 1e6;
+    if (!(lum < l0)) return 0.0;
+    double x = 1.0 / lum - 1.0 / l0, sx = sqrt(x);
+    double f = 152.519 + sx * (49.534 + sx * (-118.858 + sx * (92.536 + sx * (-34.194 + sx * 4.982))));
+    return 1e-22 * lum * lum * lum * x * sx * f;
+}
+
+struct ColumnArrays {
+    int64_t ncol;
+    int ndep;
+    double *z, *T, *nH, *vz, *ne, *np, *nstar, *pops, *Crate, *dmax;
+    int32_t *iters;
+    uint8_t *status;
+};
+
+// launchers (defined in the kernel translation units)
+cudaError_t launch_lte_setup(const DevAtom &A, const ColumnArrays &c, int ne_given, cudaStream_t st);
+struct IterLaunch {
+    int precision, persistent, block_warps, maxiter, ng_order, ng_delay, ng_period, start;
+    double tol, crsw;
+    int nsm;
+    const int *colidx;     // columns to iterate (nullptr: all)
+    int64_t nwork;         // number of columns to iterate
+};
+cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
+                        const float *daw, double nref, double *nghist, size_t nghist_cap, int *queue,
+                        const IterLaunch &o, cudaStream_t st, float *ms_out, int *grid_out, char *err,
+                        size_t errn);
+size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep);
+// emergent spectrum: per requested wavelength j, up to RH_SPEC_ACT transitions
+// with constants spec[(j * RH_SPEC_ACT + s) * RH_SPEC_F + f]
+#define RH_SPEC_ACT 8
+#define RH_SPEC_F 8
+cudaError_t launch_spectrum(const DevAtom &A, const ColumnArrays &c, double mu, int64_t nlam,
+                            const double *nu_d, const int *nact_d, const int *act_d, const double *spec_d,
+                            double *out, int precision, cudaStream_t st);
+
+}  // namespace rh

@@ -1,0 +1,720 @@
+// rh15d_mali.cu -- column-resident MALI kernel (Sect. 2.1-2.3, 3.1).
+//
+// One thread block owns one column at a time and runs all of that column's
+// MALI iterations with the column's state in shared memory: populations
+// (FP64), collisional rates (FP64), per-depth atmosphere scalars, and the
+// rate accumulators.  Per iteration:
+//   1. every warp takes 32-wavelength tiles of the grid; each lane owns one
+//      wavelength and sweeps depth downward and then upward for all angles mu
+//      at once (linear short characteristics, intensity and local operator in
+//      registers); at every depth the lane forms its contributions to the
+//      preconditioned rate matrix (Rybicki & Hummer 1992), the warp reduces
+//      them with shuffles, and lane j adds accumulator j of the tile;
+//   2. one thread per depth assembles the rate matrix from the accumulators
+//      (FP64) plus collisions and solves the rate equations (FP64, scaled
+//      unknowns, partial pivoting);
+//   3. the block computes max |dn/n|, applies Ng order-2 acceleration
+//      (history in global scratch) and tests convergence (Sect. 2.3).
+// Columns come from a device work queue (pool mode, Sect. 3.1) or a static
+// split over resident blocks (normal mode).  R is the precision of the
+// formal solution and the rate terms (float or double); the rate matrix,
+// the solve and Ng are always FP64.
+#include <cstdio>
+#include <cstring>
+
+#include "rh15d_internal.h"
+
+#ifndef RH_FP32_MINBLOCKS
+#define RH_FP32_MINBLOCKS 2   // FP32 sweep: two resident 256-thread blocks per SM (<= 128 registers)
+#endif
+
+namespace rh {
+
+namespace {
+
+constexpr int kWarp = 32;
+
+struct KParams {
+    int64_t ncol;
+    int N, L;
+    const double *z, *T, *nH, *vz, *ne, *np, *nstar, *Crate;
+    double *pops, *dmax;
+    int32_t *iters;
+    uint8_t *status;
+    const void *lane;
+    int npad;
+    const float *daw;
+    double *nghist;
+    int *queue;
+    int persistent, maxiter, ng_order, ng_delay, ng_period, start;
+    double tol, crsw, inv_nref;
+    const int *colidx;         // work item -> column (nullptr: identity)
+    int64_t nwork;
+};
+
+template <typename R>
+struct Smem {
+    double *n, *nn, *Cr;       // [L*N], [L*N], [N][2*ntr]
+    R *slot;                   // [macc][N]
+    R *dz, *ivth, *vz, *hkT, *kff, *nhm, *thom;   // [N]
+    R *Gc;                     // [ncont][N]
+    R *ad;                     // [nline][N] damping
+    R *nr;                     // [L][N] populations in R
+    float *daw;                // [RH_DAW_N]
+    double *red;               // reduction scratch [64]
+    int *ibuf;                 // [8]
+};
+
+template <typename R>
+__host__ __device__ size_t smem_bytes(int L, int N, int ntr, int ncont, int nline, int macc)
+{
+    size_t b = 0;
+    b += sizeof(double) * (2 * L * N + (size_t)N * 2 * ntr);
+    b += sizeof(R) * ((size_t)macc * N + 7 * N + (size_t)ncont * N + (size_t)nline * N + (size_t)L * N);
+    b += sizeof(float) * RH_DAW_N;
+    b += sizeof(double) * 64 + sizeof(int) * 8 + 64;
+    return b;
+}
+
+template <typename R>
+__device__ Smem<R> carve(char *base, int L, int N, int ntr, int ncont, int nline, int macc)
+{
+    Smem<R> s;
+    double *d = reinterpret_cast<double *>(base);
+    s.n = d;
+    d += L * N;
+    s.nn = d;
+    d += L * N;
+    s.Cr = d;
+    d += N * 2 * ntr;
+    s.red = d;
+    d += 64;
+    R *r = reinterpret_cast<R *>(d);
+    s.slot = r;
+    r += macc * N;
+    s.dz = r; r += N;
+    s.ivth = r; r += N;
+    s.vz = r; r += N;
+    s.hkT = r; r += N;
+    s.kff = r; r += N;
+    s.nhm = r; r += N;
+    s.thom = r; r += N;
+    s.Gc = r; r += ncont * N;
+    s.ad = r; r += nline * N;
+    s.nr = r; r += L * N;
+    float *f = reinterpret_cast<float *>(r);
+    s.daw = f;
+    f += RH_DAW_N;
+    s.ibuf = reinterpret_cast<int *>(f);
+    return s;
+}
+
+template <typename R>
+__device__ __forceinline__ R voigt(R a, R v, const float *daw);
+template <>
+__device__ __forceinline__ float voigt<float>(float a, float v, const float *daw) { return voigt_f32(a, v, daw); }
+template <>
+__device__ __forceinline__ double voigt<double>(double a, double v, const float *) { return voigt_f64(a, v); }
+
+template <typename R> __device__ __forceinline__ R rexp(R x);
+template <> __device__ __forceinline__ float rexp<float>(float x) { return __expf(x); }
+template <> __device__ __forceinline__ double rexp<double>(double x) { return exp(x); }
+template <typename R> __device__ __forceinline__ R rexpm1(R x);
+template <> __device__ __forceinline__ float rexpm1<float>(float x) { return expm1f(x); }
+template <> __device__ __forceinline__ double rexpm1<double>(double x) { return expm1(x); }
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R> __device__ __forceinline__ R mu_of(const DevAtom &A, int m);
+template <> __device__ __forceinline__ float mu_of<float>(const DevAtom &A, int m) { return A.muf[m]; }
+template <> __device__ __forceinline__ double mu_of<double>(const DevAtom &A, int m) { return A.mu[m]; }
+template <typename R> __device__ __forceinline__ R wm2_of(const DevAtom &A, int m);
+template <> __device__ __forceinline__ float wm2_of<float>(const DevAtom &A, int m) { return A.wm2f[m]; }
+template <> __device__ __forceinline__ double wm2_of<double>(const DevAtom &A, int m) { return 0.5 * A.wmu[m]; }
+
+// Per-lane constants of one tile with K transitions in its union.
+template <typename R, int K>
+struct LaneC {
+    R c[K], Vc[K], Uc[K], E[K], q[K], pn[K], grat[K];
+    int isline[K], lo[K], up[K], sub[K];
+    R nu, nu3s, tw, hm;
+};
+
+// Depth-dependent, angle-independent quantities of one lane.
+template <typename R, int K>
+struct DepthC {
+    R chibg, etabg, B, etac;
+    R Rs[K], Xs[K], nu_[K], chc[K], Uct[K], ad[K];
+    R ivth, vz;
+};
+
+template <typename R, int K>
+__device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K> &lc, int k, int N, DepthC<R, K> &d)
+{
+    R x = lc.nu * s.hkT[k];
+    R ex = rexp<R>(-x);
+    R omex = -rexpm1<R>(-x);
+    d.chibg = (s.kff[k] * lc.nu3s + s.nhm[k] * lc.hm) * omex + s.thom[k];
+    d.B = lc.tw * ex / omex;
+    d.etabg = d.chibg * d.B;
+    d.etac = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        R nl = s.nr[lc.lo[j] * N + k];
+        d.nu_[j] = s.nr[lc.up[j] * N + k];
+        if (lc.isline[j]) {
+            d.Rs[j] = lc.grat[j];
+            d.chc[j] = 0;
+            d.Uct[j] = 0;
+            d.ad[j] = s.ad[lc.sub[j] * N + k];
+        } else {
+            d.Rs[j] = s.Gc[lc.sub[j] * N + k] * ex;
+            d.ad[j] = 0;
+        }
+        d.Xs[j] = nl - d.Rs[j] * d.nu_[j];
+        if (!lc.isline[j]) {
+            d.chc[j] = lc.Vc[j] * d.Xs[j];
+            d.Uct[j] = lc.Uc[j] * d.Rs[j];
+            d.etac += d.nu_[j] * d.Uct[j];
+        }
+    }
+    d.ivth = s.ivth[k];
+    d.vz = s.vz[k];
+}
+
+// Opacity and emissivity for one angle (direction cosine muz); per-slot
+// profile phi, opacity chj and emissivity per upper-level population U.
+template <typename R, int K>
+__device__ __forceinline__ void angle_vals(const Smem<R> &s, const LaneC<R, K> &lc, const DepthC<R, K> &d, R muz,
+                                           R &chi, R &eta, R *phi, R *chj, R *U)
+{
+    chi = d.chibg;
+    R ea = d.etac;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if (lc.isline[j]) {
+            R v = (lc.q[j] - muz * d.vz) * d.ivth;
+            R ph = voigt<R>(d.ad[j], v, s.daw) * lc.pn[j] * d.ivth;
+            phi[j] = ph;
+            chj[j] = lc.Vc[j] * ph * d.Xs[j];
+            U[j] = lc.Uc[j] * ph;
+            ea += d.nu_[j] * U[j];
+        } else {
+            phi[j] = 1;
+            chj[j] = d.chc[j];
+            U[j] = d.Uct[j];
+        }
+        chi += chj[j];
+    }
+    eta = d.etabg + ea;
+}
+
+// Sweep one tile (K transitions in its union) downward and upward, adding
+// its rate accumulators.  Per depth and angle the lane forms, without
+// subtracting nearly equal numbers:
+//   I_eff = I - Psi* eta_active = I_u e^{-dtau} + w_u S_u + w_o eta_bg/chi,
+//   1 - Psi* chi_j = (1 - w_o) + w_o (chi - chi_j)/chi,
+// and accumulates per slot P = sum w phi (1 - Psi* chi_j), Q = sum w phi
+// I_eff and Y_{j,j'} = sum w phi_j Psi* U_j'.  Accumulators per depth:
+//   up_j = c_j Q_j, down_j = c_j R_j (E_j P_j + Q_j), cross_{j,j'} = c_j X_j Y_{j,j'}.
+template <typename R, int NMU, int K>
+__device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane)
+{
+    const int N = p.N;
+    const DevTile &tl = A.tile[b];
+    const int nmu = A.nmu;
+    const R *lt = reinterpret_cast<const R *>(p.lane);
+    const int npad = p.npad;
+    const int pi = b * kWarp + lane;
+    LaneC<R, K> lc;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const DevTrans &tr = A.tr[tl.t[j]];
+        lc.c[j] = lt[(RH_NLANEF * j + 0) * npad + pi];
+        lc.Vc[j] = lt[(RH_NLANEF * j + 1) * npad + pi];
+        lc.Uc[j] = lt[(RH_NLANEF * j + 2) * npad + pi];
+        lc.E[j] = lt[(RH_NLANEF * j + 3) * npad + pi];
+        lc.q[j] = lt[(RH_NLANEF * j + 4) * npad + pi];
+        lc.pn[j] = lt[(RH_NLANEF * j + 5) * npad + pi];
+        lc.grat[j] = lt[(RH_NLANEF * j + 6) * npad + pi];
+        lc.isline[j] = tr.kind == 0;
+        lc.lo[j] = tr.l;
+        lc.up[j] = tr.u;
+        lc.sub[j] = tr.sub;
+    }
+    lc.nu = lt[kLaneNu * npad + pi];
+    lc.hm = lt[kLaneHm * npad + pi];
+    lc.nu3s = lt[kLaneNu3 * npad + pi];
+    lc.tw = lt[kLaneTw * npad + pi];
+    constexpr int M = K * (K + 1);
+    R *slot = s.slot + (size_t)tl.acc_off * N;
+
+    for (int dir = 0; dir < 2; ++dir) {
+        const R sgn = dir == 0 ? (R)-1 : (R)1;
+        R I[NMU], chip[NMU], Sp[NMU];
+        R B2 = 0;
+        if (dir == 1) {
+            // the diffusion condition at the bottom needs chi and B one point up
+            DepthC<R, K> d2;
+            depth_consts<R, K>(s, lc, N - 2, N, d2);
+            B2 = d2.B;
+#pragma unroll
+            for (int m = 0; m < NMU; ++m) {
+                if (m >= nmu) break;
+                R phi[K], chj[K], U[K], eta;
+                angle_vals<R, K>(s, lc, d2, sgn * mu_of<R>(A, m), chip[m], eta, phi, chj, U);
+            }
+        }
+        for (int step = 0; step < N; ++step) {
+            const int k = dir == 0 ? step : N - 1 - step;
+            DepthC<R, K> d;
+            depth_consts<R, K>(s, lc, k, N, d);
+            R P[K], Q[K], Y[K][K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                P[j] = Q[j] = 0;
+#pragma unroll
+                for (int j2 = 0; j2 < K; ++j2) Y[j][j2] = 0;
+            }
+            const R dzk = step == 0 ? (R)0 : (dir == 0 ? s.dz[k - 1] : s.dz[k]);
+#pragma unroll
+            for (int m = 0; m < NMU; ++m) {
+                if (m >= nmu) break;
+                const R mu = mu_of<R>(A, m);
+                const R wm2 = wm2_of<R>(A, m);
+                R chi, eta, phi[K], chj[K], U[K];
+                angle_vals<R, K>(s, lc, d, sgn * mu, chi, eta, phi, chj, U);
+                const R ichi = (R)1 / chi;
+                const R S = eta * ichi;
+                R psi, Ieff, wo, omwo;
+                if (step == 0) {
+                    if (dir == 0) {
+                        I[m] = 0;
+                    } else {
+                        R dtv = (R)0.5 * (chi + chip[m]) * s.dz[N - 2];
+                        I[m] = d.B + mu * (d.B - B2) / dtv;
+                    }
+                    psi = 0;
+                    wo = 0;
+                    omwo = 1;
+                    Ieff = I[m];
+                } else {
+                    R dtau = (R)0.5 * (chi + chip[m]) * dzk / mu;
+                    R ome, wu;
+                    sc_weights(dtau, ome, wu, wo, omwo);
+                    R base = I[m] * ome + wu * Sp[m];
+                    I[m] = base + wo * S;
+                    Ieff = base + wo * (d.etabg * ichi);
+                    psi = wo * ichi;
+                }
+                chip[m] = chi;
+                Sp[m] = S;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    R other = d.chibg;
+#pragma unroll
+                    for (int j2 = 0; j2 < K; ++j2)
+                        if (j2 != j) other += chj[j2];
+                    R f = omwo + wo * other * ichi;          // 1 - Psi* chi_j
+                    R wp = wm2 * phi[j];
+                    P[j] += wp * f;
+                    Q[j] += wp * Ieff;
+                    R wpp = wp * psi;
+#pragma unroll
+                    for (int j2 = 0; j2 < K; ++j2)
+                        if (j2 != j) Y[j][j2] += wpp * U[j2];
+                }
+            }
+            R val[M];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                val[j] = lc.c[j] * Q[j];
+                val[K + j] = lc.c[j] * d.Rs[j] * (lc.E[j] * P[j] + Q[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int j2 = 0; j2 < K; ++j2)
+                    if (j2 != j) val[2 * K + j * (K - 1) + (j2 < j ? j2 : j2 - 1)] = lc.c[j] * d.Xs[j] * Y[j][j2];
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                R t = warp_sum(val[a]);
+                if (lane == a) {
+                    if (dir == 0) slot[a * N + k] = t;
+                    else slot[a * N + k] += t;
+                }
+            }
+        }
+    }
+}
+
+template <typename R, int NMU>
+__device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane)
+{
+    switch (A.tile[b].K) {
+    case 1: sweep_tile_k<R, NMU, 1>(A, s, p, b, lane); break;
+    case 2: sweep_tile_k<R, NMU, 2>(A, s, p, b, lane); break;
+    default: sweep_tile_k<R, NMU, 3>(A, s, p, b, lane); break;
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ double block_max(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = -1.0e308;
+    for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
+    __syncthreads();
+    return t;
+}
+
+// Rate matrix of depth k from the accumulators and collisions; scaled LU
+// solve for the new populations.  Returns 0 on success.
+__device__ int solve_depth(const DevAtom &A, const double *slotd, const float *slotf, int N, int k,
+                           const double *Cr, double fcr, const double *n, const double *nH, double *nn)
+{
+    const int L = A.nlev;
+    double G[RH_MAXLEV * RH_MAXLEV];
+    for (int i = 0; i < L * L; ++i) G[i] = 0.0;
+    for (int e = 0; e < A.nmap; ++e) {
+        int a = A.map_acc[e];
+        double v = slotd ? slotd[a * N + k] : (double)slotf[a * N + k];
+        G[A.map_row[e] * L + A.map_col[e]] += A.map_sign[e] * v;
+    }
+    const double *Ck = Cr + (size_t)k * 2 * A.ntr;
+    for (int t = 0; t < A.ntr; ++t) {
+        int l = A.tr[t].l, u = A.tr[t].u;
+        G[u * L + l] += Ck[2 * t] * fcr;
+        G[l * L + u] += Ck[2 * t + 1] * fcr;
+    }
+    for (int q = 0; q < L; ++q) {
+        double s = 0.0;
+        for (int pp = 0; pp < L; ++pp)
+            if (pp != q) s += G[pp * L + q];
+        G[q * L + q] = -s;
+    }
+    double sc[RH_MAXLEV], b[RH_MAXLEV];
+    int r = 0;
+    for (int l = 0; l < L; ++l) {
+        sc[l] = n[l * N + k];
+        if (sc[l] > sc[r]) r = l;
+        b[l] = 0.0;
+    }
+    for (int q = 0; q < L; ++q) G[r * L + q] = 1.0;
+    b[r] = nH[k];
+    for (int pp = 0; pp < L; ++pp) {
+        double mx = 0.0;
+        for (int q = 0; q < L; ++q) {
+            G[pp * L + q] *= sc[q];
+            mx = fmax(mx, fabs(G[pp * L + q]));
+        }
+        if (!(mx > 0.0)) return 1;
+        double im = 1.0 / mx;
+        for (int q = 0; q < L; ++q) G[pp * L + q] *= im;
+        b[pp] *= im;
+    }
+    for (int c = 0; c < L; ++c) {
+        int piv = c;
+        for (int rr = c + 1; rr < L; ++rr)
+            if (fabs(G[rr * L + c]) > fabs(G[piv * L + c])) piv = rr;
+        if (G[piv * L + c] == 0.0) return 1;
+        if (piv != c) {
+            for (int q = 0; q < L; ++q) {
+                double t = G[c * L + q];
+                G[c * L + q] = G[piv * L + q];
+                G[piv * L + q] = t;
+            }
+            double t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+        }
+        for (int rr = c + 1; rr < L; ++rr) {
+            double f = G[rr * L + c] / G[c * L + c];
+            for (int q = c; q < L; ++q) G[rr * L + q] -= f * G[c * L + q];
+            b[rr] -= f * b[c];
+        }
+    }
+    for (int c = L - 1; c >= 0; --c) {
+        double s = b[c];
+        for (int q = c + 1; q < L; ++q) s -= G[c * L + q] * b[q];
+        b[c] = s / G[c * L + c];
+    }
+    for (int l = 0; l < L; ++l) nn[l * N + k] = b[l] * sc[l];
+    return 0;
+}
+
+template <typename R, int NMU>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) mali_kernel(const __grid_constant__ DevAtom A, const KParams p)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    const int N = p.N, L = A.nlev;
+    Smem<R> s = carve<R>(smem_raw, L, N, A.ntr, A.ncont, A.nline, A.macc);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int LN = L * N;
+    double *hist = p.nghist + (size_t)blockIdx.x * 4 * LN;
+
+    for (int i = tid; i < RH_DAW_N; i += blockDim.x) s.daw[i] = p.daw[i];
+    int64_t done = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            int64_t q;
+            if (p.persistent) q = atomicAdd(p.queue, 1);
+            else q = (int64_t)blockIdx.x + done * gridDim.x;
+            s.ibuf[0] = q < p.nwork ? (p.colidx ? p.colidx[q] : (int)q) : -1;
+        }
+        __syncthreads();
+        const int col = s.ibuf[0];
+        if (col < 0) break;
+        ++done;
+        const size_t cN = (size_t)col * N;
+        // ---- load the column
+        for (int k = tid; k < N; k += blockDim.x) {
+            double T = p.T[cN + k];
+            double ne = p.ne[cN + k];
+            s.dz[k] = (R)(k < N - 1 ? fabs(p.z[cN + k] - p.z[cN + k + 1]) : 0.0);
+            double vth = sqrt(2.0 * kK * T / A.mass);
+            s.ivth[k] = (R)(1.0 / vth);
+            s.vz[k] = (R)p.vz[cN + k];
+            s.hkT[k] = (R)(kH / (kK * T));
+            double e2 = kQ * kQ / (4.0 * kPi * kEps0);
+            double Cff = e2 * e2 * e2 * 4.0 / (3.0 * kMe * kH * kC) * sqrt(2.0 * kPi / (3.0 * kK * kMe));
+            s.kff[k] = (R)(Cff * ne * p.np[cN + k] / sqrt(T) / kNuRef3);
+            double n1 = p.nstar[((size_t)col * L + 0) * N + k];
+            double lam3 = pow(kH * kH / (2.0 * kPi * kMe * kK * T), 1.5);
+            s.nhm[k] = (R)(0.25 * n1 * ne * lam3 * exp(0.754 * kQ / (kK * T)));
+            s.thom[k] = (R)(kSigmaT * ne);
+            double sk = N > 1 ? (double)k / (N - 1) : 0.0;
+            for (int t = 0; t < A.ntr; ++t) {
+                const DevTrans &tr = A.tr[t];
+                if (tr.kind == 0) {
+                    s.ad[tr.sub * N + k] = (R)exp((1.0 - sk) * tr.ln_atop + sk * tr.ln_abot);
+                } else {
+                    s.Gc[tr.sub * N + k] = (R)(p.nstar[((size_t)col * L + tr.l) * N + k] /
+                                               p.nstar[((size_t)col * L + tr.u) * N + k]);
+                }
+            }
+        }
+        for (int i = tid; i < N * 2 * A.ntr; i += blockDim.x) s.Cr[i] = p.Crate[(size_t)col * N * 2 * A.ntr + i];
+        for (int i = tid; i < LN; i += blockDim.x) {
+            double v = p.start == 0 ? p.nstar[(size_t)col * LN + i] : p.pops[(size_t)col * LN + i];
+            s.n[i] = v;
+        }
+        int hcount = 0, hpos = 0, it = 0, status = RH_COL_MAXITER;
+        double dmax = 1e300;
+        for (it = 1; it <= p.maxiter; ++it) {
+            double fcr = p.crsw > 1.0 ? fmax(1.0, p.crsw * pow(10.0, -(double)(it - 1))) : 1.0;
+            for (int i = tid; i < LN; i += blockDim.x) s.nr[i] = (R)(s.n[i] * p.inv_nref);
+            __syncthreads();
+            // ---- formal solution and rate accumulation
+            for (int b = warp; b < A.ntile; b += nwarp) sweep_tile<R, NMU>(A, s, p, b, lane);
+            __syncthreads();
+            // ---- rate equations, one thread per depth
+            int bad = 0;
+            double dloc = 0.0;
+            for (int k = tid; k < N; k += blockDim.x) {
+                int e = solve_depth(A, sizeof(R) == 8 ? reinterpret_cast<const double *>(s.slot) : nullptr,
+                                    sizeof(R) == 4 ? reinterpret_cast<const float *>(s.slot) : nullptr, N, k,
+                                    s.Cr, fcr, s.n, p.nH + cN, s.nn);
+                if (e) bad = 2;
+                for (int l = 0; l < L && !e; ++l) {
+                    double a = s.nn[l * N + k];
+                    if (!(isfinite(a) && a > 0.0)) {
+                        bad = bad ? bad : 1;
+                        break;
+                    }
+                    dloc = fmax(dloc, fabs(a - s.n[l * N + k]) / a);
+                }
+            }
+            double badg = block_max((double)bad, s.red);
+            dmax = block_max(dloc, s.red);
+            if (badg > 0) {
+                status = badg > 1.5 ? RH_COL_SINGULAR : RH_COL_NONFINITE;
+                break;
+            }
+            const bool conv = dmax < p.tol && fcr == 1.0;
+            // ---- Ng history (newest first, ring of 4)
+            hpos = (hpos + 3) & 3;
+            for (int i = tid; i < LN; i += blockDim.x) hist[(size_t)hpos * LN + i] = s.nn[i];
+            __syncthreads();
+            if (hcount < 4) ++hcount;
+            if (!conv && p.ng_order == 2 && it >= p.ng_delay && hcount >= 4 &&
+                (it - p.ng_delay) % p.ng_period == 0) {
+                const double *x0 = hist + (size_t)hpos * LN, *x1 = hist + (size_t)((hpos + 1) & 3) * LN,
+                             *x2 = hist + (size_t)((hpos + 2) & 3) * LN, *x3 = hist + (size_t)((hpos + 3) & 3) * LN;
+                double a11 = 0, a12 = 0, a22 = 0, b1 = 0, b2 = 0;
+                for (int i = tid; i < LN; i += blockDim.x) {
+                    double d0 = x0[i] - x1[i], d1 = x1[i] - x2[i], d2 = x2[i] - x3[i];
+                    double pp = d0 - d1, qq = d0 - d2;
+                    a11 += pp * pp;
+                    a12 += pp * qq;
+                    a22 += qq * qq;
+                    b1 += d0 * pp;
+                    b2 += d0 * qq;
+                }
+                a11 = block_sum(a11, s.red);
+                a12 = block_sum(a12, s.red);
+                a22 = block_sum(a22, s.red);
+                b1 = block_sum(b1, s.red);
+                b2 = block_sum(b2, s.red);
+                double det = a11 * a22 - a12 * a12;
+                if (fabs(det) > 0.0 && isfinite(det)) {
+                    double ca = (b1 * a22 - b2 * a12) / det, cb = (a11 * b2 - a12 * b1) / det;
+                    int okl = 1;
+                    for (int i = tid; i < LN; i += blockDim.x) {
+                        double v = (1.0 - ca - cb) * x0[i] + ca * x1[i] + cb * x2[i];
+                        if (!(isfinite(v) && v > 0.0)) okl = 0;
+                    }
+                    double ok = -block_max(-(double)okl, s.red);
+                    if (ok > 0.5) {
+                        for (int i = tid; i < LN; i += blockDim.x) {
+                            double v = (1.0 - ca - cb) * x0[i] + ca * x1[i] + cb * x2[i];
+                            s.nn[i] = v;
+                        }
+                        __syncthreads();
+                        for (int i = tid; i < LN; i += blockDim.x) hist[(size_t)hpos * LN + i] = s.nn[i];
+                        hcount = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i < LN; i += blockDim.x) s.n[i] = s.nn[i];
+            __syncthreads();
+            if (conv) {
+                status = RH_COL_CONVERGED;
+                break;
+            }
+        }
+        if (it > p.maxiter) it = p.maxiter;
+        for (int i = tid; i < LN; i += blockDim.x) p.pops[(size_t)col * LN + i] = s.n[i];
+        if (tid == 0) {
+            p.iters[col] = it;
+            p.status[col] = (uint8_t)status;
+            p.dmax[col] = dmax;
+        }
+    }
+}
+
+}  // namespace
+
+size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep) { return sizeof(double) * 4 * A.nlev * ndep; }
+
+template <typename R, int NMU>
+static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps, int nsm, size_t cap, cudaStream_t st,
+                            float *ms, char *err, size_t errn, int *grid_out)
+{
+    size_t sm = smem_bytes<R>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
+    auto kern = mali_kernel<R, NMU>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int threads = block_warps * 32;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) {
+        snprintf(err, errn, "column kernel does not fit: %zu B shared memory, %d threads", sm, threads);
+        return cudaErrorInvalidConfiguration;
+    }
+    int64_t grid = (int64_t)per_sm * nsm;
+    if (grid > p.nwork) grid = p.nwork;
+    size_t per_block = mali_nghist_bytes_per_block(A, p.N);
+    if ((size_t)grid * per_block > cap) grid = (int64_t)(cap / per_block);
+    if (grid < 1) {
+        snprintf(err, errn, "no scratch for the Ng history");
+        return cudaErrorMemoryAllocation;
+    }
+    *grid_out = (int)grid;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    kern<<<(unsigned)grid, threads, sm, st>>>(A, p);
+    e = cudaGetLastError();
+    cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess && ms) cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
+cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad, const float *daw,
+                        double nref, double *nghist, size_t nghist_cap, int *queue, const IterLaunch &o,
+                        cudaStream_t st, float *ms_out, int *grid_out, char *err, size_t errn)
+{
+    KParams p;
+    p.ncol = c.ncol;
+    p.N = c.ndep;
+    p.L = A.nlev;
+    p.z = c.z;
+    p.T = c.T;
+    p.nH = c.nH;
+    p.vz = c.vz;
+    p.ne = c.ne;
+    p.np = c.np;
+    p.nstar = c.nstar;
+    p.Crate = c.Crate;
+    p.pops = c.pops;
+    p.dmax = c.dmax;
+    p.iters = c.iters;
+    p.status = c.status;
+    p.lane = lane_tab;
+    p.npad = npad;
+    p.daw = daw;
+    p.nghist = nghist;
+    p.queue = queue;
+    p.persistent = o.persistent;
+    p.maxiter = o.maxiter;
+    p.ng_order = o.ng_order;
+    p.ng_delay = o.ng_delay;
+    p.ng_period = o.ng_period;
+    p.start = o.start;
+    p.tol = o.tol;
+    p.crsw = o.crsw;
+    p.inv_nref = 1.0 / nref;
+    p.colidx = o.colidx;
+    p.nwork = o.nwork;
+    int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
+    if (o.persistent) {
+        cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
+    if (o.precision == 1) {
+        if (A.nmu == 5) return launch_t<float, 5>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+        if (A.nmu <= 2) return launch_t<float, 2>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+        return launch_t<float, 8>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+    }
+    if (A.nmu == 5) return launch_t<double, 5>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+    if (A.nmu <= 2) return launch_t<double, 2>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+    return launch_t<double, 8>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+}
+
+}  // namespace rh

@@ -1,0 +1,258 @@
+"""GPU (CUDA path, through the C ABI) against the FP64 oracle.
+
+FP64 path: identical schedule (fixed iteration count, same Ng), populations
+per column within 1e-9 relative.  Mixed path (FP32 formal solution and
+rates, FP64 solve/Ng): converged populations within 1e-3 relative and
+emergent intensities within 1e-4 relative of the oracle's tight fixed point.
+"""
+import numpy as np
+import pytest
+
+import rh_synth
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9
+POP_TOL_MIXED = 1e-3
+INT_TOL_MIXED = 1e-4
+
+
+@pytest.fixture(scope="module")
+def rh():
+    import paper_1411_1079_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def atom():
+    return rh_synth.hydrogen_like_atom()
+
+
+@pytest.fixture(scope="module")
+def cols():
+    # the chromosphere column plus cube columns (cool, hot, fast flows): 7 columns
+    cube = rh_synth.chromosphere_cube(nx=32, ny=32, seed=11)
+    base = rh_synth.chromosphere_column()
+    pick = rh_synth.subset(cube, [0, 17, 300, 511, 777, 1000])
+    return {k: np.concatenate([base[k], pick[k]]) for k in base}
+
+
+def _pair(rh, orc, atom, cols):
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    g.load_columns(cols)
+    o = orc.Oracle()
+    o.setup_atom(atom)
+    o.load_columns(cols)
+    return g, o
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a / b - 1)))
+
+
+def test_grid_matches_oracle(rh, orc, atom):
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    o = orc.Oracle()
+    o.setup_atom(atom)
+    assert g.nlambda == o.nlambda == 608
+    assert np.allclose(g.grid(), o.grid()["nu"], rtol=1e-15, atol=0)
+
+
+def test_lte_setup_matches_oracle(rh, orc, atom, cols):
+    g, o = _pair(rh, orc, atom, cols)
+    ns_g, ne_g = g.lte()
+    ns_o, ne_o = o.lte()
+    assert rel(ne_g, ne_o) < 1e-12
+    assert rel(ns_g, ns_o) < 1e-12
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_fp64_fixed_schedule_matches_oracle(rh, orc, atom, cols, persistent):
+    """Identical schedule without Ng: populations per iterate within 1e-9
+    (observed ~2e-12).  Ng extrapolation divides by differences of successive
+    iterates and amplifies ~1e-12 rounding differences to ~1e-8 along the way,
+    so the schedule with Ng is compared at its converged fixed point below."""
+    g, o = _pair(rh, orc, atom, cols)
+    for it in (1, 2, 30):
+        g.load_columns(cols)
+        o.load_columns(cols)
+        sg = g.iterate(maxiter=it, tol=0.0, precision=0, persistent=persistent, ng_order=0)
+        so = o.iterate(maxiter=it, tol=0.0, ng_order=0)
+        ng, itg, stg, _ = g.populations()
+        no, ito, sto, _ = o.populations()
+        assert np.array_equal(itg, ito) and np.array_equal(stg, sto)
+        assert rel(ng, no) < FP64_TOL, it
+        assert sg["pts"] == so["pts"]
+
+
+def test_fp64_small_atom_ragged_depths(rh, orc):
+    atom = rh_synth.small_atom()
+    cols = rh_synth.subset(rh_synth.chromosphere_cube(nx=16, ny=16, ndep=13, seed=2), list(range(37)))
+    g, o = _pair(rh, orc, atom, cols)
+    g.iterate(maxiter=25, tol=0.0, precision=0, ng_order=0)
+    o.iterate(maxiter=25, tol=0.0, ng_order=0)
+    assert rel(g.populations()[0], o.populations()[0]) < FP64_TOL
+
+
+def test_fp64_with_ng_converged_fixed_point(rh, orc, atom, cols):
+    g, o = _pair(rh, orc, atom, cols)
+    g.iterate(maxiter=600, tol=1e-11, precision=0)
+    o.iterate(maxiter=600, tol=1e-11)
+    ng, itg, stg, dg = g.populations()
+    no, ito, sto, do = o.populations()
+    assert np.all(sto == 0) and np.all(stg == 0)
+    assert rel(ng, no) < FP64_TOL
+    # at the 1e-3 criterion the same columns converge, in nearly the same counts
+    g.load_columns(cols)
+    o.load_columns(cols)
+    g.iterate(maxiter=300, tol=1e-3, precision=0)
+    o.iterate(maxiter=300, tol=1e-3)
+    itg, stg = g.populations()[1:3]
+    ito, sto = o.populations()[1:3]
+    assert np.array_equal(stg, sto) and np.max(np.abs(itg - ito)) <= 3
+
+
+def test_mixed_precision_fixed_point(rh, orc, atom, cols):
+    g, o = _pair(rh, orc, atom, cols)
+    o.iterate(maxiter=1000, tol=1e-9)
+    no = o.populations()[0]
+    sg = g.iterate(maxiter=1000, tol=1e-6, precision=1)
+    ng, itg, stg, _ = g.populations()
+    assert np.all(stg == 0), stg
+    assert rel(ng, no) < POP_TOL_MIXED
+    # the mixed path at the 1e-3 stopping criterion: report-level check only
+    g.load_columns(cols)
+    g.iterate(maxiter=500, tol=1e-3, precision=1)
+    n3, it3, st3, _ = g.populations()
+    assert np.all(st3 == 0)
+    assert rel(n3, no) < 3e-2
+
+
+def test_emergent_spectrum_matches_oracle(rh, orc, atom, cols):
+    g, o = _pair(rh, orc, atom, cols)
+    o.iterate(maxiter=40, tol=1e-4)
+    n = o.populations()[0]
+    g.set_populations(n)
+    lam = np.concatenate([np.linspace(121.4e-9, 121.8e-9, 41), np.linspace(656.0e-9, 656.6e-9, 31),
+                          [91.0e-9, 364e-9, 500e-9, 1.2e-6, 4.05e-6]])
+    for mu in (1.0, 0.35):
+        Io = o.emergent_spectrum(mu, lam)
+        I64 = g.emergent_spectrum(mu, lam, precision=0)
+        I32 = g.emergent_spectrum(mu, lam, precision=1)
+        assert rel(I64, Io) < 1e-10
+        assert rel(I32, Io) < INT_TOL_MIXED
+
+
+def test_mixed_emergent_intensity_after_convergence(rh, orc, atom, cols):
+    g, o = _pair(rh, orc, atom, cols)
+    o.iterate(maxiter=1000, tol=1e-9)
+    g.iterate(maxiter=1000, tol=1e-6, precision=1)
+    lam = np.concatenate([np.linspace(121.45e-9, 121.7e-9, 26), np.linspace(656.1e-9, 656.5e-9, 21)])
+    Io = o.emergent_spectrum(1.0, lam)
+    Ig = g.emergent_spectrum(1.0, lam, precision=1)
+    assert rel(Ig, Io) < INT_TOL_MIXED
+
+
+def test_column_permutation_is_bit_exact(rh, atom, cols):
+    perm = np.array([3, 0, 6, 1, 5, 2, 4])
+    g1 = rh.Context(0)
+    g1.setup_atom(atom)
+    g1.load_columns(cols)
+    g1.iterate(maxiter=8, tol=0.0, precision=0)
+    n1 = g1.populations()[0]
+    g2 = rh.Context(0)
+    g2.setup_atom(atom)
+    g2.load_columns({k: v[perm] for k, v in cols.items()})
+    g2.iterate(maxiter=8, tol=0.0, precision=0)
+    n2 = g2.populations()[0]
+    assert np.array_equal(n2, n1[perm])
+    # and deterministic across runs, in both precisions
+    for prec in (0, 1):
+        g1.load_columns(cols)
+        g1.iterate(maxiter=8, tol=0.0, precision=prec)
+        a = g1.populations()[0]
+        g1.load_columns(cols)
+        g1.iterate(maxiter=8, tol=0.0, precision=prec)
+        assert np.array_equal(a, g1.populations()[0])
+
+
+def test_invalid_inputs_are_rejected(rh, atom, cols):
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    bad = {k: v.copy() for k, v in cols.items()}
+    bad["T"][4, 17] = np.nan
+    with pytest.raises(rh.RhError) as e:
+        g.load_columns(bad)
+    assert e.value.code == rh.RH_EINVAL and "column 4 depth 17" in str(e.value)
+    bad = {k: v.copy() for k, v in cols.items()}
+    bad["z"][2, 5] = bad["z"][2, 4]
+    with pytest.raises(rh.RhError):
+        g.load_columns(bad)
+    with pytest.raises(rh.RhError) as e:
+        g.iterate()
+    assert e.value.code == rh.RH_ESTATE
+    g.load_columns(cols)
+    with pytest.raises(rh.RhError):
+        g.iterate(ng_order=3)
+
+
+def test_maxiter_status_and_restart(rh, orc, atom, cols):
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    g.load_columns(cols)
+    s = g.iterate(maxiter=2, tol=1e-3, precision=0)
+    assert s["rc"] == rh.RH_ENOTCONV and s["n_maxiter"] == len(cols["T"])
+    n, it, st, _ = g.populations()
+    assert np.all(st == rh.COL_MAXITER) and np.all(it == 2)
+    # restart from the stored populations = continuing the iteration (no Ng
+    # so that the two schedules are the same)
+    g.load_columns(cols)
+    g.iterate(maxiter=2, tol=0.0, precision=0, ng_order=0)
+    g.iterate(maxiter=3, tol=0.0, precision=0, ng_order=0, start=2)
+    a = g.populations()[0]
+    g.load_columns(cols)
+    g.iterate(maxiter=5, tol=0.0, precision=0, ng_order=0)
+    assert rel(a, g.populations()[0]) < 1e-13
+
+
+def test_rerun_only_unconverged_leaves_converged_columns(rh, atom, cols):
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    g.load_columns(cols)
+    g.iterate(maxiter=40, tol=1e-3, precision=0)
+    n1, it1, st1, _ = g.populations()
+    assert (st1 == 0).any() and (st1 != 0).any()
+    s = g.iterate(maxiter=300, tol=1e-3, precision=0, only_unconverged=1)
+    n2, it2, st2, _ = g.populations()
+    assert s["n_processed"] == int((st1 != 0).sum())
+    assert np.array_equal(n2[st1 == 0], n1[st1 == 0]) and np.array_equal(it2[st1 == 0], it1[st1 == 0])
+    assert np.all(st2 == 0)
+
+
+def test_large_batch_sampled_against_oracle(rh, orc, atom):
+    """The bench configuration (256x256 columns, mixed, work queue, two-pass
+    strategy): every column converges; sampled columns against the oracle."""
+    cube = rh_synth.chromosphere_cube()
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    g.load_columns(cube)
+    s = g.solve(precision=1)
+    assert s["n_converged"] == 65536, s
+    n, it, st, dm = g.populations()
+    rng = np.random.default_rng(4)
+    idx = np.concatenate([rng.choice(65536, 10, replace=False), [65535]])
+    o = orc.Oracle()
+    o.setup_atom(atom)
+    o.load_columns(rh_synth.subset(cube, idx))
+    o.iterate(maxiter=1000, tol=1e-9)
+    no, _, sto, _ = o.populations()
+    ok = sto == 0
+    # at the 1e-3 stopping criterion the error against the tight fixed point
+    # is not bounded by 1e-3 (spectral radius close to 1): 3e-2 is the bound
+    assert rel(n[idx][ok], no[ok]) < 3e-2
+    # conservation on every column
+    assert np.allclose(n.sum(axis=1), cube["nH"], rtol=1e-12)
+    assert s["rerun_columns"] < 0.01 * 65536
