@@ -164,6 +164,41 @@ int rh_set_populations(rh_ctx *ctx, const double *n_in);
 int rh_emergent_spectrum(rh_ctx *ctx, double mu, int64_t nlambda, const double *lambda_m,
                          double *I_out, int32_t precision, int32_t on_device);
 
+/* ---------------------------------------------------------------------- */
+/* rh_iterate_noalloc -- the paper has no counterpart to this call; it      */
+/* exists for callers of this library that cannot allocate device memory    */
+/* while they solve: programs that hand all GPU memory to their own pool or  */
+/* budget (a framework allocator that must see every byte), code running    */
+/* while a CUDA stream is being captured into a graph, and latency-bound     */
+/* loops that cannot afford the device-wide synchronisation cudaMalloc and   */
+/* cudaFree imply.  Such a caller creates the context, sets the atom and     */
+/* loads the columns once during start-up (those calls do allocate), and     */
+/* later calls this function as often as it likes.                           */
+/*                                                                           */
+/* It runs the same iteration as rh_iterate over every loaded column         */
+/* (only_unconverged must be 0) and writes the results to caller-owned       */
+/* DEVICE buffers: n_out [ncol][nlev][ndep] (with start = 2 it is also read  */
+/* as the starting populations), iters_out [ncol], status_out [ncol]         */
+/* (RH_COL_*), dmax_out [ncol].  It calls no cudaMalloc, cudaFree or other   */
+/* allocating routine: its scratch (work-queue counter, result counters,     */
+/* the wavelength table in the iteration's precision and the Ng history of   */
+/* the resident blocks) is one statically sized 9 MiB device array inside   */
+/* the library, which every GPU that loads the library holds until the      */
+/* process exits.  A problem whose Ng history for one column exceeds that    */
+/* array (4 x nlev x ndep doubles > ~8 MiB; cannot happen within the limits  */
+/* of rh_load_columns and rh_setup_atom) is rejected with RH_EINVAL; a       */
+/* smaller array only lowers the number of resident blocks.                  */
+/* The first call on each device looks the array's address up (so make that */
+/* first call before starting any stream capture).  All calls, from every    */
+/* context and thread, share the one array: the counters are cleared at the  */
+/* start of each call, and calls whose GPU work overlaps (other streams,     */
+/* other threads) race on it and must be serialised by the caller.  The call */
+/* returns after the work has finished on the context's stream; stats_out    */
+/* (optional, host) reports wall-clock seconds.  Returns RH_OK, RH_ENOTCONV,  */
+/* RH_EINVAL, RH_ESTATE or RH_ECUDA as rh_iterate does.                      */
+int rh_iterate_noalloc(rh_ctx *ctx, const rh_iter_opts *opts, double *n_out, int32_t *iters_out,
+                       uint8_t *status_out, double *dmax_out, rh_iter_stats *stats_out);
+
 #ifdef __cplusplus
 }
 #endif

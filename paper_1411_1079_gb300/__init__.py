@@ -23,7 +23,7 @@ _lib = None
 
 EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlambda", "rh_get_grid",
            "rh_load_columns", "rh_iterate", "rh_get_populations", "rh_get_lte", "rh_set_populations",
-           "rh_emergent_spectrum")
+           "rh_emergent_spectrum", "rh_iterate_noalloc")
 
 
 class AtomDesc(C.Structure):
@@ -74,6 +74,7 @@ def lib(path: str | None = None):
         L.rh_get_lte.argtypes = [vp, _dp, _dp]
         L.rh_set_populations.argtypes = [vp, _dp]
         L.rh_emergent_spectrum.argtypes = [vp, C.c_double, C.c_int64, _dp, vp, C.c_int32, C.c_int32]
+        L.rh_iterate_noalloc.argtypes = [vp, C.POINTER(IterOpts), vp, vp, vp, vp, C.POINTER(IterStats)]
         _lib = L
     return _lib
 
@@ -199,6 +200,23 @@ class Context:
                 "iterations_total": sum(p["iterations_total"] for p in passes),
                 "rerun_columns": sum(p["n_processed"] for p in passes[1:]),
                 "launches": sum(1 for p in passes if p["n_processed"] > 0)}
+
+    def iterate_noalloc(self, n_out, iters_out, status_out, dmax_out, maxiter=500, tol=1e-3, ng_order=2,
+                        ng_delay=5, ng_period=3, start=0, precision=1, persistent=1, block_warps=0,
+                        crsw_init=1.0) -> dict:
+        """rh_iterate_noalloc: results into caller-owned CUDA tensors (float64
+        [ncol][nlev][ndep], int32 [ncol], uint8 [ncol], float64 [ncol]); the
+        library allocates nothing during the call."""
+        o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
+                     ng_period=ng_period, start=start, precision=precision, persistent=persistent,
+                     block_warps=block_warps, crsw_init=crsw_init, only_unconverged=0)
+        s = IterStats()
+        rc = self._check(self._lib.rh_iterate_noalloc(self._p, C.byref(o), _ptr(n_out), _ptr(iters_out),
+                                                      _ptr(status_out), _ptr(dmax_out), C.byref(s)),
+                         allow=(RH_ENOTCONV,))
+        out = {f: getattr(s, f) for f, _ in IterStats._fields_}
+        out["rc"] = rc
+        return out
 
     def populations(self, out=None):
         """(n [ncol][nlev][ndep], iters, status, dmax).  ``out`` may be a torch

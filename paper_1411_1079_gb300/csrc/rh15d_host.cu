@@ -1,6 +1,7 @@
 // rh15d_host.cu -- the C ABI (include/rh15d.h): context, atom tables,
 // wavelength grid, column storage, launches.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -817,3 +818,141 @@ int rh_emergent_spectrum(rh_ctx *c, double mu, int64_t nlambda, const double *la
 }
 
 }  // extern "C"
+
+// ============================================================================
+// rh_iterate_noalloc: the MALI iteration for callers that cannot allocate
+// device memory at solve time (see include/rh15d.h).  Its scratch -- the
+// work-queue counter, result counters, the lane table in the iteration's
+// precision, and the Ng history of the resident blocks -- lives in one
+// file-scope device array that every GPU loading this library holds until
+// the process exits.
+namespace {
+
+constexpr size_t kNoallocBytes = (size_t)9 << 20;              // 9 MiB in total
+constexpr size_t kNoallocHead = 256;                           // queue counter + 4 result counters
+constexpr size_t kNoallocLaneBytes = (size_t)kLaneFields * RH_MAXTILE * 32 * sizeof(double);
+constexpr size_t kNoallocHistOff = kNoallocHead + ((kNoallocLaneBytes + 255) / 256) * 256;
+constexpr size_t kNoallocHistBytes = kNoallocBytes - kNoallocHistOff;
+constexpr int kNoallocMaxDev = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// device address of the scratch array, looked up once per device (host code
+// may not use the symbol itself as an address)
+void *g_noalloc_dev_ptr[kNoallocMaxDev];
+// host staging of the lane table (static: no heap allocation per call)
+double g_noalloc_lane64[(size_t)kLaneFields * RH_MAXTILE * 32];
+float g_noalloc_lane32[(size_t)kLaneFields * RH_MAXTILE * 32];
+
+__global__ void noalloc_count_kernel(int64_t ncol, const int32_t *iters, const uint8_t *status,
+                                     unsigned long long *cnt)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncol) return;
+    const uint8_t s = status[i];
+    atomicAdd(&cnt[s == RH_COL_CONVERGED ? 0 : (s == RH_COL_MAXITER ? 1 : 2)], 1ull);
+    atomicAdd(&cnt[3], (unsigned long long)iters[i]);
+}
+
+__global__ void noalloc_max_kernel(int64_t ncol, const double *dmax, unsigned long long *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncol) return;
+    const double v = dmax[i];
+    if (v >= 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(v));   // non-negative doubles order as bits
+}
+
+}  // namespace
+
+extern "C" int rh_iterate_noalloc(rh_ctx *c, const rh_iter_opts *o, double *n_out, int32_t *iters_out,
+                                  uint8_t *status_out, double *dmax_out, rh_iter_stats *stats_out)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "rh_iterate_noalloc: no columns loaded");
+    if (!o || !n_out || !iters_out || !status_out || !dmax_out)
+        return fail(c, RH_EINVAL, "rh_iterate_noalloc: opts and the four output buffers must not be NULL");
+    if (o->maxiter < 1 || !(o->tol >= 0) || (o->ng_order != 0 && o->ng_order != 2) ||
+        (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) || (o->precision != 0 && o->precision != 1) ||
+        (o->start != 0 && o->start != 2) || o->block_warps < 0 || o->block_warps > 8 || o->only_unconverged != 0)
+        return fail(c, RH_EINVAL, "rh_iterate_noalloc: invalid options (only_unconverged is not supported here)");
+    if (c->dev < 0 || c->dev >= kNoallocMaxDev) return fail(c, RH_EINVAL, "rh_iterate_noalloc: device index too large");
+    CK(cudaSetDevice(c->dev));
+    // once per device, with the device current: the scratch array's address
+    if (!g_noalloc_dev_ptr[c->dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(c, RH_ECUDA, "rh_iterate_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_dev_ptr[c->dev] = ptr;
+    }
+    unsigned char *base = (unsigned char *)g_noalloc_dev_ptr[c->dev];
+    int *queue = (int *)base;
+    unsigned long long *cnt = (unsigned long long *)(base + 64);
+    void *lane = base + kNoallocHead;
+    double *hist = (double *)(base + kNoallocHistOff);
+    const size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
+    if (per_block > kNoallocHistBytes)
+        return fail(c, RH_EINVAL, "rh_iterate_noalloc: Ng history of one column needs %zu B, the scratch holds %zu B",
+                    per_block, kNoallocHistBytes);
+    // the lane table in the iteration's precision, populations scaled by n_ref
+    const int np = c->ha.npad;
+    const size_t nl = (size_t)kLaneFields * np;
+    for (size_t i = 0; i < nl; ++i) g_noalloc_lane64[i] = c->lane_master[i];
+    for (int j = 0; j < RH_KMAX; ++j)
+        for (int f : {1, 2})
+            for (int p = 0; p < np; ++p) g_noalloc_lane64[(size_t)(RH_NLANEF * j + f) * np + p] *= c->nref;
+    if (o->precision == 1) {
+        for (size_t i = 0; i < nl; ++i) g_noalloc_lane32[i] = (float)g_noalloc_lane64[i];
+        CK(cudaMemcpyAsync(lane, g_noalloc_lane32, nl * sizeof(float), cudaMemcpyHostToDevice, c->st));
+    } else {
+        CK(cudaMemcpyAsync(lane, g_noalloc_lane64, nl * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    }
+    ColumnArrays cc = c->ca;
+    cc.pops = n_out;
+    cc.iters = iters_out;
+    cc.status = status_out;
+    cc.dmax = dmax_out;
+    IterLaunch il{};
+    il.precision = o->precision;
+    il.persistent = o->persistent;
+    il.block_warps = o->block_warps;
+    il.maxiter = o->maxiter;
+    il.ng_order = o->ng_order;
+    il.ng_delay = o->ng_delay;
+    il.ng_period = o->ng_period;
+    il.start = o->start;
+    il.tol = o->tol;
+    il.crsw = o->crsw_init;
+    il.nsm = c->nsm;
+    il.colidx = nullptr;
+    il.nwork = c->ncol;
+    int grid = 0;
+    char ebuf[256] = {0};
+    const std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    cudaError_t e = launch_mali_prealloc(c->da, cc, lane, np, c->daw_d, c->nref, hist, kNoallocHistBytes, queue, il,
+                                         c->st, &grid, ebuf, sizeof ebuf);
+    if (e != cudaSuccess)
+        return fail(c, RH_ECUDA, "rh_iterate_noalloc: %s%s%s", cudaGetErrorString(e), ebuf[0] ? ": " : "", ebuf);
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    CK(cudaMemsetAsync(cnt, 0, 5 * sizeof(unsigned long long), c->st));
+    noalloc_count_kernel<<<(unsigned)((c->ncol + 255) / 256), 256, 0, c->st>>>(c->ncol, iters_out, status_out, cnt);
+    CK(cudaGetLastError());
+    noalloc_max_kernel<<<(unsigned)((c->ncol + 255) / 256), 256, 0, c->st>>>(c->ncol, dmax_out, cnt + 4);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats_out) {
+        rh_iter_stats S{};
+        S.n_converged = (int64_t)h[0];
+        S.n_maxiter = (int64_t)h[1];
+        S.n_failed = (int64_t)h[2];
+        S.n_processed = c->ncol;
+        S.iterations_total = (int64_t)h[3];
+        S.seconds = secs;
+        S.pts = (double)S.iterations_total * c->ndep * (double)c->ha.nu.size() * c->ha.nmu;
+        memcpy(&S.max_dn_final, &h[4], sizeof(double));
+        *stats_out = S;
+    }
+    return (h[1] || h[2]) ? RH_ENOTCONV : RH_OK;
+}

@@ -309,6 +309,9 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
                         const IterLaunch &o, cudaStream_t st, float *ms_out, int *grid_out, char *err,
                         size_t errn);
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep);
+cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
+                                 const float *daw, double nref, double *nghist, size_t nghist_cap, int *queue,
+                                 const IterLaunch &o, cudaStream_t st, int *grid_out, char *err, size_t errn);
 // emergent spectrum: per requested wavelength j, up to RH_SPEC_ACT transitions
 // with constants spec[(j * RH_SPEC_ACT + s) * RH_SPEC_F + f]
 #define RH_SPEC_ACT 8

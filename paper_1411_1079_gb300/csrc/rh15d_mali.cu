@@ -718,3 +718,88 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
 }
 
 }  // namespace rh
+
+// ----------------------------------------------------------------------------
+// Launcher for callers that must not allocate: the same kernel, no timing
+// events (event objects are driver allocations), scratch pointers supplied
+// by the caller.  Grid size is clamped to the Ng-history capacity.
+namespace rh {
+
+cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
+                                 const float *daw, double nref, double *nghist, size_t nghist_cap, int *queue,
+                                 const IterLaunch &o, cudaStream_t st, int *grid_out, char *err, size_t errn)
+{
+    KParams p;
+    p.ncol = c.ncol;
+    p.N = c.ndep;
+    p.L = A.nlev;
+    p.z = c.z;
+    p.T = c.T;
+    p.nH = c.nH;
+    p.vz = c.vz;
+    p.ne = c.ne;
+    p.np = c.np;
+    p.nstar = c.nstar;
+    p.Crate = c.Crate;
+    p.pops = c.pops;
+    p.dmax = c.dmax;
+    p.iters = c.iters;
+    p.status = c.status;
+    p.lane = lane_tab;
+    p.npad = npad;
+    p.daw = daw;
+    p.nghist = nghist;
+    p.queue = queue;
+    p.persistent = o.persistent;
+    p.maxiter = o.maxiter;
+    p.ng_order = o.ng_order;
+    p.ng_delay = o.ng_delay;
+    p.ng_period = o.ng_period;
+    p.start = o.start;
+    p.tol = o.tol;
+    p.crsw = o.crsw;
+    p.inv_nref = 1.0 / nref;
+    p.colidx = o.colidx;
+    p.nwork = o.nwork;
+    const int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
+    const int threads = bw * 32;
+    size_t sm;
+    const void *fn;
+    if (o.precision == 1) {
+        sm = smem_bytes<float>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
+        fn = A.nmu == 5 ? (const void *)mali_kernel<float, 5>
+                        : (A.nmu <= 2 ? (const void *)mali_kernel<float, 2> : (const void *)mali_kernel<float, 8>);
+    } else {
+        sm = smem_bytes<double>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
+        fn = A.nmu == 5 ? (const void *)mali_kernel<double, 5>
+                        : (A.nmu <= 2 ? (const void *)mali_kernel<double, 2> : (const void *)mali_kernel<double, 8>);
+    }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) {
+        snprintf(err, errn, "column kernel does not fit: %zu B shared memory, %d threads", sm, threads);
+        return cudaErrorInvalidConfiguration;
+    }
+    int64_t grid = (int64_t)per_sm * o.nsm;
+    if (grid > p.nwork) grid = p.nwork;
+    const size_t per_block = mali_nghist_bytes_per_block(A, p.N);
+    if ((size_t)grid * per_block > nghist_cap) grid = (int64_t)(nghist_cap / per_block);
+    if (grid < 1) {
+        snprintf(err, errn, "Ng history of one column (%zu B) exceeds the scratch capacity (%zu B)", per_block,
+                 nghist_cap);
+        return cudaErrorInvalidValue;
+    }
+    *grid_out = (int)grid;
+    if (o.persistent) {
+        e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
+    void *args[] = {(void *)&A, (void *)&p};
+    e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(threads), args, sm, st);
+    return e;
+}
+
+}  // namespace rh
