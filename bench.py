@@ -141,7 +141,7 @@ def oracle_two_pass(o, cols, cores):
     o.iterate(maxiter=MAXITER, tol=TOL, nthreads=cores)
     n, it, st, _ = o.populations()
     conv = int((st == oracle.ST_CONV).sum())
-    for f0 in (1e3, 1e5):
+    for f0 in (1e3, 1e5, 1e7):
         bad = np.where(st != oracle.ST_CONV)[0]
         if not bad.size:
             break

@@ -178,12 +178,13 @@ class Context:
 
     # Sect. 2.3: run all columns with an aggressive choice of options, then
     # re-run the columns that did not converge with other options.
-    RESCUE_PASSES = (dict(ng_order=0, crsw_init=1e3), dict(ng_order=0, crsw_init=1e5))
+    RESCUE_PASSES = (dict(ng_order=0, crsw_init=1e3), dict(ng_order=0, crsw_init=1e5),
+                     dict(ng_order=0, crsw_init=1e7))
 
     def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True):
         """All columns from LTE with Ng acceleration, then the columns that did
         not converge again from LTE with collisional-radiative switching
-        (x1e3, then x1e5) and without Ng (the paper's two-stage strategy)."""
+        (x1e3, x1e5, then x1e7) and without Ng (the paper's two-stage strategy)."""
         s = self.iterate(maxiter=maxiter, tol=tol, precision=precision, persistent=persistent,
                          block_warps=block_warps)
         passes = [s]
@@ -191,8 +192,10 @@ class Context:
             for kw in self.RESCUE_PASSES:
                 if not (s["n_maxiter"] or s["n_failed"]):
                     break
-                s = self.iterate(maxiter=maxiter, tol=tol, precision=precision, persistent=persistent,
-                                 block_warps=block_warps, only_unconverged=1, **kw)
+                args = dict(maxiter=maxiter, tol=tol, precision=precision, persistent=persistent,
+                            block_warps=block_warps, only_unconverged=1)
+                args.update(kw)
+                s = self.iterate(**args)
                 passes.append(s)
         return {"passes": passes, "n_converged": s["n_converged"], "n_maxiter": s["n_maxiter"],
                 "n_failed": s["n_failed"], "seconds": sum(p["seconds"] for p in passes),

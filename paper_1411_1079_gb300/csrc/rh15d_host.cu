@@ -52,7 +52,7 @@ struct rh_ctx {
     void *lane_d = nullptr;                 // device lane table in the current precision/scale
     int lane_prec = -1;
     double lane_nref = 0;
-    float *daw_d = nullptr;
+    float4 *vtab_d = nullptr;
     // columns
     int64_t ncol = 0;
     int ndep = 0;
@@ -318,6 +318,7 @@ int build_atom(rh_ctx *c, const rh_atom_desc *d)
         da.wmu[m] = a.wmu[m];
         da.muf[m] = (float)a.mu[m];
         da.wm2f[m] = (float)(0.5 * a.wmu[m]);
+        da.imuf[m] = (float)(1.0 / a.mu[m]);
     }
     for (int t = 0; t < a.ntr; ++t) {
         const HostTrans &h = a.tr[t];
@@ -374,6 +375,18 @@ int build_atom(rh_ctx *c, const rh_atom_desc *d)
     }
     da.macc = acc;
     da.nmap = nmap;
+    // processing order: tiles with more transitions (costlier) first, line tiles before continua
+    {
+        std::vector<int> ord(a.ntile);
+        for (int b = 0; b < a.ntile; ++b) ord[b] = b;
+        auto cost = [&](int b) {
+            int cst = 0;
+            for (int t : a.tile_union[b]) cst += a.tr[t].kind == 0 ? 4 : 1;
+            return cst;
+        };
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost(x) > cost(y); });
+        for (int b = 0; b < a.ntile; ++b) da.order[b] = (int16_t)ord[b];
+    }
 
     // lane master table (unscaled)
     const int F = kLaneFields;
@@ -465,14 +478,6 @@ __global__ void validate_kernel(int64_t ncol, int ndep, const double *z, const d
     if (!ok) atomicMin(bad, (unsigned long long)i);
 }
 
-__global__ void max_kernel(int64_t n, const double *x, unsigned long long *out)
-{
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    // positive doubles order like their bit patterns
-    atomicMax(out, (unsigned long long)__double_as_longlong(x[i]));
-}
-
 }  // namespace
 
 // ============================================================================
@@ -500,11 +505,21 @@ int rh_create(rh_ctx **out, int cuda_device, void *cuda_stream)
         c->err = std::string("rh_create: ") + cudaGetErrorString(e);
         return RH_ECUDA;
     }
-    // Dawson's integral table for the FP32 Voigt function
-    std::vector<float> daw(RH_DAW_N);
-    for (int i = 0; i < RH_DAW_N; ++i) daw[i] = (float)dawson_series(i * RH_DAW_H);
-    e = cudaMalloc(&c->daw_d, RH_DAW_N * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemcpy(c->daw_d, daw.data(), RH_DAW_N * sizeof(float), cudaMemcpyHostToDevice);
+    // coefficient table of the FP32 Voigt function, uniform in t = 1/(1+|v|)
+    std::vector<float4> vt(RH_VT_N + 1);
+    const double hh = 1.0 / RH_VT_N;
+    for (int i = 0; i <= RH_VT_N; ++i) {
+        if (i == 0) {
+            vt[i] = make_float4(0.f, 0.f, 0.f, 0.f);   // v -> infinity: H1, H3 ~ t^2
+            continue;
+        }
+        double t = i * hh, v = 1.0 / t - 1.0, h1, d1, h3, d3;
+        voigt_coeffs(v, h1, d1, h3, d3);
+        double dvdt = -1.0 / (t * t);
+        vt[i] = make_float4((float)h1, (float)(hh * d1 * dvdt), (float)h3, (float)(hh * d3 * dvdt));
+    }
+    e = cudaMalloc(&c->vtab_d, (RH_VT_N + 1) * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemcpy(c->vtab_d, vt.data(), (RH_VT_N + 1) * sizeof(float4), cudaMemcpyHostToDevice);
     *out = c;
     if (e != cudaSuccess) {
         c->err = std::string("rh_create: ") + cudaGetErrorString(e);
@@ -520,7 +535,7 @@ void rh_destroy(rh_ctx *c)
     if (c->st) cudaStreamSynchronize(c->st);
     free_columns(c);
     dfree(c->lane_d);
-    dfree(c->daw_d);
+    dfree(c->vtab_d);
     dfree(c->nghist);
     dfree(c->queue);
     dfree(c->badidx);
@@ -607,16 +622,11 @@ int rh_load_columns(rh_ctx *c, int64_t ncol, int32_t ndep, const double *z_m, co
     c->ncol = ncol;
     c->ndep = ndep;
     CK(launch_lte_setup(c->da, a, ne_m3 ? 1 : 0, c->st));
-    // reference density for the FP32 population scaling: max n_H / 1e3
-    unsigned long long mx = 0;
-    CK(cudaMemcpyAsync(c->badidx, &mx, 8, cudaMemcpyHostToDevice, c->st));
-    max_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, c->st>>>((int64_t)nd, a.nH, (unsigned long long *)c->badidx);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(&mx, c->badidx, 8, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    double mxd;
-    memcpy(&mxd, &mx, 8);
-    c->nref = mxd > 0 ? mxd / 1e3 : 1.0;
+    // reference density of the FP32 population scaling: a fixed constant, so
+    // that a column's result does not depend on which other columns are
+    // loaded (populations 1e-10 .. 1e25 m^-3 map to 1e-30 .. 1e5)
+    c->nref = 1e20;
     return RH_OK;
 }
 
@@ -676,7 +686,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     int grid = 0;
     char ebuf[256] = {0};
     if (nwork > 0) {
-        cudaError_t e = launch_mali(c->da, c->ca, c->lane_d, c->ha.npad, c->daw_d, c->nref, c->nghist,
+        cudaError_t e = launch_mali(c->da, c->ca, c->lane_d, c->ha.npad, c->vtab_d, c->nref, c->nghist,
                                     c->nghist_cap, c->queue, il, c->st, &ms, &grid, ebuf, sizeof ebuf);
         if (e != cudaSuccess)
             return fail(c, RH_ECUDA, "rh_iterate: %s%s%s", cudaGetErrorString(e), ebuf[0] ? ": " : "", ebuf);
@@ -929,7 +939,7 @@ extern "C" int rh_iterate_noalloc(rh_ctx *c, const rh_iter_opts *o, double *n_ou
     int grid = 0;
     char ebuf[256] = {0};
     const std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
-    cudaError_t e = launch_mali_prealloc(c->da, cc, lane, np, c->daw_d, c->nref, hist, kNoallocHistBytes, queue, il,
+    cudaError_t e = launch_mali_prealloc(c->da, cc, lane, np, c->vtab_d, c->nref, hist, kNoallocHistBytes, queue, il,
                                          c->st, &grid, ebuf, sizeof ebuf);
     if (e != cudaSuccess)
         return fail(c, RH_ECUDA, "rh_iterate_noalloc: %s%s%s", cudaGetErrorString(e), ebuf[0] ? ": " : "", ebuf);

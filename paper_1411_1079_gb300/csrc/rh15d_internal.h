@@ -13,8 +13,7 @@
 #define RH_MAXMU 16
 #define RH_MAXMAP 2048
 #define RH_NLANEF 7        // per-slot lane fields
-#define RH_DAW_N 321       // Dawson table on [0, 5] with spacing 1/64
-#define RH_DAW_H (1.0 / 64.0)
+#define RH_VT_N 1024       // Voigt coefficient table: intervals in t = 1/(1+|v|)
 
 namespace rh {
 
@@ -52,8 +51,10 @@ struct DevAtom {
     double lev_g2[RH_MAXLEV];     // g_i / (2 g_continuum)
     double mu[RH_MAXMU], wmu[RH_MAXMU];
     float muf[RH_MAXMU], wm2f[RH_MAXMU];   // mu and w_mu / 2 for the FP32 sweep
+    float imuf[RH_MAXMU];                    // 1/mu
     DevTrans tr[RH_MAXTR];
     DevTile tile[RH_MAXTILE];
+    int16_t order[RH_MAXTILE];               // tile processing order (most expensive first)
     // accumulator -> rate-matrix entry map: A[row][col] += sign * acc
     int16_t map_acc[RH_MAXMAP];
     int8_t map_row[RH_MAXMAP], map_col[RH_MAXMAP], map_sign[RH_MAXMAP];
@@ -148,38 +149,63 @@ __host__ __device__ inline double voigt_f64(double a, double v)
     return (-si * zr + sr * zi) / (kSqrtPi * mz) + exp(zi * zi - zr * zr) * cos(2.0 * zr * zi);
 }
 
-// Voigt function, FP32 (mixed-precision formal solution).  |v| < 5:
-// H = e^{-v^2}(1 + a^2 (1 - 2 v^2)) - a (2/sqrt pi)(1 - 2 v F) +
-//     a^3 (4/(3 sqrt pi)) (v^2 - 1 + v F (3 - 2 v^2)), the expansion in a to
-// third order, with F from a cubic-Hermite table of Dawson's integral
-// (F' = 1 - 2 v F).  |v| >= 5: e^{-v^2}(1 + a^2(1-2v^2)) +
-// (a / (sqrt pi v^2)) sum_k (2k+1)!! (2 v^2)^{-k} (12 terms).
-__device__ __forceinline__ float voigt_f32(float a, float v, const float *__restrict__ daw)
+// Coefficients of the expansion of H(a, v) in the damping a used by the FP32
+// Voigt function: H = e^{-v^2}[1 + a^2(1 - 2v^2) + a^4(2v^4/3 - 2v^2 + 1/2)]
+//                     + a H1(v) + a^3 H3(v),
+// H1 = -(2/sqrt pi)(1 - 2vF), H3 = (4/(3 sqrt pi))(v^2 - 1 + vF(3 - 2v^2)),
+// F Dawson's integral.  For v >= 8 both come from their asymptotic series
+// (no cancellation): with u = 1/(2v^2), c_k = (2k-1)!!,
+// H1 = (2/sqrt pi) sum_{k>=1} c_k u^k, H3 = (4/(3 sqrt pi)) sum_{j>=2} (1-j) c_j u^j.
+// Returns H1, H3 and their derivatives in v.
+__host__ inline void voigt_coeffs(double v, double &h1, double &d1, double &h3, double &d3)
+{
+    if (v < 8.0) {
+        double F = dawson_series(v), Fp = 1.0 - 2.0 * v * F;
+        h1 = -(2.0 / kSqrtPi) * Fp;
+        d1 = (4.0 / kSqrtPi) * (F + v * Fp);
+        h3 = (4.0 / (3.0 * kSqrtPi)) * (v * v - 1.0 + v * F * (3.0 - 2.0 * v * v));
+        d3 = (4.0 / (3.0 * kSqrtPi)) * (2.0 * v + (F + v * Fp) * (3.0 - 2.0 * v * v) - 4.0 * v * v * F);
+        return;
+    }
+    double u = 1.0 / (2.0 * v * v), du = -1.0 / (v * v * v);
+    double s1 = 0, ds1 = 0, s3 = 0, ds3 = 0, ck = 1.0, uk = 1.0;   // c_0 u^0
+    for (int k = 1; k <= 40; ++k) {
+        ck *= (2 * k - 1);
+        double ukm1 = uk;
+        uk *= u;
+        s1 += ck * uk;
+        ds1 += k * ck * ukm1;
+        if (k >= 2) {
+            s3 += (1 - k) * ck * uk;
+            ds3 += (1 - k) * k * ck * ukm1;
+        }
+    }
+    h1 = (2.0 / kSqrtPi) * s1;
+    d1 = (2.0 / kSqrtPi) * ds1 * du;
+    h3 = (4.0 / (3.0 * kSqrtPi)) * s3;
+    d3 = (4.0 / (3.0 * kSqrtPi)) * ds3 * du;
+}
+
+// Voigt function, FP32, branch-free: the expansion above with H1 and H3 from
+// a cubic-Hermite table on a uniform grid in t = 1/(1+|v|) in (0, 1]
+// (tab[i] = {H1, h dH1/dt, H3, h dH3/dt} at t_i = i h, h = 1/RH_VT_N).
+__device__ __forceinline__ float voigt_f32(float a, float v, const float4 *__restrict__ tab)
 {
     float av = fabsf(v);
     float v2 = av * av;
-    float g = __expf(-v2) * (1.0f + a * a * (1.0f - 2.0f * v2));
-    if (av < 5.0f) {
-        float x = av * 64.0f;
-        int i = min((int)x, RH_DAW_N - 2);
-        float t = x - (float)i;
-        float v0 = i * (1.0f / 64.0f), v1 = v0 + (1.0f / 64.0f);
-        float F0 = daw[i], F1 = daw[i + 1];
-        float d0 = (1.0f / 64.0f) * (1.0f - 2.0f * v0 * F0);
-        float d1 = (1.0f / 64.0f) * (1.0f - 2.0f * v1 * F1);
-        float t2 = t * t, t3 = t2 * t;
-        float F = (2.0f * t3 - 3.0f * t2 + 1.0f) * F0 + (t3 - 2.0f * t2 + t) * d0 +
-                  (-2.0f * t3 + 3.0f * t2) * F1 + (t3 - t2) * d1;
-        float vF = av * F;
-        return g - a * 1.1283791670955126f * (1.0f - 2.0f * vF) +
-               a * a * a * 0.75225277806367511f * (v2 - 1.0f + vF * (3.0f - 2.0f * v2));
-    }
-    float u = 0.5f / v2;
-    // sum_k (2k+1)!! u^k, Horner over k = 0..11
-    float s = 1.0f;
-#pragma unroll
-    for (int k = 11; k >= 1; --k) s = 1.0f + (2 * k + 1) * u * s;
-    return g + a * 0.56418958354775628f / v2 * s;
+    float g = __expf(-v2);
+    float t = __frcp_rn(1.0f + av);
+    float x = t * (float)RH_VT_N;
+    int i = min((int)x, RH_VT_N - 1);
+    float f = x - (float)i;
+    float4 p0 = tab[i], p1 = tab[i + 1];
+    float f2 = f * f, f3 = f2 * f;
+    float h00 = 2.0f * f3 - 3.0f * f2 + 1.0f, h10 = f3 - 2.0f * f2 + f, h01 = 3.0f * f2 - 2.0f * f3, h11 = f3 - f2;
+    float H1 = h00 * p0.x + h10 * p0.y + h01 * p1.x + h11 * p1.y;
+    float H3 = h00 * p0.z + h10 * p0.w + h01 * p1.z + h11 * p1.w;
+    float a2 = a * a;
+    float gpoly = 1.0f + a2 * (1.0f - 2.0f * v2) + a2 * a2 * (0.66666667f * v2 * v2 - 2.0f * v2 + 0.5f);
+    return g * gpoly + a * (H1 + a2 * H3);
 }
 
 // ----------------------------------------------------------------------------
@@ -305,12 +331,12 @@ struct IterLaunch {
     int64_t nwork;         // number of columns to iterate
 };
 cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
-                        const float *daw, double nref, double *nghist, size_t nghist_cap, int *queue,
+                        const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
                         const IterLaunch &o, cudaStream_t st, float *ms_out, int *grid_out, char *err,
                         size_t errn);
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep);
 cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
-                                 const float *daw, double nref, double *nghist, size_t nghist_cap, int *queue,
+                                 const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
                                  const IterLaunch &o, cudaStream_t st, int *grid_out, char *err, size_t errn);
 // emergent spectrum: per requested wavelength j, up to RH_SPEC_ACT transitions
 // with constants spec[(j * RH_SPEC_ACT + s) * RH_SPEC_F + f]

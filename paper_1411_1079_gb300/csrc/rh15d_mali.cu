@@ -43,7 +43,7 @@ struct KParams {
     uint8_t *status;
     const void *lane;
     int npad;
-    const float *daw;
+    const float4 *vtab;
     double *nghist;
     int *queue;
     int persistent, maxiter, ng_order, ng_delay, ng_period, start;
@@ -60,7 +60,7 @@ struct Smem {
     R *Gc;                     // [ncont][N]
     R *ad;                     // [nline][N] damping
     R *nr;                     // [L][N] populations in R
-    float *daw;                // [RH_DAW_N]
+    float4 *vtab;              // [RH_VT_N + 1] Voigt coefficient table
     double *red;               // reduction scratch [64]
     int *ibuf;                 // [8]
 };
@@ -71,7 +71,7 @@ __host__ __device__ size_t smem_bytes(int L, int N, int ntr, int ncont, int nlin
     size_t b = 0;
     b += sizeof(double) * (2 * L * N + (size_t)N * 2 * ntr);
     b += sizeof(R) * ((size_t)macc * N + 7 * N + (size_t)ncont * N + (size_t)nline * N + (size_t)L * N);
-    b += sizeof(float) * RH_DAW_N;
+    b += sizeof(float4) * (RH_VT_N + 1) + 16;
     b += sizeof(double) * 64 + sizeof(int) * 8 + 64;
     return b;
 }
@@ -102,19 +102,28 @@ __device__ Smem<R> carve(char *base, int L, int N, int ntr, int ncont, int nline
     s.Gc = r; r += ncont * N;
     s.ad = r; r += nline * N;
     s.nr = r; r += L * N;
-    float *f = reinterpret_cast<float *>(r);
-    s.daw = f;
-    f += RH_DAW_N;
-    s.ibuf = reinterpret_cast<int *>(f);
+    size_t off = (reinterpret_cast<size_t>(r) + 15) & ~(size_t)15;
+    s.vtab = reinterpret_cast<float4 *>(off);
+    s.ibuf = reinterpret_cast<int *>(s.vtab + RH_VT_N + 1);
     return s;
 }
 
 template <typename R>
-__device__ __forceinline__ R voigt(R a, R v, const float *daw);
+__device__ __forceinline__ R voigt(R a, R v, const float4 *tab);
 template <>
-__device__ __forceinline__ float voigt<float>(float a, float v, const float *daw) { return voigt_f32(a, v, daw); }
+__device__ __forceinline__ float voigt<float>(float a, float v, const float4 *tab) { return voigt_f32(a, v, tab); }
 template <>
-__device__ __forceinline__ double voigt<double>(double a, double v, const float *) { return voigt_f64(a, v); }
+__device__ __forceinline__ double voigt<double>(double a, double v, const float4 *) { return voigt_f64(a, v); }
+
+template <typename R> __device__ __forceinline__ R rcp(R x);
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
+
+// 1 - exp(-x) for x > 0: FP32 uses 1 - __expf(-x) (x = h nu / kT > 0.1 on every grid here,
+// relative error < 1e-6), FP64 expm1
+template <typename R> __device__ __forceinline__ R one_m_exp(R x, R ex);
+template <> __device__ __forceinline__ float one_m_exp<float>(float x, float ex) { return 1.0f - ex; }
+template <> __device__ __forceinline__ double one_m_exp<double>(double x, double ex) { return -expm1(-x); }
 
 template <typename R> __device__ __forceinline__ R rexp(R x);
 template <> __device__ __forceinline__ float rexp<float>(float x) { return __expf(x); }
@@ -139,6 +148,9 @@ __device__ __forceinline__ double warp_sum(double v)
 template <typename R> __device__ __forceinline__ R mu_of(const DevAtom &A, int m);
 template <> __device__ __forceinline__ float mu_of<float>(const DevAtom &A, int m) { return A.muf[m]; }
 template <> __device__ __forceinline__ double mu_of<double>(const DevAtom &A, int m) { return A.mu[m]; }
+template <typename R> __device__ __forceinline__ R imu_of(const DevAtom &A, int m);
+template <> __device__ __forceinline__ float imu_of<float>(const DevAtom &A, int m) { return A.imuf[m]; }
+template <> __device__ __forceinline__ double imu_of<double>(const DevAtom &A, int m) { return 1.0 / A.mu[m]; }
 template <typename R> __device__ __forceinline__ R wm2_of(const DevAtom &A, int m);
 template <> __device__ __forceinline__ float wm2_of<float>(const DevAtom &A, int m) { return A.wm2f[m]; }
 template <> __device__ __forceinline__ double wm2_of<double>(const DevAtom &A, int m) { return 0.5 * A.wmu[m]; }
@@ -164,9 +176,9 @@ __device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K>
 {
     R x = lc.nu * s.hkT[k];
     R ex = rexp<R>(-x);
-    R omex = -rexpm1<R>(-x);
+    R omex = one_m_exp<R>(x, ex);
     d.chibg = (s.kff[k] * lc.nu3s + s.nhm[k] * lc.hm) * omex + s.thom[k];
-    d.B = lc.tw * ex / omex;
+    d.B = lc.tw * ex * rcp<R>(omex);
     d.etabg = d.chibg * d.B;
     d.etac = 0;
 #pragma unroll
@@ -193,8 +205,9 @@ __device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K>
     d.vz = s.vz[k];
 }
 
-// Opacity and emissivity for one angle (direction cosine muz); per-slot
-// profile phi, opacity chj and emissivity per upper-level population U.
+// Opacity and emissivity for one ray direction (direction cosine muz);
+// per-slot profile phi, opacity chj and emissivity per upper-level
+// population U.
 template <typename R, int K>
 __device__ __forceinline__ void angle_vals(const Smem<R> &s, const LaneC<R, K> &lc, const DepthC<R, K> &d, R muz,
                                            R &chi, R &eta, R *phi, R *chj, R *U)
@@ -205,7 +218,7 @@ __device__ __forceinline__ void angle_vals(const Smem<R> &s, const LaneC<R, K> &
     for (int j = 0; j < K; ++j) {
         if (lc.isline[j]) {
             R v = (lc.q[j] - muz * d.vz) * d.ivth;
-            R ph = voigt<R>(d.ad[j], v, s.daw) * lc.pn[j] * d.ivth;
+            R ph = voigt<R>(d.ad[j], v, s.vtab) * lc.pn[j] * d.ivth;
             phi[j] = ph;
             chj[j] = lc.Vc[j] * ph * d.Xs[j];
             U[j] = lc.Uc[j] * ph;
@@ -220,15 +233,44 @@ __device__ __forceinline__ void angle_vals(const Smem<R> &s, const LaneC<R, K> &
     eta = d.etabg + ea;
 }
 
-// Sweep one tile (K transitions in its union) downward and upward, adding
-// its rate accumulators.  Per depth and angle the lane forms, without
-// subtracting nearly equal numbers:
+// Warp reduce-scatter of P values (P a power of two): afterwards every lane
+// holds the warp total of value index lane >> (5 - log2 P).
+template <int P, typename R>
+__device__ __forceinline__ R reduce_scatter(R (&v)[P], int lane)
+{
+    int o = 16;
+#pragma unroll
+    for (int n = P; n > 1; n >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            R send = upper ? v[i] : v[i + n / 2];
+            R keep = upper ? v[i + n / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        o >>= 1;
+    }
+    R r = v[0];
+#pragma unroll
+    for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
+template <int M> struct Pow2 { static constexpr int v = M <= 1 ? 1 : (M <= 2 ? 2 : (M <= 4 ? 4 : (M <= 8 ? 8 : (M <= 16 ? 16 : 32)))); };
+template <int P> struct Log2 { static constexpr int v = P <= 1 ? 0 : 1 + Log2<P / 2>::v; };
+template <> struct Log2<1> { static constexpr int v = 0; };
+
+// Sweep one tile (K transitions in its union) for every angle, downward and
+// upward, adding its rate accumulators.  One lane = one wavelength; the
+// angle loop runs outside the depth sweep so the lane state is scalar.  At
+// each depth the lane forms, without subtracting nearly equal numbers,
 //   I_eff = I - Psi* eta_active = I_u e^{-dtau} + w_u S_u + w_o eta_bg/chi,
 //   1 - Psi* chi_j = (1 - w_o) + w_o (chi - chi_j)/chi,
-// and accumulates per slot P = sum w phi (1 - Psi* chi_j), Q = sum w phi
-// I_eff and Y_{j,j'} = sum w phi_j Psi* U_j'.  Accumulators per depth:
-//   up_j = c_j Q_j, down_j = c_j R_j (E_j P_j + Q_j), cross_{j,j'} = c_j X_j Y_{j,j'}.
-template <typename R, int NMU, int K>
+// and its contributions (weight w = w_mu/2):
+//   up_j = c_j w phi_j I_eff,  down_j = c_j R_j w phi_j (E_j (1 - Psi* chi_j) + I_eff),
+//   cross_{j,j'} = c_j X_j w phi_j Psi* U_j';
+// the warp sums them over its wavelengths and lane a adds accumulator a.
+template <typename R, int K>
 __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane)
 {
     const int N = p.N;
@@ -258,114 +300,94 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
     lc.nu3s = lt[kLaneNu3 * npad + pi];
     lc.tw = lt[kLaneTw * npad + pi];
     constexpr int M = K * (K + 1);
+    constexpr int P = Pow2<M>::v;
+    constexpr int SH = 5 - Log2<P>::v;
     R *slot = s.slot + (size_t)tl.acc_off * N;
+    const bool writer = (lane & ((1 << SH) - 1)) == 0;
+    const int widx = lane >> SH;
 
-    for (int dir = 0; dir < 2; ++dir) {
-        const R sgn = dir == 0 ? (R)-1 : (R)1;
-        R I[NMU], chip[NMU], Sp[NMU];
-        R B2 = 0;
-        if (dir == 1) {
-            // the diffusion condition at the bottom needs chi and B one point up
-            DepthC<R, K> d2;
-            depth_consts<R, K>(s, lc, N - 2, N, d2);
-            B2 = d2.B;
-#pragma unroll
-            for (int m = 0; m < NMU; ++m) {
-                if (m >= nmu) break;
+    for (int m = 0; m < nmu; ++m) {
+        const R mu = mu_of<R>(A, m), imu = imu_of<R>(A, m), wm2 = wm2_of<R>(A, m);
+        for (int dir = 0; dir < 2; ++dir) {
+            const R muz = dir == 0 ? -mu : mu;
+            const bool first = m == 0 && dir == 0;
+            R I = 0, chip = 0, Sp = 0, B2 = 0;
+            if (dir == 1) {
+                // the diffusion condition at the bottom needs chi and B one point up
+                DepthC<R, K> d2;
+                depth_consts<R, K>(s, lc, N - 2, N, d2);
+                B2 = d2.B;
                 R phi[K], chj[K], U[K], eta;
-                angle_vals<R, K>(s, lc, d2, sgn * mu_of<R>(A, m), chip[m], eta, phi, chj, U);
+                angle_vals<R, K>(s, lc, d2, muz, chip, eta, phi, chj, U);
             }
-        }
-        for (int step = 0; step < N; ++step) {
-            const int k = dir == 0 ? step : N - 1 - step;
-            DepthC<R, K> d;
-            depth_consts<R, K>(s, lc, k, N, d);
-            R P[K], Q[K], Y[K][K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                P[j] = Q[j] = 0;
-#pragma unroll
-                for (int j2 = 0; j2 < K; ++j2) Y[j][j2] = 0;
-            }
-            const R dzk = step == 0 ? (R)0 : (dir == 0 ? s.dz[k - 1] : s.dz[k]);
-#pragma unroll
-            for (int m = 0; m < NMU; ++m) {
-                if (m >= nmu) break;
-                const R mu = mu_of<R>(A, m);
-                const R wm2 = wm2_of<R>(A, m);
+            for (int step = 0; step < N; ++step) {
+                const int k = dir == 0 ? step : N - 1 - step;
+                DepthC<R, K> d;
+                depth_consts<R, K>(s, lc, k, N, d);
                 R chi, eta, phi[K], chj[K], U[K];
-                angle_vals<R, K>(s, lc, d, sgn * mu, chi, eta, phi, chj, U);
-                const R ichi = (R)1 / chi;
+                angle_vals<R, K>(s, lc, d, muz, chi, eta, phi, chj, U);
+                const R ichi = rcp<R>(chi);
                 const R S = eta * ichi;
                 R psi, Ieff, wo, omwo;
                 if (step == 0) {
                     if (dir == 0) {
-                        I[m] = 0;
+                        I = 0;
                     } else {
-                        R dtv = (R)0.5 * (chi + chip[m]) * s.dz[N - 2];
-                        I[m] = d.B + mu * (d.B - B2) / dtv;
+                        R dtv = (R)0.5 * (chi + chip) * s.dz[N - 2];
+                        I = d.B + mu * (d.B - B2) * rcp<R>(dtv);
                     }
                     psi = 0;
                     wo = 0;
                     omwo = 1;
-                    Ieff = I[m];
+                    Ieff = I;
                 } else {
-                    R dtau = (R)0.5 * (chi + chip[m]) * dzk / mu;
+                    const R dzk = dir == 0 ? s.dz[k - 1] : s.dz[k];
+                    R dtau = (R)0.5 * (chi + chip) * dzk * imu;
                     R ome, wu;
                     sc_weights(dtau, ome, wu, wo, omwo);
-                    R base = I[m] * ome + wu * Sp[m];
-                    I[m] = base + wo * S;
+                    R base = I * ome + wu * Sp;
+                    I = base + wo * S;
                     Ieff = base + wo * (d.etabg * ichi);
                     psi = wo * ichi;
                 }
-                chip[m] = chi;
-                Sp[m] = S;
+                chip = chi;
+                Sp = S;
+                R val[P];
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
                     R other = d.chibg;
 #pragma unroll
                     for (int j2 = 0; j2 < K; ++j2)
                         if (j2 != j) other += chj[j2];
-                    R f = omwo + wo * other * ichi;          // 1 - Psi* chi_j
-                    R wp = wm2 * phi[j];
-                    P[j] += wp * f;
-                    Q[j] += wp * Ieff;
-                    R wpp = wp * psi;
+                    const R f = omwo + wo * other * ichi;          // 1 - Psi* chi_j
+                    const R cw = lc.c[j] * wm2 * phi[j];
+                    val[j] = cw * Ieff;
+                    val[K + j] = cw * d.Rs[j] * (lc.E[j] * f + Ieff);
+                    const R cx = cw * d.Xs[j] * psi;
 #pragma unroll
                     for (int j2 = 0; j2 < K; ++j2)
-                        if (j2 != j) Y[j][j2] += wpp * U[j2];
+                        if (j2 != j) val[2 * K + j * (K - 1) + (j2 < j ? j2 : j2 - 1)] = cx * U[j2];
                 }
-            }
-            R val[M];
 #pragma unroll
-            for (int j = 0; j < K; ++j) {
-                val[j] = lc.c[j] * Q[j];
-                val[K + j] = lc.c[j] * d.Rs[j] * (lc.E[j] * P[j] + Q[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-#pragma unroll
-                for (int j2 = 0; j2 < K; ++j2)
-                    if (j2 != j) val[2 * K + j * (K - 1) + (j2 < j ? j2 : j2 - 1)] = lc.c[j] * d.Xs[j] * Y[j][j2];
-#pragma unroll
-            for (int a = 0; a < M; ++a) {
-                R t = warp_sum(val[a]);
-                if (lane == a) {
-                    if (dir == 0) slot[a * N + k] = t;
-                    else slot[a * N + k] += t;
+                for (int a = M; a < P; ++a) val[a] = 0;
+                const R t = reduce_scatter<P>(val, lane);
+                if (writer && widx < M) {
+                    R *sl = slot + widx * N + k;
+                    if (first) *sl = t;
+                    else *sl += t;
                 }
             }
         }
     }
 }
 
-template <typename R, int NMU>
+template <typename R>
 __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane)
 {
     switch (A.tile[b].K) {
-    case 1: sweep_tile_k<R, NMU, 1>(A, s, p, b, lane); break;
-    case 2: sweep_tile_k<R, NMU, 2>(A, s, p, b, lane); break;
-    default: sweep_tile_k<R, NMU, 3>(A, s, p, b, lane); break;
+    case 1: sweep_tile_k<R, 1>(A, s, p, b, lane); break;
+    case 2: sweep_tile_k<R, 2>(A, s, p, b, lane); break;
+    default: sweep_tile_k<R, 3>(A, s, p, b, lane); break;
     }
 }
 
@@ -471,17 +493,17 @@ __device__ int solve_depth(const DevAtom &A, const double *slotd, const float *s
     return 0;
 }
 
-template <typename R, int NMU>
+template <typename R>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) mali_kernel(const __grid_constant__ DevAtom A, const KParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
     const int N = p.N, L = A.nlev;
     Smem<R> s = carve<R>(smem_raw, L, N, A.ntr, A.ncont, A.nline, A.macc);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int LN = L * N;
     double *hist = p.nghist + (size_t)blockIdx.x * 4 * LN;
 
-    for (int i = tid; i < RH_DAW_N; i += blockDim.x) s.daw[i] = p.daw[i];
+    for (int i = tid; i <= RH_VT_N; i += blockDim.x) s.vtab[i] = p.vtab[i];
     int64_t done = 0;
     for (;;) {
         __syncthreads();
@@ -533,9 +555,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
         for (it = 1; it <= p.maxiter; ++it) {
             double fcr = p.crsw > 1.0 ? fmax(1.0, p.crsw * pow(10.0, -(double)(it - 1))) : 1.0;
             for (int i = tid; i < LN; i += blockDim.x) s.nr[i] = (R)(s.n[i] * p.inv_nref);
+            if (tid == 0) s.ibuf[1] = 0;
             __syncthreads();
-            // ---- formal solution and rate accumulation
-            for (int b = warp; b < A.ntile; b += nwarp) sweep_tile<R, NMU>(A, s, p, b, lane);
+            // ---- formal solution and rate accumulation: warps take tiles from a
+            // block-local queue, most expensive tiles first
+            for (;;) {
+                int q = 0;
+                if (lane == 0) q = atomicAdd(&s.ibuf[1], 1);
+                q = __shfl_sync(0xffffffffu, q, 0);
+                if (q >= A.ntile) break;
+                sweep_tile<R>(A, s, p, A.order[q], lane);
+            }
             __syncthreads();
             // ---- rate equations, one thread per depth
             int bad = 0;
@@ -627,12 +657,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
 
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep) { return sizeof(double) * 4 * A.nlev * ndep; }
 
-template <typename R, int NMU>
+template <typename R>
 static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps, int nsm, size_t cap, cudaStream_t st,
                             float *ms, char *err, size_t errn, int *grid_out)
 {
     size_t sm = smem_bytes<R>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
-    auto kern = mali_kernel<R, NMU>;
+    auto kern = mali_kernel<R>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int threads = block_warps * 32;
@@ -666,7 +696,7 @@ static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps,
     return e;
 }
 
-cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad, const float *daw,
+cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad, const float4 *vtab,
                         double nref, double *nghist, size_t nghist_cap, int *queue, const IterLaunch &o,
                         cudaStream_t st, float *ms_out, int *grid_out, char *err, size_t errn)
 {
@@ -688,7 +718,7 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
     p.status = c.status;
     p.lane = lane_tab;
     p.npad = npad;
-    p.daw = daw;
+    p.vtab = vtab;
     p.nghist = nghist;
     p.queue = queue;
     p.persistent = o.persistent;
@@ -707,14 +737,8 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
     }
-    if (o.precision == 1) {
-        if (A.nmu == 5) return launch_t<float, 5>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
-        if (A.nmu <= 2) return launch_t<float, 2>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
-        return launch_t<float, 8>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
-    }
-    if (A.nmu == 5) return launch_t<double, 5>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
-    if (A.nmu <= 2) return launch_t<double, 2>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
-    return launch_t<double, 8>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+    if (o.precision == 1) return launch_t<float>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+    return launch_t<double>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
 }
 
 }  // namespace rh
@@ -726,7 +750,7 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
 namespace rh {
 
 cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
-                                 const float *daw, double nref, double *nghist, size_t nghist_cap, int *queue,
+                                 const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
                                  const IterLaunch &o, cudaStream_t st, int *grid_out, char *err, size_t errn)
 {
     KParams p;
@@ -747,7 +771,7 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     p.status = c.status;
     p.lane = lane_tab;
     p.npad = npad;
-    p.daw = daw;
+    p.vtab = vtab;
     p.nghist = nghist;
     p.queue = queue;
     p.persistent = o.persistent;
@@ -767,12 +791,10 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     const void *fn;
     if (o.precision == 1) {
         sm = smem_bytes<float>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
-        fn = A.nmu == 5 ? (const void *)mali_kernel<float, 5>
-                        : (A.nmu <= 2 ? (const void *)mali_kernel<float, 2> : (const void *)mali_kernel<float, 8>);
+        fn = (const void *)mali_kernel<float>;
     } else {
         sm = smem_bytes<double>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
-        fn = A.nmu == 5 ? (const void *)mali_kernel<double, 5>
-                        : (A.nmu <= 2 ? (const void *)mali_kernel<double, 2> : (const void *)mali_kernel<double, 8>);
+        fn = (const void *)mali_kernel<double>;
     }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -179,6 +179,20 @@ def test_column_permutation_is_bit_exact(rh, atom, cols):
         assert np.array_equal(a, g1.populations()[0])
 
 
+def test_column_result_independent_of_other_columns(rh, atom, cols):
+    # a column's result (both precisions) does not depend on which other
+    # columns are loaded with it (Sect. 2.2: independent columns)
+    for prec in (1, 0):
+        g = rh.Context(0)
+        g.setup_atom(atom)
+        g.load_columns(cols)
+        g.iterate(maxiter=6 if prec == 0 else 60, tol=1e-3, precision=prec)
+        full = g.populations()[0]
+        g.load_columns({k: v[[2, 5]] for k, v in cols.items()})
+        g.iterate(maxiter=6 if prec == 0 else 60, tol=1e-3, precision=prec)
+        assert np.array_equal(g.populations()[0], full[[2, 5]])
+
+
 def test_invalid_inputs_are_rejected(rh, atom, cols):
     g = rh.Context(0)
     g.setup_atom(atom)
