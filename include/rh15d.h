@@ -117,8 +117,9 @@ typedef struct {
     int32_t ng_order;     /* 0 (off) or 2 (Ng 1974, Sect. 2.3) */
     int32_t ng_delay;     /* first acceleration at this iteration */
     int32_t ng_period;    /* iterations between accelerations */
-    int32_t start;        /* 0: LTE populations; 2: populations set by rh_set_populations
-                             or left by the previous rh_iterate */
+    int32_t start;        /* 0: LTE populations; 1: learned initial guess (rh_surrogate_*),
+                             LTE where its prediction is not finite; 2: populations set by
+                             rh_set_populations or left by the previous rh_iterate */
     int32_t precision;    /* 0: all FP64; 1: FP32 formal solution and rates, FP64 solve and Ng */
     int32_t persistent;   /* 0: static split of columns over resident blocks (normal mode,
                              Sect. 3.1); 1: device work queue (pool mode, Sect. 3.1) */
@@ -137,6 +138,8 @@ typedef struct {
     double seconds;                /* device time of the iteration kernel */
     double pts;                    /* depth x lambda x mu points solved */
     double max_dn_final;           /* max over columns of the last max |dn/n| */
+    int64_t guess_fallback_depths; /* start = 1: depths whose prediction fell back to LTE */
+    double guess_seconds;          /* start = 1: time of the prediction (included in seconds) */
 } rh_iter_stats;
 
 /* Iterate every loaded column to convergence or maxiter.  Writes per-column
@@ -163,6 +166,58 @@ int rh_set_populations(rh_ctx *ctx, const double *n_in);
  * precision as in rh_iter_opts. */
 int rh_emergent_spectrum(rh_ctx *ctx, double mu, int64_t nlambda, const double *lambda_m,
                          double *I_out, int32_t precision, int32_t on_device);
+
+/* ---------------------------------------------------------------------- */
+/* Learned initial guess.  The paper has no such start solution; it shows   */
+/* that the start solution decides the iteration count (Sect. 2.3, Fig. 1) */
+/* and offers LTE, zero radiation and escape probabilities.  This adds a    */
+/* multilayer perceptron that maps a column's atmosphere -- T, log10 n_e,   */
+/* log10 n_H and v_z at every depth, standardised -- to the log departure   */
+/* coefficients ln(n_i/n*_i) at every depth.  It is trained on the GPU, on  */
+/* columns that rh_iterate converged, by the library's own BF16 kernels     */
+/* (tensor-core GEMMs, GELU, mean-squared error, Adam); rh_iterate with     */
+/* start = 1 evaluates it and iterates from the prediction (renormalised so  */
+/* that sum_i n_i = n_H) to the same convergence criterion.                  */
+
+/* Create the network for the loaded columns' depth count: input 4 ndep,    */
+/* nhidden hidden layers of `hidden` units (GELU), output nlev ndep; He-     */
+/* normal weights from `seed`, zero biases.  Replaces an existing network.   */
+int rh_surrogate_init(rh_ctx *ctx, int32_t hidden, int32_t nhidden, uint64_t seed);
+/* Length of the network state in floats: weights and biases layer by layer */
+/* (W [out][in] then b [out]), then the input means and inverse standard    */
+/* deviations [4 ndep] each.  0 if no network exists.                        */
+int64_t rh_surrogate_state_size(const rh_ctx *ctx);
+/* Copy the state out / in (host arrays of rh_surrogate_state_size floats); */
+/* setting resets the optimiser moments.  This is the checkpoint.            */
+int rh_surrogate_get_state(rh_ctx *ctx, float *state_out);
+int rh_surrogate_set_state(rh_ctx *ctx, const float *state_in);
+
+typedef struct {
+    int32_t epochs;          /* passes over the training columns */
+    int32_t batch;           /* columns per optimiser step */
+    float lr;                /* Adam learning rate (cosine-decayed over the run) */
+    float beta1, beta2, eps; /* Adam constants */
+    uint64_t seed;           /* shuffling */
+    int32_t standardise;     /* 1: (re)compute the input standardisation on these columns */
+} rh_train_opts;
+
+typedef struct {
+    double loss_first_epoch, loss_last_epoch;   /* mean squared error of ln b per epoch */
+    int64_t steps, samples;
+    double seconds;
+} rh_train_stats;
+
+/* Train on every loaded column whose status is RH_COL_CONVERGED (targets:  */
+/* ln(n/n*) of its current populations).  RH_ESTATE without a network or   */
+/* without converged columns.                                                */
+int rh_surrogate_train(rh_ctx *ctx, const rh_train_opts *opts, rh_train_stats *stats_out);
+/* Loss and gradient (host, rh_surrogate_state_size floats; the trailing     */
+/* standardisation entries are zero) of the current network on the loaded   */
+/* columns cols[0..ncols) with their current populations as targets.  For  */
+/* checking the training kernels against an independent implementation.    */
+int rh_surrogate_loss_grad(rh_ctx *ctx, int64_t ncols, const int32_t *cols, double *loss_out, float *grad_out);
+/* Raw prediction ln(n/n*) [ncol][nlev][ndep] (host) for every loaded column. */
+int rh_surrogate_predict(rh_ctx *ctx, float *lnb_out);
 
 /* ---------------------------------------------------------------------- */
 /* rh_iterate_noalloc -- the paper has no counterpart to this call; it      */

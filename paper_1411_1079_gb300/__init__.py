@@ -23,7 +23,9 @@ _lib = None
 
 EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlambda", "rh_get_grid",
            "rh_load_columns", "rh_iterate", "rh_get_populations", "rh_get_lte", "rh_set_populations",
-           "rh_emergent_spectrum", "rh_iterate_noalloc")
+           "rh_emergent_spectrum", "rh_iterate_noalloc", "rh_surrogate_init", "rh_surrogate_state_size",
+           "rh_surrogate_get_state", "rh_surrogate_set_state", "rh_surrogate_train", "rh_surrogate_loss_grad",
+           "rh_surrogate_predict")
 
 
 class AtomDesc(C.Structure):
@@ -47,7 +49,18 @@ class IterOpts(C.Structure):
 class IterStats(C.Structure):
     _fields_ = [("n_converged", C.c_int64), ("n_maxiter", C.c_int64), ("n_failed", C.c_int64),
                 ("n_processed", C.c_int64), ("iterations_total", C.c_int64), ("seconds", C.c_double),
-                ("pts", C.c_double), ("max_dn_final", C.c_double)]
+                ("pts", C.c_double), ("max_dn_final", C.c_double), ("guess_fallback_depths", C.c_int64),
+                ("guess_seconds", C.c_double)]
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64), ("standardise", C.c_int32)]
+
+
+class TrainStats(C.Structure):
+    _fields_ = [("loss_first_epoch", C.c_double), ("loss_last_epoch", C.c_double), ("steps", C.c_int64),
+                ("samples", C.c_int64), ("seconds", C.c_double)]
 
 
 def lib(path: str | None = None):
@@ -75,6 +88,15 @@ def lib(path: str | None = None):
         L.rh_set_populations.argtypes = [vp, _dp]
         L.rh_emergent_spectrum.argtypes = [vp, C.c_double, C.c_int64, _dp, vp, C.c_int32, C.c_int32]
         L.rh_iterate_noalloc.argtypes = [vp, C.POINTER(IterOpts), vp, vp, vp, vp, C.POINTER(IterStats)]
+        _fp = C.POINTER(C.c_float)
+        L.rh_surrogate_init.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint64]
+        L.rh_surrogate_state_size.argtypes = [vp]
+        L.rh_surrogate_state_size.restype = C.c_int64
+        L.rh_surrogate_get_state.argtypes = [vp, _fp]
+        L.rh_surrogate_set_state.argtypes = [vp, _fp]
+        L.rh_surrogate_train.argtypes = [vp, C.POINTER(TrainOpts), C.POINTER(TrainStats)]
+        L.rh_surrogate_loss_grad.argtypes = [vp, C.c_int64, _ip, C.POINTER(C.c_double), _fp]
+        L.rh_surrogate_predict.argtypes = [vp, _fp]
         _lib = L
     return _lib
 
@@ -181,12 +203,13 @@ class Context:
     RESCUE_PASSES = (dict(ng_order=0, crsw_init=1e3), dict(ng_order=0, crsw_init=1e5),
                      dict(ng_order=0, crsw_init=1e7))
 
-    def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True):
-        """All columns from LTE with Ng acceleration, then the columns that did
-        not converge again from LTE with collisional-radiative switching
-        (x1e3, x1e5, then x1e7) and without Ng (the paper's two-stage strategy)."""
+    def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True, start=0):
+        """All columns from LTE (start=0) or from the learned guess (start=1)
+        with Ng acceleration, then the columns that did not converge again
+        from LTE with collisional-radiative switching (x1e3, x1e5, then x1e7)
+        and without Ng (the paper's two-stage strategy)."""
         s = self.iterate(maxiter=maxiter, tol=tol, precision=precision, persistent=persistent,
-                         block_warps=block_warps)
+                         block_warps=block_warps, start=start)
         passes = [s]
         if rescue:
             for kw in self.RESCUE_PASSES:
@@ -203,6 +226,41 @@ class Context:
                 "iterations_total": sum(p["iterations_total"] for p in passes),
                 "rerun_columns": sum(p["n_processed"] for p in passes[1:]),
                 "launches": sum(1 for p in passes if p["n_processed"] > 0)}
+
+    # ---- learned initial guess
+    def surrogate_init(self, hidden=512, nhidden=3, seed=0):
+        self._check(self._lib.rh_surrogate_init(self._p, hidden, nhidden, seed))
+
+    def surrogate_state(self):
+        n = int(self._lib.rh_surrogate_state_size(self._p))
+        out = np.zeros(n, np.float32)
+        self._check(self._lib.rh_surrogate_get_state(self._p, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def surrogate_set_state(self, state):
+        state = np.ascontiguousarray(state, dtype=np.float32)
+        self._check(self._lib.rh_surrogate_set_state(self._p, state.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def surrogate_train(self, epochs=20, batch=512, lr=2e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0,
+                        standardise=1) -> dict:
+        o = TrainOpts(epochs=epochs, batch=batch, lr=lr, beta1=beta1, beta2=beta2, eps=eps, seed=seed,
+                      standardise=standardise)
+        s = TrainStats()
+        self._check(self._lib.rh_surrogate_train(self._p, C.byref(o), C.byref(s)))
+        return {f: getattr(s, f) for f, _ in TrainStats._fields_}
+
+    def surrogate_loss_grad(self, cols):
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        loss = C.c_double()
+        grad = np.zeros(int(self._lib.rh_surrogate_state_size(self._p)), np.float32)
+        self._check(self._lib.rh_surrogate_loss_grad(self._p, cols.size, _i(cols), C.byref(loss),
+                                                     grad.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, grad
+
+    def surrogate_predict(self):
+        out = np.zeros((self.ncol, self.nlev, self.ndep), np.float32)
+        self._check(self._lib.rh_surrogate_predict(self._p, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
 
     def iterate_noalloc(self, n_out, iters_out, status_out, dmax_out, maxiter=500, tol=1e-3, ng_order=2,
                         ng_delay=5, ng_period=3, start=0, precision=1, persistent=1, block_warps=0,

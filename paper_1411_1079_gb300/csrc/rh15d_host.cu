@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -64,6 +65,15 @@ struct rh_ctx {
     long long *badidx = nullptr;
     int *colidx = nullptr;
     int64_t colidx_cap = 0;
+    // learned initial guess
+    rh::Mlp *mlp = nullptr;
+    int mlp_ndep = 0;
+    float *feat = nullptr, *tgt = nullptr, *lnb = nullptr;
+    int64_t feat_cap = 0;
+    int *idx_d = nullptr;
+    int64_t idx_cap = 0;
+    int *nfb_d = nullptr;
+    double *loss_d = nullptr;
 };
 
 namespace {
@@ -478,10 +488,182 @@ __global__ void validate_kernel(int64_t ncol, int ndep, const double *z, const d
     if (!ok) atomicMin(bad, (unsigned long long)i);
 }
 
+// feature / target / prediction buffers for the loaded columns
+int ensure_mlp_buffers(rh_ctx *c)
+{
+    const int64_t nin = 4LL * c->ndep, nout = (int64_t)c->da.nlev * c->ndep;
+    if (c->feat_cap < c->ncol) {
+        dfree(c->feat);
+        dfree(c->tgt);
+        dfree(c->lnb);
+        CK(cudaMalloc(&c->feat, c->ncol * nin * sizeof(float)));
+        CK(cudaMalloc(&c->tgt, c->ncol * nout * sizeof(float)));
+        CK(cudaMalloc(&c->lnb, c->ncol * nout * sizeof(float)));
+        c->feat_cap = c->ncol;
+    }
+    if (!c->nfb_d) CK(cudaMalloc(&c->nfb_d, sizeof(int)));
+    if (!c->loss_d) CK(cudaMalloc(&c->loss_d, sizeof(double)));
+    return RH_OK;
+}
+
+int ensure_idx(rh_ctx *c, int64_t n)
+{
+    if (n > c->idx_cap) {
+        dfree(c->idx_d);
+        CK(cudaMalloc(&c->idx_d, n * sizeof(int)));
+        c->idx_cap = n;
+    }
+    return RH_OK;
+}
+
 }  // namespace
 
 // ============================================================================
 extern "C" {
+
+int rh_surrogate_init(rh_ctx *c, int32_t hidden, int32_t nhidden, uint64_t seed)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "rh_surrogate_init: load columns first (the network size follows ndep)");
+    if (hidden < 8 || hidden > 4096 || nhidden < 1 || nhidden > 8)
+        return fail(c, RH_EINVAL, "rh_surrogate_init: hidden in 8..4096, nhidden in 1..8");
+    cudaSetDevice(c->dev);
+    if (c->mlp) mlp_destroy(c->mlp);
+    c->mlp = nullptr;
+    CK(mlp_create(&c->mlp, 4 * c->ndep, hidden, nhidden, c->da.nlev * c->ndep, seed));
+    c->mlp_ndep = c->ndep;
+    return RH_OK;
+}
+
+int64_t rh_surrogate_state_size(const rh_ctx *c) { return (c && c->mlp) ? mlp_state_size(c->mlp) : 0; }
+
+int rh_surrogate_get_state(rh_ctx *c, float *out)
+{
+    if (!c || !out) return RH_EINVAL;
+    if (!c->mlp) return fail(c, RH_ESTATE, "no surrogate");
+    cudaSetDevice(c->dev);
+    CK(mlp_get_state(c->mlp, out));
+    return RH_OK;
+}
+
+int rh_surrogate_set_state(rh_ctx *c, const float *in)
+{
+    if (!c || !in) return RH_EINVAL;
+    if (!c->mlp) return fail(c, RH_ESTATE, "no surrogate (rh_surrogate_init first)");
+    for (int64_t i = 0; i < mlp_state_size(c->mlp); ++i)
+        if (!std::isfinite(in[i])) return fail(c, RH_EINVAL, "surrogate state entry %lld is not finite", (long long)i);
+    cudaSetDevice(c->dev);
+    CK(mlp_set_state(c->mlp, in));
+    return RH_OK;
+}
+
+int rh_surrogate_train(rh_ctx *c, const rh_train_opts *o, rh_train_stats *st)
+{
+    if (!c || !o) return RH_EINVAL;
+    if (!c->mlp || c->mlp_ndep != c->ndep) return fail(c, RH_ESTATE, "rh_surrogate_train: no surrogate for these columns");
+    if (o->epochs < 1 || o->batch < 1 || !(o->lr > 0) || !(o->beta1 >= 0 && o->beta1 < 1) ||
+        !(o->beta2 >= 0 && o->beta2 < 1) || !(o->eps > 0))
+        return fail(c, RH_EINVAL, "rh_surrogate_train: invalid options");
+    cudaSetDevice(c->dev);
+    std::vector<uint8_t> stt(c->ncol);
+    CK(cudaMemcpy(stt.data(), c->ca.status, c->ncol, cudaMemcpyDeviceToHost));
+    std::vector<int> rows;
+    for (int64_t i = 0; i < c->ncol; ++i)
+        if (stt[i] == RH_COL_CONVERGED) rows.push_back((int)i);
+    if (rows.empty()) return fail(c, RH_ESTATE, "rh_surrogate_train: no converged columns to learn from");
+    int r = ensure_mlp_buffers(c);
+    if (r) return r;
+    const int64_t nr = (int64_t)rows.size();
+    r = ensure_idx(c, std::max<int64_t>(nr, o->batch));
+    if (r) return r;
+    const auto t0 = std::chrono::steady_clock::now();
+    CK(mlp_features(c->ca, c->feat, c->st));
+    CK(mlp_targets(c->ca, c->da.nlev, c->tgt, c->st));
+    if (o->standardise) {
+        CK(cudaMemcpyAsync(c->idx_d, rows.data(), nr * sizeof(int), cudaMemcpyHostToDevice, c->st));
+        CK(mlp_set_standardisation(c->mlp, c->feat, c->idx_d, nr, c->st));
+    }
+    std::mt19937_64 rng(o->seed);
+    const int64_t B = std::min<int64_t>(o->batch, nr);
+    const int64_t per_epoch = nr / B;
+    const int64_t total = per_epoch * o->epochs;
+    rh_train_stats S{};
+    int64_t step = 0;
+    std::vector<int> perm(rows);
+    for (int ep = 0; ep < o->epochs; ++ep) {
+        std::shuffle(perm.begin(), perm.end(), rng);
+        CK(cudaMemcpyAsync(c->idx_d, perm.data(), per_epoch * B * sizeof(int), cudaMemcpyHostToDevice, c->st));
+        double esum = 0.0;
+        for (int64_t b = 0; b < per_epoch; ++b, ++step) {
+            CK(mlp_loss_grad(c->mlp, B, c->feat, c->tgt, c->idx_d + b * B, c->loss_d, c->st));
+            double loss = 0.0;
+            CK(cudaMemcpyAsync(&loss, c->loss_d, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+            float lr = (float)(o->lr * 0.5 * (1.0 + std::cos(3.14159265358979 * (double)step / (double)total)));
+            CK(mlp_adam(c->mlp, lr, o->beta1, o->beta2, o->eps, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            if (!std::isfinite(loss)) return fail(c, RH_ENOTCONV, "rh_surrogate_train: loss is not finite at step %lld",
+                                                  (long long)step);
+            esum += loss;
+        }
+        double em = esum / (double)per_epoch;
+        if (ep == 0) S.loss_first_epoch = em;
+        S.loss_last_epoch = em;
+    }
+    S.steps = step;
+    S.samples = step * B;
+    S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (st) *st = S;
+    return RH_OK;
+}
+
+int rh_surrogate_loss_grad(rh_ctx *c, int64_t ncols, const int32_t *cols, double *loss_out, float *grad_out)
+{
+    if (!c || !cols || ncols < 1) return RH_EINVAL;
+    if (!c->mlp || c->mlp_ndep != c->ndep) return fail(c, RH_ESTATE, "no surrogate for these columns");
+    for (int64_t i = 0; i < ncols; ++i)
+        if (cols[i] < 0 || cols[i] >= c->ncol) return fail(c, RH_EINVAL, "column index %d out of range", cols[i]);
+    cudaSetDevice(c->dev);
+    int r = ensure_mlp_buffers(c);
+    if (r) return r;
+    r = ensure_idx(c, ncols);
+    if (r) return r;
+    CK(mlp_features(c->ca, c->feat, c->st));
+    CK(mlp_targets(c->ca, c->da.nlev, c->tgt, c->st));
+    CK(cudaMemcpyAsync(c->idx_d, cols, ncols * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CK(mlp_loss_grad(c->mlp, ncols, c->feat, c->tgt, c->idx_d, c->loss_d, c->st));
+    double loss = 0.0;
+    CK(cudaMemcpyAsync(&loss, c->loss_d, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (grad_out) {
+        const int64_t np = mlp_nparams(c->mlp);
+        CK(cudaMemcpyAsync(grad_out, mlp_grad(c->mlp), np * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int64_t i = np; i < mlp_state_size(c->mlp); ++i) grad_out[i] = 0.f;
+    }
+    CK(cudaStreamSynchronize(c->st));
+    if (loss_out) *loss_out = loss;
+    return RH_OK;
+}
+
+int rh_surrogate_predict(rh_ctx *c, float *lnb_out)
+{
+    if (!c || !lnb_out) return RH_EINVAL;
+    if (!c->mlp || c->mlp_ndep != c->ndep) return fail(c, RH_ESTATE, "no surrogate for these columns");
+    cudaSetDevice(c->dev);
+    int r = ensure_mlp_buffers(c);
+    if (r) return r;
+    // prediction into lnb; the populations are restored afterwards
+    double *save = nullptr;
+    const size_t nv = (size_t)c->ncol * c->da.nlev * c->ndep;
+    CK(cudaMalloc(&save, nv * 8));
+    cudaError_t e = cudaMemcpyAsync(save, c->ca.pops, nv * 8, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = mlp_predict_apply(c->mlp, c->ca, c->da.nlev, c->feat, c->lnb, c->nfb_d, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ca.pops, save, nv * 8, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lnb_out, c->lnb, nv * 4, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(save);
+    if (e != cudaSuccess) return fail(c, RH_ECUDA, "rh_surrogate_predict: %s", cudaGetErrorString(e));
+    return RH_OK;
+}
 
 int rh_create(rh_ctx **out, int cuda_device, void *cuda_stream)
 {
@@ -540,6 +722,13 @@ void rh_destroy(rh_ctx *c)
     dfree(c->queue);
     dfree(c->badidx);
     dfree(c->colidx);
+    if (c->mlp) mlp_destroy(c->mlp);
+    dfree(c->feat);
+    dfree(c->tgt);
+    dfree(c->lnb);
+    dfree(c->idx_d);
+    dfree(c->nfb_d);
+    dfree(c->loss_d);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
 }
@@ -637,10 +826,38 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     if (!o) return fail(c, RH_EINVAL, "opts is NULL");
     if (o->maxiter < 1 || !(o->tol >= 0) || (o->ng_order != 0 && o->ng_order != 2) ||
         (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) || (o->precision != 0 && o->precision != 1) ||
-        (o->start != 0 && o->start != 2) || o->block_warps < 0 || o->block_warps > 8 ||
+        (o->start < 0 || o->start > 2) || o->block_warps < 0 || o->block_warps > 8 ||
         (o->only_unconverged != 0 && o->only_unconverged != 1))
         return fail(c, RH_EINVAL, "rh_iterate: invalid options");
     cudaSetDevice(c->dev);
+    int start = o->start;
+    int64_t fallback = 0;
+    double guess_s = 0.0;
+    float guess_ms = 0.f;
+    if (start == 1) {
+        if (!c->mlp || c->mlp_ndep != c->ndep)
+            return fail(c, RH_ESTATE, "rh_iterate: start = 1 needs a surrogate for %d depths (rh_surrogate_init)",
+                        c->ndep);
+        if (o->only_unconverged)
+            return fail(c, RH_EINVAL, "rh_iterate: start = 1 applies to all columns (only_unconverged = 0)");
+        int r = ensure_mlp_buffers(c);
+        if (r) return r;
+        cudaEvent_t g0, g1;
+        CK(cudaEventCreate(&g0));
+        CK(cudaEventCreate(&g1));
+        CK(cudaEventRecord(g0, c->st));
+        CK(mlp_predict_apply(c->mlp, c->ca, c->da.nlev, c->feat, c->lnb, c->nfb_d, c->st));
+        CK(cudaEventRecord(g1, c->st));
+        int nfb = 0;
+        CK(cudaMemcpyAsync(&nfb, c->nfb_d, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        cudaEventElapsedTime(&guess_ms, g0, g1);
+        cudaEventDestroy(g0);
+        cudaEventDestroy(g1);
+        fallback = nfb;
+        guess_s = guess_ms * 1e-3;
+        start = 2;
+    }
     // work list: every column, or the columns not converged so far
     int64_t nwork = c->ncol;
     const int *colidx_d = nullptr;
@@ -676,7 +893,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     il.ng_order = o->ng_order;
     il.ng_delay = o->ng_delay;
     il.ng_period = o->ng_period;
-    il.start = o->start;
+    il.start = start;
     il.tol = o->tol;
     il.crsw = o->crsw_init;
     il.nsm = c->nsm;
@@ -698,7 +915,9 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     CK(cudaMemcpy(s.data(), c->ca.status, c->ncol, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(dm.data(), c->ca.dmax, c->ncol * 8, cudaMemcpyDeviceToHost));
     rh_iter_stats S{};
-    S.seconds = ms * 1e-3;
+    S.seconds = ms * 1e-3 + guess_s;
+    S.guess_seconds = guess_s;
+    S.guess_fallback_depths = fallback;
     S.n_processed = nwork;
     std::vector<char> done(c->ncol, o->only_unconverged ? 0 : 1);
     if (o->only_unconverged) {

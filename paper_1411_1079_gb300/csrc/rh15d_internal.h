@@ -346,4 +346,24 @@ cudaError_t launch_spectrum(const DevAtom &A, const ColumnArrays &c, double mu, 
                             const double *nu_d, const int *nact_d, const int *act_d, const double *spec_d,
                             double *out, int precision, cudaStream_t st);
 
+// learned initial guess (rh15d_mlp.cu)
+struct Mlp;
+cudaError_t mlp_create(Mlp **out, int nin, int hidden, int nhid, int nout, uint64_t seed);
+void mlp_destroy(Mlp *m);
+int64_t mlp_nparams(const Mlp *m);
+int mlp_nin(const Mlp *m);
+int mlp_nout(const Mlp *m);
+int64_t mlp_state_size(const Mlp *m);
+cudaError_t mlp_get_state(const Mlp *m, float *h);
+cudaError_t mlp_set_state(Mlp *m, const float *h);
+cudaError_t mlp_features(const ColumnArrays &c, float *X, cudaStream_t st);
+cudaError_t mlp_targets(const ColumnArrays &c, int L, float *Yt, cudaStream_t st);
+cudaError_t mlp_set_standardisation(Mlp *m, const float *X, const int *idx, int64_t rows, cudaStream_t st);
+cudaError_t mlp_loss_grad(Mlp *m, int64_t rows, const float *X, const float *Yt, const int *idx, double *loss_d,
+                          cudaStream_t st);
+cudaError_t mlp_adam(Mlp *m, float lr, float b1, float b2, float eps, cudaStream_t st);
+const float *mlp_grad(const Mlp *m);
+cudaError_t mlp_predict_apply(Mlp *m, const ColumnArrays &c, int L, float *X, float *lnb, int *nfallback_d,
+                              cudaStream_t st);
+
 }  // namespace rh

@@ -411,3 +411,36 @@ def test_mali_fixed_point_solves_plain_rate_equations_and_newton(orc):
         if np.max(np.abs(dx / x)) < 1e-12:
             break
     assert np.allclose(x.reshape(L, N), n[0], rtol=1e-8)
+
+
+# ---------------------------------------------------------------- surrogate network reference
+def test_mlp_reference_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    nin, hidden, nhidden, nout = 12, 9, 2, 7
+    nwb = sum(di * do + do for di, do in mlp.layer_dims(nin, hidden, nhidden, nout))
+    state = np.concatenate([rng.standard_normal(nwb) * 0.4, rng.standard_normal(nin), rng.uniform(0.5, 2, nin)])
+    X = rng.standard_normal((5, nin))
+    Y = rng.standard_normal((5, nout))
+    dims = (nin, hidden, nhidden, nout)
+    loss, g = mlp.loss_grad(state, dims, X, Y)
+    assert loss == pytest.approx(np.mean((mlp.forward(state, dims, X) - Y) ** 2), rel=1e-14)
+    for i in rng.choice(nwb, 40, replace=False):
+        h = 1e-5
+        sp = state.copy()
+        sp[i] += h
+        sm = state.copy()
+        sm[i] -= h
+        fd = (mlp.loss_grad(sp, dims, X, Y)[0] - mlp.loss_grad(sm, dims, X, Y)[0]) / (2 * h)
+        assert fd == pytest.approx(g[i], rel=1e-6, abs=1e-10)
+    assert np.all(g[nwb:] == 0)
+
+
+def test_mlp_reference_gelu_limits():
+    from oracle import mlp
+    z = np.array([-30.0, -1.0, 0.0, 1.0, 30.0])
+    assert mlp.gelu(z)[2] == 0.0 and mlp.gelu(z)[4] == pytest.approx(30.0) and abs(mlp.gelu(z)[0]) < 1e-150
+    assert mlp.gelu(1.0) == pytest.approx(0.8413447460685429, rel=1e-14)   # Phi(1)
+    h = 1e-6
+    for x in (-2.0, 0.3, 1.7):
+        assert mlp.gelu_grad(x) == pytest.approx((mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h), rel=1e-8)

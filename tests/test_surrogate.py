@@ -1,0 +1,119 @@
+"""Learned initial guess: the CUDA training kernels against the FP64 numpy
+reference (oracle/mlp.py), training on GPU-converged columns, and what the
+trained network gains over the LTE start at equal accuracy."""
+import numpy as np
+import pytest
+
+import rh_synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rh():
+    import paper_1411_1079_gb300 as m
+    m.build()
+    return m
+
+
+def _features_targets(ctx, cols):
+    n, _, _, _ = ctx.populations()
+    ns, ne = ctx.lte()
+    from oracle import mlp
+    X = mlp.features(cols["T"], ne, cols["nH"], cols["vz"])
+    Y = np.log(n / ns).reshape(n.shape[0], -1)
+    return X, Y
+
+
+@pytest.mark.parametrize("hidden,nhidden,ncols", [(64, 2, 96), (512, 3, 256)])
+def test_gpu_gradient_matches_fp64_reference(rh, hidden, nhidden, ncols):
+    from oracle import mlp
+    atom = rh_synth.hydrogen_like_atom()
+    cols = rh_synth.subset(rh_synth.chromosphere_cube(nx=32, ny=32, seed=11), slice(0, ncols))
+    ctx = rh.Context(0)
+    ctx.setup_atom(atom)
+    ctx.load_columns(cols)
+    ctx.iterate(maxiter=25, tol=1e-3, precision=1)        # non-trivial targets ln(n/n*)
+    X, Y = _features_targets(ctx, cols)
+    ctx.surrogate_init(hidden=hidden, nhidden=nhidden, seed=7)
+    state = ctx.surrogate_state().astype(np.float64)
+    nin = X.shape[1]
+    nwb = state.size - 2 * nin
+    state[nwb:nwb + nin] = X.mean(axis=0)
+    state[nwb + nin:] = 1.0 / np.maximum(X.std(axis=0), 1e-12 * (np.abs(X.mean(axis=0)) + 1))
+    ctx.surrogate_set_state(state.astype(np.float32))
+    state32 = ctx.surrogate_state().astype(np.float64)      # the network as the GPU holds it
+    loss_g, grad_g = ctx.surrogate_loss_grad(np.arange(ncols))
+    dims = (nin, hidden, nhidden, Y.shape[1])
+    loss_o, grad_o = mlp.loss_grad(state32, dims, X, Y)
+    gg, go = grad_g[:nwb].astype(np.float64), grad_o[:nwb]
+    cos = gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go))
+    relL2 = np.linalg.norm(gg - go) / np.linalg.norm(go)
+    # BF16 weights and activations against FP64: loss to 1 %, gradient direction
+    assert loss_g == pytest.approx(loss_o, rel=1e-2)
+    assert cos > 0.999 and relL2 < 1e-2, (cos, relL2)
+
+
+def test_training_reduces_iterations_at_equal_accuracy(rh):
+    atom = rh_synth.hydrogen_like_atom()
+    train = rh_synth.chromosphere_cube(nx=64, ny=64, seed=4321)          # disjoint seed
+    ctx = rh.Context(0)
+    ctx.setup_atom(atom)
+    ctx.load_columns(train)
+    s = ctx.solve(precision=1)
+    assert s["n_converged"] > 0.99 * 4096
+    ctx.surrogate_init(hidden=512, nhidden=3, seed=0)
+    t = ctx.surrogate_train(epochs=40, batch=256, lr=2e-3, seed=1)
+    assert t["loss_last_epoch"] < 0.1 * t["loss_first_epoch"], t
+
+    evalc = rh_synth.subset(rh_synth.chromosphere_cube(nx=64, ny=64, seed=99), slice(0, 1024))
+    ctx.load_columns(evalc)
+    s0 = ctx.iterate(maxiter=500, tol=1e-3, precision=1, start=0)
+    it0, st0 = ctx.populations()[1:3]
+    ctx.load_columns(evalc)
+    s1 = ctx.iterate(maxiter=500, tol=1e-3, precision=1, start=1)
+    it1, st1 = ctx.populations()[1:3]
+    assert s1["guess_fallback_depths"] == 0
+    ok = (st0 == 0) & (st1 == 0)
+    assert ok.mean() > 0.99
+    assert it1[ok].mean() < 0.8 * it0[ok].mean(), (it0[ok].mean(), it1[ok].mean())
+
+    # same fixed point from either start
+    ctx.load_columns(evalc)
+    ctx.iterate(maxiter=1000, tol=1e-6, precision=1, start=0)
+    n0, _, a0, _ = ctx.populations()
+    ctx.load_columns(evalc)
+    ctx.iterate(maxiter=1000, tol=1e-6, precision=1, start=1)
+    n1, _, a1, _ = ctx.populations()
+    both = (a0 == 0) & (a1 == 0)
+    assert both.mean() > 0.98
+    assert np.max(np.abs(n1[both] / n0[both] - 1)) < 2e-3
+
+    # checkpoint round trip: the same network in a fresh context predicts the same
+    state = ctx.surrogate_state()
+    pred = ctx.surrogate_predict()
+    ctx2 = rh.Context(0)
+    ctx2.setup_atom(atom)
+    ctx2.load_columns(evalc)
+    ctx2.surrogate_init(hidden=512, nhidden=3, seed=5)
+    ctx2.surrogate_set_state(state)
+    assert np.array_equal(ctx2.surrogate_predict(), pred)
+
+
+def test_surrogate_errors(rh):
+    ctx = rh.Context(0)
+    ctx.setup_atom(rh_synth.small_atom())
+    with pytest.raises(rh.RhError):
+        ctx.surrogate_init()                    # no columns yet
+    ctx.load_columns(rh_synth.subset(rh_synth.chromosphere_cube(nx=16, ny=16, ndep=12, seed=1), [0, 1, 2]))
+    with pytest.raises(rh.RhError) as e:
+        ctx.iterate(start=1)                    # no network
+    assert e.value.code == rh.RH_ESTATE
+    ctx.surrogate_init(hidden=16, nhidden=1, seed=0)
+    with pytest.raises(rh.RhError) as e:
+        ctx.surrogate_train(epochs=1)           # nothing converged yet
+    assert e.value.code == rh.RH_ESTATE
+    bad = ctx.surrogate_state()
+    bad[3] = np.nan
+    with pytest.raises(rh.RhError):
+        ctx.surrogate_set_state(bad)
