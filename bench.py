@@ -2,10 +2,13 @@
 
 Workload: 256x256 = 65536 synthetic chromospheric columns of 82 heights
 (seeded; a stand-in for the paper's 3D MHD snapshot), hydrogen-like 5-level +
-continuum atom, 608 wavelengths, 5 angles; every column iterated from LTE to
-max|dn/n| < 1e-3 with Ng acceleration; FP32 formal solution and rates, FP64
-rate equations and Ng; device work queue over resident blocks.
-One step = one rh_iterate over all columns (inputs resident in HBM).
+continuum atom, 608 wavelengths, 5 angles; every column iterated from the
+learned initial guess to max|dn/n| < 1e-3 with Ng acceleration, columns that
+do not converge re-run from LTE with collisional-radiative switching; FP32
+formal solution and rates, FP64 rate equations and Ng; device work queue over
+resident blocks.  The network is trained before the timed region on a
+disjoint 256x256 cube that the same GPU MALI converged (from LTE).
+One step = one full solve of all columns (inputs resident in HBM).
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
 """
@@ -32,6 +35,8 @@ NX = NY = 256
 NDEP = 82
 TOL = 1e-3
 MAXITER = 500
+TRAIN_SEED = 4321          # training cube (disjoint from the evaluated cube, seed 1234 + rank)
+TRAIN_EPOCHS = 10
 METRIC = "converged columns/s to max|dn/n|<1e-3"
 # FP32 operations per formal-solver point (one depth x lambda x mu, both
 # sweep directions), counted from the kernel source (see the design notes)
@@ -206,9 +211,20 @@ def run_gpu(args):
     ctx = rh.Context(local, stream=stream.cuda_stream)
     atom = rh_synth.hydrogen_like_atom()
     ctx.setup_atom(atom)
+    # learned initial guess: converge a disjoint cube from LTE, train on it (untimed)
+    t0 = time.perf_counter()
+    ctx.load_columns(rh_synth.chromosphere_cube(NX, NY, NDEP, seed=TRAIN_SEED + 7919 * rank))
+    tr_solve = ctx.solve(maxiter=MAXITER, tol=TOL, precision=1)
+    ctx.surrogate_init(hidden=512, nhidden=3, seed=0)
+    tr = ctx.surrogate_train(epochs=TRAIN_EPOCHS, batch=512, lr=2e-3, seed=1)
+    train_info = {"train_columns": ncol, "train_converged": tr_solve["n_converged"],
+                  "epochs": TRAIN_EPOCHS, "loss_first_epoch": tr["loss_first_epoch"],
+                  "loss_last_epoch": tr["loss_last_epoch"], "train_seconds": tr["seconds"],
+                  "data_generation_seconds": time.perf_counter() - t0 - tr["seconds"]}
     dev = {k: torch.from_numpy(v).to("cuda") for k, v in cube.items()}
     ctx.load_columns(dev, on_device=True)
-    opts = dict(maxiter=MAXITER, tol=TOL, precision=1, persistent=1)
+    opts = dict(maxiter=MAXITER, tol=TOL, precision=1, persistent=1, start=1)
+    guess_kernels = 2 + 5 * ((ncol + 16383) // 16384)   # features, per chunk standardise + 4 GEMMs, apply
 
     def barrier():
         torch.cuda.synchronize()
@@ -234,11 +250,19 @@ def run_gpu(args):
             pts += s["pts"]
             iters += s["iterations_total"]
             conv += s["n_converged"]
-            launches += s["launches"]
+            launches += s["launches"] + guess_kernels
             rescued += s["rerun_columns"]
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
+    # the same solve from LTE, for comparison (one step)
+    lte_opts = dict(opts, start=0)
+    barrier()
+    t_l = time.perf_counter()
+    s_l = ctx.solve(**lte_opts)
+    barrier()
+    lte_s = time.perf_counter() - t_l
+    lte_iters = s_l["iterations_total"] / ncol
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -269,6 +293,23 @@ def run_gpu(args):
     e2e = {"value": ws * ncol * args.steps / e2e_s, "unit": "columns/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h + ncol * (4 + 1 + 8)}
 
+    # plain FP64 MALI from LTE on a random sample of the cube (FP64 arithmetic is
+    # slow on this part: one column per SM keeps the run under a minute)
+    fp64 = None
+    if args.fp64_columns > 0:
+        rng = np.random.default_rng(99)
+        idx = np.sort(rng.choice(ncol, size=min(args.fp64_columns, ncol), replace=False))
+        ctx.load_columns(rh_synth.subset(cube, idx))
+        barrier()
+        t_f = time.perf_counter()
+        s_f = ctx.iterate(maxiter=MAXITER, tol=TOL, precision=0, persistent=1)
+        barrier()
+        f_s = time.perf_counter() - t_f
+        fp64 = {"value": s_f["n_converged"] / f_s, "unit": "columns/s", "columns": len(idx),
+                "converged": s_f["n_converged"], "seconds": f_s,
+                "iterations_per_column": s_f["iterations_total"] / len(idx),
+                "sample": "%d random columns of the cube, LTE start, FP64 throughout, one pass" % len(idx)}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -285,15 +326,21 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "256x256 synthetic chromosphere cube (65536 columns), 82 heights, "
-                               "H-like 5-level+continuum atom, 608 wavelengths, 5 mu, tol 1e-3, LTE start",
+                               "H-like 5-level+continuum atom, 608 wavelengths, 5 mu, tol 1e-3, "
+                               "learned initial guess (MLP 328-512-512-512-492, BF16, trained on a disjoint "
+                               "GPU-converged cube)",
                    "ncol_per_gpu": ncol, "ndep": NDEP, "nlambda": ctx.nlambda, "nmu": atom["nmu"],
                    "precision": "fp32 formal solution/rates, fp64 rate equations/Ng",
                    "scheduling": "device work queue (pool mode); columns not converged are re-run "
-                                 "from LTE with collisional-radiative switching x1e3, no Ng",
+                                 "from LTE with collisional-radiative switching x1e3/x1e5/x1e7, no Ng",
                    "l2": "working set 2 GB > L2 (inputs larger than L2)",
                    "parallelism": "dp%d (independent columns)" % ws},
         "formal_solver_pts_per_s": pts_s,
         "iterations_per_column": iters / (ncol * args.steps),
+        "lte_start": {"value": ncol / lte_s, "unit": "columns/s", "iterations_per_column": lte_iters,
+                      "precision": "fp32 formal solution/rates, fp64 rate equations/Ng"},
+        "lte_start_fp64": fp64,
+        "surrogate": train_info,
         "converged_fraction": conv / (ncol * args.steps),
         "rerun_columns_per_step": rescued / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
@@ -328,6 +375,8 @@ def run_ncu_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profiler captures")
+    ap.add_argument("--fp64-columns", type=int, default=152,
+                    help="columns of the plain FP64 LTE-start comparison (0: skip)")
     ap.add_argument("--ncu-columns", type=int, default=608)
     ap.add_argument("--ncu-precision", type=int, default=1)
     ap.add_argument("--gpus", type=int, default=1)
