@@ -149,6 +149,23 @@ __host__ __device__ inline double voigt_f64(double a, double v)
     return (-si * zr + sr * zi) / (kSqrtPi * mz) + exp(zi * zi - zr * zr) * cos(2.0 * zr * zi);
 }
 
+// FP32 reciprocal for the sweep: the hardware approximation (rcp.approx, about
+// 1 ulp, denormals flushed; no operand of the sweep is denormal) unless
+// RH_RCP_APPROX is 0, then the correctly rounded __frcp_rn.
+#ifndef RH_RCP_APPROX
+#define RH_RCP_APPROX 1
+#endif
+__device__ __forceinline__ float rcp_f32(float x)
+{
+#if RH_RCP_APPROX
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+#else
+    return __frcp_rn(x);
+#endif
+}
+
 // Coefficients of the expansion of H(a, v) in the damping a used by the FP32
 // Voigt function: H = e^{-v^2}[1 + a^2(1 - 2v^2) + a^4(2v^4/3 - 2v^2 + 1/2)]
 //                     + a H1(v) + a^3 H3(v),
@@ -194,7 +211,7 @@ __device__ __forceinline__ float voigt_f32(float a, float v, const float4 *__res
     float av = fabsf(v);
     float v2 = av * av;
     float g = __expf(-v2);
-    float t = __frcp_rn(1.0f + av);
+    float t = rcp_f32(1.0f + av);
     float x = t * (float)RH_VT_N;
     int i = min((int)x, RH_VT_N - 1);
     float f = x - (float)i;
@@ -254,7 +271,7 @@ __device__ __forceinline__ void sc_weights(float d, float &one_m_e0, float &wu, 
         one_m_e0 = 1.0f - e0;
     } else {
         float ex = __expf(-d);
-        float inv = __frcp_rn(d);
+        float inv = rcp_f32(d);
         omwo = (1.0f - ex) * inv;
         wo = 1.0f - omwo;
         wu = omwo - ex;

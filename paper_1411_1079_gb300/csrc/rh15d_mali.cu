@@ -4,12 +4,13 @@
 // MALI iterations with the column's state in shared memory: populations
 // (FP64), collisional rates (FP64), per-depth atmosphere scalars, and the
 // rate accumulators.  Per iteration:
-//   1. every warp takes 32-wavelength tiles of the grid; each lane owns one
-//      wavelength and sweeps depth downward and then upward for all angles mu
-//      at once (linear short characteristics, intensity and local operator in
-//      registers); at every depth the lane forms its contributions to the
-//      preconditioned rate matrix (Rybicki & Hummer 1992), the warp reduces
-//      them with shuffles, and lane j adds accumulator j of the tile;
+//   1. warps take 32-wavelength tiles of the grid from a block-local queue;
+//      each lane owns one wavelength and, one angle mu at a time, sweeps depth
+//      downward and then upward (linear short characteristics, intensity and
+//      local operator in registers); at every depth the lane forms its
+//      contributions to the preconditioned rate matrix (Rybicki & Hummer
+//      1992), the warp reduce-scatters them with shuffles, and one lane per
+//      value adds it to the tile's accumulator;
 //   2. one thread per depth assembles the rate matrix from the accumulators
 //      (FP64) plus collisions and solves the rate equations (FP64, scaled
 //      unknowns, partial pivoting);
@@ -116,7 +117,7 @@ template <>
 __device__ __forceinline__ double voigt<double>(double a, double v, const float4 *) { return voigt_f64(a, v); }
 
 template <typename R> __device__ __forceinline__ R rcp(R x);
-template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ float rcp<float>(float x) { return rcp_f32(x); }
 template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 
 // 1 - exp(-x) for x > 0: FP32 uses 1 - __expf(-x) (x = h nu / kT > 0.1 on every grid here,
@@ -306,21 +307,69 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
     const bool writer = (lane & ((1 << SH) - 1)) == 0;
     const int widx = lane >> SH;
 
+    // contributions of one depth point to the tile's accumulators
+    auto emit = [&](int k, const DepthC<R, K> &d, const R (&phi)[K], const R (&chj)[K], const R (&U)[K], R ichi,
+                    R wo, R omwo, R psi, R Ieff, R wm2, bool first) {
+        R val[P];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            R other = d.chibg;
+#pragma unroll
+            for (int j2 = 0; j2 < K; ++j2)
+                if (j2 != j) other += chj[j2];
+            const R f = omwo + wo * other * ichi;          // 1 - Psi* chi_j
+            const R cw = lc.c[j] * wm2 * phi[j];
+            val[j] = cw * Ieff;
+            val[K + j] = cw * d.Rs[j] * (lc.E[j] * f + Ieff);
+            const R cx = cw * d.Xs[j] * psi;
+#pragma unroll
+            for (int j2 = 0; j2 < K; ++j2)
+                if (j2 != j) val[2 * K + j * (K - 1) + (j2 < j ? j2 : j2 - 1)] = cx * U[j2];
+        }
+#pragma unroll
+        for (int a = M; a < P; ++a) val[a] = 0;
+        const R t = reduce_scatter<P>(val, lane);
+        if (writer && widx < M) {
+            R *sl = slot + widx * N + k;
+            if (first) *sl = t;
+            else *sl += t;
+        }
+    };
+
     for (int m = 0; m < nmu; ++m) {
         const R mu = mu_of<R>(A, m), imu = imu_of<R>(A, m), wm2 = wm2_of<R>(A, m);
         for (int dir = 0; dir < 2; ++dir) {
             const R muz = dir == 0 ? -mu : mu;
             const bool first = m == 0 && dir == 0;
-            R I = 0, chip = 0, Sp = 0, B2 = 0;
-            if (dir == 1) {
-                // the diffusion condition at the bottom needs chi and B one point up
-                DepthC<R, K> d2;
-                depth_consts<R, K>(s, lc, N - 2, N, d2);
-                B2 = d2.B;
-                R phi[K], chj[K], U[K], eta;
-                angle_vals<R, K>(s, lc, d2, muz, chip, eta, phi, chj, U);
+            R I, chip = 0, Sp;
+            {
+                // boundary point: I = 0 at the top; at the bottom the diffusion
+                // condition, which needs chi and B one point up
+                const int k0 = dir == 0 ? 0 : N - 1;
+                R B2 = 0;
+                if (dir == 1) {
+                    DepthC<R, K> d2;
+                    depth_consts<R, K>(s, lc, N - 2, N, d2);
+                    B2 = d2.B;
+                    R phi[K], chj[K], U[K], eta;
+                    angle_vals<R, K>(s, lc, d2, muz, chip, eta, phi, chj, U);
+                }
+                DepthC<R, K> d;
+                depth_consts<R, K>(s, lc, k0, N, d);
+                R chi, eta, phi[K], chj[K], U[K];
+                angle_vals<R, K>(s, lc, d, muz, chi, eta, phi, chj, U);
+                const R ichi = rcp<R>(chi);
+                if (dir == 0) {
+                    I = 0;
+                } else {
+                    R dtv = (R)0.5 * (chi + chip) * s.dz[N - 2];
+                    I = d.B + mu * (d.B - B2) * rcp<R>(dtv);
+                }
+                chip = chi;
+                Sp = eta * ichi;
+                emit(k0, d, phi, chj, U, ichi, (R)0, (R)1, (R)0, I, wm2, first);
             }
-            for (int step = 0; step < N; ++step) {
+            for (int step = 1; step < N; ++step) {
                 const int k = dir == 0 ? step : N - 1 - step;
                 DepthC<R, K> d;
                 depth_consts<R, K>(s, lc, k, N, d);
@@ -328,54 +377,17 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 angle_vals<R, K>(s, lc, d, muz, chi, eta, phi, chj, U);
                 const R ichi = rcp<R>(chi);
                 const R S = eta * ichi;
-                R psi, Ieff, wo, omwo;
-                if (step == 0) {
-                    if (dir == 0) {
-                        I = 0;
-                    } else {
-                        R dtv = (R)0.5 * (chi + chip) * s.dz[N - 2];
-                        I = d.B + mu * (d.B - B2) * rcp<R>(dtv);
-                    }
-                    psi = 0;
-                    wo = 0;
-                    omwo = 1;
-                    Ieff = I;
-                } else {
-                    const R dzk = dir == 0 ? s.dz[k - 1] : s.dz[k];
-                    R dtau = (R)0.5 * (chi + chip) * dzk * imu;
-                    R ome, wu;
-                    sc_weights(dtau, ome, wu, wo, omwo);
-                    R base = I * ome + wu * Sp;
-                    I = base + wo * S;
-                    Ieff = base + wo * (d.etabg * ichi);
-                    psi = wo * ichi;
-                }
+                const R dzk = dir == 0 ? s.dz[k - 1] : s.dz[k];
+                const R dtau = (R)0.5 * (chi + chip) * dzk * imu;
+                R ome, wu, wo, omwo;
+                sc_weights(dtau, ome, wu, wo, omwo);
+                const R base = I * ome + wu * Sp;
+                I = base + wo * S;
+                const R Ieff = base + wo * (d.etabg * ichi);
+                const R psi = wo * ichi;
                 chip = chi;
                 Sp = S;
-                R val[P];
-#pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    R other = d.chibg;
-#pragma unroll
-                    for (int j2 = 0; j2 < K; ++j2)
-                        if (j2 != j) other += chj[j2];
-                    const R f = omwo + wo * other * ichi;          // 1 - Psi* chi_j
-                    const R cw = lc.c[j] * wm2 * phi[j];
-                    val[j] = cw * Ieff;
-                    val[K + j] = cw * d.Rs[j] * (lc.E[j] * f + Ieff);
-                    const R cx = cw * d.Xs[j] * psi;
-#pragma unroll
-                    for (int j2 = 0; j2 < K; ++j2)
-                        if (j2 != j) val[2 * K + j * (K - 1) + (j2 < j ? j2 : j2 - 1)] = cx * U[j2];
-                }
-#pragma unroll
-                for (int a = M; a < P; ++a) val[a] = 0;
-                const R t = reduce_scatter<P>(val, lane);
-                if (writer && widx < M) {
-                    R *sl = slot + widx * N + k;
-                    if (first) *sl = t;
-                    else *sl += t;
-                }
+                emit(k, d, phi, chj, U, ichi, wo, omwo, psi, Ieff, wm2, first);
             }
         }
     }
