@@ -39,8 +39,11 @@ TRAIN_SEED = 4321          # training cube (disjoint from the evaluated cube, se
 TRAIN_EPOCHS = 10
 METRIC = "converged columns/s to max|dn/n|<1e-3"
 # FP32 operations per formal-solver point (one depth x lambda x mu, both
-# sweep directions), counted from the kernel source (see the design notes)
-FLOP_PER_PT = 264
+# sweep directions): thread-level FP32 operations of the column kernel
+# (2 x FFMA + FADD + FMUL, predicated-on threads) counted by ncu on 608 cube
+# columns x 3 iterations, divided by their points; re-counted whenever the
+# kernel changes
+FLOP_PER_PT = 287
 
 
 def _peaks():
@@ -243,6 +246,9 @@ def run_gpu(args):
     launches = 0
     rescued = 0
     with ClockSampler(local) as clk:
+        # profiler range = the timed region (no effect without a profiler;
+        # ncu --profile-from-start off lists exactly these launches)
+        torch.cuda.profiler.start()
         e0.record(stream)
         for _ in range(args.steps):
             s = ctx.solve(**opts)
@@ -254,6 +260,7 @@ def run_gpu(args):
             rescued += s["rerun_columns"]
         e1.record(stream)
         barrier()
+        torch.cuda.profiler.stop()
     ms = e0.elapsed_time(e1)
     # the same solve from LTE, for comparison (one step)
     lte_opts = dict(opts, start=0)
