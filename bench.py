@@ -227,7 +227,6 @@ def run_gpu(args):
     dev = {k: torch.from_numpy(v).to("cuda") for k, v in cube.items()}
     ctx.load_columns(dev, on_device=True)
     opts = dict(maxiter=MAXITER, tol=TOL, precision=1, persistent=1, start=1)
-    guess_kernels = 2 + 5 * ((ncol + 16383) // 16384)   # features, per chunk standardise + 4 GEMMs, apply
 
     def barrier():
         torch.cuda.synchronize()
@@ -256,7 +255,7 @@ def run_gpu(args):
             pts += s["pts"]
             iters += s["iterations_total"]
             conv += s["n_converged"]
-            launches += s["launches"] + guess_kernels
+            launches += s["launches"]
             rescued += s["rerun_columns"]
         e1.record(stream)
         barrier()
@@ -348,6 +347,9 @@ def run_gpu(args):
                       "precision": "fp32 formal solution/rates, fp64 rate equations/Ng"},
         "lte_start_fp64": fp64,
         "surrogate": train_info,
+        "launch": {"block_warps": s["block_warps"], "ctas_per_sm": s["ctas_per_sm"],
+                   "cuda_graph_replayed": s["graph_replayed"], "kernels_per_step": s["launches"],
+                   "shape_from": "rh_autotune on the loaded cube"},
         "converged_fraction": conv / (ncol * args.steps),
         "rerun_columns_per_step": rescued / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",

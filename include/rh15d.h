@@ -148,6 +148,78 @@ typedef struct {
  * converge (results are still valid for the converged ones). */
 int rh_iterate(rh_ctx *ctx, const rh_iter_opts *opts, rh_iter_stats *stats_out);
 
+/* ---------------------------------------------------------------------- */
+/* The paper's two-stage strategy as one call (Sect. 2.3: aggressive       */
+/* options first, then the columns that did not converge again with other  */
+/* options).  Pass 1 iterates every column with `pass1` (start 0, 1 or 2;  */
+/* only_unconverged is ignored).  Then, for r = 0 .. nrerun-1, the columns  */
+/* whose status is not RH_COL_CONVERGED are iterated again from LTE without */
+/* Ng, with collisional-radiative switching factor rerun_crsw[r] and        */
+/* rerun_maxiter iterations -- inside the column kernel (fused_rerun = 1)   */
+/* or as separate passes over a device-selected list.  No host round trip   */
+/* happens between the passes.                                             */
+/* use_graph = 1: the whole sequence (learned guess, pass 1, selections,    */
+/* re-run passes, counters) is captured into a CUDA graph on the first call */
+/* and the instantiated graph is replayed by later calls while the loaded   */
+/* columns, the options, the lane table and the network are the same        */
+/* objects; it is re-captured otherwise.  The context's stream must not be  */
+/* the legacy default stream for capture (rh_create with NULL makes its own */
+/* stream).  autotune = 1: before the first solve for this precision,       */
+/* rh_autotune runs on the loaded columns (unless a tuning is present) and   */
+/* its choice is used whenever pass1.block_warps is 0.                       */
+/* Returns RH_OK, or RH_ENOTCONV if columns remain unconverged after all     */
+/* passes (their results are those of the last pass that iterated them).    */
+#define RH_MAX_RERUN 4
+typedef struct {
+    rh_iter_opts pass1;
+    int32_t nrerun;                    /* 0 .. RH_MAX_RERUN */
+    int32_t rerun_maxiter;             /* iterations of each re-run pass (>= 1) */
+    double rerun_crsw[RH_MAX_RERUN];   /* switching factor of each re-run pass (> 1) */
+    int32_t use_graph;                 /* 1: capture / replay a CUDA graph */
+    int32_t autotune;                  /* 1: tune the launch shape once (see rh_autotune) */
+    int32_t fused_rerun;               /* 1: the column kernel runs the re-run ladder itself: a block
+                                          whose column does not converge restarts it at once with the
+                                          next re-run options, overlapping the rest of pass 1 (same
+                                          per-column results as separate passes); 0: one kernel
+                                          launch per pass, the selection done by a device kernel */
+} rh_solve_opts;
+
+typedef struct {
+    int64_t n_converged, n_maxiter, n_failed;  /* after all passes */
+    int64_t iterations_total;          /* formal solutions over all passes */
+    int64_t pass_columns[1 + RH_MAX_RERUN];    /* columns entering each pass */
+    int64_t pass_iterations[1 + RH_MAX_RERUN]; /* formal solutions of each pass */
+    double seconds;                    /* device time of the whole sequence */
+    double pass_seconds[1 + RH_MAX_RERUN]; /* device time of each pass (pass 1 includes the guess;
+                                          with fused_rerun the re-runs are inside pass 1) */
+    double pts;                        /* depth x lambda x mu points solved */
+    int64_t guess_fallback_depths;     /* start = 1: depths that fell back to LTE */
+    int32_t kernel_launches;           /* kernels launched by the sequence */
+    int32_t graph_replayed;            /* 1: an instantiated graph was replayed */
+    int32_t block_warps, ctas_per_sm;  /* launch shape used for the column kernel */
+} rh_solve_stats;
+
+int rh_solve(rh_ctx *ctx, const rh_solve_opts *opts, rh_solve_stats *stats_out);
+
+/* Launch-shape autotuner for the column kernel (the ray tile is fixed at   */
+/* 32 wavelengths x 1 angle per warp; what is tuned is the warps per column */
+/* block and the column blocks resident per SM).  Times every candidate on  */
+/* up to 4 x SMs of the loaded columns for 2 iterations from LTE in         */
+/* `precision`, restores those columns' populations and results, and keeps  */
+/* the fastest for that precision in the context (dropped by rh_setup_atom  */
+/* and by rh_load_columns with another ndep).  cand_* receive up to          */
+/* RH_MAX_TUNE candidates (ms = -1: did not fit).                            */
+#define RH_MAX_TUNE 8
+typedef struct {
+    int32_t best_block_warps, best_ctas_per_sm;
+    int32_t ncand;
+    int32_t cand_block_warps[RH_MAX_TUNE], cand_ctas_per_sm[RH_MAX_TUNE];
+    double cand_ms[RH_MAX_TUNE];       /* device time of the candidate's run */
+    int64_t sample_columns;
+} rh_tune_result;
+
+int rh_autotune(rh_ctx *ctx, int32_t precision, rh_tune_result *out);
+
 /* Copy results to host arrays (any pointer may be NULL):
  * n_out [ncol][nlev][ndep] m^-3, iters [ncol], status [ncol] (RH_COL_*),
  * dmax [ncol].  n_out may also be a device pointer when on_device = 1. */

@@ -25,7 +25,10 @@ EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlam
            "rh_load_columns", "rh_iterate", "rh_get_populations", "rh_get_lte", "rh_set_populations",
            "rh_emergent_spectrum", "rh_iterate_noalloc", "rh_surrogate_init", "rh_surrogate_state_size",
            "rh_surrogate_get_state", "rh_surrogate_set_state", "rh_surrogate_train", "rh_surrogate_loss_grad",
-           "rh_surrogate_predict")
+           "rh_surrogate_predict", "rh_solve", "rh_autotune")
+
+MAX_RERUN = 4
+MAX_TUNE = 8
 
 
 class AtomDesc(C.Structure):
@@ -51,6 +54,27 @@ class IterStats(C.Structure):
                 ("n_processed", C.c_int64), ("iterations_total", C.c_int64), ("seconds", C.c_double),
                 ("pts", C.c_double), ("max_dn_final", C.c_double), ("guess_fallback_depths", C.c_int64),
                 ("guess_seconds", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("pass1", IterOpts), ("nrerun", C.c_int32), ("rerun_maxiter", C.c_int32),
+                ("rerun_crsw", C.c_double * MAX_RERUN), ("use_graph", C.c_int32), ("autotune", C.c_int32),
+                ("fused_rerun", C.c_int32)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("n_converged", C.c_int64), ("n_maxiter", C.c_int64), ("n_failed", C.c_int64),
+                ("iterations_total", C.c_int64), ("pass_columns", C.c_int64 * (1 + MAX_RERUN)),
+                ("pass_iterations", C.c_int64 * (1 + MAX_RERUN)), ("seconds", C.c_double),
+                ("pass_seconds", C.c_double * (1 + MAX_RERUN)), ("pts", C.c_double),
+                ("guess_fallback_depths", C.c_int64), ("kernel_launches", C.c_int32),
+                ("graph_replayed", C.c_int32), ("block_warps", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("best_block_warps", C.c_int32), ("best_ctas_per_sm", C.c_int32), ("ncand", C.c_int32),
+                ("cand_block_warps", C.c_int32 * MAX_TUNE), ("cand_ctas_per_sm", C.c_int32 * MAX_TUNE),
+                ("cand_ms", C.c_double * MAX_TUNE), ("sample_columns", C.c_int64)]
 
 
 class TrainOpts(C.Structure):
@@ -88,6 +112,8 @@ def lib(path: str | None = None):
         L.rh_set_populations.argtypes = [vp, _dp]
         L.rh_emergent_spectrum.argtypes = [vp, C.c_double, C.c_int64, _dp, vp, C.c_int32, C.c_int32]
         L.rh_iterate_noalloc.argtypes = [vp, C.POINTER(IterOpts), vp, vp, vp, vp, C.POINTER(IterStats)]
+        L.rh_solve.argtypes = [vp, C.POINTER(SolveOpts), C.POINTER(SolveStats)]
+        L.rh_autotune.argtypes = [vp, C.c_int32, C.POINTER(TuneResult)]
         _fp = C.POINTER(C.c_float)
         L.rh_surrogate_init.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint64]
         L.rh_surrogate_state_size.argtypes = [vp]
@@ -200,32 +226,51 @@ class Context:
 
     # Sect. 2.3: run all columns with an aggressive choice of options, then
     # re-run the columns that did not converge with other options.
-    RESCUE_PASSES = (dict(ng_order=0, crsw_init=1e3), dict(ng_order=0, crsw_init=1e5),
-                     dict(ng_order=0, crsw_init=1e7))
+    RERUN_CRSW = (1e3, 1e5, 1e7)
 
-    def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True, start=0):
-        """All columns from LTE (start=0) or from the learned guess (start=1)
-        with Ng acceleration, then the columns that did not converge again
-        from LTE with collisional-radiative switching (x1e3, x1e5, then x1e7)
-        and without Ng (the paper's two-stage strategy)."""
-        s = self.iterate(maxiter=maxiter, tol=tol, precision=precision, persistent=persistent,
-                         block_warps=block_warps, start=start)
-        passes = [s]
-        if rescue:
-            for kw in self.RESCUE_PASSES:
-                if not (s["n_maxiter"] or s["n_failed"]):
-                    break
-                args = dict(maxiter=maxiter, tol=tol, precision=precision, persistent=persistent,
-                            block_warps=block_warps, only_unconverged=1)
-                args.update(kw)
-                s = self.iterate(**args)
-                passes.append(s)
-        return {"passes": passes, "n_converged": s["n_converged"], "n_maxiter": s["n_maxiter"],
-                "n_failed": s["n_failed"], "seconds": sum(p["seconds"] for p in passes),
-                "pts": sum(p["pts"] for p in passes),
-                "iterations_total": sum(p["iterations_total"] for p in passes),
-                "rerun_columns": sum(p["n_processed"] for p in passes[1:]),
-                "launches": sum(1 for p in passes if p["n_processed"] > 0)}
+    def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True, start=0,
+              ng_order=2, ng_delay=5, ng_period=3, use_graph=1, autotune=1, fused_rerun=1) -> dict:
+        """rh_solve: every column from LTE (start=0), the learned guess
+        (start=1) or the current populations (start=2) with Ng acceleration,
+        then the columns that did not converge again from LTE with
+        collisional-radiative switching (x1e3, x1e5, then x1e7) and without
+        Ng (the paper's two-stage strategy): by the column kernel itself as
+        soon as a column fails (fused_rerun=1) or as separate passes over a
+        device-selected list; the sequence is replayed as a CUDA graph."""
+        o = SolveOpts()
+        o.pass1 = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay, ng_period=ng_period,
+                           start=start, precision=precision, persistent=persistent, block_warps=block_warps,
+                           crsw_init=1.0, only_unconverged=0)
+        o.nrerun = len(self.RERUN_CRSW) if rescue else 0
+        o.rerun_maxiter = maxiter
+        for i, f in enumerate(self.RERUN_CRSW):
+            o.rerun_crsw[i] = f
+        o.use_graph = int(use_graph)
+        o.autotune = int(autotune)
+        o.fused_rerun = int(fused_rerun)
+        st = SolveStats()
+        r = self._lib.rh_solve(self._p, C.byref(o), C.byref(st))
+        if r not in (0, 6):
+            self._check(r)
+        npass = 1 + o.nrerun
+        return {"n_converged": st.n_converged, "n_maxiter": st.n_maxiter, "n_failed": st.n_failed,
+                "seconds": st.seconds, "pts": st.pts, "iterations_total": st.iterations_total,
+                "pass_columns": list(st.pass_columns)[:npass], "pass_iterations": list(st.pass_iterations)[:npass],
+                "pass_seconds": list(st.pass_seconds)[:npass],
+                "rerun_columns": int(sum(list(st.pass_columns)[1:npass])),
+                "guess_fallback_depths": st.guess_fallback_depths, "launches": st.kernel_launches,
+                "graph_replayed": bool(st.graph_replayed), "block_warps": st.block_warps,
+                "ctas_per_sm": st.ctas_per_sm}
+
+    def autotune(self, precision=1) -> dict:
+        """rh_autotune: time the column kernel's launch shapes on a sample of
+        the loaded columns and keep the fastest for this precision."""
+        t = TuneResult()
+        self._check(self._lib.rh_autotune(self._p, precision, C.byref(t)))
+        n = t.ncand
+        return {"block_warps": t.best_block_warps, "ctas_per_sm": t.best_ctas_per_sm,
+                "sample_columns": t.sample_columns,
+                "candidates": [(t.cand_block_warps[i], t.cand_ctas_per_sm[i], t.cand_ms[i]) for i in range(n)]}
 
     # ---- learned initial guess
     def surrogate_init(self, hidden=512, nhidden=3, seed=0):

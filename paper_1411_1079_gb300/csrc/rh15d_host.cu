@@ -74,6 +74,16 @@ struct rh_ctx {
     int64_t idx_cap = 0;
     int *nfb_d = nullptr;
     double *loss_d = nullptr;
+    // rh_solve: device counters and the captured sequence
+    int *solve_cnt = nullptr;                   // [RH_MAX_RERUN] columns selected for each re-run pass
+    unsigned long long *solve_it = nullptr;     // [1 + RH_MAX_RERUN] formal solutions of each pass
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;            // what the captured graph was built from
+    int glaunches = 0;
+    cudaEvent_t pass_ev[1 + RH_MAX_RERUN] = {};   // end of each pass (recorded inside the sequence)
+    // rh_autotune: chosen launch shape per precision (0: none)
+    int tuned_bw[2] = {0, 0}, tuned_ctas[2] = {0, 0};
 };
 
 namespace {
@@ -102,8 +112,18 @@ void dfree(T *&p)
     p = nullptr;
 }
 
+void drop_graph(rh_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->gkey.clear();
+}
+
 void free_columns(rh_ctx *c)
 {
+    drop_graph(c);
     dfree(c->ca.z);
     dfree(c->ca.T);
     dfree(c->ca.nH);
@@ -524,6 +544,7 @@ extern "C" {
 int rh_surrogate_init(rh_ctx *c, int32_t hidden, int32_t nhidden, uint64_t seed)
 {
     if (!c) return RH_EINVAL;
+    drop_graph(c);   // network buffers may be (re)allocated
     if (!c->ncol) return fail(c, RH_ESTATE, "rh_surrogate_init: load columns first (the network size follows ndep)");
     if (hidden < 8 || hidden > 4096 || nhidden < 1 || nhidden > 8)
         return fail(c, RH_EINVAL, "rh_surrogate_init: hidden in 8..4096, nhidden in 1..8");
@@ -549,6 +570,7 @@ int rh_surrogate_get_state(rh_ctx *c, float *out)
 int rh_surrogate_set_state(rh_ctx *c, const float *in)
 {
     if (!c || !in) return RH_EINVAL;
+    drop_graph(c);   // network buffers may be (re)allocated
     if (!c->mlp) return fail(c, RH_ESTATE, "no surrogate (rh_surrogate_init first)");
     for (int64_t i = 0; i < mlp_state_size(c->mlp); ++i)
         if (!std::isfinite(in[i])) return fail(c, RH_EINVAL, "surrogate state entry %lld is not finite", (long long)i);
@@ -560,6 +582,7 @@ int rh_surrogate_set_state(rh_ctx *c, const float *in)
 int rh_surrogate_train(rh_ctx *c, const rh_train_opts *o, rh_train_stats *st)
 {
     if (!c || !o) return RH_EINVAL;
+    drop_graph(c);   // network buffers may be (re)allocated
     if (!c->mlp || c->mlp_ndep != c->ndep) return fail(c, RH_ESTATE, "rh_surrogate_train: no surrogate for these columns");
     if (o->epochs < 1 || o->batch < 1 || !(o->lr > 0) || !(o->beta1 >= 0 && o->beta1 < 1) ||
         !(o->beta2 >= 0 && o->beta2 < 1) || !(o->eps > 0))
@@ -619,6 +642,7 @@ int rh_surrogate_train(rh_ctx *c, const rh_train_opts *o, rh_train_stats *st)
 int rh_surrogate_loss_grad(rh_ctx *c, int64_t ncols, const int32_t *cols, double *loss_out, float *grad_out)
 {
     if (!c || !cols || ncols < 1) return RH_EINVAL;
+    drop_graph(c);   // network buffers may be (re)allocated
     if (!c->mlp || c->mlp_ndep != c->ndep) return fail(c, RH_ESTATE, "no surrogate for these columns");
     for (int64_t i = 0; i < ncols; ++i)
         if (cols[i] < 0 || cols[i] >= c->ncol) return fail(c, RH_EINVAL, "column index %d out of range", cols[i]);
@@ -647,6 +671,7 @@ int rh_surrogate_loss_grad(rh_ctx *c, int64_t ncols, const int32_t *cols, double
 int rh_surrogate_predict(rh_ctx *c, float *lnb_out)
 {
     if (!c || !lnb_out) return RH_EINVAL;
+    drop_graph(c);   // network buffers may be (re)allocated
     if (!c->mlp || c->mlp_ndep != c->ndep) return fail(c, RH_ESTATE, "no surrogate for these columns");
     cudaSetDevice(c->dev);
     int r = ensure_mlp_buffers(c);
@@ -729,6 +754,11 @@ void rh_destroy(rh_ctx *c)
     dfree(c->idx_d);
     dfree(c->nfb_d);
     dfree(c->loss_d);
+    dfree(c->solve_cnt);
+    dfree(c->solve_it);
+    drop_graph(c);
+    for (cudaEvent_t &ev : c->pass_ev)
+        if (ev) cudaEventDestroy(ev);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
 }
@@ -745,6 +775,8 @@ int rh_setup_atom(rh_ctx *c, const rh_atom_desc *d)
     if (r) return r;
     dfree(c->lane_d);
     c->lane_prec = -1;
+    c->tuned_bw[0] = c->tuned_bw[1] = c->tuned_ctas[0] = c->tuned_ctas[1] = 0;
+    drop_graph(c);
     c->have_atom = true;
     return RH_OK;
 }
@@ -766,6 +798,7 @@ int rh_load_columns(rh_ctx *c, int64_t ncol, int32_t ndep, const double *z_m, co
     if (ncol < 1 || ndep < 2 || ndep > 4096) return fail(c, RH_EINVAL, "need ncol >= 1 and 2 <= ndep <= 4096");
     if (!z_m || !T_K || !nH_m3 || !vz_ms) return fail(c, RH_EINVAL, "z, T, nH, vz must not be NULL");
     cudaSetDevice(c->dev);
+    if (ndep != c->ndep) c->tuned_bw[0] = c->tuned_bw[1] = c->tuned_ctas[0] = c->tuned_ctas[1] = 0;
     free_columns(c);
     const int L = c->da.nlev;
     const size_t nd = (size_t)ncol * ndep;
@@ -899,6 +932,10 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     il.nsm = c->nsm;
     il.colidx = colidx_d;
     il.nwork = nwork;
+    if (o->block_warps == 0 && c->tuned_bw[o->precision]) {
+        il.block_warps = c->tuned_bw[o->precision];
+        il.ctas_per_sm = c->tuned_ctas[o->precision];
+    }
     float ms = 0;
     int grid = 0;
     char ebuf[256] = {0};
@@ -1044,6 +1081,399 @@ int rh_emergent_spectrum(rh_ctx *c, double mu, int64_t nlambda, const double *la
     if (e != cudaSuccess) rc = fail(c, RH_ECUDA, "rh_emergent_spectrum: %s", cudaGetErrorString(e));
     cleanup();
     return rc;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// rh_solve: pass 1 and the re-run passes of Sect. 2.3 with the selection of
+// unconverged columns on the device, enqueued directly or captured once
+// into a CUDA graph and replayed; rh_autotune: the launch shape of the
+// column kernel.
+namespace {
+
+// Compact the indices of the columns whose status is not CONVERGED into
+// colidx; count receives their number (warp-aggregated atomics: the order of
+// colidx is not deterministic, the per-column results do not depend on it).
+__global__ void select_unconverged_kernel(int64_t ncol, const uint8_t *status, int *colidx, int *count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool sel = i < ncol && status[i] != RH_COL_CONVERGED;
+    const unsigned m = __ballot_sync(0xffffffffu, sel);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (sel) colidx[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+}
+
+// Sum of iters over the first n (or *count_d) work items into *out.
+__global__ void sum_iters_kernel(int64_t n, const int *colidx, const int *count_d, const int32_t *iters,
+                                 unsigned long long *out)
+{
+    const int64_t cnt = count_d ? (int64_t)*count_d : n;
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        s += (unsigned long long)iters[colidx ? colidx[i] : i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+bool valid_iter_opts(const rh_iter_opts *o)
+{
+    return o->maxiter >= 1 && o->tol >= 0 && (o->ng_order == 0 || o->ng_order == 2) &&
+           !(o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) && (o->precision == 0 || o->precision == 1) &&
+           o->start >= 0 && o->start <= 2 && o->block_warps >= 0 && o->block_warps <= 8;
+}
+
+// everything the enqueued sequence depends on, compared byte-wise
+struct SolveKey {
+    const void *ptrs[24];
+    int64_t ncol;
+    int ndep, bw, ctas, nsm;
+    rh_solve_opts o;
+};
+
+SolveKey make_key(const rh_ctx *c, const rh_solve_opts *o, int bw, int ctas)
+{
+    SolveKey k;
+    memset(&k, 0, sizeof k);
+    const void *p[] = {c->ca.z, c->ca.T, c->ca.nH, c->ca.vz, c->ca.ne, c->ca.np, c->ca.nstar, c->ca.pops,
+                       c->ca.Crate, c->ca.dmax, c->ca.iters, c->ca.status, c->lane_d, c->vtab_d, c->nghist,
+                       c->queue, c->colidx, c->solve_cnt, c->solve_it, c->mlp, c->feat, c->lnb, c->nfb_d, c->st};
+    static_assert(sizeof p / sizeof p[0] == 24, "key size");
+    memcpy(k.ptrs, p, sizeof p);
+    k.ncol = c->ncol;
+    k.ndep = c->ndep;
+    k.bw = bw;
+    k.ctas = ctas;
+    k.nsm = c->nsm;
+    memcpy(&k.o, o, sizeof *o);
+    k.o.pass1.only_unconverged = 0;
+    return k;
+}
+
+// Enqueue the whole sequence on c->st; counts the kernels it launches.
+// end-of-pass timing events: external event nodes when the sequence is captured
+cudaError_t record_pass_end(rh_ctx *c, int i, bool capturing)
+{
+    return capturing ? cudaEventRecordWithFlags(c->pass_ev[i], c->st, cudaEventRecordExternal)
+                     : cudaEventRecord(c->pass_ev[i], c->st);
+}
+
+cudaError_t enqueue_solve(rh_ctx *c, const rh_solve_opts *o, const IterLaunch &base, char *err, size_t errn,
+                          int *nkern, bool capturing)
+{
+    cudaStream_t st = c->st;
+    int nk = 0;
+    cudaError_t e = cudaMemsetAsync(c->solve_cnt, 0, RH_MAX_RERUN * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->solve_it, 0, (1 + RH_MAX_RERUN) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if (o->pass1.start == 1) {
+        if ((e = mlp_predict_apply(c->mlp, c->ca, c->da.nlev, c->feat, c->lnb, c->nfb_d, st)) != cudaSuccess) return e;
+        const int64_t nchunk = (c->ncol + 16383) / 16384;
+        nk += 2 + (int)nchunk * (1 + mlp_nlayer(c->mlp));
+    }
+    const int sgrid = 2 * c->nsm;
+    IterLaunch il = base;
+    il.start = o->pass1.start == 1 ? 2 : o->pass1.start;
+    il.colidx = nullptr;
+    il.nwork = c->ncol;
+    il.nwork_d = nullptr;
+    int grid = 0;
+    if (o->fused_rerun) {
+        // one launch: the kernel re-runs failing columns itself and counts
+        il.nrung = o->nrerun;
+        il.rung_maxiter = o->rerun_maxiter;
+        for (int r = 0; r < o->nrerun; ++r) il.rung_crsw[r] = o->rerun_crsw[r];
+        il.rung_cols = c->solve_cnt;
+        il.rung_its = c->solve_it;
+        if ((e = launch_mali_prealloc(c->da, c->ca, c->lane_d, c->ha.npad, c->vtab_d, c->nref, c->nghist,
+                                      c->nghist_cap, c->queue, il, st, &grid, err, errn)) != cudaSuccess)
+            return e;
+        *nkern = nk + 1;
+        if ((e = record_pass_end(c, 0, capturing)) != cudaSuccess) return e;
+        for (int r = 0; r < o->nrerun; ++r)
+            if ((e = record_pass_end(c, 1 + r, capturing)) != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    if ((e = launch_mali_prealloc(c->da, c->ca, c->lane_d, c->ha.npad, c->vtab_d, c->nref, c->nghist, c->nghist_cap,
+                                  c->queue, il, st, &grid, err, errn)) != cudaSuccess)
+        return e;
+    sum_iters_kernel<<<sgrid, 256, 0, st>>>(c->ncol, nullptr, nullptr, c->ca.iters, c->solve_it);
+    nk += 2;
+    if ((e = record_pass_end(c, 0, capturing)) != cudaSuccess) return e;
+    for (int r = 0; r < o->nrerun; ++r) {
+        select_unconverged_kernel<<<(unsigned)((c->ncol + 255) / 256), 256, 0, st>>>(c->ncol, c->ca.status, c->colidx,
+                                                                                   c->solve_cnt + r);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        IterLaunch ir = base;
+        ir.start = 0;
+        ir.ng_order = 0;
+        ir.crsw = o->rerun_crsw[r];
+        ir.maxiter = o->rerun_maxiter;
+        ir.colidx = c->colidx;
+        ir.nwork = c->ncol;
+        ir.nwork_d = c->solve_cnt + r;
+        if ((e = launch_mali_prealloc(c->da, c->ca, c->lane_d, c->ha.npad, c->vtab_d, c->nref, c->nghist,
+                                      c->nghist_cap, c->queue, ir, st, &grid, err, errn)) != cudaSuccess)
+            return e;
+        sum_iters_kernel<<<sgrid, 256, 0, st>>>(c->ncol, c->colidx, c->solve_cnt + r, c->ca.iters, c->solve_it + 1 + r);
+        nk += 3;
+        if ((e = record_pass_end(c, 1 + r, capturing)) != cudaSuccess) return e;
+    }
+    *nkern = nk;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int rh_autotune(rh_ctx *c, int32_t precision, rh_tune_result *out)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "rh_autotune: no columns loaded");
+    if (precision != 0 && precision != 1) return fail(c, RH_EINVAL, "rh_autotune: precision 0 or 1");
+    cudaSetDevice(c->dev);
+    int r = ensure_lane(c, precision);
+    if (r) return r;
+    const size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
+    const size_t want = per_block * (size_t)c->nsm * 4;
+    if (c->nghist_cap < want) {
+        drop_graph(c);
+        dfree(c->nghist);
+        CK(cudaMalloc(&c->nghist, want));
+        c->nghist_cap = want;
+    }
+    const int L = c->da.nlev, N = c->ndep;
+    const int64_t S = std::min<int64_t>(c->ncol, (int64_t)4 * c->nsm);
+    // keep the sample columns' state: the candidates overwrite it
+    double *sv_n = nullptr, *sv_d = nullptr;
+    int32_t *sv_i = nullptr;
+    uint8_t *sv_s = nullptr;
+    CK(cudaMalloc(&sv_n, (size_t)S * L * N * 8));
+    CK(cudaMalloc(&sv_d, S * 8));
+    CK(cudaMalloc(&sv_i, S * 4));
+    CK(cudaMalloc(&sv_s, S));
+    auto cleanup = [&]() {
+        cudaFree(sv_n);
+        cudaFree(sv_d);
+        cudaFree(sv_i);
+        cudaFree(sv_s);
+    };
+    cudaError_t e = cudaMemcpyAsync(sv_n, c->ca.pops, (size_t)S * L * N * 8, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv_d, c->ca.dmax, S * 8, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv_i, c->ca.iters, S * 4, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv_s, c->ca.status, S, cudaMemcpyDeviceToDevice, c->st);
+    rh_tune_result R;
+    memset(&R, 0, sizeof R);
+    R.sample_columns = S;
+    const int bws[3] = {precision ? 4 : 2, precision ? 8 : 4, 8};
+    const int nbw = precision ? 2 : 3;
+    for (int ib = 0; ib < nbw && e == cudaSuccess; ++ib) {
+        const int maxc = mali_max_ctas_per_sm(c->da, N, precision, bws[ib]);
+        for (int ct = 1; ct <= std::min(maxc, 2) && R.ncand < RH_MAX_TUNE; ++ct) {
+            IterLaunch il;
+            il.precision = precision;
+            il.persistent = 1;
+            il.block_warps = bws[ib];
+            il.ctas_per_sm = ct;
+            il.maxiter = 2;
+            il.tol = 0.0;
+            il.start = 0;
+            il.nsm = c->nsm;
+            il.nwork = S;
+            double best = -1;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // first run: warm-up
+                float ms = 0;
+                int grid = 0;
+                char eb[256] = {0};
+                e = launch_mali(c->da, c->ca, c->lane_d, c->ha.npad, c->vtab_d, c->nref, c->nghist, c->nghist_cap,
+                                c->queue, il, c->st, &ms, &grid, eb, sizeof eb);
+                if (rep == 1) best = ms;
+            }
+            R.cand_block_warps[R.ncand] = bws[ib];
+            R.cand_ctas_per_sm[R.ncand] = ct;
+            R.cand_ms[R.ncand] = best;
+            R.ncand++;
+        }
+        if (maxc < 1 && R.ncand < RH_MAX_TUNE) {
+            R.cand_block_warps[R.ncand] = bws[ib];
+            R.cand_ctas_per_sm[R.ncand] = 0;
+            R.cand_ms[R.ncand] = -1;
+            R.ncand++;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ca.pops, sv_n, (size_t)S * L * N * 8, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ca.dmax, sv_d, S * 8, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ca.iters, sv_i, S * 4, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ca.status, sv_s, S, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cleanup();
+    if (e != cudaSuccess) return fail(c, RH_ECUDA, "rh_autotune: %s", cudaGetErrorString(e));
+    int bi = -1;
+    for (int i = 0; i < R.ncand; ++i)
+        if (R.cand_ms[i] > 0 && (bi < 0 || R.cand_ms[i] < R.cand_ms[bi])) bi = i;
+    if (bi < 0) return fail(c, RH_ECUDA, "rh_autotune: no launch shape fits");
+    R.best_block_warps = R.cand_block_warps[bi];
+    R.best_ctas_per_sm = R.cand_ctas_per_sm[bi];
+    c->tuned_bw[precision] = R.best_block_warps;
+    c->tuned_ctas[precision] = R.best_ctas_per_sm;
+    drop_graph(c);
+    if (out) *out = R;
+    return RH_OK;
+}
+
+int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "rh_solve: no columns loaded");
+    if (!o) return fail(c, RH_EINVAL, "opts is NULL");
+    if (!valid_iter_opts(&o->pass1) || o->nrerun < 0 || o->nrerun > RH_MAX_RERUN ||
+        (o->nrerun > 0 && o->rerun_maxiter < 1) || (o->use_graph != 0 && o->use_graph != 1) ||
+        (o->autotune != 0 && o->autotune != 1) || (o->fused_rerun != 0 && o->fused_rerun != 1))
+        return fail(c, RH_EINVAL, "rh_solve: invalid options");
+    for (int r = 0; r < o->nrerun; ++r)
+        if (!(o->rerun_crsw[r] >= 1.0)) return fail(c, RH_EINVAL, "rh_solve: rerun_crsw must be >= 1");
+    cudaSetDevice(c->dev);
+    const int prec = o->pass1.precision;
+    if (o->pass1.start == 1) {
+        if (!c->mlp || c->mlp_ndep != c->ndep)
+            return fail(c, RH_ESTATE, "rh_solve: start = 1 needs a surrogate for %d depths (rh_surrogate_init)",
+                        c->ndep);
+        int r = ensure_mlp_buffers(c);
+        if (r) return r;
+        CK(mlp_prepare_predict(c->mlp, c->ncol));
+    }
+    if (o->autotune && o->pass1.block_warps == 0 && !c->tuned_bw[prec]) {
+        int r = rh_autotune(c, prec, nullptr);
+        if (r) return r;
+    }
+    // everything the sequence touches exists before it is enqueued or captured
+    int r = ensure_lane(c, prec);
+    if (r) return r;
+    const size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
+    const size_t want = per_block * (size_t)c->nsm * 4;
+    if (c->nghist_cap < want) {
+        dfree(c->nghist);
+        CK(cudaMalloc(&c->nghist, want));
+        c->nghist_cap = want;
+    }
+    if (c->colidx_cap < c->ncol) {
+        dfree(c->colidx);
+        CK(cudaMalloc(&c->colidx, c->ncol * sizeof(int)));
+        c->colidx_cap = c->ncol;
+    }
+    for (cudaEvent_t &ev : c->pass_ev)
+        if (!ev) CK(cudaEventCreate(&ev));
+    if (!c->solve_cnt) CK(cudaMalloc(&c->solve_cnt, RH_MAX_RERUN * sizeof(int)));
+    if (!c->solve_it) CK(cudaMalloc(&c->solve_it, (1 + RH_MAX_RERUN) * sizeof(unsigned long long)));
+
+    IterLaunch base;
+    base.precision = prec;
+    base.persistent = o->pass1.persistent;
+    base.block_warps = o->pass1.block_warps;
+    base.maxiter = o->pass1.maxiter;
+    base.ng_order = o->pass1.ng_order;
+    base.ng_delay = o->pass1.ng_delay;
+    base.ng_period = o->pass1.ng_period;
+    base.tol = o->pass1.tol;
+    base.crsw = o->pass1.crsw_init;
+    base.nsm = c->nsm;
+    if (o->pass1.block_warps == 0 && c->tuned_bw[prec]) {
+        base.block_warps = c->tuned_bw[prec];
+        base.ctas_per_sm = c->tuned_ctas[prec];
+    }
+    const int bw_used = base.block_warps > 0 ? base.block_warps : (prec ? 8 : 4);
+    const int ctas_max = mali_max_ctas_per_sm(c->da, c->ndep, prec, bw_used);
+    const int ctas_used = base.ctas_per_sm > 0 ? std::min(base.ctas_per_sm, ctas_max) : ctas_max;
+
+    char eb[256] = {0};
+    int replayed = 0, nkern = 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    cudaError_t e = cudaSuccess;
+    if (o->use_graph) {
+        SolveKey k = make_key(c, o, bw_used, ctas_used);
+        const unsigned char *kb = reinterpret_cast<const unsigned char *>(&k);
+        if (!(c->gexec && c->gkey.size() == sizeof k && memcmp(c->gkey.data(), kb, sizeof k) == 0)) {
+            drop_graph(c);
+            e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t eq = enqueue_solve(c, o, base, eb, sizeof eb, &nkern, true);
+                cudaGraph_t g = nullptr;
+                e = cudaStreamEndCapture(c->st, &g);
+                if (eq != cudaSuccess) e = eq;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
+                if (e == cudaSuccess) {
+                    c->graph = g;
+                    c->gkey.assign(kb, kb + sizeof k);
+                    c->glaunches = nkern;
+                } else if (g) {
+                    cudaGraphDestroy(g);
+                }
+            }
+        } else {
+            replayed = 1;
+        }
+        nkern = c->glaunches;
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(c->gexec, c->st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+    } else {
+        e = cudaEventRecord(e0, c->st);
+        if (e == cudaSuccess) e = enqueue_solve(c, o, base, eb, sizeof eb, &nkern, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0, pms[1 + RH_MAX_RERUN] = {};
+    if (e == cudaSuccess) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        for (int i = 0; i <= o->nrerun; ++i) cudaEventElapsedTime(&pms[i], i ? c->pass_ev[i - 1] : e0, c->pass_ev[i]);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        drop_graph(c);
+        return fail(c, RH_ECUDA, "rh_solve: %s%s%s", cudaGetErrorString(e), eb[0] ? ": " : "", eb);
+    }
+    int cnt[RH_MAX_RERUN];
+    unsigned long long its[1 + RH_MAX_RERUN];
+    int nfb = 0;
+    CK(cudaMemcpy(cnt, c->solve_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(its, c->solve_it, sizeof its, cudaMemcpyDeviceToHost));
+    if (o->pass1.start == 1) CK(cudaMemcpy(&nfb, c->nfb_d, sizeof nfb, cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> s(c->ncol);
+    CK(cudaMemcpy(s.data(), c->ca.status, c->ncol, cudaMemcpyDeviceToHost));
+    rh_solve_stats S;
+    memset(&S, 0, sizeof S);
+    for (int64_t i = 0; i < c->ncol; ++i) {
+        if (s[i] == RH_COL_CONVERGED) S.n_converged++;
+        else if (s[i] == RH_COL_MAXITER) S.n_maxiter++;
+        else S.n_failed++;
+    }
+    S.pass_columns[0] = c->ncol;
+    S.pass_iterations[0] = (int64_t)its[0];
+    S.iterations_total = (int64_t)its[0];
+    for (int r2 = 0; r2 < o->nrerun; ++r2) {
+        S.pass_columns[1 + r2] = cnt[r2];
+        S.pass_iterations[1 + r2] = (int64_t)its[1 + r2];
+        S.iterations_total += (int64_t)its[1 + r2];
+    }
+    S.seconds = ms * 1e-3;
+    for (int i = 0; i <= o->nrerun; ++i) S.pass_seconds[i] = pms[i] * 1e-3;
+    S.pts = (double)S.iterations_total * c->ndep * (double)c->ha.nu.size() * c->ha.nmu;
+    S.guess_fallback_depths = nfb;
+    S.kernel_launches = nkern;
+    S.graph_replayed = replayed;
+    S.block_warps = bw_used;
+    S.ctas_per_sm = ctas_used;
+    if (st) *st = S;
+    return (S.n_maxiter || S.n_failed) ? RH_ENOTCONV : RH_OK;
 }
 
 }  // extern "C"

@@ -341,17 +341,27 @@ struct ColumnArrays {
 // launchers (defined in the kernel translation units)
 cudaError_t launch_lte_setup(const DevAtom &A, const ColumnArrays &c, int ne_given, cudaStream_t st);
 struct IterLaunch {
-    int precision, persistent, block_warps, maxiter, ng_order, ng_delay, ng_period, start;
-    double tol, crsw;
-    int nsm;
-    const int *colidx;     // columns to iterate (nullptr: all)
-    int64_t nwork;         // number of columns to iterate
+    int precision = 1, persistent = 1, block_warps = 0, maxiter = 1, ng_order = 0, ng_delay = 0, ng_period = 1,
+        start = 0;
+    double tol = 0.0, crsw = 1.0;
+    int nsm = 1;
+    const int *colidx = nullptr;   // columns to iterate (nullptr: all)
+    int64_t nwork = 0;             // number of columns to iterate
+    const int *nwork_d = nullptr;  // device count of columns to iterate (overrides nwork; set by an
+                                   // earlier kernel on the same stream)
+    int ctas_per_sm = 0;           // resident column blocks per SM (0: as many as fit)
+    // re-run ladder run by the kernel itself for columns that do not converge
+    int nrung = 0, rung_maxiter = 1;
+    double rung_crsw[RH_MAX_RERUN] = {1.0, 1.0, 1.0, 1.0};
+    int *rung_cols = nullptr;                 // [nrung] columns entering each rung
+    unsigned long long *rung_its = nullptr;   // [1 + nrung] formal solutions per pass / rung
 };
 cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
                         const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
                         const IterLaunch &o, cudaStream_t st, float *ms_out, int *grid_out, char *err,
                         size_t errn);
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep);
+int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_warps);
 cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
                                  const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
                                  const IterLaunch &o, cudaStream_t st, int *grid_out, char *err, size_t errn);
@@ -369,6 +379,7 @@ cudaError_t mlp_create(Mlp **out, int nin, int hidden, int nhid, int nout, uint6
 void mlp_destroy(Mlp *m);
 int64_t mlp_nparams(const Mlp *m);
 int mlp_nin(const Mlp *m);
+int mlp_nlayer(const Mlp *m);
 int mlp_nout(const Mlp *m);
 int64_t mlp_state_size(const Mlp *m);
 cudaError_t mlp_get_state(const Mlp *m, float *h);
@@ -382,5 +393,6 @@ cudaError_t mlp_adam(Mlp *m, float lr, float b1, float b2, float eps, cudaStream
 const float *mlp_grad(const Mlp *m);
 cudaError_t mlp_predict_apply(Mlp *m, const ColumnArrays &c, int L, float *X, float *lnb, int *nfallback_d,
                               cudaStream_t st);
+cudaError_t mlp_prepare_predict(Mlp *m, int64_t ncol);   // allocates what mlp_predict_apply needs
 
 }  // namespace rh

@@ -34,6 +34,8 @@ namespace rh {
 namespace {
 
 constexpr int kWarp = 32;
+constexpr int kNgLanes = 64;                    // fixed partition of the Ng dot products
+constexpr int kRedDoubles = 5 * kNgLanes + 8;   // block reduction scratch
 
 struct KParams {
     int64_t ncol;
@@ -51,6 +53,14 @@ struct KParams {
     double tol, crsw, inv_nref;
     const int *colidx;         // work item -> column (nullptr: identity)
     int64_t nwork;
+    const int *nwork_d;        // device count of work items (overrides nwork when set)
+    // re-run ladder inside the kernel (Sect. 2.3): a column not converged
+    // after its pass is restarted from LTE without Ng with switching factor
+    // rung_crsw[r] and rung_maxiter iterations, r = 0 .. nrung-1
+    int nrung, rung_maxiter;
+    double rung_crsw[RH_MAX_RERUN];
+    int *rung_cols;                  // [nrung] columns entering each rung (nullptr: not counted)
+    unsigned long long *rung_its;    // [1 + nrung] formal solutions of the pass and of each rung
 };
 
 template <typename R>
@@ -62,7 +72,7 @@ struct Smem {
     R *ad;                     // [nline][N] damping
     R *nr;                     // [L][N] populations in R
     float4 *vtab;              // [RH_VT_N + 1] Voigt coefficient table
-    double *red;               // reduction scratch [64]
+    double *red;               // reduction scratch [kRedDoubles]
     int *ibuf;                 // [8]
 };
 
@@ -73,7 +83,7 @@ __host__ __device__ size_t smem_bytes(int L, int N, int ntr, int ncont, int nlin
     b += sizeof(double) * (2 * L * N + (size_t)N * 2 * ntr);
     b += sizeof(R) * ((size_t)macc * N + 7 * N + (size_t)ncont * N + (size_t)nline * N + (size_t)L * N);
     b += sizeof(float4) * (RH_VT_N + 1) + 16;
-    b += sizeof(double) * 64 + sizeof(int) * 8 + 64;
+    b += sizeof(double) * kRedDoubles + sizeof(int) * 8 + 64;
     return b;
 }
 
@@ -89,7 +99,7 @@ __device__ Smem<R> carve(char *base, int L, int N, int ntr, int ncont, int nline
     s.Cr = d;
     d += N * 2 * ntr;
     s.red = d;
-    d += 64;
+    d += kRedDoubles;
     R *r = reinterpret_cast<R *>(d);
     s.slot = r;
     r += macc * N;
@@ -129,22 +139,6 @@ template <> __device__ __forceinline__ double one_m_exp<double>(double x, double
 template <typename R> __device__ __forceinline__ R rexp(R x);
 template <> __device__ __forceinline__ float rexp<float>(float x) { return __expf(x); }
 template <> __device__ __forceinline__ double rexp<double>(double x) { return exp(x); }
-template <typename R> __device__ __forceinline__ R rexpm1(R x);
-template <> __device__ __forceinline__ float rexpm1<float>(float x) { return expm1f(x); }
-template <> __device__ __forceinline__ double rexpm1<double>(double x) { return expm1(x); }
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 template <typename R> __device__ __forceinline__ R mu_of(const DevAtom &A, int m);
 template <> __device__ __forceinline__ float mu_of<float>(const DevAtom &A, int m) { return A.muf[m]; }
@@ -403,19 +397,6 @@ __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, c
     }
 }
 
-__device__ __forceinline__ double block_sum(double v, double *red)
-{
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < nw; ++i) t += red[i];
-    __syncthreads();
-    return t;
-}
-
 __device__ __forceinline__ double block_max(double v, double *red)
 {
 #pragma unroll
@@ -516,6 +497,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
     double *hist = p.nghist + (size_t)blockIdx.x * 4 * LN;
 
     for (int i = tid; i <= RH_VT_N; i += blockDim.x) s.vtab[i] = p.vtab[i];
+    const int64_t nwork = p.nwork_d ? (int64_t)*p.nwork_d : p.nwork;
     int64_t done = 0;
     for (;;) {
         __syncthreads();
@@ -523,7 +505,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
             int64_t q;
             if (p.persistent) q = atomicAdd(p.queue, 1);
             else q = (int64_t)blockIdx.x + done * gridDim.x;
-            s.ibuf[0] = q < p.nwork ? (p.colidx ? p.colidx[q] : (int)q) : -1;
+            s.ibuf[0] = q < nwork ? (p.colidx ? p.colidx[q] : (int)q) : -1;
         }
         __syncthreads();
         const int col = s.ibuf[0];
@@ -558,14 +540,20 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
             }
         }
         for (int i = tid; i < N * 2 * A.ntr; i += blockDim.x) s.Cr[i] = p.Crate[(size_t)col * N * 2 * A.ntr + i];
+        int start = p.start, ng_order = p.ng_order, maxiter = p.maxiter, rung = 0;
+        double crsw = p.crsw;
+        int it = 0, status = RH_COL_MAXITER;
+        double dmax = 1e300;
+      restart:
         for (int i = tid; i < LN; i += blockDim.x) {
-            double v = p.start == 0 ? p.nstar[(size_t)col * LN + i] : p.pops[(size_t)col * LN + i];
+            double v = start == 0 ? p.nstar[(size_t)col * LN + i] : p.pops[(size_t)col * LN + i];
             s.n[i] = v;
         }
-        int hcount = 0, hpos = 0, it = 0, status = RH_COL_MAXITER;
-        double dmax = 1e300;
-        for (it = 1; it <= p.maxiter; ++it) {
-            double fcr = p.crsw > 1.0 ? fmax(1.0, p.crsw * pow(10.0, -(double)(it - 1))) : 1.0;
+        int hcount = 0, hpos = 0;
+        status = RH_COL_MAXITER;
+        dmax = 1e300;
+        for (it = 1; it <= maxiter; ++it) {
+            double fcr = crsw > 1.0 ? fmax(1.0, crsw * pow(10.0, -(double)(it - 1))) : 1.0;
             for (int i = tid; i < LN; i += blockDim.x) s.nr[i] = (R)(s.n[i] * p.inv_nref);
             if (tid == 0) s.ibuf[1] = 0;
             __syncthreads();
@@ -608,25 +596,37 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
             for (int i = tid; i < LN; i += blockDim.x) hist[(size_t)hpos * LN + i] = s.nn[i];
             __syncthreads();
             if (hcount < 4) ++hcount;
-            if (!conv && p.ng_order == 2 && it >= p.ng_delay && hcount >= 4 &&
+            if (!conv && ng_order == 2 && it >= p.ng_delay && hcount >= 4 &&
                 (it - p.ng_delay) % p.ng_period == 0) {
                 const double *x0 = hist + (size_t)hpos * LN, *x1 = hist + (size_t)((hpos + 1) & 3) * LN,
                              *x2 = hist + (size_t)((hpos + 2) & 3) * LN, *x3 = hist + (size_t)((hpos + 3) & 3) * LN;
-                double a11 = 0, a12 = 0, a22 = 0, b1 = 0, b2 = 0;
-                for (int i = tid; i < LN; i += blockDim.x) {
-                    double d0 = x0[i] - x1[i], d1 = x1[i] - x2[i], d2 = x2[i] - x3[i];
-                    double pp = d0 - d1, qq = d0 - d2;
-                    a11 += pp * pp;
-                    a12 += pp * qq;
-                    a22 += qq * qq;
-                    b1 += d0 * pp;
-                    b2 += d0 * qq;
+                // dot products over a fixed partition of kNgLanes partial sums,
+                // added in a fixed order: the result does not depend on the
+                // block size
+                for (int v = tid; v < kNgLanes; v += blockDim.x) {
+                    double q[5] = {0, 0, 0, 0, 0};
+                    for (int i = v; i < LN; i += kNgLanes) {
+                        double d0 = x0[i] - x1[i], d1 = x1[i] - x2[i], d2 = x2[i] - x3[i];
+                        double pp = d0 - d1, qq = d0 - d2;
+                        q[0] += pp * pp;
+                        q[1] += pp * qq;
+                        q[2] += qq * qq;
+                        q[3] += d0 * pp;
+                        q[4] += d0 * qq;
+                    }
+                    for (int j = 0; j < 5; ++j) s.red[j * kNgLanes + v] = q[j];
                 }
-                a11 = block_sum(a11, s.red);
-                a12 = block_sum(a12, s.red);
-                a22 = block_sum(a22, s.red);
-                b1 = block_sum(b1, s.red);
-                b2 = block_sum(b2, s.red);
+                __syncthreads();
+                if (tid < 5) {
+                    double t = 0.0;
+                    for (int i = 0; i < kNgLanes; ++i) t += s.red[tid * kNgLanes + i];
+                    s.red[5 * kNgLanes + tid] = t;
+                }
+                __syncthreads();
+                const double a11 = s.red[5 * kNgLanes + 0], a12 = s.red[5 * kNgLanes + 1],
+                             a22 = s.red[5 * kNgLanes + 2], b1 = s.red[5 * kNgLanes + 3],
+                             b2 = s.red[5 * kNgLanes + 4];
+                __syncthreads();
                 double det = a11 * a22 - a12 * a12;
                 if (fabs(det) > 0.0 && isfinite(det)) {
                     double ca = (b1 * a22 - b2 * a12) / det, cb = (a11 * b2 - a12 * b1) / det;
@@ -655,7 +655,19 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 break;
             }
         }
-        if (it > p.maxiter) it = p.maxiter;
+        if (it > maxiter) it = maxiter;
+        if (tid == 0 && p.rung_its) atomicAdd(&p.rung_its[rung], (unsigned long long)it);
+        if (status != RH_COL_CONVERGED && rung < p.nrung) {
+            // next rung of the re-run ladder: from LTE, no Ng, stronger switching
+            start = 0;
+            ng_order = 0;
+            crsw = p.rung_crsw[rung];
+            maxiter = p.rung_maxiter;
+            ++rung;
+            if (tid == 0 && p.rung_cols) atomicAdd(&p.rung_cols[rung - 1], 1);
+            __syncthreads();
+            goto restart;
+        }
         for (int i = tid; i < LN; i += blockDim.x) p.pops[(size_t)col * LN + i] = s.n[i];
         if (tid == 0) {
             p.iters[col] = it;
@@ -669,9 +681,26 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
 
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep) { return sizeof(double) * 4 * A.nlev * ndep; }
 
+int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_warps)
+{
+    size_t sm;
+    const void *fn;
+    if (precision == 1) {
+        sm = smem_bytes<float>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc);
+        fn = (const void *)mali_kernel<float>;
+    } else {
+        sm = smem_bytes<double>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc);
+        fn = (const void *)mali_kernel<double>;
+    }
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block_warps * 32, sm) != cudaSuccess) return 0;
+    return per_sm;
+}
+
 template <typename R>
-static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps, int nsm, size_t cap, cudaStream_t st,
-                            float *ms, char *err, size_t errn, int *grid_out)
+static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps, int ctas_per_sm, int nsm, size_t cap,
+                            cudaStream_t st, float *ms, char *err, size_t errn, int *grid_out)
 {
     size_t sm = smem_bytes<R>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
     auto kern = mali_kernel<R>;
@@ -685,8 +714,9 @@ static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps,
         snprintf(err, errn, "column kernel does not fit: %zu B shared memory, %d threads", sm, threads);
         return cudaErrorInvalidConfiguration;
     }
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     int64_t grid = (int64_t)per_sm * nsm;
-    if (grid > p.nwork) grid = p.nwork;
+    if (!p.nwork_d && grid > p.nwork) grid = p.nwork;
     size_t per_block = mali_nghist_bytes_per_block(A, p.N);
     if ((size_t)grid * per_block > cap) grid = (int64_t)(cap / per_block);
     if (grid < 1) {
@@ -744,13 +774,20 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
     p.inv_nref = 1.0 / nref;
     p.colidx = o.colidx;
     p.nwork = o.nwork;
+    p.nwork_d = o.nwork_d;
+    p.nrung = o.nrung;
+    p.rung_maxiter = o.rung_maxiter;
+    for (int r = 0; r < RH_MAX_RERUN; ++r) p.rung_crsw[r] = o.rung_crsw[r];
+    p.rung_cols = o.rung_cols;
+    p.rung_its = o.rung_its;
     int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
     if (o.persistent) {
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
     }
-    if (o.precision == 1) return launch_t<float>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
-    return launch_t<double>(A, p, bw, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+    if (o.precision == 1)
+        return launch_t<float>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+    return launch_t<double>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
 }
 
 }  // namespace rh
@@ -797,6 +834,12 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     p.inv_nref = 1.0 / nref;
     p.colidx = o.colidx;
     p.nwork = o.nwork;
+    p.nwork_d = o.nwork_d;
+    p.nrung = o.nrung;
+    p.rung_maxiter = o.rung_maxiter;
+    for (int r = 0; r < RH_MAX_RERUN; ++r) p.rung_crsw[r] = o.rung_crsw[r];
+    p.rung_cols = o.rung_cols;
+    p.rung_its = o.rung_its;
     const int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
     const int threads = bw * 32;
     size_t sm;
@@ -817,8 +860,9 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
         snprintf(err, errn, "column kernel does not fit: %zu B shared memory, %d threads", sm, threads);
         return cudaErrorInvalidConfiguration;
     }
+    if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) per_sm = o.ctas_per_sm;
     int64_t grid = (int64_t)per_sm * o.nsm;
-    if (grid > p.nwork) grid = p.nwork;
+    if (!p.nwork_d && grid > p.nwork) grid = p.nwork;
     const size_t per_block = mali_nghist_bytes_per_block(A, p.N);
     if ((size_t)grid * per_block > nghist_cap) grid = (int64_t)(nghist_cap / per_block);
     if (grid < 1) {

@@ -327,6 +327,7 @@ void mlp_destroy(Mlp *m)
 
 int64_t mlp_nparams(const Mlp *m) { return m ? m->nparam : 0; }
 int mlp_nin(const Mlp *m) { return m ? m->nin : 0; }
+int mlp_nlayer(const Mlp *m) { return m ? m->nlayer : 0; }
 int mlp_nout(const Mlp *m) { return m ? m->nout : 0; }
 
 // He-normal initialisation (seeded), zero biases, identity standardisation
@@ -525,6 +526,8 @@ cudaError_t mlp_targets(const ColumnArrays &c, int L, float *Yt, cudaStream_t st
 const float *mlp_grad(const Mlp *m) { return m->g; }
 
 // predictions for every loaded column, in chunks, applied as start populations
+cudaError_t mlp_prepare_predict(Mlp *m, int64_t ncol) { return mlp_ensure_work(m, std::min<int64_t>(16384, ncol)); }
+
 cudaError_t mlp_predict_apply(Mlp *m, const ColumnArrays &c, int L, float *X, float *lnb, int *nfallback_d,
                               cudaStream_t st)
 {
