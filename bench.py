@@ -269,6 +269,17 @@ def run_gpu(args):
     barrier()
     lte_s = time.perf_counter() - t_l
     lte_iters = s_l["iterations_total"] / ncol
+    # the paper's other start solutions (Sect. 2.3), one step each
+    other = {}
+    for name, kind in (("zero_radiation", 3), ("escape_probability", 4)):
+        barrier()
+        t_o = time.perf_counter()
+        s_o = ctx.solve(**dict(opts, start=kind))
+        barrier()
+        dt_o = time.perf_counter() - t_o
+        other[name] = {"value": ncol / dt_o, "unit": "columns/s",
+                       "iterations_per_column": s_o["iterations_total"] / ncol,
+                       "converged": s_o["n_converged"]}
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -346,6 +357,7 @@ def run_gpu(args):
         "lte_start": {"value": ncol / lte_s, "unit": "columns/s", "iterations_per_column": lte_iters,
                       "precision": "fp32 formal solution/rates, fp64 rate equations/Ng"},
         "lte_start_fp64": fp64,
+        "other_starts": other,
         "surrogate": train_info,
         "launch": {"block_warps": s["block_warps"], "ctas_per_sm": s["ctas_per_sm"],
                    "cuda_graph_replayed": s["graph_replayed"], "kernels_per_step": s["launches"],

@@ -119,7 +119,9 @@ typedef struct {
     int32_t ng_period;    /* iterations between accelerations */
     int32_t start;        /* 0: LTE populations; 1: learned initial guess (rh_surrogate_*),
                              LTE where its prediction is not finite; 2: populations set by
-                             rh_set_populations or left by the previous rh_iterate */
+                             rh_set_populations or left by the previous rh_iterate;
+                             3: zero radiation; 4: escape probability iterations
+                             (Sect. 2.3; see rh_start_populations) */
     int32_t precision;    /* 0: all FP64; 1: FP32 formal solution and rates, FP64 solve and Ng */
     int32_t persistent;   /* 0: static split of columns over resident blocks (normal mode,
                              Sect. 3.1); 1: device work queue (pool mode, Sect. 3.1) */
@@ -147,6 +149,22 @@ typedef struct {
  * rh_get_populations).  Returns RH_OK, or RH_ENOTCONV if any column did not
  * converge (results are still valid for the converged ones). */
 int rh_iterate(rh_ctx *ctx, const rh_iter_opts *opts, rh_iter_stats *stats_out);
+
+/* ---------------------------------------------------------------------- */
+/* Start solutions (Sect. 2.3: "LTE populations, zero radiation, and ...     */
+/* escape probability iterations"), written into the current populations of */
+/* every loaded column (iterate from them with start = 2).  kind 0: LTE.     */
+/* kind 3, zero radiation: the rate equations with J = 0 -- radiative rates  */
+/* are spontaneous only (A_ul; for a continuum the recombination            */
+/* 4 pi sum w (2 h nu^3/c^2) alpha (n*_l/n*_c) e^{-h nu/kT} / (h nu) over its */
+/* wavelength points) -- plus collisions, solved once per depth.  kind 4,    */
+/* escape probability: from LTE, 3 solves of the same equations with each    */
+/* spontaneous rate multiplied by the probability of escape through the top  */
+/* p = beta(tau)/2, beta(tau) = (1 - e^{-tau})/tau, tau the line-centre       */
+/* (Doppler core) or edge optical depth from the top at the previous         */
+/* populations.  FP64.  Status of each column: RH_COL_NOTRUN, or             */
+/* RH_COL_SINGULAR where a solve failed (its populations are then LTE).      */
+int rh_start_populations(rh_ctx *ctx, int32_t kind);
 
 /* ---------------------------------------------------------------------- */
 /* The paper's two-stage strategy as one call (Sect. 2.3: aggressive       */

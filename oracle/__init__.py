@@ -74,6 +74,8 @@ def lib():
         L.rho_iterate.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
         L.rho_rate_matrix.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int32, _dp]
         L.rho_collision_rates.argtypes = [C.c_void_p, C.c_int64, _dp]
+        L.rho_escape_probabilities.argtypes = [C.c_void_p, C.c_int64, _dp, _dp]
+        L.rho_start_populations.argtypes = [C.c_void_p, C.c_int32]
         L.rho_emergent_spectrum.argtypes = [C.c_void_p, C.c_double, C.c_int64, _dp, _dp, C.c_int32]
         L.rho_electron_density.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.rho_electron_density.restype = C.c_double
@@ -287,6 +289,18 @@ class Oracle:
         A = np.zeros((self.ndep, self.nlev, self.nlev))
         self._check(self._lib.rho_rate_matrix(self._p, col, _d(n), mode, _d(A)))
         return A
+
+    def escape_probabilities(self, col, n):
+        """p[t][k] of the escape-probability start for populations n of one column."""
+        n = np.ascontiguousarray(n, dtype=np.float64)
+        e = np.zeros((self.ntr, self.ndep))
+        self._check(self._lib.rho_escape_probabilities(self._p, col, _d(n), _d(e)))
+        return e
+
+    def start_populations(self, kind):
+        """Write the start populations (0 LTE, 3 zero radiation, 4 escape
+        probability) of every column into the current populations."""
+        self._check(self._lib.rho_start_populations(self._p, kind))
 
     def collision_rates(self, col):
         Cm = np.zeros((self.ndep, self.nlev, self.nlev))

@@ -74,7 +74,7 @@ typedef struct {
     int32_t maxiter;
     double tol;
     int32_t ng_order, ng_delay, ng_period;
-    int32_t start;      /* 0 LTE, 2 user populations */
+    int32_t start;      /* 0 LTE, 2 user populations, 3 zero radiation, 4 escape probability */
     double crsw_init;   /* collisional-radiative switching start factor; <=1 off */
 } rho_iter_opts;
 
@@ -1056,6 +1056,122 @@ static int stateq(const rho_ctx *c, int64_t col, work_t *w, const double *nold, 
     return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Start solutions other than LTE (Sect. 2.3: "LTE populations, zero
+ * radiation, and ... escape probability iterations").
+ *
+ * Rate matrix with the radiation field replaced by zero: no radiative
+ * excitation or ionisation; radiative de-excitation is spontaneous only --
+ * A_ul for a line, and for a continuum the spontaneous recombination
+ * 4 pi sum_lambda w_lambda (2 h nu^3/c^2) alpha(nu) (n*_l/n*_c) e^{-h nu/kT} / (h nu)
+ * over the continuum's own quadrature weights.  esc[t * N + k] multiplies the
+ * spontaneous rate of transition t at depth k (NULL: 1, zero radiation; the
+ * escape probability for the escape-probability start, where it is the net
+ * radiative bracket).  Collisions are added as in rate_matrix. */
+static void spont_rate_matrix(const rho_ctx *c, int64_t col, work_t *w, const double *esc)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    double *G = w->Gam;
+    memset(G, 0, sizeof(double) * N * L * L);
+    for (int t = 0; t < a->ntr; ++t) {
+        int l = a->tl[t], u = a->tu[t];
+        for (int k = 0; k < N; ++k) {
+            double R;
+            if (a->kind[t] == 0) {
+                R = a->A[t];
+            } else {
+                double G_lu = c->nstar[((size_t)col * L + l) * N + k] / c->nstar[((size_t)col * L + u) * N + k];
+                R = 0.0;
+                for (int64_t i = 0; i < a->nlam; ++i)
+                    for (int s2 = 0; s2 < a->nact[i]; ++s2) {
+                        if (a->act[i * MAXACT + s2] != t) continue;
+                        double nu = a->nu[i], r = a->nu0[t] / nu;
+                        double alpha = a->alpha0[t] * r * r * r;
+                        double tw = 2.0 * HPLANCK * nu * nu * nu / (CLIGHT * CLIGHT);
+                        R += 4.0 * PI_D * a->wq[i * MAXACT + s2] * tw * alpha * G_lu * w->ex[i * N + k] / (HPLANCK * nu);
+                    }
+            }
+            if (esc) R *= esc[(size_t)t * N + k];
+            G[(size_t)k * L * L + l * L + u] += R;
+        }
+    }
+    for (int k = 0; k < N; ++k) {
+        double *Gk = G + (size_t)k * L * L;
+        const double *Ck = w->C + (size_t)k * L * L;
+        for (int p = 0; p < L; ++p)
+            for (int q = 0; q < L; ++q)
+                if (p != q) Gk[q * L + p] += Ck[p * L + q];
+        for (int q = 0; q < L; ++q) {
+            double sum = 0.0;
+            for (int p = 0; p < L; ++p)
+                if (p != q) sum += Gk[p * L + q];
+            Gk[q * L + q] = -sum;
+        }
+    }
+}
+
+/* Escape probability of every transition at every depth for populations n:
+ * the line-centre (Doppler core, phi_0 = 1/(sqrt(pi) dnu_D)) or edge opacity
+ * chi_0 = (n_l - n_u g_l/g_u) (h nu0/4 pi) B_lu phi_0, resp. (n_l - n_u
+ * (n*_l/n*_u) e^{-h nu0/kT}) alpha0, clipped at zero; its optical depth
+ * from the top tau(k) by the trapezoid rule along z; and the probability of
+ * escape through the top of a semi-infinite atmosphere, averaged over
+ * directions, p = beta(tau)/2 with beta(tau) = (1 - e^{-tau})/tau (the
+ * single-flight escape probability; beta(0) = 1). */
+static void escape_probabilities(const rho_ctx *c, int64_t col, const work_t *w, const double *n, double *esc)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    const double *T = c->T + col * N;
+    for (int t = 0; t < a->ntr; ++t) {
+        int l = a->tl[t], u = a->tu[t];
+        double tau = 0.0, chip = 0.0;
+        for (int k = 0; k < N; ++k) {
+            double chi;
+            if (a->kind[t] == 0) {
+                double dnuD = a->nu0[t] / CLIGHT * sqrt(2.0 * KBOLTZ * T[k] / a->mass);
+                chi = (n[l * N + k] - n[u * N + k] * a->g[l] / a->g[u]) * HPLANCK * a->nu0[t] / (4.0 * PI_D) *
+                      a->Blu[t] / (sqrt(PI_D) * dnuD);
+            } else {
+                double G_lu = c->nstar[((size_t)col * L + l) * N + k] / c->nstar[((size_t)col * L + u) * N + k];
+                chi = (n[l * N + k] - n[u * N + k] * G_lu * exp(-HPLANCK * a->nu0[t] / (KBOLTZ * T[k]))) * a->alpha0[t];
+            }
+            if (chi < 0.0) chi = 0.0;
+            if (k > 0) tau += 0.5 * (chi + chip) * w->dz[k - 1];
+            chip = chi;
+            double beta = tau > 0.0 ? -expm1(-tau) / tau : 1.0;
+            esc[(size_t)t * N + k] = 0.5 * beta;
+        }
+    }
+}
+
+#define EP_ITERATIONS 3
+
+/* Start populations of one column: kind 3 zero radiation (one solve of the
+ * spontaneous-only rate equations, row choice and scaling from n*); kind 4
+ * escape probability (from LTE, EP_ITERATIONS solves, each with the escape
+ * probabilities of the previous populations).  Requires column_setup. */
+static int start_column(const rho_ctx *c, int64_t col, work_t *w, int kind, double *n)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    size_t nv = (size_t)L * N;
+    memcpy(n, c->nstar + (size_t)col * nv, nv * 8);
+    double *nn = malloc(nv * 8), *esc = malloc((size_t)a->ntr * N * 8);
+    int st = 0;
+    int nit = kind == 3 ? 1 : EP_ITERATIONS;
+    for (int it = 0; it < nit && !st; ++it) {
+        if (kind == 4) escape_probabilities(c, col, w, n, esc);
+        spont_rate_matrix(c, col, w, kind == 4 ? esc : NULL);
+        st = stateq(c, col, w, n, nn);
+        if (!st) memcpy(n, nn, nv * 8);
+    }
+    free(nn);
+    free(esc);
+    return st;
+}
+
 /* Ng (1974) acceleration of order 2 in the formulation of Auer (1987):
  * x0 newest .. x3 oldest; minimise |d0 - a(d0 - d1) - b(d0 - d2)|_w with
  * d_j = x_j - x_{j+1}; return (1-a-b) x0 + a x1 + b x2.  Weights: uniform
@@ -1107,6 +1223,18 @@ static void iterate_column(rho_ctx *c, int64_t col, const rho_iter_opts *o, work
         memcpy(n, c->nstar + (size_t)col * nv, nv * 8);
     int hcount = 0, it = 0, status = ST_MAXITER;
     double dmax = INFINITY;
+    if (o->start == 3 || o->start == 4) {
+        int st0 = start_column(c, col, w, o->start, n);
+        if (st0) {
+            c->iters[col] = 0;
+            c->status[col] = (uint8_t)st0;
+            c->dmax[col] = dmax;
+            *pts_out = 0.0;
+            free(nnew);
+            free(Cbase);
+            return;
+        }
+    }
     for (it = 1; it <= o->maxiter; ++it) {
         /* collisional-radiative switching (Hummer & Voels 1988): C scaled by
          * max(1, f0 10^{-(it-1)}) */
@@ -1218,16 +1346,64 @@ int rho_iterate(rho_ctx *c, const rho_iter_opts *o, rho_iter_stats *st, int32_t 
     return 0;
 }
 
-/* Rate matrix of one column at given populations (see rate_matrix for the
- * modes); A_out is [ndep][nlev][nlev]. */
+/* Rate matrix of one column at given populations (see rate_matrix for modes
+ * 0-2; mode 3 zero radiation, mode 4 escape probabilities from n; see
+ * spont_rate_matrix); A_out is [ndep][nlev][nlev]. */
 int rho_rate_matrix(rho_ctx *c, int64_t col, const double *n, int32_t mode, double *A_out)
 {
     if (col < 0 || col >= c->ncol) return fail(c, "column out of range");
     work_t w;
     work_alloc(&w, &c->at, c->ndep);
     column_setup(c, col, &w);
-    rate_matrix(c, col, &w, n, mode);
+    if (mode == 3) {
+        spont_rate_matrix(c, col, &w, NULL);
+    } else if (mode == 4) {
+        double *esc = malloc((size_t)c->at.ntr * c->ndep * 8);
+        escape_probabilities(c, col, &w, n, esc);
+        spont_rate_matrix(c, col, &w, esc);
+        free(esc);
+    } else {
+        rate_matrix(c, col, &w, n, mode);
+    }
     memcpy(A_out, w.Gam, sizeof(double) * c->ndep * c->at.nlev * c->at.nlev);
+    work_free(&w);
+    return 0;
+}
+
+/* Start populations (kind 0 LTE, 3 zero radiation, 4 escape probability)
+ * of every loaded column into the current populations; columns whose start
+ * solve fails get status ST_SINGULAR (others ST_NOTRUN). */
+int rho_start_populations(rho_ctx *c, int32_t kind)
+{
+    if (!c->ncol) return fail(c, "no columns loaded"), 4;
+    if (kind != 0 && kind != 3 && kind != 4) return fail(c, "start kind must be 0, 3 or 4");
+    const atom_t *a = &c->at;
+    size_t nv = (size_t)a->nlev * c->ndep;
+    work_t w;
+    work_alloc(&w, a, c->ndep);
+    for (int64_t col = 0; col < c->ncol; ++col) {
+        double *n = c->pops + (size_t)col * nv;
+        int st = 0;
+        if (kind == 0) {
+            memcpy(n, c->nstar + (size_t)col * nv, nv * 8);
+        } else {
+            column_setup(c, col, &w);
+            st = start_column(c, col, &w, kind, n);
+        }
+        c->status[col] = (uint8_t)(st ? st : ST_NOTRUN);
+    }
+    work_free(&w);
+    return 0;
+}
+
+/* escape probabilities esc[t][k] of one column for populations n */
+int rho_escape_probabilities(rho_ctx *c, int64_t col, const double *n, double *esc_out)
+{
+    if (col < 0 || col >= c->ncol) return fail(c, "column out of range");
+    work_t w;
+    work_alloc(&w, &c->at, c->ndep);
+    column_setup(c, col, &w);
+    escape_probabilities(c, col, &w, n, esc_out);
     work_free(&w);
     return 0;
 }

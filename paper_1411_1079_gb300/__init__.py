@@ -25,7 +25,7 @@ EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlam
            "rh_load_columns", "rh_iterate", "rh_get_populations", "rh_get_lte", "rh_set_populations",
            "rh_emergent_spectrum", "rh_iterate_noalloc", "rh_surrogate_init", "rh_surrogate_state_size",
            "rh_surrogate_get_state", "rh_surrogate_set_state", "rh_surrogate_train", "rh_surrogate_loss_grad",
-           "rh_surrogate_predict", "rh_solve", "rh_autotune")
+           "rh_surrogate_predict", "rh_solve", "rh_autotune", "rh_start_populations")
 
 MAX_RERUN = 4
 MAX_TUNE = 8
@@ -114,6 +114,7 @@ def lib(path: str | None = None):
         L.rh_iterate_noalloc.argtypes = [vp, C.POINTER(IterOpts), vp, vp, vp, vp, C.POINTER(IterStats)]
         L.rh_solve.argtypes = [vp, C.POINTER(SolveOpts), C.POINTER(SolveStats)]
         L.rh_autotune.argtypes = [vp, C.c_int32, C.POINTER(TuneResult)]
+        L.rh_start_populations.argtypes = [vp, C.c_int32]
         _fp = C.POINTER(C.c_float)
         L.rh_surrogate_init.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint64]
         L.rh_surrogate_state_size.argtypes = [vp]
@@ -261,6 +262,13 @@ class Context:
                 "guess_fallback_depths": st.guess_fallback_depths, "launches": st.kernel_launches,
                 "graph_replayed": bool(st.graph_replayed), "block_warps": st.block_warps,
                 "ctas_per_sm": st.ctas_per_sm}
+
+    START_LTE, START_LEARNED, START_CURRENT, START_ZERO_RADIATION, START_ESCAPE = 0, 1, 2, 3, 4
+
+    def start_populations(self, kind):
+        """rh_start_populations: write the LTE (0), zero-radiation (3) or
+        escape-probability (4) start into the current populations."""
+        self._check(self._lib.rh_start_populations(self._p, kind))
 
     def autotune(self, precision=1) -> dict:
         """rh_autotune: time the column kernel's launch shapes on a sample of

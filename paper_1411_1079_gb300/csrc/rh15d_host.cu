@@ -36,6 +36,10 @@ struct HostAtom {
     std::vector<int> lane_point;            // grid index of each padded lane, -1 padding
     std::vector<std::vector<int>> tile_union;
     double mu[RH_MAXMU], wmu[RH_MAXMU];
+    // spontaneous-recombination sums of the start solutions: per transition
+    // its continuum points (frequency, 4 pi w (2 h nu^3/c^2) alpha / (h nu))
+    std::vector<int> sp_off;
+    std::vector<double> sp_nu, sp_ce;
 };
 
 }  // namespace
@@ -82,6 +86,9 @@ struct rh_ctx {
     std::vector<unsigned char> gkey;            // what the captured graph was built from
     int glaunches = 0;
     cudaEvent_t pass_ev[1 + RH_MAX_RERUN] = {};   // end of each pass (recorded inside the sequence)
+    // start solutions: device copy of the continuum point lists
+    int *sp_off_d = nullptr;
+    double *sp_nu_d = nullptr, *sp_ce_d = nullptr;
     // rh_autotune: chosen launch shape per precision (0: none)
     int tuned_bw[2] = {0, 0}, tuned_ctas[2] = {0, 0};
 };
@@ -467,6 +474,22 @@ int build_atom(rh_ctx *c, const rh_atom_desc *d)
             }
         }
     }
+    a.sp_off.assign(1, 0);
+    for (int t = 0; t < a.ntr; ++t) {
+        const HostTrans &h = a.tr[t];
+        if (h.kind != 0) {
+            for (size_t gi = 0; gi < a.nu.size(); ++gi) {
+                auto it = std::find(a.act[gi].begin(), a.act[gi].end(), t);
+                if (it == a.act[gi].end()) continue;
+                const double nu = a.nu[gi], w = a.wq[gi][it - a.act[gi].begin()];
+                const double r = h.nu0 / nu, alpha = h.alpha0 * r * r * r;
+                const double tw = 2.0 * kH * nu * nu * nu / (kC * kC);
+                a.sp_nu.push_back(nu);
+                a.sp_ce.push_back(4.0 * kPi * w * tw * alpha / (kH * nu));
+            }
+        }
+        a.sp_off.push_back((int)a.sp_nu.size());
+    }
     c->ha = std::move(a);
     return RH_OK;
 }
@@ -493,6 +516,22 @@ int ensure_lane(rh_ctx *c, int prec)
     }
     c->lane_prec = prec;
     c->lane_nref = c->nref;
+    return RH_OK;
+}
+
+int ensure_start_tables(rh_ctx *c)
+{
+    if (c->sp_off_d) return RH_OK;
+    const HostAtom &a = c->ha;
+    const size_t np = std::max<size_t>(1, a.sp_nu.size());
+    CK(cudaMalloc(&c->sp_off_d, a.sp_off.size() * sizeof(int)));
+    CK(cudaMalloc(&c->sp_nu_d, np * sizeof(double)));
+    CK(cudaMalloc(&c->sp_ce_d, np * sizeof(double)));
+    CK(cudaMemcpy(c->sp_off_d, a.sp_off.data(), a.sp_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!a.sp_nu.empty()) {
+        CK(cudaMemcpy(c->sp_nu_d, a.sp_nu.data(), a.sp_nu.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->sp_ce_d, a.sp_ce.data(), a.sp_ce.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
     return RH_OK;
 }
 
@@ -756,6 +795,9 @@ void rh_destroy(rh_ctx *c)
     dfree(c->loss_d);
     dfree(c->solve_cnt);
     dfree(c->solve_it);
+    dfree(c->sp_off_d);
+    dfree(c->sp_nu_d);
+    dfree(c->sp_ce_d);
     drop_graph(c);
     for (cudaEvent_t &ev : c->pass_ev)
         if (ev) cudaEventDestroy(ev);
@@ -774,6 +816,9 @@ int rh_setup_atom(rh_ctx *c, const rh_atom_desc *d)
     int r = build_atom(c, d);
     if (r) return r;
     dfree(c->lane_d);
+    dfree(c->sp_off_d);
+    dfree(c->sp_nu_d);
+    dfree(c->sp_ce_d);
     c->lane_prec = -1;
     c->tuned_bw[0] = c->tuned_bw[1] = c->tuned_ctas[0] = c->tuned_ctas[1] = 0;
     drop_graph(c);
@@ -859,7 +904,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     if (!o) return fail(c, RH_EINVAL, "opts is NULL");
     if (o->maxiter < 1 || !(o->tol >= 0) || (o->ng_order != 0 && o->ng_order != 2) ||
         (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) || (o->precision != 0 && o->precision != 1) ||
-        (o->start < 0 || o->start > 2) || o->block_warps < 0 || o->block_warps > 8 ||
+        (o->start < 0 || o->start > 4) || o->block_warps < 0 || o->block_warps > 8 ||
         (o->only_unconverged != 0 && o->only_unconverged != 1))
         return fail(c, RH_EINVAL, "rh_iterate: invalid options");
     cudaSetDevice(c->dev);
@@ -888,6 +933,23 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
         cudaEventDestroy(g0);
         cudaEventDestroy(g1);
         fallback = nfb;
+        guess_s = guess_ms * 1e-3;
+        start = 2;
+    } else if (start == 3 || start == 4) {
+        if (o->only_unconverged)
+            return fail(c, RH_EINVAL, "rh_iterate: start = %d applies to all columns (only_unconverged = 0)", start);
+        int r = ensure_start_tables(c);
+        if (r) return r;
+        cudaEvent_t g0, g1;
+        CK(cudaEventCreate(&g0));
+        CK(cudaEventCreate(&g1));
+        CK(cudaEventRecord(g0, c->st));
+        CK(launch_start(c->da, c->ca, start, c->sp_off_d, c->sp_nu_d, c->sp_ce_d, c->st));
+        CK(cudaEventRecord(g1, c->st));
+        CK(cudaEventSynchronize(g1));
+        cudaEventElapsedTime(&guess_ms, g0, g1);
+        cudaEventDestroy(g0);
+        cudaEventDestroy(g1);
         guess_s = guess_ms * 1e-3;
         start = 2;
     }
@@ -1125,12 +1187,12 @@ bool valid_iter_opts(const rh_iter_opts *o)
 {
     return o->maxiter >= 1 && o->tol >= 0 && (o->ng_order == 0 || o->ng_order == 2) &&
            !(o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) && (o->precision == 0 || o->precision == 1) &&
-           o->start >= 0 && o->start <= 2 && o->block_warps >= 0 && o->block_warps <= 8;
+           o->start >= 0 && o->start <= 4 && o->block_warps >= 0 && o->block_warps <= 8;
 }
 
 // everything the enqueued sequence depends on, compared byte-wise
 struct SolveKey {
-    const void *ptrs[24];
+    const void *ptrs[27];
     int64_t ncol;
     int ndep, bw, ctas, nsm;
     rh_solve_opts o;
@@ -1142,8 +1204,9 @@ SolveKey make_key(const rh_ctx *c, const rh_solve_opts *o, int bw, int ctas)
     memset(&k, 0, sizeof k);
     const void *p[] = {c->ca.z, c->ca.T, c->ca.nH, c->ca.vz, c->ca.ne, c->ca.np, c->ca.nstar, c->ca.pops,
                        c->ca.Crate, c->ca.dmax, c->ca.iters, c->ca.status, c->lane_d, c->vtab_d, c->nghist,
-                       c->queue, c->colidx, c->solve_cnt, c->solve_it, c->mlp, c->feat, c->lnb, c->nfb_d, c->st};
-    static_assert(sizeof p / sizeof p[0] == 24, "key size");
+                       c->queue, c->colidx, c->solve_cnt, c->solve_it, c->mlp, c->feat, c->lnb, c->nfb_d, c->st,
+                       c->sp_off_d, c->sp_nu_d, c->sp_ce_d};
+    static_assert(sizeof p / sizeof p[0] == 27, "key size");
     memcpy(k.ptrs, p, sizeof p);
     k.ncol = c->ncol;
     k.ndep = c->ndep;
@@ -1175,10 +1238,14 @@ cudaError_t enqueue_solve(rh_ctx *c, const rh_solve_opts *o, const IterLaunch &b
         if ((e = mlp_predict_apply(c->mlp, c->ca, c->da.nlev, c->feat, c->lnb, c->nfb_d, st)) != cudaSuccess) return e;
         const int64_t nchunk = (c->ncol + 16383) / 16384;
         nk += 2 + (int)nchunk * (1 + mlp_nlayer(c->mlp));
+    } else if (o->pass1.start == 3 || o->pass1.start == 4) {
+        if ((e = launch_start(c->da, c->ca, o->pass1.start, c->sp_off_d, c->sp_nu_d, c->sp_ce_d, st)) != cudaSuccess)
+            return e;
+        nk += 1;
     }
     const int sgrid = 2 * c->nsm;
     IterLaunch il = base;
-    il.start = o->pass1.start == 1 ? 2 : o->pass1.start;
+    il.start = o->pass1.start == 0 ? 0 : 2;
     il.colidx = nullptr;
     il.nwork = c->ncol;
     il.nwork_d = nullptr;
@@ -1231,6 +1298,25 @@ cudaError_t enqueue_solve(rh_ctx *c, const rh_solve_opts *o, const IterLaunch &b
 }  // namespace
 
 extern "C" {
+
+int rh_start_populations(rh_ctx *c, int32_t kind)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "rh_start_populations: no columns loaded");
+    if (kind != 0 && kind != 3 && kind != 4) return fail(c, RH_EINVAL, "rh_start_populations: kind 0, 3 or 4");
+    cudaSetDevice(c->dev);
+    const size_t nv = (size_t)c->ncol * c->ndep * c->da.nlev;
+    if (kind == 0) {
+        CK(cudaMemcpyAsync(c->ca.pops, c->ca.nstar, nv * 8, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemsetAsync(c->ca.status, RH_COL_NOTRUN, c->ncol, c->st));
+    } else {
+        int r = ensure_start_tables(c);
+        if (r) return r;
+        CK(launch_start(c->da, c->ca, kind, c->sp_off_d, c->sp_nu_d, c->sp_ce_d, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    return RH_OK;
+}
 
 int rh_autotune(rh_ctx *c, int32_t precision, rh_tune_result *out)
 {
@@ -1347,6 +1433,10 @@ int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
         int r = ensure_mlp_buffers(c);
         if (r) return r;
         CK(mlp_prepare_predict(c->mlp, c->ncol));
+    }
+    if (o->pass1.start == 3 || o->pass1.start == 4) {
+        int r = ensure_start_tables(c);
+        if (r) return r;
     }
     if (o->autotune && o->pass1.block_warps == 0 && !c->tuned_bw[prec]) {
         int r = rh_autotune(c, prec, nullptr);

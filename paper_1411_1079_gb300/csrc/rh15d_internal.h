@@ -365,6 +365,13 @@ int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_wa
 cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
                                  const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
                                  const IterLaunch &o, cudaStream_t st, int *grid_out, char *err, size_t errn);
+// start populations other than LTE: kind 3 zero radiation, 4 escape
+// probability (kStartEscapeIterations solves); sp_* list, per continuum
+// transition t, its wavelength points sp_off[t] .. sp_off[t+1]-1 (frequency and
+// 4 pi w (2 h nu^3/c^2) alpha / (h nu)); lines have empty ranges
+constexpr int kStartEscapeIterations = 3;
+cudaError_t launch_start(const DevAtom &A, const ColumnArrays &c, int kind, const int *sp_off, const double *sp_nu,
+                         const double *sp_ce, cudaStream_t st);
 // emergent spectrum: per requested wavelength j, up to RH_SPEC_ACT transitions
 // with constants spec[(j * RH_SPEC_ACT + s) * RH_SPEC_F + f]
 #define RH_SPEC_ACT 8

@@ -149,6 +149,156 @@ __global__ void spectrum_kernel(const __grid_constant__ DevAtom A, ColumnArrays 
     out[idx] = (double)I;
 }
 
+// ----------------------------------------------------------------------------
+// Start populations other than LTE (Sect. 2.3: zero radiation, escape
+// probability iterations).  One block per column, FP64.  The radiative rates
+// keep only spontaneous emission -- A_ul for a line; for a continuum the
+// recombination sum_j ce_j e^{-h nu_j/kT} (n*_l/n*_c) over the continuum's
+// wavelength points, ce_j = 4 pi w_j (2 h nu_j^3/c^2) alpha(nu_j)/(h nu_j) --
+// times, for the escape-probability start, the probability of escape through
+// the top p = beta(tau)/2, beta(tau) = (1 - e^{-tau})/tau, tau the line-centre
+// (Doppler core) or edge optical depth from the top by the trapezoid rule at
+// the current populations (opacity clipped at zero).  Each solve: the rate
+// matrix with collisions, the row of the most populated level (current
+// populations) replaced by particle conservation, unknowns scaled by the
+// current populations, rows equilibrated, partial pivoting.  A column whose
+// solve fails keeps its LTE populations and gets status SINGULAR.
+__device__ int start_solve_depth(const DevAtom &A, const double *R, const double *esc, const double *Cr, int N,
+                                 int k, const double *n, double nH, double *nn)
+{
+    const int L = A.nlev;
+    double G[RH_MAXLEV * RH_MAXLEV];
+    for (int i = 0; i < L * L; ++i) G[i] = 0.0;
+    for (int t = 0; t < A.ntr; ++t) {
+        const int l = A.tr[t].l, u = A.tr[t].u;
+        G[l * L + u] += R[t * N + k] * esc[t * N + k] + Cr[2 * t + 1];
+        G[u * L + l] += Cr[2 * t];
+    }
+    for (int q = 0; q < L; ++q) {
+        double s = 0.0;
+        for (int pp = 0; pp < L; ++pp)
+            if (pp != q) s += G[pp * L + q];
+        G[q * L + q] = -s;
+    }
+    double sc[RH_MAXLEV], b[RH_MAXLEV];
+    int r = 0;
+    for (int l = 0; l < L; ++l) {
+        sc[l] = n[l * N + k];
+        if (sc[l] > sc[r]) r = l;
+        b[l] = 0.0;
+    }
+    for (int q = 0; q < L; ++q) G[r * L + q] = 1.0;
+    b[r] = nH;
+    for (int pp = 0; pp < L; ++pp) {
+        double mx = 0.0;
+        for (int q = 0; q < L; ++q) {
+            G[pp * L + q] *= sc[q];
+            mx = fmax(mx, fabs(G[pp * L + q]));
+        }
+        if (!(mx > 0.0)) return 1;
+        for (int q = 0; q < L; ++q) G[pp * L + q] /= mx;
+        b[pp] /= mx;
+    }
+    for (int cc = 0; cc < L; ++cc) {
+        int piv = cc;
+        for (int rr = cc + 1; rr < L; ++rr)
+            if (fabs(G[rr * L + cc]) > fabs(G[piv * L + cc])) piv = rr;
+        if (G[piv * L + cc] == 0.0) return 1;
+        if (piv != cc) {
+            for (int q = 0; q < L; ++q) {
+                double tmp = G[cc * L + q];
+                G[cc * L + q] = G[piv * L + q];
+                G[piv * L + q] = tmp;
+            }
+            double tmp = b[cc];
+            b[cc] = b[piv];
+            b[piv] = tmp;
+        }
+        for (int rr = cc + 1; rr < L; ++rr) {
+            double f = G[rr * L + cc] / G[cc * L + cc];
+            for (int q = cc; q < L; ++q) G[rr * L + q] -= f * G[cc * L + q];
+            b[rr] -= f * b[cc];
+        }
+    }
+    for (int cc = L - 1; cc >= 0; --cc) {
+        double s = b[cc];
+        for (int q = cc + 1; q < L; ++q) s -= G[cc * L + q] * b[q];
+        b[cc] = s / G[cc * L + cc];
+    }
+    for (int l = 0; l < L; ++l) {
+        const double v = b[l] * sc[l];
+        if (!(isfinite(v) && v > 0.0)) return 1;
+        nn[l * N + k] = v;
+    }
+    return 0;
+}
+
+__global__ void start_kernel(const __grid_constant__ DevAtom A, ColumnArrays c, int kind, int nit, const int *sp_off,
+                             const double *sp_nu, const double *sp_ce)
+{
+    extern __shared__ double sm[];
+    const int N = c.ndep, L = A.nlev, NT = A.ntr, LN = L * N;
+    double *n = sm, *nn = n + LN, *R = nn + LN, *esc = R + NT * N;
+    __shared__ int bad;
+    const int64_t col = blockIdx.x;
+    const int tid = threadIdx.x;
+    const size_t cN = (size_t)col * N;
+    const double *nstar = c.nstar + (size_t)col * LN;
+    if (tid == 0) bad = 0;
+    for (int i = tid; i < LN; i += blockDim.x) n[i] = nstar[i];
+    for (int i = tid; i < NT * N; i += blockDim.x) {
+        const int t = i / N, k = i % N;
+        const DevTrans &tr = A.tr[t];
+        double r;
+        if (tr.kind == 0) {
+            r = tr.A;
+        } else {
+            const double kT = kK * c.T[cN + k], G = nstar[tr.l * N + k] / nstar[tr.u * N + k];
+            double s = 0.0;
+            for (int j = sp_off[t]; j < sp_off[t + 1]; ++j) s += sp_ce[j] * exp(-kH * sp_nu[j] / kT);
+            r = s * G;
+        }
+        R[i] = r;
+        esc[i] = 1.0;
+    }
+    __syncthreads();
+    const double *Crc = c.Crate + cN * 2 * NT;
+    for (int it = 0; it < nit; ++it) {
+        if (kind == 4) {
+            for (int t = tid; t < NT; t += blockDim.x) {
+                const DevTrans &tr = A.tr[t];
+                double tau = 0.0, chip = 0.0;
+                for (int k = 0; k < N; ++k) {
+                    const double T = c.T[cN + k];
+                    double chi;
+                    if (tr.kind == 0) {
+                        const double dnuD = tr.nu0 / kC * sqrt(2.0 * kK * T / A.mass);
+                        chi = (n[tr.l * N + k] - n[tr.u * N + k] * (tr.Bul / tr.Blu)) * (kH * tr.nu0 / (4.0 * kPi)) *
+                              tr.Blu / (kSqrtPi * dnuD);
+                    } else {
+                        const double G = nstar[tr.l * N + k] / nstar[tr.u * N + k];
+                        chi = (n[tr.l * N + k] - n[tr.u * N + k] * G * exp(-kH * tr.nu0 / (kK * T))) * tr.alpha0;
+                    }
+                    chi = fmax(chi, 0.0);
+                    if (k > 0) tau += 0.5 * (chi + chip) * fabs(c.z[cN + k - 1] - c.z[cN + k]);
+                    chip = chi;
+                    esc[t * N + k] = 0.5 * (tau > 0.0 ? -expm1(-tau) / tau : 1.0);
+                }
+            }
+            __syncthreads();
+        }
+        for (int k = tid; k < N; k += blockDim.x)
+            if (start_solve_depth(A, R, esc, Crc + (size_t)k * 2 * NT, N, k, n, c.nH[cN + k], nn)) bad = 1;
+        __syncthreads();
+        if (bad) break;
+        for (int i = tid; i < LN; i += blockDim.x) n[i] = nn[i];
+        __syncthreads();
+    }
+    double *pops = c.pops + (size_t)col * LN;
+    for (int i = tid; i < LN; i += blockDim.x) pops[i] = bad ? nstar[i] : n[i];
+    if (tid == 0) c.status[col] = (uint8_t)(bad ? RH_COL_SINGULAR : RH_COL_NOTRUN);
+}
+
 }  // namespace
 
 cudaError_t launch_lte_setup(const DevAtom &A, const ColumnArrays &c, int ne_given, cudaStream_t st)
@@ -158,6 +308,18 @@ cudaError_t launch_lte_setup(const DevAtom &A, const ColumnArrays &c, int ne_giv
     int threads = 128;
     int64_t blocks = (n + threads - 1) / threads;
     lte_setup_kernel<<<(unsigned)blocks, threads, 0, st>>>(A, c, ne_given);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_start(const DevAtom &A, const ColumnArrays &c, int kind, const int *sp_off, const double *sp_nu,
+                         const double *sp_ce, cudaStream_t st)
+{
+    if (c.ncol == 0) return cudaSuccess;
+    const size_t sm = sizeof(double) * (2 * (size_t)A.nlev * c.ndep + 2 * (size_t)A.ntr * c.ndep);
+    cudaError_t e = cudaFuncSetAttribute(start_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    start_kernel<<<(unsigned)c.ncol, 128, sm, st>>>(A, c, kind, kind == 4 ? kStartEscapeIterations : 1, sp_off, sp_nu,
+                                                    sp_ce);
     return cudaGetLastError();
 }
 

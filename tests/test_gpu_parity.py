@@ -270,3 +270,26 @@ def test_large_batch_sampled_against_oracle(rh, orc, atom):
     # conservation on every column
     assert np.allclose(n.sum(axis=1), cube["nH"], rtol=1e-12)
     assert s["rerun_columns"] < 0.01 * 65536
+
+
+@pytest.mark.parametrize("kind", [3, 4])
+def test_start_solutions_match_oracle(rh, orc, atom, cols, kind):
+    """Zero-radiation (3) and escape-probability (4) starts, FP64, and a fixed
+    FP64 schedule without Ng from them."""
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    g.load_columns(cols)
+    g.start_populations(kind)
+    n, _, st, _ = g.populations()
+    o = orc.Oracle()
+    o.setup_atom(atom)
+    o.load_columns(cols)
+    o.start_populations(kind)
+    no, _, sto, _ = o.populations()
+    assert np.array_equal(st, sto) and np.all(st == 4)
+    assert rel(n, no) < FP64_TOL
+    ns, _ = o.lte()
+    assert rel(n, ns) > 1e-2            # a start of its own, not LTE
+    g.iterate(maxiter=4, tol=0.0, precision=0, start=kind, ng_order=0)
+    o.iterate(maxiter=4, tol=0.0, start=kind, ng_order=0)
+    assert rel(g.populations()[0], o.populations()[0]) < FP64_TOL

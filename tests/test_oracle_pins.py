@@ -341,6 +341,111 @@ def test_lte_limit_with_dominant_collisions(orc):
         assert np.allclose(Sl, B, rtol=1e-5)
 
 
+# ---------------------------------------------------------------- start solutions (Sect. 2.3)
+def test_zero_radiation_rates_are_spontaneous_emission(orc, column_oracle):
+    # J = 0: no radiative excitation or ionisation; a line de-excites at the
+    # Einstein A (textbook relation to f), a continuum recombines at the
+    # spontaneous Milne rate (adaptive quadrature of the exact integral)
+    from scipy.integrate import quad
+    o = column_oracle
+    ns, _ = o.lte()
+    A3 = o.rate_matrix(0, ns[0], 3)
+    Cm = o.collision_rates(0)
+    atom = rh_synth.hydrogen_like_atom()
+    E, g = atom["E_J"], atom["g"]
+    T = rh_synth.chromosphere_column()["T"][0]
+    nl = len(atom["line_l"])
+    e2 = sc.e ** 2 / (4 * np.pi * sc.epsilon_0)
+    for k in (3, 41, 80):
+        R = A3[k] - Cm[k].T                 # radiative part: R[r][q] = rate q -> r
+        np.fill_diagonal(R, 0.0)
+        for t, (l, u) in enumerate(zip(atom["line_l"], atom["line_u"])):
+            nu = (E[u] - E[l]) / sc.h
+            A_ul = 8 * np.pi ** 2 * e2 * nu ** 2 / (sc.m_e * sc.c ** 3) * g[l] / g[u] * atom["line_f"][t]
+            assert R[l, u] == pytest.approx(A_ul, rel=1e-8)
+            assert abs(R[u, l]) <= 1e-12 * R[l, u]
+        ic = len(E) - 1
+        grid = o.grid()
+        for j, l in enumerate(atom["cont_l"]):
+            nu0 = (E[ic] - E[l]) / sc.h
+            G = ns[0, l, k] / ns[0, ic, k]
+            a = sc.h / (sc.k * T[k])
+            cst = 4 * np.pi * 2 / sc.c ** 2 * atom["cont_alpha0"][j] * nu0 ** 3 * G
+
+            def f(nu):                      # = cst e^{-a nu} / nu
+                return cst * np.exp(-a * nu) / nu
+
+            def f2(nu):                     # second and fourth derivatives
+                return cst * np.exp(-a * nu) * (a * a / nu + 2 * a / nu ** 2 + 2 / nu ** 3)
+
+            def f4(nu):
+                return cst * np.exp(-a * nu) * (a ** 4 / nu + 4 * a ** 3 / nu ** 2 + 12 * a * a / nu ** 3
+                                                + 24 * a / nu ** 4 + 24 / nu ** 5)
+            exact = quad(f, nu0, nu0 * atom["cont_ratio"][j], epsrel=1e-13, limit=400)[0]
+            # the trapezoid rule on the grid's points of this continuum exceeds
+            # the integral by its error expansion about the interval midpoints,
+            # sum h^3 f2/12 + h^5 f4/480 + O(h^7)
+            pts = np.sort(grid["nu"][(grid["act"] == nl + j).any(axis=1)])
+            h = np.diff(pts)
+            mid = 0.5 * (pts[1:] + pts[:-1])
+            err = np.sum(h ** 3 * f2(mid)) / 12 + np.sum(h ** 5 * f4(mid)) / 480
+            assert pts[0] == pytest.approx(nu0, rel=1e-14)
+            assert R[l, ic] == pytest.approx(exact + err, rel=1e-4), (k, j, R[l, ic] / exact - 1, err / exact)
+            assert abs(R[ic, l]) <= 1e-12 * R[l, ic]
+
+
+@pytest.mark.parametrize("kind", [3, 4])
+def test_start_solutions_tend_to_lte_when_collisions_dominate(orc, kind):
+    # collisional rates scale with n_e: the departures of the start populations
+    # from Saha-Boltzmann fall as 1/f
+    atom = rh_synth.hydrogen_like_atom()
+    cols = rh_synth.chromosphere_column()
+    o0 = orc.Oracle()
+    o0.setup_atom(atom)
+    o0.load_columns(cols)
+    _, ne = o0.lte()
+    dev = {}
+    for f in (1e10, 1e12):
+        o = orc.Oracle()
+        o.setup_atom(atom)
+        o.load_columns(cols, ne=ne * f)
+        o.start_populations(kind)
+        n = o.populations()[0]
+        ns, _ = o.lte()
+        dev[f] = np.max(np.abs(n / ns - 1))
+    assert dev[1e12] < 1e-4
+    assert dev[1e12] / dev[1e10] == pytest.approx(1e-2, rel=0.1)
+
+
+def test_escape_probability_limits(orc, column_oracle):
+    o = column_oracle
+    ns, _ = o.lte()
+    p = o.escape_probabilities(0, ns[0])
+    # at the surface half the photons escape (upward half of the directions)
+    assert np.allclose(p[:, 0], 0.5, rtol=0, atol=1e-15)
+    # non-increasing with depth; Lyman alpha is thermalised at the bottom
+    assert np.all(np.diff(p, axis=1) <= 1e-15)
+    assert p[0, -1] < 1e-8
+    # beta(tau) = (1 - e^-tau)/tau: ~ 1/(2 tau) deep down, with tau of Lyman
+    # alpha at the bottom > 1e8
+
+
+def test_every_start_reaches_the_same_fixed_point(orc):
+    atom = rh_synth.small_atom()
+    cols = rh_synth.subset(rh_synth.chromosphere_cube(nx=16, ny=16, ndep=24, seed=3), [0, 5, 77])
+    res = {}
+    for kind in (0, 3, 4):
+        o = orc.Oracle()
+        o.setup_atom(atom)
+        o.load_columns(cols)
+        o.iterate(maxiter=2000, tol=1e-11, start=kind)
+        n, it, st, _ = o.populations()
+        assert np.all(st == 0), (kind, st)
+        res[kind] = n
+    assert np.allclose(res[3], res[0], rtol=1e-8)
+    assert np.allclose(res[4], res[0], rtol=1e-8)
+
+
 def test_mali_converges_with_conservation(orc, column_oracle):
     o = column_oracle
     st = o.iterate(maxiter=300, tol=1e-3)

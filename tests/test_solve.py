@@ -117,3 +117,30 @@ def test_solve_rejects_bad_options(rh, atom, cols):
         g.solve(maxiter=0)
     with pytest.raises(rh.RhError):
         g.solve(start=1)          # no network
+
+
+def test_solve_from_every_start(rh, atom, cols):
+    """Every start (LTE, zero radiation, escape probability) converges every
+    column under the two-stage strategy; at a tight criterion they reach the
+    same solutions (a column that differs must show that both states solve
+    the equations: the discrete problem can have more than one solution).
+    At the paper's 1e-3 the stopping points of different starts differ by up
+    to a few 1e-2, so the comparison is made at 1e-5."""
+    res = {}
+    for kind in (0, 3, 4):
+        g = ctx(rh, atom, cols)
+        s = g.solve(precision=1, start=kind)
+        assert s["n_converged"] == len(g.populations()[1]), (kind, s)
+        g.load_columns(cols)
+        s = g.solve(precision=1, start=kind, tol=1e-5, maxiter=1000)
+        assert s["n_converged"] == len(g.populations()[1]), (kind, s)
+        res[kind] = (g, g.populations()[0])
+    for kind in (3, 4):
+        d = np.abs(res[kind][1] / res[0][1] - 1).max(axis=(1, 2))
+        differ = d > 2e-3
+        assert differ.mean() < 0.01, (kind, np.sort(d)[-5:])
+        for k2 in (0, kind):
+            g, n = res[k2]
+            g.set_populations(n)
+            g.iterate(maxiter=1, tol=0.0, ng_order=0, start=2, precision=1)
+            assert np.all(g.populations()[3][differ] < 1e-4), (kind, k2)
