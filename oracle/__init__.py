@@ -81,6 +81,11 @@ def lib():
         L.rho_electron_density.restype = C.c_double
         L.rho_hminus_sigma.restype = C.c_double
         L.rho_hminus_sigma.argtypes = [C.c_double]
+        L.rho_faddeeva.restype = None
+        L.rho_faddeeva.argtypes = [C.c_double, C.c_double, _dp, _dp]
+        L.rho_stokes_sweep.restype = None
+        L.rho_stokes_sweep.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp]
+        L.rho_emergent_stokes.argtypes = [C.c_void_p, C.c_int32, C.c_double, _dp, _dp, _dp, C.c_int64, _dp, _dp]
     return _lib
 
 
@@ -118,6 +123,27 @@ class IterStats(C.Structure):
 def voigt(a, v):
     L = lib()
     return float(L.rho_voigt(float(a), float(v)))
+
+
+def faddeeva(a, v):
+    """(H, L) = (Re, Im) of w(v + i a)."""
+    h = C.c_double()
+    l_ = C.c_double()
+    lib().rho_faddeeva(float(a), float(v), C.byref(h), C.byref(l_))
+    return h.value, l_.value
+
+
+def stokes_sweep(dtau, Kp, S, Ib):
+    """DELO-linear polarised sweep from k = N-1 to k = 0; returns the Stokes
+    vector at k = 0.  dtau [N-1], Kp [N][6] = (eQ, eU, eV, rQ, rU, rV)/eI,
+    S [N][4] emission / eI, Ib [4]."""
+    dtau = np.ascontiguousarray(dtau, dtype=np.float64)
+    Kp = np.ascontiguousarray(Kp, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    Ib = np.ascontiguousarray(Ib, dtype=np.float64)
+    out = np.zeros(4)
+    lib().rho_stokes_sweep(S.shape[0], _d(dtau), _d(Kp), _d(S), _d(Ib), _d(out))
+    return out
 
 
 def expE1(y):
@@ -301,6 +327,15 @@ class Oracle:
         """Write the start populations (0 LTE, 3 zero radiation, 4 escape
         probability) of every column into the current populations."""
         self._check(self._lib.rho_start_populations(self._p, kind))
+
+    def emergent_stokes(self, line, geff, B_T, theta, chi, lam_m):
+        """Stokes (I, Q, U, V) at mu = 1 of line `line` with Zeeman splitting;
+        B_T, theta, chi [ncol][ndep]; returns [ncol][nlam][4]."""
+        B_T, theta, chi, lam_m = (np.ascontiguousarray(x, dtype=np.float64) for x in (B_T, theta, chi, lam_m))
+        out = np.zeros((self.ncol, lam_m.size, 4))
+        self._check(self._lib.rho_emergent_stokes(self._p, line, geff, _d(B_T), _d(theta), _d(chi), lam_m.size,
+                                                  _d(lam_m), _d(out)))
+        return out
 
     def collision_rates(self, col):
         Cm = np.zeros((self.ndep, self.nlev, self.nlev))

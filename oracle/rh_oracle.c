@@ -204,6 +204,61 @@ double rho_voigt(double a, double v)
     return near + far;
 }
 
+/* Faddeeva function w(v + i a) = H(a,v) + i L(a,v), a > 0: H as rho_voigt;
+ * the dispersion part L(a,v) = (1/pi) int exp(-u^2) (v - u)/((v-u)^2 + a^2) du
+ *  |v| >= 8: from the same continued fraction (Im w = Re f/(sqrt(pi)|f|^2));
+ *  |v| <  8: the convolution integral, split at |u - v| = D = 1/2: near part
+ *     with s = u - v the kernel is odd, (1/pi) int_0^D [g(-s) - g(s)] s/(s^2+a^2) ds,
+ *     g(s) = exp(-(v+s)^2), on 24 geometrically shrinking panels towards s = 0
+ *     (10-point Gauss-Legendre); far part |u - v| > D, u in [-9, 9], panels of
+ *     width <= 1/2.  L is odd in v.  Pinned against scipy.special.wofz. */
+static double disp_far(double a, double v, double lo, double hi)
+{
+    if (!(hi > lo)) return 0.0;
+    int np = (int)ceil((hi - lo) / 0.5);
+    double h = (hi - lo) / np, s = 0.0;
+    for (int p = 0; p < np; ++p)
+        for (int i = 0; i < 10; ++i) {
+            double u = lo + h * (p + gl10_x[i]);
+            double d = v - u;
+            s += gl10_w[i] * h * exp(-u * u) * d / (a * a + d * d);
+        }
+    return s;
+}
+
+void rho_faddeeva(double a, double v, double *H, double *L)
+{
+    double av = fabs(v), sg = v < 0 ? -1.0 : 1.0;
+    if (av >= 8.0) {
+        double fr = av, fi = a;
+        for (int k = 60; k >= 1; --k) {
+            double d = fr * fr + fi * fi;
+            double qr = 0.5 * k * fr / d, qi = -0.5 * k * fi / d;
+            fr = av - qr;
+            fi = a - qi;
+        }
+        double m = sqrt(PI_D) * (fr * fr + fi * fi);
+        *H = fi / m;
+        *L = sg * fr / m;
+        return;
+    }
+    *H = rho_voigt(a, v);
+    pthread_once(&gl10_once, gl10_init);
+    const double D = 0.5;
+    double near = 0.0;
+    for (int j = 0; j < 24; ++j) {
+        double hi = D * ldexp(1.0, -j), lo = j == 23 ? 0.0 : 0.5 * hi;
+        double h = hi - lo;
+        for (int i = 0; i < 10; ++i) {
+            double sv = lo + h * gl10_x[i];
+            double gp = exp(-(av + sv) * (av + sv)), gm = exp(-(av - sv) * (av - sv));
+            near += gl10_w[i] * h * (gm - gp) * sv / (a * a + sv * sv);
+        }
+    }
+    double far = disp_far(a, av, -9.0, av - D) + disp_far(a, av, av + D, 9.0);
+    *L = sg * (near + far) / PI_D;
+}
+
 /* e^y E1(y) for y > 0: power series for y <= 1, continued fraction
  * E1(y) = e^{-y} / (y + 1 - 1/(y + 3 - 4/(y + 5 - ...))) otherwise
  * (Abramowitz & Stegun 5.1.11 and 5.1.22).  Pinned against scipy.special.exp1. */
@@ -1523,6 +1578,152 @@ int rho_emergent_spectrum(rho_ctx *c, double mu, int64_t nl, const double *lam, 
 /* ================================================================== */
 
 /* Jbar and Lambda-bar* for a given S */
+/* ------------------------------------------------------------------ */
+/* Polarised formal solution (NEXT: Zeeman Stokes spectra of one line).
+ * dI/dtau = I - S_eff along the ray, tau measured with eta_I, S_eff = S - K' I,
+ * K' = K/eta_I - 1 (zero diagonal), in the convention
+ *     K = [[eI, eQ, eU, eV], [eQ, eI, rV, -rU], [eU, -rV, eI, rQ], [eV, rU, -rQ, eI]]
+ * (Landi Degl'Innocenti & Landolfi 2004).  DELO-linear (Rees, Durrant &
+ * Murphy 1989): S_eff interpolated linearly on each interval, the local K'I
+ * taken implicitly:
+ *     (1 + w_o K'_o) I_o = e^{-dtau} I_u + w_u (S_u - K'_u I_u) + w_o S_o
+ * with the weights of the scalar linear short characteristics (which it
+ * reduces to when K' = 0).  Kp[k] = (eQ, eU, eV, rQ, rU, rV)/eI, S[k] the
+ * emission vector / eI.  The ray starts at k = N-1 with Ib and ends at k = 0. */
+static void kprime(const double *kp, double M[4][4])
+{
+    double eQ = kp[0], eU = kp[1], eV = kp[2], rQ = kp[3], rU = kp[4], rV = kp[5];
+    double m[4][4] = {{0, eQ, eU, eV}, {eQ, 0, rV, -rU}, {eU, -rV, 0, rQ}, {eV, rU, -rQ, 0}};
+    memcpy(M, m, sizeof m);
+}
+
+void rho_stokes_sweep(int N, const double *dtau, const double *Kp, const double *S, const double *Ib, double *Itop)
+{
+    double I[4];
+    memcpy(I, Ib, sizeof I);
+    for (int k = N - 2; k >= 0; --k) {
+        double ex, wu, wo, omwo;
+        sc_step_weights(dtau[k], &ex, &wu, &wo, &omwo);
+        double Mu[4][4], Mo[4][4];
+        kprime(Kp + (size_t)(k + 1) * 6, Mu);
+        kprime(Kp + (size_t)k * 6, Mo);
+        double rhs[4], A[16];
+        for (int i = 0; i < 4; ++i) {
+            double ku = 0.0;
+            for (int j = 0; j < 4; ++j) ku += Mu[i][j] * I[j];
+            rhs[i] = ex * I[i] + wu * (S[(size_t)(k + 1) * 4 + i] - ku) + wo * S[(size_t)k * 4 + i];
+            for (int j = 0; j < 4; ++j) A[i * 4 + j] = (i == j ? 1.0 : 0.0) + wo * Mo[i][j];
+        }
+        lu_solve(4, A, rhs);
+        memcpy(I, rhs, sizeof I);
+    }
+    memcpy(Itop, I, sizeof I);
+}
+
+/* Emergent Stokes vector at mu = 1 (vertical ray) of one column for line t
+ * with Zeeman splitting (normal triplet of effective Lande factor g_eff):
+ * sigma_b / pi / sigma_r profiles H(a, v - v_B), H(a, v), H(a, v + v_B) and
+ * dispersion profiles L likewise, v = (nu - nu0)/dnu_D - v_z/v_th,
+ * v_B = g_eff e B/(4 pi m_e) / dnu_D; field strength B [T], inclination
+ * theta to the vertical and azimuth chi per depth.
+ *   eI = chi_c + chi_others + (k_l/2)[p sin^2 th + (b + r)(1 + cos^2 th)/2]
+ *   eQ = (k_l/2)[p - (b + r)/2] sin^2 th cos 2chi, eU likewise with sin 2chi,
+ *   eV = (k_l/2)(r - b) cos th,  rQ, rU, rV the same with the dispersion
+ *   profiles, k_l = (n_l B_lu - n_u B_ul) h nu/(4 pi) / (sqrt(pi) dnu_D);
+ * emission: background and the other transitions unpolarised, the line
+ * S_l (eI_l, eQ, eU, eV) with S_l = n_u A_ul/(n_l B_lu - n_u B_ul) (no atomic
+ * polarisation; the same profile for absorption and emission).  Bottom: I =
+ * B + dB/dtau (diffusion), Q = U = V = 0. */
+static void emergent_stokes_column(rho_ctx *c, int64_t col, int t0, double geff, const double *Bf, const double *th,
+                                   const double *az, int64_t nl, const double *lam, double *out)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    const double *z = c->z + col * N, *T = c->T + col * N, *vz = c->vz + col * N;
+    const double *ne = c->ne + col * N, *np = c->np + col * N;
+    const double *n = c->pops + (size_t)col * L * N;
+    double *Kp = malloc((size_t)N * 6 * 8), *Sv = malloc((size_t)N * 4 * 8), *eI = malloc(N * 8);
+    double *dtau = malloc(N * 8), *B = malloc(N * 8);
+    const double Cff = rho_cff();
+    int l0 = a->tl[t0], u0 = a->tu[t0];
+    for (int64_t j = 0; j < nl; ++j) {
+        double nu = CLIGHT / lam[j];
+        for (int k = 0; k < N; ++k) {
+            double x = HPLANCK * nu / (KBOLTZ * T[k]);
+            B[k] = rho_planck(nu, T[k]);
+            double nhm = hminus_density(c->nstar[((size_t)col * L + 0) * N + k], ne[k], T[k]);
+            double ch = (Cff * ne[k] * np[k] / sqrt(T[k]) / (nu * nu * nu) + nhm * rho_hminus_sigma(lam[j]))
+                        * (-expm1(-x)) + SIGMA_T * ne[k];
+            double et = ch * B[k];
+            for (int t = 0; t < a->ntr; ++t) {
+                if (t == t0) continue;
+                if (!(nu >= a->nu_lo[t] * (1 - 1e-13) && nu <= a->nu_hi[t] * (1 + 1e-13))) continue;
+                int l = a->tl[t], u = a->tu[t];
+                double Vlu, Vul, U;
+                if (a->kind[t] == 0) {
+                    double p = line_profile(a, t, nu, T[k], vz[k], 1.0, damping(a, t, k, N));
+                    double h4 = HPLANCK * nu / (4.0 * PI_D);
+                    Vlu = h4 * a->Blu[t] * p;
+                    Vul = a->g[l] / a->g[u] * Vlu;
+                    U = h4 * a->A[t] * p;
+                } else {
+                    double r = a->nu0[t] / nu;
+                    double G = c->nstar[((size_t)col * L + l) * N + k] / c->nstar[((size_t)col * L + u) * N + k];
+                    Vlu = a->alpha0[t] * r * r * r;
+                    Vul = G * exp(-x) * Vlu;
+                    U = 2.0 * HPLANCK * nu * nu * nu / (CLIGHT * CLIGHT) * Vul;
+                }
+                ch += n[l * N + k] * Vlu - n[u * N + k] * Vul;
+                et += n[u * N + k] * U;
+            }
+            /* the polarised line */
+            double vth = sqrt(2.0 * KBOLTZ * T[k] / a->mass);
+            double dnuD = a->nu0[t0] * vth / CLIGHT;
+            double v = (nu - a->nu0[t0]) / dnuD - vz[k] / vth;
+            double vB = geff * QELEC * Bf[k] / (4.0 * PI_D * MELEC) / dnuD;
+            double ad = damping(a, t0, k, N);
+            double Hb, Lb, Hp, Lp, Hr, Lr;
+            rho_faddeeva(ad, v - vB, &Hb, &Lb);
+            rho_faddeeva(ad, v, &Hp, &Lp);
+            rho_faddeeva(ad, v + vB, &Hr, &Lr);
+            double h4 = HPLANCK * nu / (4.0 * PI_D);
+            double kl = (n[l0 * N + k] * a->Blu[t0] - n[u0 * N + k] * a->Bul[t0]) * h4 / (sqrt(PI_D) * dnuD);
+            double Sl = n[u0 * N + k] * a->A[t0] / (n[l0 * N + k] * a->Blu[t0] - n[u0 * N + k] * a->Bul[t0]);
+            double s2 = sin(th[k]) * sin(th[k]), ct = cos(th[k]), c2 = cos(2.0 * az[k]), sn2 = sin(2.0 * az[k]);
+            double lI = 0.5 * kl * (Hp * s2 + 0.5 * (Hb + Hr) * (1.0 + ct * ct));
+            double lq = 0.5 * kl * (Hp - 0.5 * (Hb + Hr)) * s2;
+            double lV = 0.5 * kl * (Hr - Hb) * ct;
+            double rq = 0.5 * kl * (Lp - 0.5 * (Lb + Lr)) * s2;
+            double rV = 0.5 * kl * (Lr - Lb) * ct;
+            double etaI = ch + lI;
+            eI[k] = etaI;
+            double e[6] = {lq * c2, lq * sn2, lV, rq * c2, rq * sn2, rV};
+            for (int i = 0; i < 6; ++i) Kp[(size_t)k * 6 + i] = e[i] / etaI;
+            Sv[(size_t)k * 4 + 0] = (et + Sl * lI) / etaI;
+            Sv[(size_t)k * 4 + 1] = Sl * e[0] / etaI;
+            Sv[(size_t)k * 4 + 2] = Sl * e[1] / etaI;
+            Sv[(size_t)k * 4 + 3] = Sl * e[2] / etaI;
+        }
+        for (int k = 0; k < N - 1; ++k) dtau[k] = 0.5 * (eI[k] + eI[k + 1]) * fabs(z[k] - z[k + 1]);
+        double dtv = 0.5 * (eI[N - 1] + eI[N - 2]) * fabs(z[N - 2] - z[N - 1]);
+        double Ib[4] = {B[N - 1] + (B[N - 1] - B[N - 2]) / dtv, 0.0, 0.0, 0.0};
+        rho_stokes_sweep(N, dtau, Kp, Sv, Ib, out + (size_t)j * 4);
+    }
+    free(Kp); free(Sv); free(eI); free(dtau); free(B);
+}
+
+/* Stokes I, Q, U, V at mu = 1 for line `line` (index among the lines),
+ * out [ncol][nl][4]; B_T, theta, chi [ncol][ndep]. */
+int rho_emergent_stokes(rho_ctx *c, int32_t line, double geff, const double *B_T, const double *theta,
+                        const double *chi, int64_t nl, const double *lam, double *out)
+{
+    if (line < 0 || line >= c->at.nline) return fail(c, "line index out of range");
+    for (int64_t col = 0; col < c->ncol; ++col)
+        emergent_stokes_column(c, col, line, geff, B_T + col * c->ndep, theta + col * c->ndep, chi + col * c->ndep,
+                               nl, lam, out + (size_t)col * nl * 4);
+    return 0;
+}
+
 int rho_two_level_jbar(int N, const double *tau0, int nfreq, double xmax, int nmu, double B,
                        const double *S, double *Jbar, double *Lstar)
 {

@@ -549,3 +549,110 @@ def test_mlp_reference_gelu_limits():
     h = 1e-6
     for x in (-2.0, 0.3, 1.7):
         assert mlp.gelu_grad(x) == pytest.approx((mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h), rel=1e-8)
+
+
+# ---------------------------------------------------------------- Zeeman Stokes (NEXT-2)
+def test_faddeeva_matches_library(orc):
+    v = np.concatenate([np.linspace(-12, 12, 241), [7.999, 8.0, 8.001, 50.0, -50.0]])
+    for a in (1e-3, 1e-2, 5e-2):
+        w = wofz(v + 1j * a)
+        got = np.array([orc.faddeeva(a, x) for x in v])
+        assert np.max(np.abs(got[:, 0] / w.real - 1)) < 1e-13
+        assert np.max(np.abs(got[:, 1] - w.imag) / np.abs(w)) < 1e-13
+    assert orc.faddeeva(1e-2, -3.3)[1] == pytest.approx(-orc.faddeeva(1e-2, 3.3)[1], rel=1e-14)
+
+
+def _me_matrix(eta0, a, vB, theta, chi, v, orc):
+    Hb, Lb = orc.faddeeva(a, v - vB)
+    Hp, Lp = orc.faddeeva(a, v)
+    Hr, Lr = orc.faddeeva(a, v + vB)
+    k = eta0 / np.sqrt(np.pi)
+    s2, ct = np.sin(theta) ** 2, np.cos(theta)
+    eI = 1 + 0.5 * k * (Hp * s2 + 0.5 * (Hb + Hr) * (1 + ct * ct))
+    lq = 0.5 * k * (Hp - 0.5 * (Hb + Hr)) * s2
+    rq = 0.5 * k * (Lp - 0.5 * (Lb + Lr)) * s2
+    eQ, eU, eV = lq * np.cos(2 * chi), lq * np.sin(2 * chi), 0.5 * k * (Hr - Hb) * ct
+    rQ, rU, rV = rq * np.cos(2 * chi), rq * np.sin(2 * chi), 0.5 * k * (Lr - Lb) * ct
+    return eI, eQ, eU, eV, rQ, rU, rV
+
+
+def test_stokes_solver_exact_for_milne_eddington(orc):
+    # constant propagation matrix and S = S0 + S1 tau_c: the effective source
+    # S - K'I of the DELO scheme is exactly linear, so DELO-linear must return
+    # the Unno-Rachkovsky solution (printed closed form, and S0 e0 + S1 K^-1 e0
+    # by a library solve) to rounding on any grid
+    S0, S1 = 1.0, 2.5
+    tau = np.concatenate([[0.0], np.logspace(-3, np.log10(80.0), 60)])
+    for (eta0, a, vB, th, ch, v) in ((8.0, 0.05, 1.2, 0.9, 0.4, 0.3), (30.0, 0.01, 0.4, 2.1, 2.5, -1.1),
+                                      (3.0, 0.2, 3.0, 0.2, 1.0, 2.4)):
+        eI, eQ, eU, eV, rQ, rU, rV = _me_matrix(eta0, a, vB, th, ch, v, orc)
+        K = np.array([[eI, eQ, eU, eV], [eQ, eI, rV, -rU], [eU, -rV, eI, rQ], [eV, rU, -rQ, eI]])
+        kp = np.array([eQ, eU, eV, rQ, rU, rV]) / eI
+        N = tau.size
+        S = np.outer(S0 + S1 * tau, np.array([eI, eQ, eU, eV]) / eI)
+        Ib = (S0 + S1 * tau[-1]) * np.array([1, 0, 0, 0]) + S1 * np.linalg.solve(K, [1, 0, 0, 0])
+        got = orc.stokes_sweep(eI * np.diff(tau), np.tile(kp, (N, 1)), S, Ib)
+        ref = S0 * np.array([1, 0, 0, 0]) + S1 * np.linalg.solve(K, [1, 0, 0, 0])
+        P = eQ * rQ + eU * rU + eV * rV
+        D = eI ** 2 * (eI ** 2 - eQ ** 2 - eU ** 2 - eV ** 2 + rQ ** 2 + rU ** 2 + rV ** 2) - P ** 2
+        ur = np.array([S0 + S1 * eI * (eI ** 2 + rQ ** 2 + rU ** 2 + rV ** 2) / D,
+                       -S1 * (eI ** 2 * eQ + eI * (eV * rU - eU * rV) + rQ * P) / D,
+                       -S1 * (eI ** 2 * eU + eI * (eQ * rV - eV * rQ) + rU * P) / D,
+                       -S1 * (eI ** 2 * eV + eI * (eU * rQ - eQ * rU) + rV * P) / D])
+        assert np.allclose(ref, ur, rtol=1e-12, atol=1e-14)
+        assert np.allclose(got, ref, rtol=1e-11, atol=1e-12 * abs(ref[0]))
+
+
+@pytest.fixture(scope="module")
+def halpha(column_oracle):
+    atom = rh_synth.hydrogen_like_atom()
+    t = [i for i, (l, u) in enumerate(zip(atom["line_l"], atom["line_u"])) if (l, u) == (1, 2)][0]
+    nu0 = column_oracle.atom_info()["nu0"][t]
+    return t, nu0
+
+
+def test_stokes_zero_field_is_the_scalar_solution(orc, column_oracle, halpha):
+    t, nu0 = halpha
+    o = column_oracle
+    lam = sc.c / nu0 + np.linspace(-2e-10, 2e-10, 41)
+    N = o.ndep
+    z = np.zeros((1, N))
+    st = o.emergent_stokes(t, 1.5, z, z + 0.7, z + 0.3, lam)
+    I = o.emergent_spectrum(1.0, lam)
+    assert np.allclose(st[0, :, 0], I[0], rtol=1e-13)
+    assert np.all(st[0, :, 1:] == 0.0)
+
+
+def test_stokes_weak_field_and_symmetries(orc, column_oracle, halpha):
+    t, nu0 = halpha
+    o = column_oracle
+    N = o.ndep
+    lam = sc.c / nu0 + np.linspace(-1.5e-10, 1.5e-10, 601)
+    nu = sc.c / lam
+    one = np.ones((1, N))
+    B = 1e-4                                   # 1 G: v_B ~ 1e-4 Doppler widths
+    th = 0.6
+    st = o.emergent_stokes(t, 1.5, B * one, th * one, 0.0 * one, lam)[0]
+    I0 = o.emergent_stokes(t, 1.5, 0 * one, th * one, 0.0 * one, lam)[0, :, 0]
+    # weak-field limit: V = dnu_B cos(theta) dI/dnu, dnu_B = g e B / (4 pi m_e)
+    dnuB = 1.5 * sc.e * B / (4 * np.pi * sc.m_e)
+    dIdnu = np.gradient(I0, nu)
+    ref = dnuB * np.cos(th) * dIdnu
+    big = np.abs(dIdnu) > 0.1 * np.abs(dIdnu).max()
+    assert big.sum() > 50
+    assert np.allclose(st[big, 3], ref[big], rtol=1e-2)
+    # linear polarisation is second order in B; transverse field: no V
+    tr = o.emergent_stokes(t, 1.5, B * one, 0.5 * np.pi * one, 0.0 * one, lam)[0]
+    tr2 = o.emergent_stokes(t, 1.5, 2 * B * one, 0.5 * np.pi * one, 0.0 * one, lam)[0]
+    assert np.max(np.abs(tr[:, 3])) < 1e-12 * np.max(tr[:, 0])
+    sel = np.abs(tr[:, 1]) > 0.1 * np.abs(tr[:, 1]).max()
+    assert np.allclose(tr2[sel, 1] / tr[sel, 1], 4.0, rtol=1e-2)
+    # azimuth: turning the field by 45 degrees turns (Q, U) into (-U, Q)
+    # (Faraday rotation makes U nonzero even at chi = 0)
+    ro = o.emergent_stokes(t, 1.5, 0.1 * one, 1.0 * one, (np.pi / 4) * one, lam)[0]
+    r0 = o.emergent_stokes(t, 1.5, 0.1 * one, 1.0 * one, 0.0 * one, lam)[0]
+    tol = 1e-12 * r0[:, 0].max()
+    assert np.allclose(ro[:, 2], r0[:, 1], rtol=1e-10, atol=tol)
+    assert np.allclose(ro[:, 1], -r0[:, 2], rtol=1e-10, atol=tol)
+    assert np.allclose(ro[:, [0, 3]], r0[:, [0, 3]], rtol=1e-12)
+    assert np.abs(r0[:, 1]).max() > np.abs(r0[:, 2]).max() > 0
