@@ -151,6 +151,26 @@ typedef struct {
 int rh_iterate(rh_ctx *ctx, const rh_iter_opts *opts, rh_iter_stats *stats_out);
 
 /* ---------------------------------------------------------------------- */
+/* Emergent Stokes vector I, Q, U, V at mu = 1 (vertical ray, Sect. 2.2) of  */
+/* line `line` (index among the lines of the atom) with Zeeman splitting of  */
+/* a normal triplet of effective Lande factor g_eff, for the current         */
+/* populations; the paper's 1.5D final spectra with a magnetic field         */
+/* (Sect. 1, Stokes vector).  Field strength B_T [T], inclination theta to   */
+/* the vertical and azimuth chi [rad] per depth, layout [ncol][ndep] (host,  */
+/* or device when on_device = 1).  The line's propagation matrix and        */
+/* emission follow Landi Degl'Innocenti & Landolfi (2004) without atomic     */
+/* polarisation (source function S_l = n_u A/(n_l B_lu - n_u B_ul) for all   */
+/* components); the background and other transitions are unpolarised.       */
+/* Formal solver DELO-linear (Rees, Durrant & Murphy 1989); bottom boundary  */
+/* I = B + dB/dtau, Q = U = V = 0.  With B_T = 0 the result equals           */
+/* rh_emergent_spectrum at mu = 1 (I) and Q = U = V = 0.  iquv_out           */
+/* [ncol][nlambda][4] (host, or device when on_device = 1).  precision 0:    */
+/* FP64; 1: FP32 profiles and solver (opacities FP64).                       */
+int rh_emergent_stokes(rh_ctx *ctx, int32_t line, double g_eff, const double *B_T, const double *theta,
+                       const double *chi, int64_t nlambda, const double *lambda_m, double *iquv_out,
+                       int32_t precision, int32_t on_device);
+
+/* ---------------------------------------------------------------------- */
 /* Start solutions (Sect. 2.3: "LTE populations, zero radiation, and ...     */
 /* escape probability iterations"), written into the current populations of */
 /* every loaded column (iterate from them with start = 2).  kind 0: LTE.     */

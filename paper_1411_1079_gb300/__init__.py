@@ -25,7 +25,8 @@ EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlam
            "rh_load_columns", "rh_iterate", "rh_get_populations", "rh_get_lte", "rh_set_populations",
            "rh_emergent_spectrum", "rh_iterate_noalloc", "rh_surrogate_init", "rh_surrogate_state_size",
            "rh_surrogate_get_state", "rh_surrogate_set_state", "rh_surrogate_train", "rh_surrogate_loss_grad",
-           "rh_surrogate_predict", "rh_solve", "rh_autotune", "rh_start_populations")
+           "rh_surrogate_predict", "rh_solve", "rh_autotune", "rh_start_populations",
+           "rh_emergent_stokes")
 
 MAX_RERUN = 4
 MAX_TUNE = 8
@@ -115,6 +116,8 @@ def lib(path: str | None = None):
         L.rh_solve.argtypes = [vp, C.POINTER(SolveOpts), C.POINTER(SolveStats)]
         L.rh_autotune.argtypes = [vp, C.c_int32, C.POINTER(TuneResult)]
         L.rh_start_populations.argtypes = [vp, C.c_int32]
+        L.rh_emergent_stokes.argtypes = [vp, C.c_int32, C.c_double, vp, vp, vp, C.c_int64, _dp, vp, C.c_int32,
+                                         C.c_int32]
         _fp = C.POINTER(C.c_float)
         L.rh_surrogate_init.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint64]
         L.rh_surrogate_state_size.argtypes = [vp]
@@ -262,6 +265,21 @@ class Context:
                 "guess_fallback_depths": st.guess_fallback_depths, "launches": st.kernel_launches,
                 "graph_replayed": bool(st.graph_replayed), "block_warps": st.block_warps,
                 "ctas_per_sm": st.ctas_per_sm}
+
+    def emergent_stokes(self, line, g_eff, B_T, theta, chi, lam_m, precision=0, out=None):
+        """rh_emergent_stokes: (I, Q, U, V) at mu = 1 of line `line` with Zeeman
+        splitting; B_T, theta, chi [ncol][ndep] (numpy, or CUDA tensors with
+        out a CUDA tensor [ncol][nlam][4]); returns [ncol][nlam][4]."""
+        lam_m = np.ascontiguousarray(lam_m, dtype=np.float64)
+        if out is not None:
+            self._check(self._lib.rh_emergent_stokes(self._p, line, g_eff, _ptr(B_T), _ptr(theta), _ptr(chi),
+                                                     lam_m.size, _d(lam_m), _ptr(out), precision, 1))
+            return out
+        B_T, theta, chi = (np.ascontiguousarray(x, dtype=np.float64) for x in (B_T, theta, chi))
+        res = np.zeros((self.ncol, lam_m.size, 4))
+        self._check(self._lib.rh_emergent_stokes(self._p, line, g_eff, _ptr(B_T), _ptr(theta), _ptr(chi),
+                                                 lam_m.size, _d(lam_m), _ptr(res), precision, 0))
+        return res
 
     START_LTE, START_LEARNED, START_CURRENT, START_ZERO_RADIATION, START_ESCAPE = 0, 1, 2, 3, 4
 

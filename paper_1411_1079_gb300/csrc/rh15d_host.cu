@@ -58,6 +58,7 @@ struct rh_ctx {
     int lane_prec = -1;
     double lane_nref = 0;
     float4 *vtab_d = nullptr;
+    float4 *dtab_d = nullptr;               // FP32 dispersion-function coefficient table
     // columns
     int64_t ncol = 0;
     int ndep = 0;
@@ -535,6 +536,46 @@ int ensure_start_tables(rh_ctx *c)
     return RH_OK;
 }
 
+// per requested wavelength: its frequency and up to RH_SPEC_ACT active
+// transitions with their constants (see launch_spectrum)
+int spectrum_tables(rh_ctx *c, int64_t nlambda, const double *lambda_m, std::vector<double> &nu,
+                    std::vector<int> &nact, std::vector<int> &act, std::vector<double> &spec)
+{
+    const HostAtom &a = c->ha;
+    nu.assign(nlambda, 0.0);
+    spec.assign((size_t)nlambda * RH_SPEC_ACT * RH_SPEC_F, 0.0);
+    nact.assign(nlambda, 0);
+    act.assign((size_t)nlambda * RH_SPEC_ACT, 0);
+    for (int64_t j = 0; j < nlambda; ++j) {
+        if (!(lambda_m[j] > 0) || !std::isfinite(lambda_m[j]))
+            return fail(c, RH_EINVAL, "wavelength %lld is not positive", (long long)j);
+        double f = kC / lambda_m[j];
+        nu[j] = f;
+        for (int t = 0; t < a.ntr; ++t) {
+            const HostTrans &h = a.tr[t];
+            if (!(f >= h.nu_lo * (1 - 1e-13) && f <= h.nu_hi * (1 + 1e-13))) continue;
+            if (nact[j] >= RH_SPEC_ACT) return fail(c, RH_EINVAL, "more than %d transitions at one wavelength", RH_SPEC_ACT);
+            int s = nact[j]++;
+            act[j * RH_SPEC_ACT + s] = t;
+            double *p = &spec[((size_t)j * RH_SPEC_ACT + s) * RH_SPEC_F];
+            if (h.kind == 0) {
+                double h4 = kH * f / (4.0 * kPi);
+                p[0] = h4 * h.Blu;
+                p[1] = h4 * h.A;
+                p[2] = a.g[h.l] / a.g[h.u];
+                p[3] = kC * ((f - h.nu0) / h.nu0);
+                p[4] = kC / (kSqrtPi * h.nu0);
+            } else {
+                double r = h.nu0 / f;
+                double alpha = h.alpha0 * r * r * r;
+                p[0] = alpha;
+                p[1] = 2.0 * kH * f * f * f / (kC * kC) * alpha;
+            }
+        }
+    }
+    return RH_OK;
+}
+
 __global__ void validate_kernel(int64_t ncol, int ndep, const double *z, const double *T, const double *ne,
                                 const double *nH, const double *vz, unsigned long long *bad)
 {
@@ -766,6 +807,20 @@ int rh_create(rh_ctx **out, int cuda_device, void *cuda_stream)
     }
     e = cudaMalloc(&c->vtab_d, (RH_VT_N + 1) * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemcpy(c->vtab_d, vt.data(), (RH_VT_N + 1) * sizeof(float4), cudaMemcpyHostToDevice);
+    // and of the FP32 dispersion function (L0 ~ t/sqrt(pi), L2 ~ t^3 as t -> 0)
+    std::vector<float4> dt(RH_VT_N + 1);
+    for (int i = 0; i <= RH_VT_N; ++i) {
+        if (i == 0) {
+            dt[i] = make_float4(0.f, (float)(hh / kSqrtPi), 0.f, 0.f);
+            continue;
+        }
+        double t = i * hh, v = 1.0 / t - 1.0, l0, d0, l2, d2;
+        dispersion_coeffs(v, l0, d0, l2, d2);
+        double dvdt = -1.0 / (t * t);
+        dt[i] = make_float4((float)l0, (float)(hh * d0 * dvdt), (float)l2, (float)(hh * d2 * dvdt));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c->dtab_d, (RH_VT_N + 1) * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemcpy(c->dtab_d, dt.data(), (RH_VT_N + 1) * sizeof(float4), cudaMemcpyHostToDevice);
     *out = c;
     if (e != cudaSuccess) {
         c->err = std::string("rh_create: ") + cudaGetErrorString(e);
@@ -782,6 +837,7 @@ void rh_destroy(rh_ctx *c)
     free_columns(c);
     dfree(c->lane_d);
     dfree(c->vtab_d);
+    dfree(c->dtab_d);
     dfree(c->nghist);
     dfree(c->queue);
     dfree(c->badidx);
@@ -1084,36 +1140,10 @@ int rh_emergent_spectrum(rh_ctx *c, double mu, int64_t nlambda, const double *la
     if (nlambda < 1 || !lambda_m || !I_out) return fail(c, RH_EINVAL, "need nlambda >= 1 and buffers");
     if (precision != 0 && precision != 1) return fail(c, RH_EINVAL, "precision must be 0 or 1");
     cudaSetDevice(c->dev);
-    const HostAtom &a = c->ha;
-    std::vector<double> nu(nlambda), spec((size_t)nlambda * RH_SPEC_ACT * RH_SPEC_F, 0.0);
-    std::vector<int> nact(nlambda, 0), act((size_t)nlambda * RH_SPEC_ACT, 0);
-    for (int64_t j = 0; j < nlambda; ++j) {
-        if (!(lambda_m[j] > 0) || !std::isfinite(lambda_m[j]))
-            return fail(c, RH_EINVAL, "wavelength %lld is not positive", (long long)j);
-        double f = kC / lambda_m[j];
-        nu[j] = f;
-        for (int t = 0; t < a.ntr; ++t) {
-            const HostTrans &h = a.tr[t];
-            if (!(f >= h.nu_lo * (1 - 1e-13) && f <= h.nu_hi * (1 + 1e-13))) continue;
-            if (nact[j] >= RH_SPEC_ACT) return fail(c, RH_EINVAL, "more than %d transitions at one wavelength", RH_SPEC_ACT);
-            int s = nact[j]++;
-            act[j * RH_SPEC_ACT + s] = t;
-            double *p = &spec[((size_t)j * RH_SPEC_ACT + s) * RH_SPEC_F];
-            if (h.kind == 0) {
-                double h4 = kH * f / (4.0 * kPi);
-                p[0] = h4 * h.Blu;
-                p[1] = h4 * h.A;
-                p[2] = a.g[h.l] / a.g[h.u];
-                p[3] = kC * ((f - h.nu0) / h.nu0);
-                p[4] = kC / (kSqrtPi * h.nu0);
-            } else {
-                double r = h.nu0 / f;
-                double alpha = h.alpha0 * r * r * r;
-                p[0] = alpha;
-                p[1] = 2.0 * kH * f * f * f / (kC * kC) * alpha;
-            }
-        }
-    }
+    std::vector<double> nu, spec;
+    std::vector<int> nact, act;
+    int r0 = spectrum_tables(c, nlambda, lambda_m, nu, nact, act, spec);
+    if (r0) return r0;
     double *nu_d = nullptr, *spec_d = nullptr, *out_d = nullptr;
     int *nact_d = nullptr, *act_d = nullptr;
     int rc = RH_OK;
@@ -1141,6 +1171,72 @@ int rh_emergent_spectrum(rh_ctx *c, double mu, int64_t nlambda, const double *la
         e = cudaMemcpyAsync(I_out, out_d, (size_t)c->ncol * nlambda * 8, cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) rc = fail(c, RH_ECUDA, "rh_emergent_spectrum: %s", cudaGetErrorString(e));
+    cleanup();
+    return rc;
+}
+
+int rh_emergent_stokes(rh_ctx *c, int32_t line, double g_eff, const double *B_T, const double *theta,
+                       const double *chi, int64_t nlambda, const double *lambda_m, double *iquv_out,
+                       int32_t precision, int32_t on_device)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "no columns loaded");
+    if (line < 0 || line >= c->da.nline) return fail(c, RH_EINVAL, "rh_emergent_stokes: line index out of range");
+    if (!std::isfinite(g_eff)) return fail(c, RH_EINVAL, "rh_emergent_stokes: g_eff must be finite");
+    if (nlambda < 1 || !lambda_m || !iquv_out || !B_T || !theta || !chi)
+        return fail(c, RH_EINVAL, "need nlambda >= 1 and buffers");
+    if (precision != 0 && precision != 1) return fail(c, RH_EINVAL, "precision must be 0 or 1");
+    if (on_device != 0 && on_device != 1) return fail(c, RH_EINVAL, "on_device must be 0 or 1");
+    cudaSetDevice(c->dev);
+    const size_t nd = (size_t)c->ncol * c->ndep;
+    if (!on_device)
+        for (size_t i = 0; i < nd; ++i)
+            if (!std::isfinite(B_T[i]) || B_T[i] < 0 || !std::isfinite(theta[i]) || !std::isfinite(chi[i]))
+                return fail(c, RH_EINVAL, "rh_emergent_stokes: field entry %zu not finite (or B < 0)", i);
+    std::vector<double> nu, spec;
+    std::vector<int> nact, act;
+    int r0 = spectrum_tables(c, nlambda, lambda_m, nu, nact, act, spec);
+    if (r0) return r0;
+    double *nu_d = nullptr, *spec_d = nullptr, *out_d = nullptr, *fld = nullptr;
+    int *nact_d = nullptr, *act_d = nullptr;
+    auto cleanup = [&]() {
+        dfree(nu_d);
+        dfree(spec_d);
+        dfree(nact_d);
+        dfree(act_d);
+        dfree(fld);
+        if (!on_device) dfree(out_d);
+    };
+    const double *Bd = B_T, *td = theta, *cd = chi;
+    cudaError_t e = cudaMalloc(&nu_d, nlambda * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&spec_d, spec.size() * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&nact_d, nlambda * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&act_d, act.size() * 4);
+    if (e == cudaSuccess && !on_device) {
+        e = cudaMalloc(&fld, 3 * nd * 8);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(fld, B_T, nd * 8, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(fld + nd, theta, nd * 8, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(fld + 2 * nd, chi, nd * 8, cudaMemcpyHostToDevice, c->st);
+        Bd = fld;
+        td = fld + nd;
+        cd = fld + 2 * nd;
+    }
+    if (e == cudaSuccess) {
+        if (on_device) out_d = iquv_out;
+        else e = cudaMalloc(&out_d, (size_t)c->ncol * nlambda * 4 * 8);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nu_d, nu.data(), nlambda * 8, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(spec_d, spec.data(), spec.size() * 8, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nact_d, nact.data(), nlambda * 4, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(act_d, act.data(), act.size() * 4, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess)
+        e = launch_stokes(c->da, c->ca, line, g_eff, Bd, td, cd, nlambda, nu_d, nact_d, act_d, spec_d, c->vtab_d,
+                          c->dtab_d, out_d, precision, c->st);
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(iquv_out, out_d, (size_t)c->ncol * nlambda * 4 * 8, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    int rc = RH_OK;
+    if (e != cudaSuccess) rc = fail(c, RH_ECUDA, "rh_emergent_stokes: %s", cudaGetErrorString(e));
     cleanup();
     return rc;
 }

@@ -149,6 +149,98 @@ __host__ __device__ inline double voigt_f64(double a, double v)
     return (-si * zr + sr * zi) / (kSqrtPi * mz) + exp(zi * zi - zr * zr) * cos(2.0 * zr * zi);
 }
 
+// Faddeeva function w(v + i a) = H + i L, FP64, by the same two branches as
+// voigt_f64 (Taylor expansion in a about the real axis for |v| < 6, the
+// asymptotic series above); H is even and L odd in v.
+__host__ __device__ inline void faddeeva_f64(double a, double v, double &H, double &L)
+{
+    double av = fabs(v), sg = v < 0.0 ? -1.0 : 1.0;
+    if (av < 6.0) {
+        double e = exp(-av * av);
+        double F = dawson_series(av);
+        double wr[10], wi[10];
+        wr[0] = e;
+        wi[0] = 2.0 / kSqrtPi * F;
+        wr[1] = -2.0 * av * wr[0];
+        wi[1] = -2.0 * av * wi[0] + 2.0 / kSqrtPi;
+        for (int n = 1; n < 9; ++n) {
+            wr[n + 1] = -2.0 * (av * wr[n] + n * wr[n - 1]);
+            wi[n + 1] = -2.0 * (av * wi[n] + n * wi[n - 1]);
+        }
+        // sum_n (i a)^n / n! w^{(n)}: real and imaginary parts
+        double h = 0.0, l = 0.0, pw = 1.0;
+        for (int n = 0; n <= 9; ++n) {
+            switch (n & 3) {
+            case 0: h += pw * wr[n]; l += pw * wi[n]; break;
+            case 1: h -= pw * wi[n]; l += pw * wr[n]; break;
+            case 2: h -= pw * wr[n]; l -= pw * wi[n]; break;
+            default: h += pw * wi[n]; l -= pw * wr[n]; break;
+            }
+            pw *= a / (n + 1);
+        }
+        H = h;
+        L = sg * l;
+        return;
+    }
+    double zr = av, zi = a;
+    double z2r = 2.0 * (zr * zr - zi * zi), z2i = 2.0 * (2.0 * zr * zi);
+    double d = z2r * z2r + z2i * z2i;
+    double ir = z2r / d, ii = -z2i / d;
+    double sr = 0.0, si = 0.0, tr = 1.0, ti = 0.0;
+    for (int k = 0; k <= 36; ++k) {
+        sr += tr;
+        si += ti;
+        double nr = (tr * ir - ti * ii) * (2 * k + 1), ni = (tr * ii + ti * ir) * (2 * k + 1);
+        tr = nr;
+        ti = ni;
+    }
+    // w = i S conj(z) / (sqrt(pi)|z|^2) + exp(-z^2)
+    double mz = zr * zr + zi * zi, ez = exp(zi * zi - zr * zr);
+    H = (-si * zr + sr * zi) / (kSqrtPi * mz) + ez * cos(2.0 * zr * zi);
+    L = sg * ((sr * zr + si * zi) / (kSqrtPi * mz) - ez * sin(2.0 * zr * zi));
+}
+
+// Coefficients of the expansion of the dispersion function in the damping a
+// used by the FP32 path: L(a, v) = L0 - (a^2/2) L2 - 2 a v e^{-v^2}
+// + (a^3/6)(8 v^3 - 12 v) e^{-v^2} + O(a^4), L0 = (2/sqrt pi) F(v), L2 = L0''
+// (F Dawson's integral: F' = 1 - 2vF, F'' = -2v + (4v^2 - 2)F, F''' = -2 + 8vF +
+// (4v^2 - 2)F').  For v >= 8 from the asymptotic series F = sum_k c_k v^{-(2k+1)},
+// c_k = (2k-1)!!/2^{k+1}, term by term (no cancellation).  Returns L0, L2 and
+// their derivatives in v, for v >= 0.
+__host__ inline void dispersion_coeffs(double v, double &l0, double &d0, double &l2, double &d2)
+{
+    const double k2 = 2.0 / kSqrtPi;
+    if (v < 8.0) {
+        double F = dawson_series(v), F1 = 1.0 - 2.0 * v * F;
+        double F2 = -2.0 * v + (4.0 * v * v - 2.0) * F, F3 = -2.0 + 8.0 * v * F + (4.0 * v * v - 2.0) * F1;
+        l0 = k2 * F;
+        d0 = k2 * F1;
+        l2 = k2 * F2;
+        d2 = k2 * F3;
+        return;
+    }
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0, ck = 0.5, vp = 1.0 / v;   // c_0 v^{-1}
+    const double iv2 = 1.0 / (v * v);
+    for (int k = 0; k < 30; ++k) {
+        const double n = 2.0 * k + 1.0;
+        s0 += ck * vp;
+        s1 -= n * ck * vp / v;
+        s2 += n * (n + 1) * ck * vp * iv2;
+        s3 -= n * (n + 1) * (n + 2) * ck * vp * iv2 / v;
+        ck *= (2.0 * k + 1.0) / 2.0;
+        vp *= iv2;
+    }
+    l0 = k2 * s0;
+    d0 = k2 * s1;
+    l2 = k2 * s2;
+    d2 = k2 * s3;
+}
+
+// Dispersion function, FP32, branch-free: the expansion above with L0, L2
+// from a cubic-Hermite table in t = 1/(1+|v|) (tab[i] = {L0, h dL0/dt, L2,
+// h dL2/dt} at t_i = i h, h = 1/RH_VT_N); odd in v.
+__device__ __forceinline__ float disp_f32(float a, float v, const float4 *__restrict__ tab);
+
 // FP32 reciprocal for the sweep: the hardware approximation (rcp.approx, about
 // 1 ulp, denormals flushed; no operand of the sweep is denormal) unless
 // RH_RCP_APPROX is 0, then the correctly rounded __frcp_rn.
@@ -223,6 +315,25 @@ __device__ __forceinline__ float voigt_f32(float a, float v, const float4 *__res
     float a2 = a * a;
     float gpoly = 1.0f + a2 * (1.0f - 2.0f * v2) + a2 * a2 * (0.66666667f * v2 * v2 - 2.0f * v2 + 0.5f);
     return g * gpoly + a * (H1 + a2 * H3);
+}
+
+__device__ __forceinline__ float disp_f32(float a, float v, const float4 *__restrict__ tab)
+{
+    float av = fabsf(v);
+    float v2 = av * av;
+    float g = __expf(-v2);
+    float t = rcp_f32(1.0f + av);
+    float x = t * (float)RH_VT_N;
+    int i = min((int)x, RH_VT_N - 1);
+    float f = x - (float)i;
+    float4 p0 = tab[i], p1 = tab[i + 1];
+    float f2 = f * f, f3 = f2 * f;
+    float h00 = 2.0f * f3 - 3.0f * f2 + 1.0f, h10 = f3 - 2.0f * f2 + f, h01 = 3.0f * f2 - 2.0f * f3, h11 = f3 - f2;
+    float L0 = h00 * p0.x + h10 * p0.y + h01 * p1.x + h11 * p1.y;
+    float L2 = h00 * p0.z + h10 * p0.w + h01 * p1.z + h11 * p1.w;
+    float a2 = a * a;
+    float l = L0 - 0.5f * a2 * L2 + a * g * av * (-2.0f + a2 * (1.3333333f * v2 - 2.0f));
+    return v < 0.0f ? -l : l;
 }
 
 // ----------------------------------------------------------------------------
@@ -379,6 +490,13 @@ cudaError_t launch_start(const DevAtom &A, const ColumnArrays &c, int kind, cons
 cudaError_t launch_spectrum(const DevAtom &A, const ColumnArrays &c, double mu, int64_t nlam,
                             const double *nu_d, const int *nact_d, const int *act_d, const double *spec_d,
                             double *out, int precision, cudaStream_t st);
+
+// emergent Stokes vector at mu = 1 of transition t0 (a line) with Zeeman
+// splitting; B_T, theta, chi [ncol][ndep]; out [ncol][nlam][4]
+cudaError_t launch_stokes(const DevAtom &A, const ColumnArrays &c, int t0, double geff, const double *B_T,
+                          const double *theta, const double *chi, int64_t nlam, const double *nu_d, const int *nact_d,
+                          const int *act_d, const double *spec_d, const float4 *vtab, const float4 *dtab, double *out,
+                          int precision, cudaStream_t st);
 
 // learned initial guess (rh15d_mlp.cu)
 struct Mlp;

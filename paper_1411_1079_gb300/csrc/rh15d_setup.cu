@@ -299,6 +299,226 @@ __global__ void start_kernel(const __grid_constant__ DevAtom A, ColumnArrays c, 
     if (tid == 0) c.status[col] = (uint8_t)(bad ? RH_COL_SINGULAR : RH_COL_NOTRUN);
 }
 
+// ----------------------------------------------------------------------------
+// Emergent Stokes vector at mu = 1 of one line with Zeeman splitting (normal
+// triplet, effective Lande factor geff), one thread per (column, requested
+// wavelength).  Opacities of the background and of the other transitions as
+// in spectrum_kernel (unpolarised); the polarised line's propagation matrix
+// in the convention
+//   K = [[eI, eQ, eU, eV], [eQ, eI, rV, -rU], [eU, -rV, eI, rQ], [eV, rU, -rQ, eI]],
+//   eI_l = (k/2)[p sin^2 th + (b + r)(1 + cos^2 th)/2], eQ = (k/2)[p - (b+r)/2] sin^2 th cos 2chi,
+//   eU = ... sin 2chi, eV = (k/2)(r - b) cos th, rQ/rU/rV likewise with the
+//   dispersion profiles; b, p, r at v - v_B, v, v + v_B; v_B = geff e B/(4 pi m_e)/dnu_D;
+// emission: the background and other transitions unpolarised, the line
+// S_l (eI_l, eQ, eU, eV).  DELO-linear along the ray (Rees, Durrant & Murphy
+// 1989): (1 + w_o K'_o) I_o = e^{-dtau} I_u + w_u (S_u - K'_u I_u) + w_o S_o with
+// K' = K/eI - 1 and S the emission / eI; 4 x 4 solve with partial pivoting.
+// Bottom: I = B + dB/dtau (diffusion), Q = U = V = 0.
+template <typename R>
+__device__ __forceinline__ void zeeman_profiles(R a, R v, R vB, const float4 *vtab, const float4 *dtab, R *H, R *L);
+template <>
+__device__ __forceinline__ void zeeman_profiles<double>(double a, double v, double vB, const float4 *,
+                                                        const float4 *, double *H, double *L)
+{
+    faddeeva_f64(a, v - vB, H[0], L[0]);
+    faddeeva_f64(a, v, H[1], L[1]);
+    faddeeva_f64(a, v + vB, H[2], L[2]);
+}
+template <>
+__device__ __forceinline__ void zeeman_profiles<float>(float a, float v, float vB, const float4 *vtab,
+                                                       const float4 *dtab, float *H, float *L)
+{
+    const float vs[3] = {v - vB, v, v + vB};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        H[i] = voigt_f32(a, vs[i], vtab);
+        L[i] = disp_f32(a, vs[i], dtab);
+    }
+}
+
+template <typename R>
+__device__ void delo_step(R ex, R wu, R wo, const R *Ku, const R *Ko, const R *Su, const R *So, R *I)
+{
+    // K'(k) from (eQ, eU, eV, rQ, rU, rV)/eI
+    auto kp = [](const R *k, R M[4][4]) {
+        M[0][0] = 0; M[0][1] = k[0]; M[0][2] = k[1]; M[0][3] = k[2];
+        M[1][0] = k[0]; M[1][1] = 0; M[1][2] = k[5]; M[1][3] = -k[4];
+        M[2][0] = k[1]; M[2][1] = -k[5]; M[2][2] = 0; M[2][3] = k[3];
+        M[3][0] = k[2]; M[3][1] = k[4]; M[3][2] = -k[3]; M[3][3] = 0;
+    };
+    R Mu[4][4], A[4][4], b[4];
+    kp(Ku, Mu);
+    kp(Ko, A);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        R kI = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) kI += Mu[i][j] * I[j];
+        b[i] = ex * I[i] + wu * (Su[i] - kI) + wo * So[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) A[i][j] = (i == j ? (R)1 : (R)0) + wo * A[i][j];
+    }
+    // Gaussian elimination with partial pivoting (fixed size, unrolled)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (r == piv && piv != c) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    R tq = A[c][q];
+                    A[c][q] = A[r][q];
+                    A[r][q] = tq;
+                }
+                R tb = b[c];
+                b[c] = b[r];
+                b[r] = tb;
+            }
+        const R ip = (R)1 / A[c][c];
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) {
+            const R f = A[r][c] * ip;
+#pragma unroll
+            for (int q = c; q < 4; ++q) A[r][q] -= f * A[c][q];
+            b[r] -= f * b[c];
+        }
+    }
+#pragma unroll
+    for (int c = 3; c >= 0; --c) {
+        R s = b[c];
+#pragma unroll
+        for (int q = c + 1; q < 4; ++q) s -= A[c][q] * b[q];
+        b[c] = s / A[c][c];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) I[i] = b[i];
+}
+
+template <typename R>
+__global__ void stokes_kernel(const __grid_constant__ DevAtom A, ColumnArrays c, int t0, double geff, const double *Bf,
+                              const double *thf, const double *azf, int64_t nlam, const double *nu_d,
+                              const int *nact_d, const int *act_d, const double *spec, const float4 *vtab_g,
+                              const float4 *dtab_g, double *out)
+{
+    __shared__ float4 tabs[sizeof(R) == 4 ? 2 * (RH_VT_N + 1) : 1];
+    const float4 *vtab = tabs, *dtab = tabs + (RH_VT_N + 1);
+    if (sizeof(R) == 4) {
+        for (int i = threadIdx.x; i <= RH_VT_N; i += blockDim.x) {
+            tabs[i] = vtab_g[i];
+            tabs[RH_VT_N + 1 + i] = dtab_g[i];
+        }
+        __syncthreads();
+    }
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= c.ncol * nlam) return;
+    const int64_t col = idx / nlam, j = idx % nlam;
+    const int N = c.ndep, L = A.nlev;
+    const double nu = nu_d[j];
+    const int na = nact_d[j];
+    const double e2 = kQ * kQ / (4.0 * kPi * kEps0);
+    const double Cff = e2 * e2 * e2 * 4.0 / (3.0 * kMe * kH * kC) * sqrt(2.0 * kPi / (3.0 * kK * kMe));
+    const double hm = hminus_sigma(kC / nu);
+    const double tw = 2.0 * kH * nu * nu * nu / (kC * kC);
+    const size_t cN = (size_t)col * N;
+    const DevTrans &tr0 = A.tr[t0];
+    const double h4 = kH * nu / (4.0 * kPi);
+    const double nuB = geff * kQ / (4.0 * kPi * kMe);   // Zeeman splitting per tesla, Hz
+    R I[4] = {0, 0, 0, 0}, Ku[6], Su[4], eIu = 0, Bu = 0;
+    for (int step = 0; step < N; ++step) {
+        const int k = N - 1 - step;
+        const double T = c.T[cN + k];
+        const double ne = c.ne[cN + k];
+        const double x = kH * nu / (kK * T);
+        const double lam3 = pow(kH * kH / (2.0 * kPi * kMe * kK * T), 1.5);
+        const double nhm = 0.25 * c.nstar[((size_t)col * L + 0) * N + k] * ne * lam3 * exp(0.754 * kQ / (kK * T));
+        const double omex = -expm1(-x);
+        double chi = (Cff * ne * c.np[cN + k] / sqrt(T) / (nu * nu * nu) + nhm * hm) * omex + kSigmaT * ne;
+        const double B = tw * exp(-x) / omex;
+        double eta = chi * B;
+        const double vth = sqrt(2.0 * kK * T / A.mass);
+        const double sk = N > 1 ? (double)k / (N - 1) : 0.0;
+        for (int s2 = 0; s2 < na; ++s2) {
+            const int t = act_d[j * RH_SPEC_ACT + s2];
+            if (t == t0) continue;
+            const DevTrans &tr = A.tr[t];
+            const double *f = spec + ((size_t)j * RH_SPEC_ACT + s2) * RH_SPEC_F;
+            const double nl = c.pops[((size_t)col * L + tr.l) * N + k];
+            const double nu_ = c.pops[((size_t)col * L + tr.u) * N + k];
+            double Vlu, Vul, U;
+            if (tr.kind == 0) {
+                const double a = exp((1.0 - sk) * tr.ln_atop + sk * tr.ln_abot);
+                const double v = (f[3] - c.vz[cN + k]) / vth;
+                const double ph = voigt_f64(a, v) * f[4] / vth;
+                Vlu = f[0] * ph;
+                Vul = f[2] * Vlu;
+                U = f[1] * ph;
+            } else {
+                const double G = c.nstar[((size_t)col * L + tr.l) * N + k] / c.nstar[((size_t)col * L + tr.u) * N + k];
+                Vlu = f[0];
+                Vul = G * exp(-x) * f[0];
+                U = f[1] * G * exp(-x);
+            }
+            chi += nl * Vlu - nu_ * Vul;
+            eta += nu_ * U;
+        }
+        // the polarised line
+        const double dnuD = tr0.nu0 * vth / kC;
+        const double nl0 = c.pops[((size_t)col * L + tr0.l) * N + k];
+        const double nu0 = c.pops[((size_t)col * L + tr0.u) * N + k];
+        const double kl = (nl0 * tr0.Blu - nu0 * tr0.Bul) * h4 / (kSqrtPi * dnuD);
+        const double Sl = nu0 * tr0.A / (nl0 * tr0.Blu - nu0 * tr0.Bul);
+        const double a0 = exp((1.0 - sk) * tr0.ln_atop + sk * tr0.ln_abot);
+        const R v = (R)(kC * ((nu - tr0.nu0) / tr0.nu0) / vth - c.vz[cN + k] / vth);
+        const R vB = (R)(nuB * Bf[cN + k] / dnuD);
+        R Hz[3], Lz[3];
+        zeeman_profiles<R>((R)a0, v, vB, vtab, dtab, Hz, Lz);
+        const double th = thf[cN + k], az = azf[cN + k];
+        const R s2 = (R)(sin(th) * sin(th)), ct = (R)cos(th), c2 = (R)cos(2.0 * az), sn2 = (R)sin(2.0 * az);
+        const R hk = (R)(0.5 * kl);
+        const R lI = hk * (Hz[1] * s2 + (R)0.5 * (Hz[0] + Hz[2]) * ((R)1 + ct * ct));
+        const R lq = hk * (Hz[1] - (R)0.5 * (Hz[0] + Hz[2])) * s2;
+        const R lV = hk * (Hz[2] - Hz[0]) * ct;
+        const R rq = hk * (Lz[1] - (R)0.5 * (Lz[0] + Lz[2])) * s2;
+        const R rV = hk * (Lz[2] - Lz[0]) * ct;
+        const R eI = (R)chi + lI;
+        const R ie = (R)1 / eI;
+        const R e6[6] = {lq * c2, lq * sn2, lV, rq * c2, rq * sn2, rV};
+        R Ko[6], So[4];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) Ko[i] = e6[i] * ie;
+        So[0] = ((R)eta + (R)Sl * lI) * ie;
+        So[1] = (R)Sl * e6[0] * ie;
+        So[2] = (R)Sl * e6[1] * ie;
+        So[3] = (R)Sl * e6[2] * ie;
+        if (step == 0) {
+            eIu = eI;
+            Bu = (R)B;
+        } else {
+            if (step == 1) {
+                // diffusion condition at the bottom point (vertical optical depth)
+                const R dtv = (R)0.5 * (eI + eIu) * (R)fabs(c.z[cN + N - 2] - c.z[cN + N - 1]);
+                I[0] = Bu + (Bu - (R)B) / dtv;
+            }
+            const R dtau = (R)0.5 * (eI + eIu) * (R)fabs(c.z[cN + k] - c.z[cN + k + 1]);
+            R ome, wu, wo;
+            sc_weights(dtau, ome, wu, wo);
+            delo_step<R>(ome, wu, wo, Ku, Ko, Su, So, I);
+            eIu = eI;
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) Ku[i] = Ko[i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Su[i] = So[i];
+    }
+    double *o = out + (size_t)idx * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = (double)I[i];
+}
+
 }  // namespace
 
 cudaError_t launch_lte_setup(const DevAtom &A, const ColumnArrays &c, int ne_given, cudaStream_t st)
@@ -320,6 +540,24 @@ cudaError_t launch_start(const DevAtom &A, const ColumnArrays &c, int kind, cons
     if (e != cudaSuccess) return e;
     start_kernel<<<(unsigned)c.ncol, 128, sm, st>>>(A, c, kind, kind == 4 ? kStartEscapeIterations : 1, sp_off, sp_nu,
                                                     sp_ce);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stokes(const DevAtom &A, const ColumnArrays &c, int t0, double geff, const double *B_T,
+                          const double *theta, const double *chi, int64_t nlam, const double *nu_d, const int *nact_d,
+                          const int *act_d, const double *spec_d, const float4 *vtab, const float4 *dtab, double *out,
+                          int precision, cudaStream_t st)
+{
+    int64_t n = c.ncol * nlam;
+    if (n == 0) return cudaSuccess;
+    int threads = 128;
+    int64_t blocks = (n + threads - 1) / threads;
+    if (precision == 1)
+        stokes_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(A, c, t0, geff, B_T, theta, chi, nlam, nu_d, nact_d,
+                                                                 act_d, spec_d, vtab, dtab, out);
+    else
+        stokes_kernel<double><<<(unsigned)blocks, threads, 0, st>>>(A, c, t0, geff, B_T, theta, chi, nlam, nu_d,
+                                                                  nact_d, act_d, spec_d, vtab, dtab, out);
     return cudaGetLastError();
 }
 

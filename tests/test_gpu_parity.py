@@ -293,3 +293,49 @@ def test_start_solutions_match_oracle(rh, orc, atom, cols, kind):
     g.iterate(maxiter=4, tol=0.0, precision=0, start=kind, ng_order=0)
     o.iterate(maxiter=4, tol=0.0, start=kind, ng_order=0)
     assert rel(g.populations()[0], o.populations()[0]) < FP64_TOL
+
+
+@pytest.fixture(scope="module")
+def stokes_case(rh, orc, atom, cols):
+    """Populations after a few FP64 iterations, a seeded field per depth."""
+    rng = np.random.default_rng(17)
+    shape = cols["T"].shape
+    fld = (rng.uniform(0, 0.2, shape), np.arccos(rng.uniform(-1, 1, shape)), rng.uniform(0, 2 * np.pi, shape))
+    t = [i for i, (l, u) in enumerate(zip(atom["line_l"], atom["line_u"])) if (l, u) == (1, 2)][0]
+    o = orc.Oracle()
+    o.setup_atom(atom)
+    o.load_columns(cols)
+    o.iterate(maxiter=6, tol=0.0)
+    n = o.populations()[0]
+    lam0 = 2.99792458e8 / o.atom_info()["nu0"][t]
+    lam = np.concatenate([lam0 + np.linspace(-2e-10, 2e-10, 61), [lam0 + 1.5e-9]])
+    ref = o.emergent_stokes(t, 1.5, *fld, lam)
+    return t, fld, lam, n, ref
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, INT_TOL_MIXED)])
+def test_emergent_stokes_matches_oracle(rh, atom, cols, stokes_case, precision, tol):
+    t, fld, lam, n, ref = stokes_case
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    g.load_columns(cols)
+    g.set_populations(n)
+    got = g.emergent_stokes(t, 1.5, *fld, lam, precision=precision)
+    I = ref[..., 0]
+    assert rel(got[..., 0], I) < tol
+    assert np.max(np.abs(got[..., 1:] - ref[..., 1:]) / I[..., None]) < tol
+    assert np.max(np.abs(ref[..., 3]) / I) > 1e-3          # the field leaves a real signal
+
+
+def test_emergent_stokes_zero_field_equals_scalar(rh, atom, cols, stokes_case):
+    t, fld, lam, n, ref = stokes_case
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    g.load_columns(cols)
+    g.set_populations(n)
+    z = np.zeros_like(fld[0])
+    for precision, tol in ((0, 1e-12), (1, 1e-5)):
+        st = g.emergent_stokes(t, 1.5, z, fld[1], fld[2], lam, precision=precision)
+        I = g.emergent_spectrum(1.0, lam, precision=precision)
+        assert rel(st[..., 0], I) < tol
+        assert np.max(np.abs(st[..., 1:])) == 0.0
