@@ -310,6 +310,36 @@ def run_gpu(args):
     e2e = {"value": ws * ncol * args.steps / e2e_s, "unit": "columns/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h + ncol * (4 + 1 + 8)}
 
+    # Zeeman Stokes spectra of H alpha after convergence (FP32, mu = 1, 400
+    # wavelengths over +-2 A; per column |B| ~ U(0, 2 kG), cos(theta) ~ U(-1, 1),
+    # chi ~ U(0, 2 pi), constant with height)
+    stokes = None
+    if args.stokes:
+        ctx.load_columns(dev, on_device=True)
+        ctx.solve(**opts)
+        rng_f = np.random.default_rng(2024 + rank)
+        Bc = rng_f.uniform(0.0, 0.2, ncol)
+        thc = np.arccos(rng_f.uniform(-1.0, 1.0, ncol))
+        chc = rng_f.uniform(0.0, 2 * np.pi, ncol)
+        fld = [torch.from_numpy(np.repeat(x[:, None], NDEP, axis=1)).to("cuda") for x in (Bc, thc, chc)]
+        ha = [i for i, (l, u) in enumerate(zip(atom["line_l"], atom["line_u"])) if (l, u) == (1, 2)][0]
+        nu_ha = (atom["E_J"][2] - atom["E_J"][1]) / 6.62607015e-34
+        lam = 2.99792458e8 / nu_ha + np.linspace(-2e-10, 2e-10, 400)
+        iquv = torch.empty((ncol, lam.size, 4), dtype=torch.float64, device="cuda")
+        ctx.emergent_stokes(ha, 1.5, *fld, lam, precision=1, out=iquv)      # warm-up
+        barrier()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        ctx.emergent_stokes(ha, 1.5, *fld, lam, precision=1, out=iquv)
+        s1.record(stream)
+        barrier()
+        st_ms = s0.elapsed_time(s1)
+        vmax = float((iquv[..., 3].abs() / iquv[..., 0]).max())
+        stokes = {"value": ncol / (st_ms / 1e3), "unit": "columns/s", "nlambda": int(lam.size),
+                  "ms": st_ms, "line": "H alpha (n=2-3), g_eff 1.5", "precision": "fp32 profiles and DELO solver",
+                  "max_abs_V_over_I": vmax}
+
     # plain FP64 MALI from LTE on a random sample of the cube (FP64 arithmetic is
     # slow on this part: one column per SM keeps the run under a minute)
     fp64 = None
@@ -358,6 +388,7 @@ def run_gpu(args):
                       "precision": "fp32 formal solution/rates, fp64 rate equations/Ng"},
         "lte_start_fp64": fp64,
         "other_starts": other,
+        "stokes": stokes,
         "surrogate": train_info,
         "launch": {"block_warps": s["block_warps"], "ctas_per_sm": s["ctas_per_sm"],
                    "cuda_graph_replayed": s["graph_replayed"], "kernels_per_step": s["launches"],
@@ -396,6 +427,8 @@ def run_ncu_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profiler captures")
+    ap.add_argument("--no-stokes", dest="stokes", action="store_false",
+                    help="skip the Zeeman Stokes spectrum timing")
     ap.add_argument("--fp64-columns", type=int, default=152,
                     help="columns of the plain FP64 LTE-start comparison (0: skip)")
     ap.add_argument("--ncu-columns", type=int, default=608)

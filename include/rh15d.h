@@ -191,9 +191,10 @@ int rh_start_populations(rh_ctx *ctx, int32_t kind);
 /* options first, then the columns that did not converge again with other  */
 /* options).  Pass 1 iterates every column with `pass1` (start 0, 1 or 2;  */
 /* only_unconverged is ignored).  Then, for r = 0 .. nrerun-1, the columns  */
-/* whose status is not RH_COL_CONVERGED are iterated again from LTE without */
-/* Ng, with collisional-radiative switching factor rerun_crsw[r] and        */
-/* rerun_maxiter iterations -- inside the column kernel (fused_rerun = 1)   */
+/* whose status is not RH_COL_CONVERGED are iterated again from LTE with    */
+/* collisional-radiative switching factor rerun_crsw[r] (>= 1; 1: none),     */
+/* Ng as rerun_ng[r] says and rerun_maxiter iterations -- inside the column */
+/* kernel (fused_rerun = 1)                                                  */
 /* or as separate passes over a device-selected list.  No host round trip   */
 /* happens between the passes.                                             */
 /* use_graph = 1: the whole sequence (learned guess, pass 1, selections,    */
@@ -212,9 +213,12 @@ typedef struct {
     rh_iter_opts pass1;
     int32_t nrerun;                    /* 0 .. RH_MAX_RERUN */
     int32_t rerun_maxiter;             /* iterations of each re-run pass (>= 1) */
-    double rerun_crsw[RH_MAX_RERUN];   /* switching factor of each re-run pass (> 1) */
+    double rerun_crsw[RH_MAX_RERUN];   /* switching factor of each re-run pass (>= 1; 1: none) */
     int32_t use_graph;                 /* 1: capture / replay a CUDA graph */
     int32_t autotune;                  /* 1: tune the launch shape once (see rh_autotune) */
+    int32_t rerun_ng[RH_MAX_RERUN];    /* 1: Ng acceleration in that re-run pass (pass 1's order,
+                                          delay and period); 0: none (the usual choice together
+                                          with collisional-radiative switching) */
     int32_t fused_rerun;               /* 1: the column kernel runs the re-run ladder itself: a block
                                           whose column does not converge restarts it at once with the
                                           next re-run options, overlapping the rest of pass 1 (same

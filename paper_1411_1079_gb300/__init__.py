@@ -60,7 +60,7 @@ class IterStats(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("pass1", IterOpts), ("nrerun", C.c_int32), ("rerun_maxiter", C.c_int32),
                 ("rerun_crsw", C.c_double * MAX_RERUN), ("use_graph", C.c_int32), ("autotune", C.c_int32),
-                ("fused_rerun", C.c_int32)]
+                ("rerun_ng", C.c_int32 * MAX_RERUN), ("fused_rerun", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -235,20 +235,26 @@ class Context:
     def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True, start=0,
               ng_order=2, ng_delay=5, ng_period=3, use_graph=1, autotune=1, fused_rerun=1) -> dict:
         """rh_solve: every column from LTE (start=0), the learned guess
-        (start=1) or the current populations (start=2) with Ng acceleration,
-        then the columns that did not converge again from LTE with
-        collisional-radiative switching (x1e3, x1e5, then x1e7) and without
-        Ng (the paper's two-stage strategy): by the column kernel itself as
+        (start=1), the current populations (start=2), zero radiation (3) or
+        escape probabilities (4) with Ng acceleration, then the columns that
+        did not converge again from LTE -- first with the same options when
+        pass 1 started elsewhere, then with collisional-radiative switching
+        (x1e3, x1e5, then x1e7) and without Ng (the paper's two-stage
+        strategy): by the column kernel itself as
         soon as a column fails (fused_rerun=1) or as separate passes over a
         device-selected list; the sequence is replayed as a CUDA graph."""
         o = SolveOpts()
         o.pass1 = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay, ng_period=ng_period,
                            start=start, precision=precision, persistent=persistent, block_warps=block_warps,
                            crsw_init=1.0, only_unconverged=0)
-        o.nrerun = len(self.RERUN_CRSW) if rescue else 0
+        # the ladder: from a start other than LTE, first LTE with the same
+        # options; then stronger and stronger switching without Ng
+        rungs = ([(1.0, 1)] if start != 0 else []) + [(f, 0) for f in self.RERUN_CRSW]
+        o.nrerun = len(rungs) if rescue else 0
         o.rerun_maxiter = maxiter
-        for i, f in enumerate(self.RERUN_CRSW):
+        for i, (f, ng) in enumerate(rungs[:o.nrerun]):
             o.rerun_crsw[i] = f
+            o.rerun_ng[i] = ng
         o.use_graph = int(use_graph)
         o.autotune = int(autotune)
         o.fused_rerun = int(fused_rerun)

@@ -1350,7 +1350,10 @@ cudaError_t enqueue_solve(rh_ctx *c, const rh_solve_opts *o, const IterLaunch &b
         // one launch: the kernel re-runs failing columns itself and counts
         il.nrung = o->nrerun;
         il.rung_maxiter = o->rerun_maxiter;
-        for (int r = 0; r < o->nrerun; ++r) il.rung_crsw[r] = o->rerun_crsw[r];
+        for (int r = 0; r < o->nrerun; ++r) {
+            il.rung_crsw[r] = o->rerun_crsw[r];
+            il.rung_ng[r] = o->rerun_ng[r] ? o->pass1.ng_order : 0;
+        }
         il.rung_cols = c->solve_cnt;
         il.rung_its = c->solve_it;
         if ((e = launch_mali_prealloc(c->da, c->ca, c->lane_d, c->ha.npad, c->vtab_d, c->nref, c->nghist,
@@ -1374,7 +1377,7 @@ cudaError_t enqueue_solve(rh_ctx *c, const rh_solve_opts *o, const IterLaunch &b
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         IterLaunch ir = base;
         ir.start = 0;
-        ir.ng_order = 0;
+        ir.ng_order = o->rerun_ng[r] ? o->pass1.ng_order : 0;
         ir.crsw = o->rerun_crsw[r];
         ir.maxiter = o->rerun_maxiter;
         ir.colidx = c->colidx;
@@ -1519,7 +1522,8 @@ int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
         (o->autotune != 0 && o->autotune != 1) || (o->fused_rerun != 0 && o->fused_rerun != 1))
         return fail(c, RH_EINVAL, "rh_solve: invalid options");
     for (int r = 0; r < o->nrerun; ++r)
-        if (!(o->rerun_crsw[r] >= 1.0)) return fail(c, RH_EINVAL, "rh_solve: rerun_crsw must be >= 1");
+        if (!(o->rerun_crsw[r] >= 1.0) || (o->rerun_ng[r] != 0 && o->rerun_ng[r] != 1))
+            return fail(c, RH_EINVAL, "rh_solve: rerun_crsw must be >= 1 and rerun_ng 0 or 1");
     cudaSetDevice(c->dev);
     const int prec = o->pass1.precision;
     if (o->pass1.start == 1) {

@@ -464,6 +464,7 @@ struct IterLaunch {
     // re-run ladder run by the kernel itself for columns that do not converge
     int nrung = 0, rung_maxiter = 1;
     double rung_crsw[RH_MAX_RERUN] = {1.0, 1.0, 1.0, 1.0};
+    int rung_ng[RH_MAX_RERUN] = {0, 0, 0, 0};   // Ng order of each rung (0 or the pass's)
     int *rung_cols = nullptr;                 // [nrung] columns entering each rung
     unsigned long long *rung_its = nullptr;   // [1 + nrung] formal solutions per pass / rung
 };

@@ -55,10 +55,11 @@ struct KParams {
     int64_t nwork;
     const int *nwork_d;        // device count of work items (overrides nwork when set)
     // re-run ladder inside the kernel (Sect. 2.3): a column not converged
-    // after its pass is restarted from LTE without Ng with switching factor
-    // rung_crsw[r] and rung_maxiter iterations, r = 0 .. nrung-1
+    // after its pass is restarted from LTE with switching factor rung_crsw[r],
+    // Ng order rung_ng[r] and rung_maxiter iterations, r = 0 .. nrung-1
     int nrung, rung_maxiter;
     double rung_crsw[RH_MAX_RERUN];
+    int rung_ng[RH_MAX_RERUN];
     int *rung_cols;                  // [nrung] columns entering each rung (nullptr: not counted)
     unsigned long long *rung_its;    // [1 + nrung] formal solutions of the pass and of each rung
 };
@@ -658,9 +659,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
         if (it > maxiter) it = maxiter;
         if (tid == 0 && p.rung_its) atomicAdd(&p.rung_its[rung], (unsigned long long)it);
         if (status != RH_COL_CONVERGED && rung < p.nrung) {
-            // next rung of the re-run ladder: from LTE, no Ng, stronger switching
+            // next rung of the re-run ladder: from LTE, its own switching and Ng
             start = 0;
-            ng_order = 0;
+            ng_order = p.rung_ng[rung];
             crsw = p.rung_crsw[rung];
             maxiter = p.rung_maxiter;
             ++rung;
@@ -777,7 +778,10 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
     p.nwork_d = o.nwork_d;
     p.nrung = o.nrung;
     p.rung_maxiter = o.rung_maxiter;
-    for (int r = 0; r < RH_MAX_RERUN; ++r) p.rung_crsw[r] = o.rung_crsw[r];
+    for (int r = 0; r < RH_MAX_RERUN; ++r) {
+        p.rung_crsw[r] = o.rung_crsw[r];
+        p.rung_ng[r] = o.rung_ng[r];
+    }
     p.rung_cols = o.rung_cols;
     p.rung_its = o.rung_its;
     int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
@@ -837,7 +841,10 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     p.nwork_d = o.nwork_d;
     p.nrung = o.nrung;
     p.rung_maxiter = o.rung_maxiter;
-    for (int r = 0; r < RH_MAX_RERUN; ++r) p.rung_crsw[r] = o.rung_crsw[r];
+    for (int r = 0; r < RH_MAX_RERUN; ++r) {
+        p.rung_crsw[r] = o.rung_crsw[r];
+        p.rung_ng[r] = o.rung_ng[r];
+    }
     p.rung_cols = o.rung_cols;
     p.rung_its = o.rung_its;
     const int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
