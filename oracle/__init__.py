@@ -81,6 +81,8 @@ def lib():
         L.rho_electron_density.restype = C.c_double
         L.rho_hminus_sigma.restype = C.c_double
         L.rho_hminus_sigma.argtypes = [C.c_double]
+        L.rho_r2a.restype = C.c_double
+        L.rho_r2a.argtypes = [C.c_double, C.c_double, C.c_double]
         L.rho_faddeeva.restype = None
         L.rho_faddeeva.argtypes = [C.c_double, C.c_double, _dp, _dp]
         L.rho_stokes_sweep.restype = None
@@ -105,13 +107,13 @@ class AtomDesc(C.Structure):
                 ("ncont", C.c_int32), ("cont_l", _ip), ("cont_alpha0", _dp),
                 ("cont_nlambda", _ip), ("cont_ratio", _dp),
                 ("mass_amu", C.c_double), ("T_ref", C.c_double), ("nmu", C.c_int32),
-                ("metal_floor", C.c_double)]
+                ("metal_floor", C.c_double), ("line_prd", _ip)]
 
 
 class IterOpts(C.Structure):
     _fields_ = [("maxiter", C.c_int32), ("tol", C.c_double), ("ng_order", C.c_int32),
                 ("ng_delay", C.c_int32), ("ng_period", C.c_int32), ("start", C.c_int32),
-                ("crsw_init", C.c_double)]
+                ("crsw_init", C.c_double), ("prd_eps0", C.c_double)]
 
 
 class IterStats(C.Structure):
@@ -123,6 +125,11 @@ class IterStats(C.Structure):
 def voigt(a, v):
     L = lib()
     return float(L.rho_voigt(float(a), float(v)))
+
+
+def r2a(a, xp, x):
+    """Angle-averaged redistribution function R_II-A(x', x), Doppler units."""
+    return float(lib().rho_r2a(float(a), float(xp), float(x)))
 
 
 def faddeeva(a, v):
@@ -235,6 +242,9 @@ class Oracle:
                      cont_alpha0=_d(a["cont_alpha0"]), cont_nlambda=_i(a["cont_nlambda"]),
                      cont_ratio=_d(a["cont_ratio"]), mass_amu=a["mass_amu"], T_ref=a["T_ref"],
                      nmu=a["nmu"], metal_floor=a["metal_floor"])
+        if "line_prd" in a:
+            a["line_prd"] = np.ascontiguousarray(a["line_prd"], dtype=np.int32)
+            d.line_prd = _i(a["line_prd"])
         self._check(self._lib.rho_setup_atom(self._p, C.byref(d)))
         self.nlev = a["nlev"]
         self.ntr = len(a["line_l"]) + len(a["cont_l"])
@@ -300,9 +310,9 @@ class Oracle:
         self._check(self._lib.rho_set_populations(self._p, _d(n)))
 
     def iterate(self, maxiter=500, tol=1e-3, ng_order=2, ng_delay=5, ng_period=3, start=0,
-                crsw_init=1.0, nthreads=None):
+                crsw_init=1.0, nthreads=None, prd_eps0=0.0):
         o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
-                     ng_period=ng_period, start=start, crsw_init=crsw_init)
+                     ng_period=ng_period, start=start, crsw_init=crsw_init, prd_eps0=prd_eps0)
         s = IterStats()
         if nthreads is None:
             nthreads = os.cpu_count() or 1

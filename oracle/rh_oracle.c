@@ -68,6 +68,7 @@ typedef struct {
     double mass_amu, T_ref;
     int32_t nmu;
     double metal_floor;
+    const int32_t *line_prd;   /* per line: 1 angle-averaged partial redistribution (NULL: none) */
 } rho_atom_desc;
 
 typedef struct {
@@ -76,6 +77,7 @@ typedef struct {
     int32_t ng_order, ng_delay, ng_period;
     int32_t start;      /* 0 LTE, 2 user populations, 3 zero radiation, 4 escape probability */
     double crsw_init;   /* collisional-radiative switching start factor; <=1 off */
+    double prd_eps0;    /* PRD switching (Eq. 1): eps = min(1, eps0 it^2); <= 0: off (eps = 1) */
 } rho_iter_opts;
 
 typedef struct {
@@ -108,6 +110,11 @@ typedef struct {
     double *wq;                   /* [nlam][MAXACT] quadrature weight (Hz) of that transition */
     int *prof_slot;               /* [nlam][MAXACT] line-profile block index, -1 for continua */
     int nprof;                    /* number of (lambda, line) pairs */
+    /* partial redistribution: per PRD line its grid points in frequency order */
+    int prd[MAXTR];
+    int nprd_line, prd_t[MAXTR], prd_np[MAXTR];
+    int *prd_pts[MAXTR];          /* grid indices */
+    double *prd_w[MAXTR];         /* the line's quadrature weight at each point (Hz) */
 } atom_t;
 
 struct rho_ctx {
@@ -257,6 +264,79 @@ void rho_faddeeva(double a, double v, double *H, double *L)
     }
     double far = disp_far(a, av, -9.0, av - D) + disp_far(a, av, av + D, 9.0);
     *L = sg * (near + far) / PI_D;
+}
+
+/* Angle-averaged redistribution function R_II-A (Hummer 1962), in Doppler
+ * units, normalised so that int R(x', x) dx' = H(a, x)/sqrt(pi):
+ *   R(x', x) = pi^{-3/2} int_{(xb - xs)/2}^inf e^{-u^2}
+ *                  [atan((xs + u)/a) - atan((xb - u)/a)] du,
+ *   xs = min(x, x'), xb = max(x, x') (signed).
+ * Adaptive Gauss-Kronrod (7/15 points) with the atan steps of width a at
+ * u = xb and u = -xs as breakpoints and the range ended at max + 8 (e^{-64}),
+ * to a tolerance relative to a first estimate of the integral.
+ * Pinned: normalisation, symmetry, the a -> 0 limit (1/2) erfc(max(|x|, |x'|)). */
+static const double gk_x[8] = {0.991455371120812639206854697526329, 0.949107912342758524526189684047851,
+                               0.864864423359769072789712788640926, 0.741531185599394439863864773280788,
+                               0.586087235467691130294144845693013, 0.405845151377397166906606412076961,
+                               0.207784955007898467600689403773245, 0.0};
+static const double gk_wk[8] = {0.022935322010529224963732008058970, 0.063092092629978553290700663189204,
+                                0.104790010322250183839876322541518, 0.140653259715525918745189590510238,
+                                0.169004726639267902826583426598550, 0.190350578064785409913256402421014,
+                                0.204432940075298892414161999234649, 0.209482141084727828012999174891714};
+static const double gk_wg[4] = {0.129484966168869693270611432679082, 0.279705391489276667901467771423780,
+                                0.381830050505118944950369775488975, 0.417959183673469387755102040816327};
+
+/* atan((xs+u)/a) - atan((xb-u)/a) = atan2(a (xs + 2u - xb), a^2 + (xs+u)(xb-u)):
+ * no cancellation between two arctangents near pi/2 (xs + 2u - xb =
+ * 2 (u - u0) >= 0 on the range; atan2 takes the branch where the denominator
+ * turns negative) */
+static double r2_integrand(double u, double xs, double xb, double a)
+{
+    return exp(-u * u) * atan2(a * (xs + 2.0 * u - xb), a * a + (xs + u) * (xb - u));
+}
+
+static double r2_gk(double lo, double hi, double xs, double xb, double a, double *err)
+{
+    double c = 0.5 * (lo + hi), h = 0.5 * (hi - lo);
+    double fc = r2_integrand(c, xs, xb, a);
+    double k = gk_wk[7] * fc, g = gk_wg[3] * fc;
+    for (int j = 0; j < 7; ++j) {
+        double f = r2_integrand(c - h * gk_x[j], xs, xb, a) + r2_integrand(c + h * gk_x[j], xs, xb, a);
+        k += gk_wk[j] * f;
+        if (j & 1) g += gk_wg[j / 2] * f;
+    }
+    *err = fabs(k - g) * h;
+    return k * h;
+}
+
+static double r2_adapt(double lo, double hi, double xs, double xb, double a, double tol, int depth)
+{
+    double err, v = r2_gk(lo, hi, xs, xb, a, &err);
+    /* stop at the tolerance, at the rounding level of the panel, or at depth 30 */
+    if (depth >= 30 || err <= tol || err <= 1e-14 * fabs(v)) return v;
+    double c = 0.5 * (lo + hi);
+    return r2_adapt(lo, c, xs, xb, a, 0.5 * tol, depth + 1) + r2_adapt(c, hi, xs, xb, a, 0.5 * tol, depth + 1);
+}
+
+double rho_r2a(double a, double xp, double x)
+{
+    double xs = fmin(x, xp), xb = fmax(x, xp);
+    double u0 = 0.5 * (xb - xs), top = fmax(u0, fmax(xb, -xs)) + 8.0;
+    double br[4] = {u0, xb, -xs, top};
+    int nb = 0;
+    double pts[4];
+    for (int i = 0; i < 4; ++i)
+        if (br[i] >= u0 && br[i] <= top) pts[nb++] = br[i];
+    for (int i = 1; i < nb; ++i)       /* sort the few breakpoints */
+        for (int j = i; j > 0 && pts[j] < pts[j - 1]; --j) {
+            double t = pts[j]; pts[j] = pts[j - 1]; pts[j - 1] = t;
+        }
+    double est = 0.0, e;
+    for (int i = 0; i + 1 < nb; ++i) est += fabs(r2_gk(pts[i], pts[i + 1], xs, xb, a, &e));
+    double tol = 1e-15 * est + 1e-300, s = 0.0;
+    for (int i = 0; i + 1 < nb; ++i)
+        if (pts[i + 1] > pts[i]) s += r2_adapt(pts[i], pts[i + 1], xs, xb, a, tol / (nb - 1), 0);
+    return s / (PI_D * sqrt(PI_D));
 }
 
 /* e^y E1(y) for y > 0: power series for y <= 1, continued fraction
@@ -410,6 +490,10 @@ static int cmp_dbl_idx(const void *a, const void *b)
 
 static void atom_free(atom_t *a)
 {
+    for (int q = 0; q < a->nprd_line; ++q) {
+        free(a->prd_pts[q]);
+        free(a->prd_w[q]);
+    }
     free(a->nu);
     free(a->nact);
     free(a->act);
@@ -553,6 +637,42 @@ static int atom_build(rho_ctx *c, const rho_atom_desc *d)
         for (int s = 0; s < MAXACT; ++s)
             a->prof_slot[i * MAXACT + s] = (s < a->nact[i] && a->kind[a->act[i * MAXACT + s]] == 0) ? np++ : -1;
     a->nprof = np;
+    /* partial redistribution lines: their grid points in frequency order with
+     * the line's quadrature weights; two PRD lines may not share a point */
+    for (int t = 0; t < d->nline; ++t) {
+        if (!(d->line_prd && d->line_prd[t])) continue;
+        int q = a->nprd_line++;
+        a->prd[t] = 1;
+        a->prd_t[q] = t;
+        int cnt = 0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int s2 = 0; s2 < a->nact[i]; ++s2)
+                if (a->act[i * MAXACT + s2] == t) ++cnt;
+        a->prd_np[q] = cnt;
+        a->prd_pts[q] = malloc(cnt * sizeof(int));
+        a->prd_w[q] = malloc(cnt * sizeof(double));
+        double *b2 = malloc(2 * cnt * sizeof(double));
+        int j = 0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int s2 = 0; s2 < a->nact[i]; ++s2)
+                if (a->act[i * MAXACT + s2] == t) {
+                    b2[2 * j] = a->nu[i];
+                    b2[2 * j + 1] = (double)i;
+                    ++j;
+                }
+        qsort(b2, cnt, 2 * sizeof(double), cmp_dbl_idx);
+        for (j = 0; j < cnt; ++j) {
+            int64_t i = (int64_t)b2[2 * j + 1];
+            a->prd_pts[q][j] = (int)i;
+            for (int s2 = 0; s2 < a->nact[i]; ++s2) {
+                int t2 = a->act[i * MAXACT + s2];
+                if (t2 == t) a->prd_w[q][j] = a->wq[i * MAXACT + s2];
+                else if (t2 < d->nline && d->line_prd && d->line_prd[t2])
+                    return free(b2), fail(c, "two PRD lines share a wavelength point");
+            }
+        }
+        free(b2);
+    }
     return 0;
 }
 
@@ -780,11 +900,18 @@ typedef struct {
     double *chi, *eta, *etaact, *S, *dtau, *I, *lam, *Ieff, *omlam, *Sbg;
     double *chit, *Vlu, *Vul, *Ut;   /* [MAXACT][N] */
     double *hist;     /* Ng history [4][L*N] */
+    /* partial redistribution */
+    double *rho;      /* [nlam][N] psi/phi of the PRD line at each grid point (1 elsewhere) */
+    double *Jp;       /* [nlam][N] angle-averaged mean intensity at the PRD points */
+    double *Pup, *Pdn;    /* [ntr][N] plain radiative rate coefficients (actual I, not I_eff) */
+    double *prdK[MAXTR];   /* per PRD line [N][np][np]: normalised redistribution kernel */
+    double *prdf[MAXTR];   /* per PRD line [N][np]: weights of J-bar */
 } work_t;
 
 static void work_alloc(work_t *w, const atom_t *a, int N)
 {
     int L = a->nlev;
+    memset(w, 0, sizeof *w);
     w->N = N;
     w->dz = malloc(N * 8);
     w->Bnu = malloc(a->nlam * N * 8);
@@ -800,6 +927,15 @@ static void work_alloc(work_t *w, const atom_t *a, int N)
     w->chit = malloc(MAXACT * N * 8); w->Vlu = malloc(MAXACT * N * 8);
     w->Vul = malloc(MAXACT * N * 8); w->Ut = malloc(MAXACT * N * 8);
     w->hist = malloc(4 * L * N * 8);
+    w->rho = malloc(a->nlam * N * 8);
+    w->Jp = malloc(a->nlam * N * 8);
+    w->Pup = malloc((size_t)a->ntr * N * 8);
+    w->Pdn = malloc((size_t)a->ntr * N * 8);
+    for (int64_t i = 0; i < a->nlam * N; ++i) w->rho[i] = 1.0;
+    for (int q = 0; q < a->nprd_line; ++q) {
+        w->prdK[q] = malloc((size_t)N * a->prd_np[q] * a->prd_np[q] * 8);
+        w->prdf[q] = malloc((size_t)N * a->prd_np[q] * 8);
+    }
 }
 
 static void work_free(work_t *w)
@@ -809,6 +945,11 @@ static void work_free(work_t *w)
     free(w->dtau); free(w->I); free(w->lam); free(w->chit); free(w->Vlu); free(w->Vul);
     free(w->Ieff); free(w->omlam); free(w->Sbg);
     free(w->Ut); free(w->hist);
+    free(w->rho); free(w->Jp); free(w->Pup); free(w->Pdn);
+    for (int q = 0; q < MAXTR; ++q) {
+        if (w->prdK[q]) free(w->prdK[q]);
+        if (w->prdf[q]) free(w->prdf[q]);
+    }
 }
 
 /* free-free (Kramers, g_ff = 1) absorption coefficient constant, SI:
@@ -903,6 +1044,81 @@ static void column_setup(const rho_ctx *c, int64_t col, work_t *w)
         for (int l = 0; l < L; ++l) ns[l] = c->nstar[((size_t)col * L + l) * N + k];
         collision_rates(a, T[k], ne[k], ns, w->C + (size_t)k * L * L);
     }
+    /* partial redistribution: per PRD line and depth the redistribution
+     * kernel on the line's points, K[i][j] = R(x_j, x_i) w_j / sum_j (...) (the
+     * discrete normalisation makes a frequency-independent J give rho = 1),
+     * and the weights of J-bar, f_j = H(a, x_j) w_j / sum (...); x in Doppler
+     * units of the depth, static frame */
+    for (int q = 0; q < a->nprd_line; ++q) {
+        int t = a->prd_t[q], m = a->prd_np[q];
+        for (int k = 0; k < N; ++k) {
+            double dnuD = a->nu0[t] / CLIGHT * sqrt(2.0 * KBOLTZ * T[k] / a->mass);
+            double ad = damping(a, t, k, N);
+            double *K = w->prdK[q] + (size_t)k * m * m, *f = w->prdf[q] + (size_t)k * m;
+            double fs = 0.0;
+            for (int j = 0; j < m; ++j) {
+                double xj = (a->nu[a->prd_pts[q][j]] - a->nu0[t]) / dnuD;
+                f[j] = rho_voigt(ad, xj) * a->prd_w[q][j];
+                fs += f[j];
+            }
+            for (int j = 0; j < m; ++j) f[j] /= fs;
+            for (int i = 0; i < m; ++i) {
+                double xi = (a->nu[a->prd_pts[q][i]] - a->nu0[t]) / dnuD, rs = 0.0;
+                for (int j = 0; j < m; ++j) {
+                    double xj = (a->nu[a->prd_pts[q][j]] - a->nu0[t]) / dnuD;
+                    K[i * m + j] = rho_r2a(ad, xj, xi) * a->prd_w[q][j];
+                    rs += K[i * m + j];
+                }
+                for (int j = 0; j < m; ++j) K[i * m + j] /= rs;
+            }
+        }
+    }
+}
+
+/* rho = psi/phi of every PRD line after a solve (Uitenbroek 2001, Eq. 14,
+ * angle-averaged, coherent scattering in the atom's frame, gamma = 1):
+ *   rho_i = 1 + F [sum_j K_ij J_j / Jbar - 1],  Jbar = sum_j f_j J_j,
+ *   F = n_l R_lu / sum_k n_k P_ku,
+ * the fraction of the upper level's supply that is absorption in the line,
+ * with the actual (not preconditioned) radiative rates of the formal solution
+ * just done plus collisions and the populations of the next iteration; at
+ * statistical equilibrium sum_k n_k P_ku = n_u P_u and R_lu = B_lu Jbar, the
+ * usual n_l B_lu (sum K J - Jbar)/(n_u P_u), and F in [0, 1] keeps rho >= 0
+ * on the way there.  Then PRD switching (Eq. 1) rho' = eps rho + (1 - eps),
+ * eps = min(1, eps0 it^2) for the next iteration it (eps0 <= 0: eps = 1),
+ * and the new rho is the mean of rho' and the previous rho (under-relaxation:
+ * the plain lagged update diverged without Ng on thick Lyman alpha wings). */
+static void prd_update(const rho_ctx *c, int64_t col, work_t *w, const double *n, int it_next, double eps0)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, L = a->nlev;
+    double eps = eps0 > 0.0 ? fmin(1.0, eps0 * (double)it_next * (double)it_next) : 1.0;
+    (void)col;
+    for (int q = 0; q < a->nprd_line; ++q) {
+        int t = a->prd_t[q], m = a->prd_np[q], l = a->tl[t], u = a->tu[t];
+        for (int k = 0; k < N; ++k) {
+            const double *K = w->prdK[q] + (size_t)k * m * m, *f = w->prdf[q] + (size_t)k * m;
+            /* supply of the upper level: radiative (plain) and collisional */
+            double in = 0.0;
+            for (int t2 = 0; t2 < a->ntr; ++t2) {
+                if (a->tu[t2] == u) in += n[a->tl[t2] * N + k] * w->Pup[(size_t)t2 * N + k];
+                if (a->tl[t2] == u) in += n[a->tu[t2] * N + k] * w->Pdn[(size_t)t2 * N + k];
+            }
+            for (int p = 0; p < L; ++p)
+                if (p != u) in += n[p * N + k] * w->C[(size_t)k * L * L + p * L + u];
+            double F = n[l * N + k] * w->Pup[(size_t)t * N + k] / in;
+            double jbar = 0.0;
+            for (int j = 0; j < m; ++j) jbar += f[j] * w->Jp[(size_t)a->prd_pts[q][j] * N + k];
+            for (int i = 0; i < m; ++i) {
+                double sr = 0.0;
+                for (int j = 0; j < m; ++j) sr += K[i * m + j] * w->Jp[(size_t)a->prd_pts[q][j] * N + k];
+                double r = 1.0 + F * (sr / jbar - 1.0);
+                /* under-relaxed by 1/2: the lagged update alone diverged without Ng */
+                double *rp = &w->rho[(size_t)a->prd_pts[q][i] * N + k];
+                *rp = 0.5 * *rp + 0.5 * (eps * r + (1.0 - eps));
+            }
+        }
+    }
 }
 
 /* per-transition V_lu, V_ul, U_ul and chi_t on all depths for grid point i, ray (m,d) */
@@ -919,9 +1135,12 @@ static void transition_coeffs(const rho_ctx *c, int64_t col, const work_t *w, co
             const double *p = w->prof + (((size_t)a->prof_slot[i * MAXACT + s] * a->nmu + m) * 2 + d) * N;
             double h4 = HPLANCK * nu / (4.0 * PI_D);
             for (int k = 0; k < N; ++k) {
+                /* partial redistribution: emission and stimulated emission
+                 * with psi = rho phi */
+                double r = a->prd[t] ? w->rho[i * N + k] : 1.0;
                 Vlu[k] = h4 * a->Blu[t] * p[k];
-                Vul[k] = a->g[l] / a->g[u] * Vlu[k];
-                U[k] = h4 * a->A[t] * p[k];
+                Vul[k] = a->g[l] / a->g[u] * Vlu[k] * r;
+                U[k] = h4 * a->A[t] * p[k] * r;
             }
         } else {
             double r = a->nu0[t] / nu;
@@ -993,12 +1212,21 @@ static void rate_matrix(const rho_ctx *c, int64_t col, work_t *w, const double *
     const double *T = c->T + col * N;
     double *G = w->Gam;
     memset(G, 0, sizeof(double) * N * L * L);
+    if (a->nprd_line) {
+        memset(w->Jp, 0, sizeof(double) * a->nlam * N);
+        memset(w->Pup, 0, sizeof(double) * a->ntr * N);
+        memset(w->Pdn, 0, sizeof(double) * a->ntr * N);
+    }
     for (int64_t i = 0; i < a->nlam; ++i) {
         double nu = a->nu[i];
+        int prd_pt = 0;
+        for (int s = 0; s < a->nact[i]; ++s) prd_pt |= a->prd[a->act[i * MAXACT + s]];
         for (int m = 0; m < a->nmu; ++m)
             for (int d = 0; d < 2; ++d) {
                 transition_coeffs(c, col, w, n, i, m, d);
                 if (mode != 2) formal_ray(c, col, w, n, i, m, d);
+                if (prd_pt && mode != 2)
+                    for (int k = 0; k < N; ++k) w->Jp[i * N + k] += 0.5 * a->wmu[m] * w->I[k];
                 for (int k = 0; k < N; ++k) {
                     double psi = (mode == 0) ? w->lam[k] / w->chi[k] : 0.0;
                     double Ieff = (mode == 2) ? 0.0 : (mode == 0 ? w->Ieff[k] : w->I[k]);
@@ -1018,6 +1246,11 @@ static void rate_matrix(const rho_ctx *c, int64_t col, work_t *w, const double *
                         }
                         Gk[u * L + l] += W * w->Vlu[s * N + k] * Ik;
                         Gk[l * L + u] += W * (spont + w->Vul[s * N + k] * Ik);
+                        if (a->nprd_line && mode != 2) {
+                            /* plain rates (actual intensity), for the PRD update */
+                            w->Pup[(size_t)t * N + k] += W * w->Vlu[s * N + k] * w->I[k];
+                            w->Pdn[(size_t)t * N + k] += W * (Ut + w->Vul[s * N + k] * w->I[k]);
+                        }
                         if (psi != 0.0) {
                             for (int s2 = 0; s2 < a->nact[i]; ++s2) {
                                 if (s2 == s) continue;
@@ -1278,6 +1511,7 @@ static void iterate_column(rho_ctx *c, int64_t col, const rho_iter_opts *o, work
         memcpy(n, c->nstar + (size_t)col * nv, nv * 8);
     int hcount = 0, it = 0, status = ST_MAXITER;
     double dmax = INFINITY;
+    for (int64_t q = 0; q < a->nlam * N; ++q) w->rho[q] = 1.0;   /* PRD starts as CRD */
     if (o->start == 3 || o->start == 4) {
         int st0 = start_column(c, col, w, o->start, n);
         if (st0) {
@@ -1329,6 +1563,7 @@ static void iterate_column(rho_ctx *c, int64_t col, const rho_iter_opts *o, work
         }
         memcpy(n, nnew, nv * 8);
         if (converged) { status = ST_CONV; break; }
+        if (a->nprd_line) prd_update(c, col, w, n, it + 1, o->prd_eps0);
     }
     if (it > o->maxiter) it = o->maxiter;
     c->iters[col] = it;

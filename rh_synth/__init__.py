@@ -51,11 +51,14 @@ def hydrogen_like_atom(nbound: int = 5,
                        a_bot: float = 1e-2,
                        nmu: int = 5,
                        T_ref: float = 5000.0,
-                       metal_floor: float = 1e-4) -> dict:
+                       metal_floor: float = 1e-4,
+                       prd_lines=()) -> dict:
     """Atom description of the H-like model atom (arrays are numpy, SI units).
 
     Level index i = n - 1 for bound levels, the continuum is the last level.
     With the defaults the wavelength grid has 4*64 + 6*32 + 5*32 = 608 points.
+    ``prd_lines``: (lower n, upper n) pairs treated in partial redistribution,
+    e.g. ((1, 2), (1, 3)) for Lyman alpha and beta.
     """
     nlev = nbound + 1
     E = np.array([E_RYD_EV * (1.0 - 1.0 / n ** 2) for n in range(1, nbound + 1)]
@@ -80,7 +83,8 @@ def hydrogen_like_atom(nbound: int = 5,
         cont_l=np.array(cont_l, np.int32), cont_alpha0=np.array(alpha0),
         cont_nlambda=np.full(nbound, cont_nlambda, np.int32),
         cont_ratio=np.full(nbound, cont_ratio),
-        mass_amu=AMU_H, T_ref=T_ref, nmu=nmu, metal_floor=metal_floor)
+        mass_amu=AMU_H, T_ref=T_ref, nmu=nmu, metal_floor=metal_floor,
+        line_prd=np.array([1 if (l + 1, u + 1) in tuple(prd_lines) else 0 for l, u in zip(ll, lu)], np.int32))
 
 
 def small_atom(nbound: int = 3, nlambda: int = 8, cont_nlambda: int = 6,

@@ -656,3 +656,68 @@ def test_stokes_weak_field_and_symmetries(orc, column_oracle, halpha):
     assert np.allclose(ro[:, 1], -r0[:, 2], rtol=1e-10, atol=tol)
     assert np.allclose(ro[:, [0, 3]], r0[:, [0, 3]], rtol=1e-12)
     assert np.abs(r0[:, 1]).max() > np.abs(r0[:, 2]).max() > 0
+
+
+# ---------------------------------------------------------------- partial redistribution (NEXT-1)
+def test_redistribution_function_pins(orc):
+    from scipy.integrate import quad
+    from scipy.special import erfc
+    # normalisation: int R_II-A(x', x) dx' = H(a, x)/sqrt(pi) (Hummer 1962); R
+    # falls like erfc beyond max(|x|, |x'|), so |x'| <= |x| + 8 is complete
+    for a in (1e-3, 1e-2):
+        for x in (0.0, 0.7, 2.5, -6.0, 20.0):
+            X = abs(x) + 8.0
+            pts = sorted({-X, X, x, -x, 0.0})
+            tot = sum(quad(lambda xp: orc.r2a(a, xp, x), lo, hi, epsabs=0, epsrel=1e-12, limit=400)[0]
+                      for lo, hi in zip(pts[:-1], pts[1:]))
+            assert tot == pytest.approx(orc.faddeeva(a, x)[0] / np.sqrt(np.pi), rel=1e-10), (a, x)
+    # symmetries
+    for (xp, x) in ((1.3, -0.4), (5.0, 5.2), (-2.0, 0.3)):
+        r = orc.r2a(1e-2, xp, x)
+        assert orc.r2a(1e-2, x, xp) == pytest.approx(r, rel=1e-13)
+        assert orc.r2a(1e-2, -xp, -x) == pytest.approx(r, rel=1e-13)
+    # no damping: Hummer's R_I-A, (1/2) erfc(max(|x|, |x'|))
+    for (xp, x) in ((0.5, 2.0), (-0.5, 2.0), (-3.0, -1.0), (0.0, 0.0), (1.7, -1.2)):
+        assert orc.r2a(1e-12, xp, x) == pytest.approx(0.5 * erfc(max(abs(x), abs(xp))), rel=1e-9)
+
+
+def _prd_atom(prd=True):
+    a = rh_synth.hydrogen_like_atom(nbound=3, lyman_nlambda=24, line_nlambda=12, cont_nlambda=10, nmu=3,
+                                    prd_lines=((1, 2),))
+    if not prd:
+        a["line_prd"] = a["line_prd"] * 0
+    return a
+
+
+def test_prd_reduces_to_crd_when_collisions_dominate(orc):
+    # with collisions scaled by 1e10 the line supplies a vanishing fraction of
+    # the upper level, rho -> 1: PRD and CRD populations coincide
+    cols = rh_synth.chromosphere_column(ndep=24)
+    o0 = orc.Oracle()
+    o0.setup_atom(_prd_atom(False))
+    o0.load_columns(cols)
+    _, ne = o0.lte()
+    res = []
+    for prd in (False, True):
+        o = orc.Oracle()
+        o.setup_atom(_prd_atom(prd))
+        o.load_columns(cols, ne=ne * 1e10)
+        o.iterate(maxiter=60, tol=1e-12)
+        res.append(o.populations()[0])
+    assert np.allclose(res[1], res[0], rtol=1e-8)
+
+
+def test_prd_converges_and_differs_from_crd(orc):
+    cols = rh_synth.subset(rh_synth.chromosphere_cube(nx=16, ny=16, ndep=32, seed=3), [0, 5])
+    res = {}
+    for prd in (False, True):
+        o = orc.Oracle()
+        o.setup_atom(_prd_atom(prd))
+        o.load_columns(cols)
+        o.iterate(maxiter=400, tol=1e-3)
+        n, it, st, _ = o.populations()
+        assert np.all(st == 0), (prd, st)
+        res[prd] = n
+        # conservation holds with PRD too
+        assert np.allclose(n.sum(axis=1), cols["nH"], rtol=1e-12)
+    assert np.max(np.abs(res[True] / res[False] - 1)) > 1e-2
