@@ -82,6 +82,9 @@ typedef struct {
     double T_ref;                  /* K, reference temperature of the line grids */
     int32_t nmu;                   /* Gauss-Legendre angles on (0,1], 1..8 */
     double metal_floor;            /* electrons per hydrogen atom from metals */
+    const int32_t *line_prd;       /* [nline] 1: angle-averaged partial redistribution (Hummer R_II-A),
+                                      NULL or 0: complete redistribution; at most 4 PRD lines, no two
+                                      sharing a wavelength point */
 } rh_atom_desc;
 
 /* Copy the atom, build the wavelength grid (line bands on a sinh-stretched
@@ -131,6 +134,8 @@ typedef struct {
     int32_t only_unconverged; /* 1: iterate only the columns whose status is not RH_COL_CONVERGED
                              (Sect. 2.3: re-run the columns that did not converge with other
                              options); converged columns are left untouched */
+    double prd_eps0;      /* PRD switching (Eq. 1): rho' = eps rho + (1 - eps), eps = min(1, eps0 it^2);
+                             <= 0: off (eps = 1).  Atoms with PRD lines only */
 } rh_iter_opts;
 
 typedef struct {

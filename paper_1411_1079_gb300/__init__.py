@@ -40,14 +40,14 @@ class AtomDesc(C.Structure):
                 ("ncont", C.c_int32), ("cont_l", _ip), ("cont_alpha0", _dp),
                 ("cont_nlambda", _ip), ("cont_ratio", _dp),
                 ("mass_amu", C.c_double), ("T_ref", C.c_double), ("nmu", C.c_int32),
-                ("metal_floor", C.c_double)]
+                ("metal_floor", C.c_double), ("line_prd", _ip)]
 
 
 class IterOpts(C.Structure):
     _fields_ = [("maxiter", C.c_int32), ("tol", C.c_double), ("ng_order", C.c_int32),
                 ("ng_delay", C.c_int32), ("ng_period", C.c_int32), ("start", C.c_int32),
                 ("precision", C.c_int32), ("persistent", C.c_int32), ("block_warps", C.c_int32),
-                ("crsw_init", C.c_double), ("only_unconverged", C.c_int32)]
+                ("crsw_init", C.c_double), ("only_unconverged", C.c_int32), ("prd_eps0", C.c_double)]
 
 
 class IterStats(C.Structure):
@@ -190,6 +190,9 @@ class Context:
                      cont_nlambda=_i(a["cont_nlambda"]), cont_ratio=_d(a["cont_ratio"]),
                      mass_amu=a["mass_amu"], T_ref=a["T_ref"], nmu=a["nmu"],
                      metal_floor=a["metal_floor"])
+        if "line_prd" in a:
+            a["line_prd"] = np.ascontiguousarray(a["line_prd"], dtype=np.int32)
+            d.line_prd = _i(a["line_prd"])
         self._check(self._lib.rh_setup_atom(self._p, C.byref(d)))
         self.nlev = a["nlev"]
         self.nmu = a["nmu"]
@@ -218,10 +221,12 @@ class Context:
         self.ncol, self.ndep = int(ncol), int(ndep)
 
     def iterate(self, maxiter=500, tol=1e-3, ng_order=2, ng_delay=5, ng_period=3, start=0,
-                precision=1, persistent=1, block_warps=0, crsw_init=1.0, only_unconverged=0) -> dict:
+                precision=1, persistent=1, block_warps=0, crsw_init=1.0, only_unconverged=0,
+                prd_eps0=0.0) -> dict:
         o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
                      ng_period=ng_period, start=start, precision=precision, persistent=persistent,
-                     block_warps=block_warps, crsw_init=crsw_init, only_unconverged=only_unconverged)
+                     block_warps=block_warps, crsw_init=crsw_init, only_unconverged=only_unconverged,
+                     prd_eps0=prd_eps0)
         s = IterStats()
         rc = self._check(self._lib.rh_iterate(self._p, C.byref(o), C.byref(s)), allow=(RH_ENOTCONV,))
         out = {f: getattr(s, f) for f, _ in IterStats._fields_}
@@ -233,7 +238,8 @@ class Context:
     RERUN_CRSW = (1e3, 1e5, 1e7)
 
     def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True, start=0,
-              ng_order=2, ng_delay=5, ng_period=3, use_graph=1, autotune=1, fused_rerun=1) -> dict:
+              ng_order=2, ng_delay=5, ng_period=3, use_graph=1, autotune=1, fused_rerun=1,
+              prd_eps0=0.0) -> dict:
         """rh_solve: every column from LTE (start=0), the learned guess
         (start=1), the current populations (start=2), zero radiation (3) or
         escape probabilities (4) with Ng acceleration, then the columns that
@@ -246,7 +252,7 @@ class Context:
         o = SolveOpts()
         o.pass1 = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay, ng_period=ng_period,
                            start=start, precision=precision, persistent=persistent, block_warps=block_warps,
-                           crsw_init=1.0, only_unconverged=0)
+                           crsw_init=1.0, only_unconverged=0, prd_eps0=prd_eps0)
         # the ladder: from a start other than LTE, first LTE with the same
         # options; then stronger and stronger switching without Ng
         rungs = ([(1.0, 1)] if start != 0 else []) + [(f, 0) for f in self.RERUN_CRSW]

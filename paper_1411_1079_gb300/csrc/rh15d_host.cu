@@ -17,7 +17,7 @@ using namespace rh;
 namespace {
 
 struct HostTrans {
-    int l, u, kind, sub;
+    int l, u, kind, sub, prd = 0;
     double nu0, f, A, Blu, Bul, a_top, a_bot, qwing, alpha0, ratio, nu_lo, nu_hi;
     int nlam;
 };
@@ -40,6 +40,10 @@ struct HostAtom {
     // its continuum points (frequency, 4 pi w (2 h nu^3/c^2) alpha / (h nu))
     std::vector<int> sp_off;
     std::vector<double> sp_nu, sp_ce;
+    // partial redistribution: PRD point of each padded lane (-1: none), and
+    // per PRD point (PRD lines in order, frequency order) frequency and weight
+    std::vector<int> lane_prd;
+    std::vector<double> prd_nu, prd_w;
 };
 
 }  // namespace
@@ -87,6 +91,11 @@ struct rh_ctx {
     std::vector<unsigned char> gkey;            // what the captured graph was built from
     int glaunches = 0;
     cudaEvent_t pass_ev[1 + RH_MAX_RERUN] = {};   // end of each pass (recorded inside the sequence)
+    // partial redistribution: device tables and per-block scratch
+    int *lane_prd_d = nullptr;
+    double *prd_nu_d = nullptr, *prd_w_d = nullptr;
+    void *prd_scr = nullptr;
+    size_t prd_cap = 0;
     // start solutions: device copy of the continuum point lists
     int *sp_off_d = nullptr;
     double *sp_nu_d = nullptr, *sp_ce_d = nullptr;
@@ -223,6 +232,7 @@ int build_atom(rh_ctx *c, const rh_atom_desc *d)
             return fail(c, RH_EINVAL, "line %d: f, qwing must be > 0 and damping in (0, 0.05]", t);
         h.kind = 0;
         h.sub = t;
+        h.prd = (d->line_prd && d->line_prd[t]) ? 1 : 0;
         h.nu0 = (a.E[h.u] - a.E[h.l]) / kH;
         if (!(h.nu0 > 0)) return fail(c, RH_EINVAL, "line %d: upper level not above lower", t);
         h.f = d->line_f[t];
@@ -413,6 +423,59 @@ int build_atom(rh_ctx *c, const rh_atom_desc *d)
     }
     da.macc = acc;
     da.nmap = nmap;
+    // partial redistribution
+    {
+        int np_lines = 0;
+        for (int t = 0; t < a.ntr; ++t) np_lines += a.tr[t].prd;
+        if (np_lines > RH_MAXPRD) return fail(c, RH_EINVAL, "at most %d PRD lines", RH_MAXPRD);
+        int pacc = 0;
+        for (int b = 0; b < a.ntile; ++b) {
+            DevTile &tl = da.tile[b];
+            tl.prd_slot = -1;
+            for (int j = 0; j < tl.K; ++j)
+                if (a.tr[tl.t[j]].prd) {
+                    if (tl.prd_slot >= 0) return fail(c, RH_EINVAL, "two PRD lines overlap in wavelength");
+                    tl.prd_slot = j;
+                }
+            tl.pacc_off = pacc;
+            if (np_lines) pacc += 2 * tl.K;
+        }
+        da.pacc = pacc;
+        std::vector<int> gi2lane(a.nu.size(), -1);
+        for (int p = 0; p < a.npad; ++p)
+            if (a.lane_point[p] >= 0) gi2lane[a.lane_point[p]] = p;
+        a.lane_prd.assign(a.npad, -1);
+        a.prd_nu.clear();
+        a.prd_w.clear();
+        da.nprd = 0;
+        da.prd_off[0] = 0;
+        da.prd_koff[0] = 0;
+        for (int t = 0; t < a.ntr; ++t) {
+            if (!a.tr[t].prd) continue;
+            std::vector<std::pair<double, int>> pts;
+            for (size_t gi = 0; gi < a.nu.size(); ++gi) {
+                auto it = std::find(a.act[gi].begin(), a.act[gi].end(), t);
+                if (it != a.act[gi].end()) pts.push_back({a.nu[gi], (int)gi});
+            }
+            std::sort(pts.begin(), pts.end());
+            const int q = da.nprd++;
+            da.prd_t[q] = t;
+            for (auto &pr : pts) {
+                const int gi = pr.second;
+                const int pp = (int)a.prd_nu.size();
+                if (pp >= RH_MAXPRDPT) return fail(c, RH_EINVAL, "more than %d PRD wavelength points", RH_MAXPRDPT);
+                if (a.lane_prd[gi2lane[gi]] >= 0) return fail(c, RH_EINVAL, "two PRD lines share a wavelength point");
+                a.lane_prd[gi2lane[gi]] = pp;
+                a.prd_nu.push_back(pr.first);
+                auto it = std::find(a.act[gi].begin(), a.act[gi].end(), t);
+                a.prd_w.push_back(a.wq[gi][it - a.act[gi].begin()]);
+            }
+            const int npq = (int)pts.size();
+            da.prd_off[q + 1] = da.prd_off[q] + npq;
+            da.prd_koff[q + 1] = da.prd_koff[q] + npq * npq;
+        }
+        da.npp = (int)a.prd_nu.size();
+    }
     // processing order: tiles with more transitions (costlier) first, line tiles before continua
     {
         std::vector<int> ord(a.ntile);
@@ -518,6 +581,40 @@ int ensure_lane(rh_ctx *c, int prec)
     c->lane_prec = prec;
     c->lane_nref = c->nref;
     return RH_OK;
+}
+
+// PRD tables and the per-block scratch of the column kernel (as many blocks
+// as the Ng history: 4 per SM)
+int ensure_prd(rh_ctx *c, int precision)
+{
+    if (!c->da.nprd) return RH_OK;
+    const HostAtom &a = c->ha;
+    if (!c->lane_prd_d) {
+        CK(cudaMalloc(&c->lane_prd_d, a.lane_prd.size() * sizeof(int)));
+        CK(cudaMalloc(&c->prd_nu_d, a.prd_nu.size() * sizeof(double)));
+        CK(cudaMalloc(&c->prd_w_d, a.prd_w.size() * sizeof(double)));
+        CK(cudaMemcpy(c->lane_prd_d, a.lane_prd.data(), a.lane_prd.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->prd_nu_d, a.prd_nu.data(), a.prd_nu.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->prd_w_d, a.prd_w.data(), a.prd_w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    const size_t want = mali_prd_bytes_per_block(c->da, c->ndep, precision) * (size_t)c->nsm * 4;
+    if (c->prd_cap < want) {
+        drop_graph(c);
+        dfree(c->prd_scr);
+        CK(cudaMalloc(&c->prd_scr, want));
+        c->prd_cap = want;
+    }
+    return RH_OK;
+}
+
+void set_prd(const rh_ctx *c, IterLaunch &il, double eps0)
+{
+    il.prd_eps0 = eps0;
+    il.lane_prd = c->lane_prd_d;
+    il.prd_nu = c->prd_nu_d;
+    il.prd_w = c->prd_w_d;
+    il.prd_scr = c->prd_scr;
+    il.prd_cap = c->prd_cap;
 }
 
 int ensure_start_tables(rh_ctx *c)
@@ -839,6 +936,7 @@ void rh_destroy(rh_ctx *c)
     dfree(c->vtab_d);
     dfree(c->dtab_d);
     dfree(c->nghist);
+    dfree(c->prd_scr);
     dfree(c->queue);
     dfree(c->badidx);
     dfree(c->colidx);
@@ -855,6 +953,9 @@ void rh_destroy(rh_ctx *c)
     dfree(c->sp_nu_d);
     dfree(c->sp_ce_d);
     drop_graph(c);
+    dfree(c->lane_prd_d);
+    dfree(c->prd_nu_d);
+    dfree(c->prd_w_d);
     for (cudaEvent_t &ev : c->pass_ev)
         if (ev) cudaEventDestroy(ev);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -875,6 +976,9 @@ int rh_setup_atom(rh_ctx *c, const rh_atom_desc *d)
     dfree(c->sp_off_d);
     dfree(c->sp_nu_d);
     dfree(c->sp_ce_d);
+    dfree(c->lane_prd_d);
+    dfree(c->prd_nu_d);
+    dfree(c->prd_w_d);
     c->lane_prec = -1;
     c->tuned_bw[0] = c->tuned_bw[1] = c->tuned_ctas[0] = c->tuned_ctas[1] = 0;
     drop_graph(c);
@@ -961,7 +1065,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     if (o->maxiter < 1 || !(o->tol >= 0) || (o->ng_order != 0 && o->ng_order != 2) ||
         (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) || (o->precision != 0 && o->precision != 1) ||
         (o->start < 0 || o->start > 4) || o->block_warps < 0 || o->block_warps > 8 ||
-        (o->only_unconverged != 0 && o->only_unconverged != 1))
+        (o->only_unconverged != 0 && o->only_unconverged != 1) || !std::isfinite(o->prd_eps0))
         return fail(c, RH_EINVAL, "rh_iterate: invalid options");
     cudaSetDevice(c->dev);
     int start = o->start;
@@ -1029,6 +1133,8 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     }
     int r = ensure_lane(c, o->precision);
     if (r) return r;
+    r = ensure_prd(c, o->precision);
+    if (r) return r;
     size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
     size_t want = per_block * (size_t)c->nsm * 4;
     if (c->nghist_cap < want) {
@@ -1054,6 +1160,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
         il.block_warps = c->tuned_bw[o->precision];
         il.ctas_per_sm = c->tuned_ctas[o->precision];
     }
+    set_prd(c, il, o->prd_eps0);
     float ms = 0;
     int grid = 0;
     char ebuf[256] = {0};
@@ -1288,7 +1395,7 @@ bool valid_iter_opts(const rh_iter_opts *o)
 
 // everything the enqueued sequence depends on, compared byte-wise
 struct SolveKey {
-    const void *ptrs[27];
+    const void *ptrs[31];
     int64_t ncol;
     int ndep, bw, ctas, nsm;
     rh_solve_opts o;
@@ -1301,8 +1408,9 @@ SolveKey make_key(const rh_ctx *c, const rh_solve_opts *o, int bw, int ctas)
     const void *p[] = {c->ca.z, c->ca.T, c->ca.nH, c->ca.vz, c->ca.ne, c->ca.np, c->ca.nstar, c->ca.pops,
                        c->ca.Crate, c->ca.dmax, c->ca.iters, c->ca.status, c->lane_d, c->vtab_d, c->nghist,
                        c->queue, c->colidx, c->solve_cnt, c->solve_it, c->mlp, c->feat, c->lnb, c->nfb_d, c->st,
-                       c->sp_off_d, c->sp_nu_d, c->sp_ce_d};
-    static_assert(sizeof p / sizeof p[0] == 27, "key size");
+                       c->sp_off_d, c->sp_nu_d, c->sp_ce_d, c->lane_prd_d, c->prd_nu_d, c->prd_w_d,
+                       c->prd_scr};
+    static_assert(sizeof p / sizeof p[0] == 31, "key size");
     memcpy(k.ptrs, p, sizeof p);
     k.ncol = c->ncol;
     k.ndep = c->ndep;
@@ -1425,6 +1533,8 @@ int rh_autotune(rh_ctx *c, int32_t precision, rh_tune_result *out)
     cudaSetDevice(c->dev);
     int r = ensure_lane(c, precision);
     if (r) return r;
+    r = ensure_prd(c, precision);
+    if (r) return r;
     const size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
     const size_t want = per_block * (size_t)c->nsm * 4;
     if (c->nghist_cap < want) {
@@ -1471,6 +1581,7 @@ int rh_autotune(rh_ctx *c, int32_t precision, rh_tune_result *out)
             il.start = 0;
             il.nsm = c->nsm;
             il.nwork = S;
+            set_prd(c, il, 0.0);
             double best = -1;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // first run: warm-up
                 float ms = 0;
@@ -1545,6 +1656,8 @@ int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
     // everything the sequence touches exists before it is enqueued or captured
     int r = ensure_lane(c, prec);
     if (r) return r;
+    r = ensure_prd(c, prec);
+    if (r) return r;
     const size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
     const size_t want = per_block * (size_t)c->nsm * 4;
     if (c->nghist_cap < want) {
@@ -1577,6 +1690,7 @@ int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
         base.block_warps = c->tuned_bw[prec];
         base.ctas_per_sm = c->tuned_ctas[prec];
     }
+    set_prd(c, base, o->pass1.prd_eps0);
     const int bw_used = base.block_warps > 0 ? base.block_warps : (prec ? 8 : 4);
     const int ctas_max = mali_max_ctas_per_sm(c->da, c->ndep, prec, bw_used);
     const int ctas_used = base.ctas_per_sm > 0 ? std::min(base.ctas_per_sm, ctas_max) : ctas_max;
@@ -1724,6 +1838,7 @@ extern "C" int rh_iterate_noalloc(rh_ctx *c, const rh_iter_opts *o, double *n_ou
         (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) || (o->precision != 0 && o->precision != 1) ||
         (o->start != 0 && o->start != 2) || o->block_warps < 0 || o->block_warps > 8 || o->only_unconverged != 0)
         return fail(c, RH_EINVAL, "rh_iterate_noalloc: invalid options (only_unconverged is not supported here)");
+    if (c->da.nprd) return fail(c, RH_EINVAL, "rh_iterate_noalloc: atoms with PRD lines need scratch; use rh_iterate");
     if (c->dev < 0 || c->dev >= kNoallocMaxDev) return fail(c, RH_EINVAL, "rh_iterate_noalloc: device index too large");
     CK(cudaSetDevice(c->dev));
     // once per device, with the device current: the scratch array's address

@@ -14,6 +14,8 @@
 #define RH_MAXMAP 2048
 #define RH_NLANEF 7        // per-slot lane fields
 #define RH_VT_N 1024       // Voigt coefficient table: intervals in t = 1/(1+|v|)
+#define RH_MAXPRD 4        // lines in partial redistribution
+#define RH_MAXPRDPT 1024   // wavelength points of all PRD lines together
 
 namespace rh {
 
@@ -40,6 +42,8 @@ struct DevTile {
     int t[RH_KMAX];
     int acc_off;                  // first accumulator of the tile (per depth)
     int m;                        // accumulators of the tile = K (K + 1)
+    int prd_slot;                 // slot j of a PRD line in the union, -1: none
+    int pacc_off;                 // first plain-rate accumulator (2 per slot), PRD atoms only
 };
 
 // Everything the column kernel needs about the atom, passed by value as a
@@ -58,6 +62,12 @@ struct DevAtom {
     // accumulator -> rate-matrix entry map: A[row][col] += sign * acc
     int16_t map_acc[RH_MAXMAP];
     int8_t map_row[RH_MAXMAP], map_col[RH_MAXMAP], map_sign[RH_MAXMAP];
+    // partial redistribution: PRD lines, their points (offsets into the point
+    // arrays, frequency order) and redistribution-kernel blocks (offsets, np^2)
+    int nprd, npp, pacc;
+    int prd_t[RH_MAXPRD];
+    int prd_off[RH_MAXPRD + 1];
+    int prd_koff[RH_MAXPRD + 1];
 };
 
 // Lane-table fields (structure of arrays, [field][npad]); per-slot fields are
@@ -337,6 +347,92 @@ __device__ __forceinline__ float disp_f32(float a, float v, const float4 *__rest
 }
 
 // ----------------------------------------------------------------------------
+// Angle-averaged redistribution function R_II-A (Hummer 1962) in Doppler
+// units, integrated by parts:
+//   R(x', x) = (1/2pi) int_{u0}^{u0+6.5} erfc(u) [L(u + xs) + L(u - xb)] du,
+//   L(s) = a/(a^2 + s^2), xs = min(x,x'), xb = max(x,x'), u0 = (xb - xs)/2
+// (erfc(u0 + 6.5) < 1e-20 erfc(u0)).  Each Lorentzian term: within +-1 of its
+// centre c the substitution u = c + a sinh z turns L du into dz/cosh z
+// (panels of length ZP in z); elsewhere Gauss-Legendre in u (panels of
+// length UP); NG-point rules.  FP64: NG = 8, ZP = 1, UP = 1/2; FP32: NG = 6,
+// ZP = 2, UP = 1.
+template <typename R> struct R2Rule;
+template <> struct R2Rule<double> {
+    static constexpr int NG = 8;
+    static constexpr double ZP = 1.0, UP = 0.5;
+};
+template <> struct R2Rule<float> {
+    static constexpr int NG = 6;
+    static constexpr double ZP = 2.0, UP = 1.0;
+};
+__host__ __device__ inline void gl_rule(int n, double *x, double *w)
+{
+    // nodes and weights on [-1, 1] for n = 6 or 8
+    if (n == 6) {
+        const double xs[3] = {0.2386191860831969086, 0.6612093864662645136, 0.9324695142031520278};
+        const double ws[3] = {0.4679139345726910473, 0.3607615730481386076, 0.1713244923791703450};
+        for (int i = 0; i < 3; ++i) {
+            x[i] = -xs[i]; x[5 - i] = xs[i];
+            w[i] = ws[i]; w[5 - i] = ws[i];
+        }
+    } else {
+        const double xs[4] = {0.1834346424956498049, 0.5255324099163289858, 0.7966664774136267396,
+                              0.9602898564975362317};
+        const double ws[4] = {0.3626837833783619830, 0.3137066458778872873, 0.2223810344533744706,
+                              0.1012285362903762592};
+        for (int i = 0; i < 4; ++i) {
+            x[i] = -xs[i]; x[7 - i] = xs[i];
+            w[i] = ws[i]; w[7 - i] = ws[i];
+        }
+    }
+}
+
+template <typename R>
+__device__ inline R r2_lorentz(R a, R c, R lo, R hi, const double *gx, const double *gw)
+{
+    constexpr int NG = R2Rule<R>::NG;
+    const R ZP = (R)R2Rule<R>::ZP, UP = (R)R2Rule<R>::UP;
+    R s = 0;
+    // plain parts [lo, min(hi, c-1)] and [max(lo, c+1), hi]
+    for (int side = 0; side < 2; ++side) {
+        const R p = side == 0 ? lo : (lo > c + 1 ? lo : c + 1);
+        const R q = side == 0 ? (hi < c - 1 ? hi : c - 1) : hi;
+        if (!(q > p)) continue;
+        const int n = (int)ceil((double)((q - p) / UP));
+        const R h = (q - p) / (R)n;
+        for (int k = 0; k < n; ++k)
+            for (int g = 0; g < NG; ++g) {
+                const R u = p + h * (R)(k + 0.5 * (gx[g] + 1.0));
+                const R d = u - c;
+                s += (R)(0.5 * gw[g]) * h * erfc(u) * a / (a * a + d * d);
+            }
+    }
+    // near part in z, u = c + a sinh z
+    const R nlo = lo > c - 1 ? lo : c - 1, nhi = hi < c + 1 ? hi : c + 1;
+    if (nhi > nlo) {
+        const R z0 = asinh((nlo - c) / a), z1 = asinh((nhi - c) / a);
+        const int n = (int)ceil((double)((z1 - z0) / ZP));
+        const R h = (z1 - z0) / (R)n;
+        for (int k = 0; k < n; ++k)
+            for (int g = 0; g < NG; ++g) {
+                const R z = z0 + h * (R)(k + 0.5 * (gx[g] + 1.0));
+                s += (R)(0.5 * gw[g]) * h * erfc(c + a * sinh(z)) / cosh(z);
+            }
+    }
+    return s;
+}
+
+template <typename R>
+__device__ inline R r2a_dev(R a, R xp, R x)
+{
+    double gx[8], gw[8];
+    gl_rule(R2Rule<R>::NG, gx, gw);
+    const R xs = xp < x ? xp : x, xb = xp < x ? x : xp;
+    const R u0 = (R)0.5 * (xb - xs), U = u0 + (R)6.5;
+    return (r2_lorentz<R>(a, -xs, u0, U, gx, gw) + r2_lorentz<R>(a, xb, u0, U, gx, gw)) / (R)(2.0 * kPi);
+}
+
+// ----------------------------------------------------------------------------
 // Linear short characteristics weights: e0 = 1 - exp(-d), e1 = d - e0,
 // w_o = e1/d, w_u = e0 - w_o; also 1 - w_o = e0/d, formed without
 // cancellation (it carries the preconditioned rates in optically thick
@@ -467,6 +563,12 @@ struct IterLaunch {
     int rung_ng[RH_MAX_RERUN] = {0, 0, 0, 0};   // Ng order of each rung (0 or the pass's)
     int *rung_cols = nullptr;                 // [nrung] columns entering each rung
     unsigned long long *rung_its = nullptr;   // [1 + nrung] formal solutions per pass / rung
+    // partial redistribution (atoms with PRD lines)
+    double prd_eps0 = 0.0;                    // PRD switching eps = min(1, eps0 it^2); <= 0: off
+    const int *lane_prd = nullptr;            // [npad] PRD point of each lane, -1: none
+    const double *prd_nu = nullptr, *prd_w = nullptr;   // [npp] frequency, quadrature weight
+    void *prd_scr = nullptr;                  // per-block scratch (mali_prd_bytes_per_block)
+    size_t prd_cap = 0;
 };
 cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
                         const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
@@ -474,6 +576,7 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
                         size_t errn);
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep);
 int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_warps);
+size_t mali_prd_bytes_per_block(const DevAtom &A, int ndep, int precision);
 cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
                                  const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
                                  const IterLaunch &o, cudaStream_t st, int *grid_out, char *err, size_t errn);

@@ -62,7 +62,50 @@ struct KParams {
     int rung_ng[RH_MAX_RERUN];
     int *rung_cols;                  // [nrung] columns entering each rung (nullptr: not counted)
     unsigned long long *rung_its;    // [1 + nrung] formal solutions of the pass and of each rung
+    // partial redistribution
+    double prd_eps0;
+    const int *lane_prd;
+    const double *prd_nu, *prd_w;
+    char *prd_scr;
+    size_t prd_stride;               // bytes of scratch per block
 };
+
+// Per-block PRD scratch: in R, the redistribution kernels K [sum np^2][N] (per
+// line [k][i][j]), then per PRD point [npp][N] the J-bar weights f, the mean
+// intensity J and rho, then the plain-rate accumulators [pacc][N]; in FP64
+// the supply fraction F and J-bar per line [nprd][N].
+template <typename R>
+struct PrdScr {
+    R *K, *f, *J, *rho, *plain;
+    double *F, *Jbar;
+};
+template <typename R>
+__host__ __device__ inline size_t prd_bytes(const DevAtom &A, int N)
+{
+    size_t r = sizeof(R) * ((size_t)A.prd_koff[A.nprd] * N + 3 * (size_t)A.npp * N + (size_t)A.pacc * N);
+    r = (r + 255) & ~(size_t)255;
+    return r + sizeof(double) * 2 * (size_t)A.nprd * N + 256;
+}
+template <typename R>
+__device__ inline PrdScr<R> prd_carve(char *base, const DevAtom &A, int N)
+{
+    PrdScr<R> q;
+    R *r = reinterpret_cast<R *>(base);
+    q.K = r;
+    r += (size_t)A.prd_koff[A.nprd] * N;
+    q.f = r;
+    r += (size_t)A.npp * N;
+    q.J = r;
+    r += (size_t)A.npp * N;
+    q.rho = r;
+    r += (size_t)A.npp * N;
+    q.plain = r;
+    r += (size_t)A.pacc * N;
+    size_t off = (reinterpret_cast<size_t>(r) + 255) & ~(size_t)255;
+    q.F = reinterpret_cast<double *>(off);
+    q.Jbar = q.F + (size_t)A.nprd * N;
+    return q;
+}
 
 template <typename R>
 struct Smem {
@@ -164,11 +207,13 @@ template <typename R, int K>
 struct DepthC {
     R chibg, etabg, B, etac;
     R Rs[K], Xs[K], nu_[K], chc[K], Uct[K], ad[K];
+    R rf[K];                   // partial redistribution: psi/phi of the slot (1 otherwise)
     R ivth, vz;
 };
 
-template <typename R, int K>
-__device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K> &lc, int k, int N, DepthC<R, K> &d)
+template <typename R, int K, bool PRD = false>
+__device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K> &lc, int k, int N, DepthC<R, K> &d,
+                                             const R *rho_lane = nullptr, int prd_slot = -1)
 {
     R x = lc.nu * s.hkT[k];
     R ex = rexp<R>(-x);
@@ -183,10 +228,16 @@ __device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K>
         d.nu_[j] = s.nr[lc.up[j] * N + k];
         if (lc.isline[j]) {
             d.Rs[j] = lc.grat[j];
+            if constexpr (PRD) {
+                // psi = rho phi in stimulated and spontaneous emission
+                d.rf[j] = (j == prd_slot && rho_lane) ? rho_lane[k] : (R)1;
+                d.Rs[j] *= d.rf[j];
+            }
             d.chc[j] = 0;
             d.Uct[j] = 0;
             d.ad[j] = s.ad[lc.sub[j] * N + k];
         } else {
+            if constexpr (PRD) d.rf[j] = 1;
             d.Rs[j] = s.Gc[lc.sub[j] * N + k] * ex;
             d.ad[j] = 0;
         }
@@ -204,7 +255,7 @@ __device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K>
 // Opacity and emissivity for one ray direction (direction cosine muz);
 // per-slot profile phi, opacity chj and emissivity per upper-level
 // population U.
-template <typename R, int K>
+template <typename R, int K, bool PRD = false>
 __device__ __forceinline__ void angle_vals(const Smem<R> &s, const LaneC<R, K> &lc, const DepthC<R, K> &d, R muz,
                                            R &chi, R &eta, R *phi, R *chj, R *U)
 {
@@ -218,6 +269,7 @@ __device__ __forceinline__ void angle_vals(const Smem<R> &s, const LaneC<R, K> &
             phi[j] = ph;
             chj[j] = lc.Vc[j] * ph * d.Xs[j];
             U[j] = lc.Uc[j] * ph;
+            if constexpr (PRD) U[j] *= d.rf[j];
             ea += d.nu_[j] * U[j];
         } else {
             phi[j] = 1;
@@ -266,8 +318,13 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 //   up_j = c_j w phi_j I_eff,  down_j = c_j R_j w phi_j (E_j (1 - Psi* chi_j) + I_eff),
 //   cross_{j,j'} = c_j X_j w phi_j Psi* U_j';
 // the warp sums them over its wavelengths and lane a adds accumulator a.
-template <typename R, int K>
-__device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane)
+// PRD: the tile's PRD slot emits with psi = rho phi (rho of the lane's point
+// and depth from the block's scratch), PRD lanes accumulate the angle-averaged
+// mean intensity J, and every slot also accumulates its plain rates (actual
+// intensity) cw I and cw R (E + I), for the PRD update.
+template <typename R, int K, bool PRD>
+__device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane, R *prd_rho,
+                             R *prd_J, R *prd_plain)
 {
     const int N = p.N;
     const DevTile &tl = A.tile[b];
@@ -296,15 +353,24 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
     lc.nu3s = lt[kLaneNu3 * npad + pi];
     lc.tw = lt[kLaneTw * npad + pi];
     constexpr int M = K * (K + 1);
-    constexpr int P = Pow2<M>::v;
+    constexpr int MP = PRD ? M + 2 * K : M;        // with the plain rates
+    constexpr int P = Pow2<MP>::v;
     constexpr int SH = 5 - Log2<P>::v;
     R *slot = s.slot + (size_t)tl.acc_off * N;
     const bool writer = (lane & ((1 << SH) - 1)) == 0;
     const int widx = lane >> SH;
+    int pp = -1;                                   // PRD point of the lane
+    const R *rho_lane = nullptr;
+    R *plain = nullptr;
+    if constexpr (PRD) {
+        pp = tl.prd_slot >= 0 ? p.lane_prd[pi] : -1;
+        rho_lane = pp >= 0 ? prd_rho + (size_t)pp * N : nullptr;
+        plain = prd_plain + (size_t)tl.pacc_off * N;
+    }
 
     // contributions of one depth point to the tile's accumulators
     auto emit = [&](int k, const DepthC<R, K> &d, const R (&phi)[K], const R (&chj)[K], const R (&U)[K], R ichi,
-                    R wo, R omwo, R psi, R Ieff, R wm2, bool first) {
+                    R wo, R omwo, R psi, R Ieff, R Ik, R wm2, bool first) {
         R val[P];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -321,13 +387,32 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
             for (int j2 = 0; j2 < K; ++j2)
                 if (j2 != j) val[2 * K + j * (K - 1) + (j2 < j ? j2 : j2 - 1)] = cx * U[j2];
         }
+        if constexpr (PRD) {
 #pragma unroll
-        for (int a = M; a < P; ++a) val[a] = 0;
+            for (int j = 0; j < K; ++j) {
+                const R cw = lc.c[j] * wm2 * phi[j];
+                val[M + 2 * j] = cw * Ik;
+                val[M + 2 * j + 1] = cw * d.Rs[j] * (lc.E[j] + Ik);
+            }
+            if (pp >= 0) {
+                R *jp = prd_J + (size_t)pp * N + k;
+                *jp = first ? wm2 * Ik : *jp + wm2 * Ik;
+            }
+        }
+#pragma unroll
+        for (int a = MP; a < P; ++a) val[a] = 0;
         const R t = reduce_scatter<P>(val, lane);
         if (writer && widx < M) {
             R *sl = slot + widx * N + k;
             if (first) *sl = t;
             else *sl += t;
+        }
+        if constexpr (PRD) {
+            if (writer && widx >= M && widx < MP) {
+                R *sl = plain + (widx - M) * N + k;
+                if (first) *sl = t;
+                else *sl += t;
+            }
         }
     };
 
@@ -344,15 +429,15 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 R B2 = 0;
                 if (dir == 1) {
                     DepthC<R, K> d2;
-                    depth_consts<R, K>(s, lc, N - 2, N, d2);
+                    depth_consts<R, K, PRD>(s, lc, N - 2, N, d2, rho_lane, tl.prd_slot);
                     B2 = d2.B;
                     R phi[K], chj[K], U[K], eta;
-                    angle_vals<R, K>(s, lc, d2, muz, chip, eta, phi, chj, U);
+                    angle_vals<R, K, PRD>(s, lc, d2, muz, chip, eta, phi, chj, U);
                 }
                 DepthC<R, K> d;
-                depth_consts<R, K>(s, lc, k0, N, d);
+                depth_consts<R, K, PRD>(s, lc, k0, N, d, rho_lane, tl.prd_slot);
                 R chi, eta, phi[K], chj[K], U[K];
-                angle_vals<R, K>(s, lc, d, muz, chi, eta, phi, chj, U);
+                angle_vals<R, K, PRD>(s, lc, d, muz, chi, eta, phi, chj, U);
                 const R ichi = rcp<R>(chi);
                 if (dir == 0) {
                     I = 0;
@@ -362,14 +447,14 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 }
                 chip = chi;
                 Sp = eta * ichi;
-                emit(k0, d, phi, chj, U, ichi, (R)0, (R)1, (R)0, I, wm2, first);
+                emit(k0, d, phi, chj, U, ichi, (R)0, (R)1, (R)0, I, I, wm2, first);
             }
             for (int step = 1; step < N; ++step) {
                 const int k = dir == 0 ? step : N - 1 - step;
                 DepthC<R, K> d;
-                depth_consts<R, K>(s, lc, k, N, d);
+                depth_consts<R, K, PRD>(s, lc, k, N, d, rho_lane, tl.prd_slot);
                 R chi, eta, phi[K], chj[K], U[K];
-                angle_vals<R, K>(s, lc, d, muz, chi, eta, phi, chj, U);
+                angle_vals<R, K, PRD>(s, lc, d, muz, chi, eta, phi, chj, U);
                 const R ichi = rcp<R>(chi);
                 const R S = eta * ichi;
                 const R dzk = dir == 0 ? s.dz[k - 1] : s.dz[k];
@@ -382,19 +467,20 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 const R psi = wo * ichi;
                 chip = chi;
                 Sp = S;
-                emit(k, d, phi, chj, U, ichi, wo, omwo, psi, Ieff, wm2, first);
+                emit(k, d, phi, chj, U, ichi, wo, omwo, psi, Ieff, I, wm2, first);
             }
         }
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane)
+template <typename R, bool PRD>
+__device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane,
+                                           R *prd_rho, R *prd_J, R *prd_plain)
 {
     switch (A.tile[b].K) {
-    case 1: sweep_tile_k<R, 1>(A, s, p, b, lane); break;
-    case 2: sweep_tile_k<R, 2>(A, s, p, b, lane); break;
-    default: sweep_tile_k<R, 3>(A, s, p, b, lane); break;
+    case 1: sweep_tile_k<R, 1, PRD>(A, s, p, b, lane, prd_rho, prd_J, prd_plain); break;
+    case 2: sweep_tile_k<R, 2, PRD>(A, s, p, b, lane, prd_rho, prd_J, prd_plain); break;
+    default: sweep_tile_k<R, 3, PRD>(A, s, p, b, lane, prd_rho, prd_J, prd_plain); break;
     }
 }
 
@@ -487,7 +573,7 @@ __device__ int solve_depth(const DevAtom &A, const double *slotd, const float *s
     return 0;
 }
 
-template <typename R>
+template <typename R, bool PRD>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) mali_kernel(const __grid_constant__ DevAtom A, const KParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
@@ -499,6 +585,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
 
     for (int i = tid; i <= RH_VT_N; i += blockDim.x) s.vtab[i] = p.vtab[i];
     const int64_t nwork = p.nwork_d ? (int64_t)*p.nwork_d : p.nwork;
+    PrdScr<R> ps{};
+    if constexpr (PRD) ps = prd_carve<R>(p.prd_scr + (size_t)blockIdx.x * p.prd_stride, A, N);
     int64_t done = 0;
     for (;;) {
         __syncthreads();
@@ -541,11 +629,53 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
             }
         }
         for (int i = tid; i < N * 2 * A.ntr; i += blockDim.x) s.Cr[i] = p.Crate[(size_t)col * N * 2 * A.ntr + i];
+        if constexpr (PRD) {
+            // redistribution kernels of the column: K_ij = R(x_j, x_i) w_j / sum_j (.),
+            // x in Doppler units of the depth (static frame), and the J-bar weights
+            // f_j = H(a, x_j) w_j / sum_j (.)
+            for (int q = 0; q < A.nprd; ++q) {
+                const DevTrans &tr = A.tr[A.prd_t[q]];
+                const int off = A.prd_off[q], np = A.prd_off[q + 1] - off;
+                R *Kq = ps.K + (size_t)A.prd_koff[q] * N;
+                for (int e = tid; e < np * np * N; e += blockDim.x) {
+                    const int k = e / (np * np), r = e % (np * np), i = r / np, j = r % np;
+                    const double T = p.T[cN + k], sk = N > 1 ? (double)k / (N - 1) : 0.0;
+                    const double dnuD = tr.nu0 / kC * sqrt(2.0 * kK * T / A.mass);
+                    const double a = exp((1.0 - sk) * tr.ln_atop + sk * tr.ln_abot);
+                    const double xi = (p.prd_nu[off + i] - tr.nu0) / dnuD, xj = (p.prd_nu[off + j] - tr.nu0) / dnuD;
+                    Kq[e] = r2a_dev<R>((R)a, (R)xj, (R)xi) * (R)p.prd_w[off + j];
+                }
+            }
+            __syncthreads();
+            for (int q = 0; q < A.nprd; ++q) {
+                const DevTrans &tr = A.tr[A.prd_t[q]];
+                const int off = A.prd_off[q], np = A.prd_off[q + 1] - off;
+                R *Kq = ps.K + (size_t)A.prd_koff[q] * N;
+                for (int e = tid; e < np * N; e += blockDim.x) {
+                    R *row = Kq + (size_t)e * np;          // e = k np + i
+                    double sr = 0.0;
+                    for (int j = 0; j < np; ++j) sr += (double)row[j];
+                    for (int j = 0; j < np; ++j) row[j] = (R)((double)row[j] / sr);
+                }
+                for (int k = tid; k < N; k += blockDim.x) {
+                    const double T = p.T[cN + k], sk = N > 1 ? (double)k / (N - 1) : 0.0;
+                    const double dnuD = tr.nu0 / kC * sqrt(2.0 * kK * T / A.mass);
+                    const double a = exp((1.0 - sk) * tr.ln_atop + sk * tr.ln_abot);
+                    double fs = 0.0;
+                    for (int j = 0; j < np; ++j) fs += voigt_f64(a, (p.prd_nu[off + j] - tr.nu0) / dnuD) * p.prd_w[off + j];
+                    for (int j = 0; j < np; ++j)
+                        ps.f[(size_t)(off + j) * N + k] =
+                            (R)(voigt_f64(a, (p.prd_nu[off + j] - tr.nu0) / dnuD) * p.prd_w[off + j] / fs);
+                }
+            }
+        }
         int start = p.start, ng_order = p.ng_order, maxiter = p.maxiter, rung = 0;
         double crsw = p.crsw;
         int it = 0, status = RH_COL_MAXITER;
         double dmax = 1e300;
       restart:
+        if constexpr (PRD)
+            for (int i = tid; i < A.npp * N; i += blockDim.x) ps.rho[i] = 1;   // PRD starts as CRD
         for (int i = tid; i < LN; i += blockDim.x) {
             double v = start == 0 ? p.nstar[(size_t)col * LN + i] : p.pops[(size_t)col * LN + i];
             s.n[i] = v;
@@ -565,7 +695,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 if (lane == 0) q = atomicAdd(&s.ibuf[1], 1);
                 q = __shfl_sync(0xffffffffu, q, 0);
                 if (q >= A.ntile) break;
-                sweep_tile<R>(A, s, p, A.order[q], lane);
+                sweep_tile<R, PRD>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.plain);
             }
             __syncthreads();
             // ---- rate equations, one thread per depth
@@ -655,6 +785,55 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 status = RH_COL_CONVERGED;
                 break;
             }
+            if constexpr (PRD) {
+                // rho for the next iteration (Uitenbroek 2001, Eq. 14, angle-averaged,
+                // gamma = 1): rho = 1 + F (sum_j K_ij J_j / Jbar - 1), F = n_l R_lu /
+                // (supply of the upper level) with the plain rates of this formal
+                // solution and the collisions, n the next iteration's populations;
+                // PRD switching (Eq. 1) and under-relaxation by 1/2
+                const double eps =
+                    p.prd_eps0 > 0.0 ? fmin(1.0, p.prd_eps0 * (double)(it + 1) * (double)(it + 1)) : 1.0;
+                for (int e = tid; e < A.nprd * N; e += blockDim.x) {
+                    const int q = e / N, k = e % N, tq = A.prd_t[q];
+                    const int u = A.tr[tq].u, l = A.tr[tq].l;
+                    double in = 0.0, up_line = 0.0;
+                    for (int b = 0; b < A.ntile; ++b) {
+                        const DevTile &tb = A.tile[b];
+                        for (int j = 0; j < tb.K; ++j) {
+                            const DevTrans &t2 = A.tr[tb.t[j]];
+                            const double pu = (double)ps.plain[(size_t)(tb.pacc_off + 2 * j) * N + k];
+                            const double pd = (double)ps.plain[(size_t)(tb.pacc_off + 2 * j + 1) * N + k];
+                            if (t2.u == u) in += s.n[t2.l * N + k] * pu;
+                            if (t2.l == u) in += s.n[t2.u * N + k] * pd;
+                            if (tb.t[j] == tq) up_line += pu;
+                        }
+                    }
+                    const double *Ck = s.Cr + (size_t)k * 2 * A.ntr;
+                    for (int t = 0; t < A.ntr; ++t) {
+                        if (A.tr[t].u == u) in += s.n[A.tr[t].l * N + k] * Ck[2 * t] * fcr;
+                        if (A.tr[t].l == u) in += s.n[A.tr[t].u * N + k] * Ck[2 * t + 1] * fcr;
+                    }
+                    ps.F[e] = s.n[l * N + k] * up_line / in;
+                    const int off = A.prd_off[q], np = A.prd_off[q + 1] - off;
+                    double jb = 0.0;
+                    for (int j = 0; j < np; ++j)
+                        jb += (double)ps.f[(size_t)(off + j) * N + k] * (double)ps.J[(size_t)(off + j) * N + k];
+                    ps.Jbar[e] = jb;
+                }
+                __syncthreads();
+                for (int e = tid; e < A.npp * N; e += blockDim.x) {
+                    const int pp = e / N, k = e % N;
+                    int q = 0;
+                    while (pp >= A.prd_off[q + 1]) ++q;
+                    const int off = A.prd_off[q], np = A.prd_off[q + 1] - off, i = pp - off;
+                    const R *Krow = ps.K + (size_t)A.prd_koff[q] * N + ((size_t)k * np + i) * np;
+                    double sr = 0.0;
+                    for (int j = 0; j < np; ++j) sr += (double)Krow[j] * (double)ps.J[(size_t)(off + j) * N + k];
+                    const double r = 1.0 + ps.F[q * N + k] * (sr / ps.Jbar[q * N + k] - 1.0);
+                    ps.rho[e] = (R)(0.5 * (double)ps.rho[e] + 0.5 * (eps * r + (1.0 - eps)));
+                }
+                __syncthreads();
+            }
         }
         if (it > maxiter) it = maxiter;
         if (tid == 0 && p.rung_its) atomicAdd(&p.rung_its[rung], (unsigned long long)it);
@@ -682,16 +861,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
 
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep) { return sizeof(double) * 4 * A.nlev * ndep; }
 
+size_t mali_prd_bytes_per_block(const DevAtom &A, int ndep, int precision)
+{
+    if (!A.nprd) return 0;
+    return precision == 1 ? prd_bytes<float>(A, ndep) : prd_bytes<double>(A, ndep);
+}
+
 int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_warps)
 {
     size_t sm;
     const void *fn;
     if (precision == 1) {
         sm = smem_bytes<float>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc);
-        fn = (const void *)mali_kernel<float>;
+        fn = A.nprd ? (const void *)mali_kernel<float, true> : (const void *)mali_kernel<float, false>;
     } else {
         sm = smem_bytes<double>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc);
-        fn = (const void *)mali_kernel<double>;
+        fn = A.nprd ? (const void *)mali_kernel<double, true> : (const void *)mali_kernel<double, false>;
     }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
     int per_sm = 0;
@@ -701,10 +886,10 @@ int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_wa
 
 template <typename R>
 static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps, int ctas_per_sm, int nsm, size_t cap,
-                            cudaStream_t st, float *ms, char *err, size_t errn, int *grid_out)
+                            size_t prd_cap, cudaStream_t st, float *ms, char *err, size_t errn, int *grid_out)
 {
     size_t sm = smem_bytes<R>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
-    auto kern = mali_kernel<R>;
+    auto kern = A.nprd ? mali_kernel<R, true> : mali_kernel<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int threads = block_warps * 32;
@@ -720,6 +905,7 @@ static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps,
     if (!p.nwork_d && grid > p.nwork) grid = p.nwork;
     size_t per_block = mali_nghist_bytes_per_block(A, p.N);
     if ((size_t)grid * per_block > cap) grid = (int64_t)(cap / per_block);
+    if (A.nprd && (size_t)grid * p.prd_stride > prd_cap) grid = (int64_t)(prd_cap / p.prd_stride);
     if (grid < 1) {
         snprintf(err, errn, "no scratch for the Ng history");
         return cudaErrorMemoryAllocation;
@@ -784,14 +970,21 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
     }
     p.rung_cols = o.rung_cols;
     p.rung_its = o.rung_its;
+    p.prd_eps0 = o.prd_eps0;
+    p.lane_prd = o.lane_prd;
+    p.prd_nu = o.prd_nu;
+    p.prd_w = o.prd_w;
+    p.prd_scr = reinterpret_cast<char *>(o.prd_scr);
+    p.prd_stride = A.nprd ? (o.precision == 1 ? prd_bytes<float>(A, c.ndep) : prd_bytes<double>(A, c.ndep)) : 0;
     int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
     if (o.persistent) {
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
     }
     if (o.precision == 1)
-        return launch_t<float>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
-    return launch_t<double>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, st, ms_out, err, errn, grid_out);
+        return launch_t<float>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, o.prd_cap, st, ms_out, err, errn,
+                               grid_out);
+    return launch_t<double>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, o.prd_cap, st, ms_out, err, errn, grid_out);
 }
 
 }  // namespace rh
@@ -847,16 +1040,22 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     }
     p.rung_cols = o.rung_cols;
     p.rung_its = o.rung_its;
+    p.prd_eps0 = o.prd_eps0;
+    p.lane_prd = o.lane_prd;
+    p.prd_nu = o.prd_nu;
+    p.prd_w = o.prd_w;
+    p.prd_scr = reinterpret_cast<char *>(o.prd_scr);
+    p.prd_stride = A.nprd ? (o.precision == 1 ? prd_bytes<float>(A, c.ndep) : prd_bytes<double>(A, c.ndep)) : 0;
     const int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
     const int threads = bw * 32;
     size_t sm;
     const void *fn;
     if (o.precision == 1) {
         sm = smem_bytes<float>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
-        fn = (const void *)mali_kernel<float>;
+        fn = A.nprd ? (const void *)mali_kernel<float, true> : (const void *)mali_kernel<float, false>;
     } else {
         sm = smem_bytes<double>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
-        fn = (const void *)mali_kernel<double>;
+        fn = A.nprd ? (const void *)mali_kernel<double, true> : (const void *)mali_kernel<double, false>;
     }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -872,6 +1071,7 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     if (!p.nwork_d && grid > p.nwork) grid = p.nwork;
     const size_t per_block = mali_nghist_bytes_per_block(A, p.N);
     if ((size_t)grid * per_block > nghist_cap) grid = (int64_t)(nghist_cap / per_block);
+    if (A.nprd && (size_t)grid * p.prd_stride > o.prd_cap) grid = (int64_t)(o.prd_cap / p.prd_stride);
     if (grid < 1) {
         snprintf(err, errn, "Ng history of one column (%zu B) exceeds the scratch capacity (%zu B)", per_block,
                  nghist_cap);
