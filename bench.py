@@ -340,6 +340,28 @@ def run_gpu(args):
                   "ms": st_ms, "line": "H alpha (n=2-3), g_eff 1.5", "precision": "fp32 profiles and DELO solver",
                   "max_abs_V_over_I": vmax}
 
+    # angle-averaged PRD in Lyman alpha and beta (LTE start, FP32), on the
+    # first PRD_COLUMNS columns of the cube: a separate context and atom
+    prd = None
+    if args.prd_columns > 0:
+        pctx = rh.Context(local, stream=stream.cuda_stream)
+        patom = rh_synth.hydrogen_like_atom(prd_lines=((1, 2), (1, 3)))
+        pctx.setup_atom(patom)
+        psub = rh_synth.subset(cube, slice(0, min(args.prd_columns, ncol)))
+        pctx.load_columns(psub)
+        pctx.solve(maxiter=MAXITER, tol=TOL, precision=1, prd_eps0=0.05)      # warm-up, tuning
+        pctx.load_columns(psub)
+        barrier()
+        t_p = time.perf_counter()
+        s_p = pctx.solve(maxiter=MAXITER, tol=TOL, precision=1, prd_eps0=0.05)
+        barrier()
+        dt_p = time.perf_counter() - t_p
+        npc = len(psub["T"])
+        prd = {"value": npc / dt_p, "unit": "columns/s", "columns": npc, "converged": s_p["n_converged"],
+               "iterations_per_column": s_p["iterations_total"] / npc,
+               "lines": "Lyman alpha and beta, 64 wavelengths each, R_II-A, PRD switching eps0 = 0.05",
+               "precision": "fp32 formal solution/rates/redistribution, fp64 rate equations/Ng"}
+
     # plain FP64 MALI from LTE on a random sample of the cube (FP64 arithmetic is
     # slow on this part: one column per SM keeps the run under a minute)
     fp64 = None
@@ -389,6 +411,7 @@ def run_gpu(args):
         "lte_start_fp64": fp64,
         "other_starts": other,
         "stokes": stokes,
+        "prd": prd,
         "surrogate": train_info,
         "launch": {"block_warps": s["block_warps"], "ctas_per_sm": s["ctas_per_sm"],
                    "cuda_graph_replayed": s["graph_replayed"], "kernels_per_step": s["launches"],
@@ -429,6 +452,8 @@ def main():
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profiler captures")
     ap.add_argument("--no-stokes", dest="stokes", action="store_false",
                     help="skip the Zeeman Stokes spectrum timing")
+    ap.add_argument("--prd-columns", type=int, default=8192,
+                    help="columns of the partial-redistribution timing (0: skip)")
     ap.add_argument("--fp64-columns", type=int, default=152,
                     help="columns of the plain FP64 LTE-start comparison (0: skip)")
     ap.add_argument("--ncu-columns", type=int, default=608)
