@@ -118,6 +118,30 @@ def _dist():
     return ws, rank, local
 
 
+# ---- multi-GPU: independent replicas (weak scaling).  Columns are independent
+# (Sect. 2.2, 3.1): each rank solves its own cube, no collective touches the
+# data path; only the timings are combined.
+def rank_seeds(rank):
+    """Seeds of the inputs of one rank: its evaluated cube, its training cube
+    and its magnetic field, disjoint across ranks."""
+    return {"cube": 1234 + rank, "train": TRAIN_SEED + 7919 * rank, "field": 2024 + rank}
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The slowest rank's time (x on every rank), via all_reduce(MAX)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, steps, seconds):
+    """Units all ranks processed per second of the slowest rank."""
+    return ws * units_per_rank * steps / seconds
+
+
 def cpu_baseline(cube, seconds_target=15.0):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample."""
     import oracle
@@ -208,7 +232,8 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cube = rh_synth.chromosphere_cube(NX, NY, NDEP, seed=1234 + rank)
+    seeds = rank_seeds(rank)
+    cube = rh_synth.chromosphere_cube(NX, NY, NDEP, seed=seeds["cube"])
     ncol = NX * NY
     stream = torch.cuda.current_stream()
     ctx = rh.Context(local, stream=stream.cuda_stream)
@@ -216,7 +241,7 @@ def run_gpu(args):
     ctx.setup_atom(atom)
     # learned initial guess: converge a disjoint cube from LTE, train on it (untimed)
     t0 = time.perf_counter()
-    ctx.load_columns(rh_synth.chromosphere_cube(NX, NY, NDEP, seed=TRAIN_SEED + 7919 * rank))
+    ctx.load_columns(rh_synth.chromosphere_cube(NX, NY, NDEP, seed=seeds["train"]))
     tr_solve = ctx.solve(maxiter=MAXITER, tol=TOL, precision=1)
     ctx.surrogate_init(hidden=512, nhidden=3, seed=0)
     tr = ctx.surrogate_train(epochs=TRAIN_EPOCHS, batch=512, lr=2e-3, seed=1)
@@ -280,12 +305,9 @@ def run_gpu(args):
         other[name] = {"value": ncol / dt_o, "unit": "columns/s",
                        "iterations_per_column": s_o["iterations_total"] / ncol,
                        "converged": s_o["n_converged"]}
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     clocks = clk.summary()
-    value = ws * ncol * args.steps / (ms / 1e3)
+    value = whole_job_rate(ncol, ws, args.steps, ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers
     pin = {k: torch.from_numpy(v).pin_memory() for k, v in cube.items()}
@@ -303,11 +325,8 @@ def run_gpu(args):
         ctx.populations(out=out)
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * ncol * args.steps / e2e_s, "unit": "columns/s",
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e = {"value": whole_job_rate(ncol, ws, args.steps, e2e_s), "unit": "columns/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h + ncol * (4 + 1 + 8)}
 
     # Zeeman Stokes spectra of H alpha after convergence (FP32, mu = 1, 400
@@ -317,7 +336,7 @@ def run_gpu(args):
     if args.stokes:
         ctx.load_columns(dev, on_device=True)
         ctx.solve(**opts)
-        rng_f = np.random.default_rng(2024 + rank)
+        rng_f = np.random.default_rng(seeds["field"])
         Bc = rng_f.uniform(0.0, 0.2, ncol)
         thc = np.arccos(rng_f.uniform(-1.0, 1.0, ncol))
         chc = rng_f.uniform(0.0, 2 * np.pi, ncol)
