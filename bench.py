@@ -43,7 +43,11 @@ METRIC = "converged columns/s to max|dn/n|<1e-3"
 # (2 x FFMA + FADD + FMUL, predicated-on threads) counted by ncu on 608 cube
 # columns x 3 iterations, divided by their points; re-counted whenever the
 # kernel changes
-FLOP_PER_PT = 287
+FLOP_PER_PT = 289
+# DRAM bytes (read + write) per column of the column kernel, from the same ncu
+# capture (18.54 MB for 608 columns): the column's inputs and results, once
+# per column (the iterations stay on chip), so a launch moves this per column
+DRAM_BYTES_PER_COLUMN = 18.5385e6 / 608
 
 
 def _peaks():
@@ -438,7 +442,10 @@ def run_gpu(args):
         "converged_fraction": conv / (ncol * args.steps),
         "rerun_columns_per_step": rescued / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
+                     "frac": achieved / peak_tflops,
+                     "traffic": DRAM_BYTES_PER_COLUMN * (ncol + rescued / args.steps),
+                     "traffic_note": "bytes per launch: ncu DRAM bytes per column on the 608-column case "
+                                     "x columns of one launch (each column read and written once)",
                      "kernel": "mali_kernel<float,5>",
                      "peak_note": "FP32 FMA peak = %d SMs x 128 lanes x 2 x %.0f MHz (median SM clock "
                                   "sampled during the timed region)" % (nsm, sm_mhz)},
