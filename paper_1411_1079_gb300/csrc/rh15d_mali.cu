@@ -25,6 +25,9 @@
 
 #include "rh15d_internal.h"
 
+#ifndef RH_ANGLE_PAIRS
+#define RH_ANGLE_PAIRS 1      // two angles per sweep pass (CRD); 0: one
+#endif
 #ifndef RH_FP32_MINBLOCKS
 #define RH_FP32_MINBLOCKS 2   // FP32 sweep: two resident 256-thread blocks per SM (<= 128 registers)
 #endif
@@ -368,10 +371,9 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
         plain = prd_plain + (size_t)tl.pacc_off * N;
     }
 
-    // contributions of one depth point to the tile's accumulators
-    auto emit = [&](int k, const DepthC<R, K> &d, const R (&phi)[K], const R (&chj)[K], const R (&U)[K], R ichi,
-                    R wo, R omwo, R psi, R Ieff, R Ik, R wm2, bool first) {
-        R val[P];
+    // rate contributions of one ray at one depth point (add: accumulate into val)
+    auto contrib = [&](const DepthC<R, K> &d, const R (&phi)[K], const R (&chj)[K], const R (&U)[K], R ichi, R wo,
+                       R omwo, R psi, R Ieff, R wm2, R (&val)[P], bool add) {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             R other = d.chibg;
@@ -380,13 +382,35 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 if (j2 != j) other += chj[j2];
             const R f = omwo + wo * other * ichi;          // 1 - Psi* chi_j
             const R cw = lc.c[j] * wm2 * phi[j];
-            val[j] = cw * Ieff;
-            val[K + j] = cw * d.Rs[j] * (lc.E[j] * f + Ieff);
+            const R v0 = cw * Ieff, v1 = cw * d.Rs[j] * (lc.E[j] * f + Ieff);
+            val[j] = add ? val[j] + v0 : v0;
+            val[K + j] = add ? val[K + j] + v1 : v1;
             const R cx = cw * d.Xs[j] * psi;
 #pragma unroll
             for (int j2 = 0; j2 < K; ++j2)
-                if (j2 != j) val[2 * K + j * (K - 1) + (j2 < j ? j2 : j2 - 1)] = cx * U[j2];
+                if (j2 != j) {
+                    const int a = 2 * K + j * (K - 1) + (j2 < j ? j2 : j2 - 1);
+                    val[a] = add ? val[a] + cx * U[j2] : cx * U[j2];
+                }
         }
+    };
+    // reduce the warp's contributions and add them to the tile's accumulators
+    auto flush = [&](int k, R (&val)[P], bool first) {
+#pragma unroll
+        for (int a = MP; a < P; ++a) val[a] = 0;
+        const R t = reduce_scatter<P>(val, lane);
+        if (writer && widx < M) {
+            R *sl = slot + widx * N + k;
+            if (first) *sl = t;
+            else *sl += t;
+        }
+    };
+
+    // contributions of one depth point to the tile's accumulators
+    auto emit = [&](int k, const DepthC<R, K> &d, const R (&phi)[K], const R (&chj)[K], const R (&U)[K], R ichi,
+                    R wo, R omwo, R psi, R Ieff, R Ik, R wm2, bool first) {
+        R val[P];
+        contrib(d, phi, chj, U, ichi, wo, omwo, psi, Ieff, wm2, val, false);
         if constexpr (PRD) {
 #pragma unroll
             for (int j = 0; j < K; ++j) {
@@ -416,6 +440,94 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
         }
     };
 
+#if RH_ANGLE_PAIRS
+    if constexpr (!PRD) {
+        // two angles per pass: the depth terms once per depth, the angles'
+        // contributions summed in registers, one warp reduction per depth
+        for (int m0 = 0; m0 < nmu; m0 += 2) {
+            const bool two = m0 + 1 < nmu;
+            const int m1 = two ? m0 + 1 : m0;
+            const R mu0 = mu_of<R>(A, m0), imu0 = imu_of<R>(A, m0), wa = wm2_of<R>(A, m0);
+            const R mu1 = mu_of<R>(A, m1), imu1 = imu_of<R>(A, m1), wb = wm2_of<R>(A, m1);
+            for (int dir = 0; dir < 2; ++dir) {
+                const R z0 = dir == 0 ? -mu0 : mu0, z1 = dir == 0 ? -mu1 : mu1;
+                const bool first = m0 == 0 && dir == 0;
+                R Ia, chipa = 0, Spa, Ib = 0, chipb = 0, Spb = 0;
+                {
+                    const int k0 = dir == 0 ? 0 : N - 1;
+                    R B2 = 0;
+                    if (dir == 1) {
+                        DepthC<R, K> d2;
+                        depth_consts<R, K>(s, lc, N - 2, N, d2);
+                        B2 = d2.B;
+                        R phi[K], chj[K], U[K], eta;
+                        angle_vals<R, K>(s, lc, d2, z0, chipa, eta, phi, chj, U);
+                        if (two) angle_vals<R, K>(s, lc, d2, z1, chipb, eta, phi, chj, U);
+                    }
+                    DepthC<R, K> d;
+                    depth_consts<R, K>(s, lc, k0, N, d);
+                    R val[P];
+                    {
+                        R chi, eta, phi[K], chj[K], U[K];
+                        angle_vals<R, K>(s, lc, d, z0, chi, eta, phi, chj, U);
+                        const R ichi = rcp<R>(chi);
+                        Ia = dir == 0 ? (R)0 : d.B + mu0 * (d.B - B2) * rcp<R>((R)0.5 * (chi + chipa) * s.dz[N - 2]);
+                        chipa = chi;
+                        Spa = eta * ichi;
+                        contrib(d, phi, chj, U, ichi, (R)0, (R)1, (R)0, Ia, wa, val, false);
+                    }
+                    if (two) {
+                        R chi, eta, phi[K], chj[K], U[K];
+                        angle_vals<R, K>(s, lc, d, z1, chi, eta, phi, chj, U);
+                        const R ichi = rcp<R>(chi);
+                        Ib = dir == 0 ? (R)0 : d.B + mu1 * (d.B - B2) * rcp<R>((R)0.5 * (chi + chipb) * s.dz[N - 2]);
+                        chipb = chi;
+                        Spb = eta * ichi;
+                        contrib(d, phi, chj, U, ichi, (R)0, (R)1, (R)0, Ib, wb, val, true);
+                    }
+                    flush(k0, val, first);
+                }
+                for (int step = 1; step < N; ++step) {
+                    const int k = dir == 0 ? step : N - 1 - step;
+                    DepthC<R, K> d;
+                    depth_consts<R, K>(s, lc, k, N, d);
+                    const R dzk = dir == 0 ? s.dz[k - 1] : s.dz[k];
+                    R val[P];
+                    {
+                        R chi, eta, phi[K], chj[K], U[K];
+                        angle_vals<R, K>(s, lc, d, z0, chi, eta, phi, chj, U);
+                        const R ichi = rcp<R>(chi);
+                        const R S = eta * ichi;
+                        R ome, wu, wo, omwo;
+                        sc_weights((R)0.5 * (chi + chipa) * dzk * imu0, ome, wu, wo, omwo);
+                        const R base = Ia * ome + wu * Spa;
+                        Ia = base + wo * S;
+                        chipa = chi;
+                        Spa = S;
+                        contrib(d, phi, chj, U, ichi, wo, omwo, wo * ichi, base + wo * (d.etabg * ichi), wa, val,
+                                false);
+                    }
+                    if (two) {
+                        R chi, eta, phi[K], chj[K], U[K];
+                        angle_vals<R, K>(s, lc, d, z1, chi, eta, phi, chj, U);
+                        const R ichi = rcp<R>(chi);
+                        const R S = eta * ichi;
+                        R ome, wu, wo, omwo;
+                        sc_weights((R)0.5 * (chi + chipb) * dzk * imu1, ome, wu, wo, omwo);
+                        const R base = Ib * ome + wu * Spb;
+                        Ib = base + wo * S;
+                        chipb = chi;
+                        Spb = S;
+                        contrib(d, phi, chj, U, ichi, wo, omwo, wo * ichi, base + wo * (d.etabg * ichi), wb, val,
+                                true);
+                    }
+                    flush(k, val, first);
+                }
+            }
+        }
+        return;
+    }
+#endif
     for (int m = 0; m < nmu; ++m) {
         const R mu = mu_of<R>(A, m), imu = imu_of<R>(A, m), wm2 = wm2_of<R>(A, m);
         for (int dir = 0; dir < 2; ++dir) {
