@@ -43,11 +43,11 @@ METRIC = "converged columns/s to max|dn/n|<1e-3"
 # (2 x FFMA + FADD + FMUL, predicated-on threads) counted by ncu on 608 cube
 # columns x 3 iterations, divided by their points; re-counted whenever the
 # kernel changes
-FLOP_PER_PT = 289
+FLOP_PER_PT = 271
 # DRAM bytes (read + write) per column of the column kernel, from the same ncu
-# capture (18.54 MB for 608 columns): the column's inputs and results, once
+# capture (18.65 MB for 608 columns): the column's inputs and results, once
 # per column (the iterations stay on chip), so a launch moves this per column
-DRAM_BYTES_PER_COLUMN = 18.5385e6 / 608
+DRAM_BYTES_PER_COLUMN = 18.6455e6 / 608
 
 
 def _peaks():
