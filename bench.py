@@ -128,7 +128,7 @@ def _dist():
 def rank_seeds(rank):
     """Seeds of the inputs of one rank: its evaluated cube, its training cube
     and its magnetic field, disjoint across ranks."""
-    return {"cube": 1234 + rank, "train": TRAIN_SEED + 7919 * rank, "field": 2024 + rank}
+    return {"cube": 1234 + rank, "train": TRAIN_SEED + 7919 * rank, "field": 2024 + rank, "big": 5678 + rank}
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -333,6 +333,30 @@ def run_gpu(args):
     e2e = {"value": whole_job_rate(ncol, ws, args.steps, e2e_s), "unit": "columns/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h + ncol * (4 + 1 + 8)}
 
+    # the 512 x 512 cube (82 heights, seed disjoint from the training and
+    # evaluated cubes) from the learned guess, one step: the full-size target
+    big = None
+    if args.cube512:
+        cube512 = rh_synth.chromosphere_cube(512, 512, NDEP, seed=seeds["big"])
+        dev512 = {k: torch.from_numpy(v).to("cuda") for k, v in cube512.items()}
+        del cube512
+        ctx.load_columns(dev512, on_device=True)
+        ctx.solve(**dict(opts, maxiter=2))                 # graph capture for this size
+        ctx.load_columns(dev512, on_device=True)
+        barrier()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        s_b = ctx.solve(**opts)
+        b1.record(stream)
+        barrier()
+        big_ms = max_over_ranks(b0.elapsed_time(b1), dist, "cuda")
+        nb = 512 * 512
+        big = {"value": whole_job_rate(nb, ws, 1, big_ms / 1e3), "unit": "columns/s", "columns": nb,
+               "converged": s_b["n_converged"], "iterations_per_column": s_b["iterations_total"] / nb,
+               "ms": big_ms, "workload": "512x512 synthetic chromosphere cube, 82 heights, learned start, one step"}
+        del dev512
+
     # Zeeman Stokes spectra of H alpha after convergence (FP32, mu = 1, 400
     # wavelengths over +-2 A; per column |B| ~ U(0, 2 kG), cos(theta) ~ U(-1, 1),
     # chi ~ U(0, 2 pi), constant with height)
@@ -433,6 +457,7 @@ def run_gpu(args):
                       "precision": "fp32 formal solution/rates, fp64 rate equations/Ng"},
         "lte_start_fp64": fp64,
         "other_starts": other,
+        "cube_512": big,
         "stokes": stokes,
         "prd": prd,
         "surrogate": train_info,
@@ -478,7 +503,9 @@ def main():
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profiler captures")
     ap.add_argument("--no-stokes", dest="stokes", action="store_false",
                     help="skip the Zeeman Stokes spectrum timing")
-    ap.add_argument("--prd-columns", type=int, default=8192,
+    ap.add_argument("--no-cube512", dest="cube512", action="store_false",
+                    help="skip the one-step 512x512 cube measurement")
+    ap.add_argument("--prd-columns", type=int, default=4096,
                     help="columns of the partial-redistribution timing (0: skip)")
     ap.add_argument("--fp64-columns", type=int, default=152,
                     help="columns of the plain FP64 LTE-start comparison (0: skip)")
