@@ -360,10 +360,12 @@ template <typename R> struct R2Rule;
 template <> struct R2Rule<double> {
     static constexpr int NG = 8;
     static constexpr double ZP = 1.0, UP = 0.5;
+    static constexpr double CUT = 6.0;    // R <= erfc(u0) < 2e-17 beyond
 };
 template <> struct R2Rule<float> {
     static constexpr int NG = 6;
     static constexpr double ZP = 2.0, UP = 1.0;
+    static constexpr double CUT = 5.0;    // R <= erfc(u0) < 2e-12 beyond
 };
 __host__ __device__ inline void gl_rule(int n, double *x, double *w)
 {
@@ -388,7 +390,7 @@ __host__ __device__ inline void gl_rule(int n, double *x, double *w)
 }
 
 template <typename R>
-__device__ inline R r2_lorentz(R a, R c, R lo, R hi, const double *gx, const double *gw)
+__device__ inline R r2_lorentz(R a, R c, R lo, R hi, const R *gx, const R *gw)
 {
     constexpr int NG = R2Rule<R>::NG;
     const R ZP = (R)R2Rule<R>::ZP, UP = (R)R2Rule<R>::UP;
@@ -398,25 +400,25 @@ __device__ inline R r2_lorentz(R a, R c, R lo, R hi, const double *gx, const dou
         const R p = side == 0 ? lo : (lo > c + 1 ? lo : c + 1);
         const R q = side == 0 ? (hi < c - 1 ? hi : c - 1) : hi;
         if (!(q > p)) continue;
-        const int n = (int)ceil((double)((q - p) / UP));
+        const int n = (int)ceil((q - p) / UP);
         const R h = (q - p) / (R)n;
         for (int k = 0; k < n; ++k)
             for (int g = 0; g < NG; ++g) {
-                const R u = p + h * (R)(k + 0.5 * (gx[g] + 1.0));
+                const R u = p + h * ((R)k + gx[g]);
                 const R d = u - c;
-                s += (R)(0.5 * gw[g]) * h * erfc(u) * a / (a * a + d * d);
+                s += gw[g] * h * erfc(u) * a / (a * a + d * d);
             }
     }
     // near part in z, u = c + a sinh z
     const R nlo = lo > c - 1 ? lo : c - 1, nhi = hi < c + 1 ? hi : c + 1;
     if (nhi > nlo) {
         const R z0 = asinh((nlo - c) / a), z1 = asinh((nhi - c) / a);
-        const int n = (int)ceil((double)((z1 - z0) / ZP));
+        const int n = (int)ceil((z1 - z0) / ZP);
         const R h = (z1 - z0) / (R)n;
         for (int k = 0; k < n; ++k)
             for (int g = 0; g < NG; ++g) {
-                const R z = z0 + h * (R)(k + 0.5 * (gx[g] + 1.0));
-                s += (R)(0.5 * gw[g]) * h * erfc(c + a * sinh(z)) / cosh(z);
+                const R z = z0 + h * ((R)k + gx[g]);
+                s += gw[g] * h * erfc(c + a * sinh(z)) / cosh(z);
             }
     }
     return s;
@@ -425,10 +427,17 @@ __device__ inline R r2_lorentz(R a, R c, R lo, R hi, const double *gx, const dou
 template <typename R>
 __device__ inline R r2a_dev(R a, R xp, R x)
 {
-    double gx[8], gw[8];
-    gl_rule(R2Rule<R>::NG, gx, gw);
     const R xs = xp < x ? xp : x, xb = xp < x ? x : xp;
     const R u0 = (R)0.5 * (xb - xs), U = u0 + (R)6.5;
+    if (u0 > (R)R2Rule<R>::CUT) return 0;      // R <= erfc(u0): negligible
+    // nodes on [0, 1] and half weights, in the working precision
+    double dx[8], dw[8];
+    gl_rule(R2Rule<R>::NG, dx, dw);
+    R gx[8], gw[8];
+    for (int g = 0; g < R2Rule<R>::NG; ++g) {
+        gx[g] = (R)(0.5 * (dx[g] + 1.0));
+        gw[g] = (R)(0.5 * dw[g]);
+    }
     return (r2_lorentz<R>(a, -xs, u0, U, gx, gw) + r2_lorentz<R>(a, xb, u0, U, gx, gw)) / (R)(2.0 * kPi);
 }
 

@@ -216,7 +216,7 @@ struct DepthC {
 
 template <typename R, int K, bool PRD = false>
 __device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K> &lc, int k, int N, DepthC<R, K> &d,
-                                             const R *rho_lane = nullptr, int prd_slot = -1)
+                                             R rho_k = (R)1, int prd_slot = -1)
 {
     R x = lc.nu * s.hkT[k];
     R ex = rexp<R>(-x);
@@ -233,7 +233,7 @@ __device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K>
             d.Rs[j] = lc.grat[j];
             if constexpr (PRD) {
                 // psi = rho phi in stimulated and spontaneous emission
-                d.rf[j] = (j == prd_slot && rho_lane) ? rho_lane[k] : (R)1;
+                d.rf[j] = j == prd_slot ? rho_k : (R)1;
                 d.Rs[j] *= d.rf[j];
             }
             d.chc[j] = 0;
@@ -418,10 +418,9 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 val[M + 2 * j] = cw * Ik;
                 val[M + 2 * j + 1] = cw * d.Rs[j] * (lc.E[j] + Ik);
             }
-            if (pp >= 0) {
-                R *jp = prd_J + (size_t)pp * N + k;
-                *jp = first ? wm2 * Ik : *jp + wm2 * Ik;
-            }
+            // fire-and-forget reductions (zeroed before the sweep): one lane per
+            // location, adding in program order, so the sum is deterministic
+            if (pp >= 0) atomicAdd(prd_J + (size_t)pp * N + k, wm2 * Ik);
         }
 #pragma unroll
         for (int a = MP; a < P; ++a) val[a] = 0;
@@ -432,11 +431,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
             else *sl += t;
         }
         if constexpr (PRD) {
-            if (writer && widx >= M && widx < MP) {
-                R *sl = plain + (widx - M) * N + k;
-                if (first) *sl = t;
-                else *sl += t;
-            }
+            if (writer && widx >= M && widx < MP) atomicAdd(plain + (widx - M) * N + k, t);
         }
     };
 
@@ -541,13 +536,13 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 R B2 = 0;
                 if (dir == 1) {
                     DepthC<R, K> d2;
-                    depth_consts<R, K, PRD>(s, lc, N - 2, N, d2, rho_lane, tl.prd_slot);
+                    depth_consts<R, K, PRD>(s, lc, N - 2, N, d2, rho_lane ? rho_lane[N - 2] : (R)1, tl.prd_slot);
                     B2 = d2.B;
                     R phi[K], chj[K], U[K], eta;
                     angle_vals<R, K, PRD>(s, lc, d2, muz, chip, eta, phi, chj, U);
                 }
                 DepthC<R, K> d;
-                depth_consts<R, K, PRD>(s, lc, k0, N, d, rho_lane, tl.prd_slot);
+                depth_consts<R, K, PRD>(s, lc, k0, N, d, rho_lane ? rho_lane[k0] : (R)1, tl.prd_slot);
                 R chi, eta, phi[K], chj[K], U[K];
                 angle_vals<R, K, PRD>(s, lc, d, muz, chi, eta, phi, chj, U);
                 const R ichi = rcp<R>(chi);
@@ -561,10 +556,14 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 Sp = eta * ichi;
                 emit(k0, d, phi, chj, U, ichi, (R)0, (R)1, (R)0, I, I, wm2, first);
             }
+            // rho of the lane's PRD point (global scratch) loaded one depth step ahead
+            R rho_nx = (PRD && rho_lane) ? rho_lane[dir == 0 ? 1 : N - 2] : (R)1;
             for (int step = 1; step < N; ++step) {
                 const int k = dir == 0 ? step : N - 1 - step;
+                const R rho_k = rho_nx;
+                if (PRD && rho_lane && step + 1 < N) rho_nx = rho_lane[dir == 0 ? step + 1 : N - 2 - step];
                 DepthC<R, K> d;
-                depth_consts<R, K, PRD>(s, lc, k, N, d, rho_lane, tl.prd_slot);
+                depth_consts<R, K, PRD>(s, lc, k, N, d, rho_k, tl.prd_slot);
                 R chi, eta, phi[K], chj[K], U[K];
                 angle_vals<R, K, PRD>(s, lc, d, muz, chi, eta, phi, chj, U);
                 const R ichi = rcp<R>(chi);
@@ -749,13 +748,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 const DevTrans &tr = A.tr[A.prd_t[q]];
                 const int off = A.prd_off[q], np = A.prd_off[q + 1] - off;
                 R *Kq = ps.K + (size_t)A.prd_koff[q] * N;
+                // R is symmetric: one evaluation per unordered pair (j >= i)
                 for (int e = tid; e < np * np * N; e += blockDim.x) {
                     const int k = e / (np * np), r = e % (np * np), i = r / np, j = r % np;
+                    if (j < i) continue;
                     const double T = p.T[cN + k], sk = N > 1 ? (double)k / (N - 1) : 0.0;
                     const double dnuD = tr.nu0 / kC * sqrt(2.0 * kK * T / A.mass);
                     const double a = exp((1.0 - sk) * tr.ln_atop + sk * tr.ln_abot);
                     const double xi = (p.prd_nu[off + i] - tr.nu0) / dnuD, xj = (p.prd_nu[off + j] - tr.nu0) / dnuD;
-                    Kq[e] = r2a_dev<R>((R)a, (R)xj, (R)xi) * (R)p.prd_w[off + j];
+                    const R rv = r2a_dev<R>((R)a, (R)xj, (R)xi);
+                    Kq[e] = rv * (R)p.prd_w[off + j];
+                    Kq[(size_t)k * np * np + (size_t)j * np + i] = rv * (R)p.prd_w[off + i];
                 }
             }
             __syncthreads();
@@ -798,6 +801,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
         for (it = 1; it <= maxiter; ++it) {
             double fcr = crsw > 1.0 ? fmax(1.0, crsw * pow(10.0, -(double)(it - 1))) : 1.0;
             for (int i = tid; i < LN; i += blockDim.x) s.nr[i] = (R)(s.n[i] * p.inv_nref);
+            if constexpr (PRD) {
+                for (int i = tid; i < A.npp * N; i += blockDim.x) ps.J[i] = 0;
+                for (int i = tid; i < A.pacc * N; i += blockDim.x) ps.plain[i] = 0;
+            }
             if (tid == 0) s.ibuf[1] = 0;
             __syncthreads();
             // ---- formal solution and rate accumulation: warps take tiles from a
