@@ -16,35 +16,53 @@ def rh():
     return m
 
 
-def _features_targets(ctx, cols):
-    n, _, _, _ = ctx.populations()
-    ns, ne = ctx.lte()
+def _oracle_features_targets(orc, atom, cols):
+    """Populations after a few oracle iterations, and the reference features
+    and targets ln(n/n*) from the oracle's own LTE values."""
     from oracle import mlp
+    o = orc.Oracle()
+    o.setup_atom(atom)
+    o.load_columns(cols)
+    o.iterate(maxiter=25, tol=1e-3)
+    n = o.populations()[0]
+    ns, ne = o.lte()
     X = mlp.features(cols["T"], ne, cols["nH"], cols["vz"])
     Y = np.log(n / ns).reshape(n.shape[0], -1)
-    return X, Y
+    return n, X, Y
+
+
+def _seeded_state(rng, dims4, X):
+    """Network parameters drawn here (He-scaled weights, zero biases) and the
+    standardisation of X, in the library's layout."""
+    from oracle import mlp
+    parts = []
+    for di, do in mlp.layer_dims(*dims4):
+        parts.append(rng.standard_normal(do * di) * np.sqrt(2.0 / di))
+        parts.append(np.zeros(do))
+    parts.append(X.mean(axis=0))
+    parts.append(1.0 / np.maximum(X.std(axis=0), 1e-12 * (np.abs(X.mean(axis=0)) + 1)))
+    return np.concatenate(parts)
 
 
 @pytest.mark.parametrize("hidden,nhidden,ncols", [(64, 2, 96), (512, 3, 256)])
-def test_gpu_gradient_matches_fp64_reference(rh, hidden, nhidden, ncols):
+def test_gpu_gradient_matches_fp64_reference(rh, orc, hidden, nhidden, ncols):
+    # every input of the reference comes from this test or the oracle: the
+    # populations (targets), LTE values (features) and the seeded network
     from oracle import mlp
     atom = rh_synth.hydrogen_like_atom()
     cols = rh_synth.subset(rh_synth.chromosphere_cube(nx=32, ny=32, seed=11), slice(0, ncols))
+    n, X, Y = _oracle_features_targets(orc, atom, cols)
     ctx = rh.Context(0)
     ctx.setup_atom(atom)
     ctx.load_columns(cols)
-    ctx.iterate(maxiter=25, tol=1e-3, precision=1)        # non-trivial targets ln(n/n*)
-    X, Y = _features_targets(ctx, cols)
+    ctx.set_populations(n)
     ctx.surrogate_init(hidden=hidden, nhidden=nhidden, seed=7)
-    state = ctx.surrogate_state().astype(np.float64)
-    nin = X.shape[1]
-    nwb = state.size - 2 * nin
-    state[nwb:nwb + nin] = X.mean(axis=0)
-    state[nwb + nin:] = 1.0 / np.maximum(X.std(axis=0), 1e-12 * (np.abs(X.mean(axis=0)) + 1))
-    ctx.surrogate_set_state(state.astype(np.float32))
-    state32 = ctx.surrogate_state().astype(np.float64)      # the network as the GPU holds it
+    dims = (X.shape[1], hidden, nhidden, Y.shape[1])
+    state32 = _seeded_state(np.random.default_rng(7), dims, X).astype(np.float32)
+    ctx.surrogate_set_state(state32)
+    state32 = state32.astype(np.float64)
+    nwb = state32.size - 2 * X.shape[1]
     loss_g, grad_g = ctx.surrogate_loss_grad(np.arange(ncols))
-    dims = (nin, hidden, nhidden, Y.shape[1])
     loss_o, grad_o = mlp.loss_grad(state32, dims, X, Y)
     gg, go = grad_g[:nwb].astype(np.float64), grad_o[:nwb]
     cos = gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go))
