@@ -471,7 +471,7 @@ def run_gpu(args):
                      "traffic": DRAM_BYTES_PER_COLUMN * (ncol + rescued / args.steps),
                      "traffic_note": "bytes per launch: ncu DRAM bytes per column on the 608-column case "
                                      "x columns of one launch (each column read and written once)",
-                     "kernel": "mali_kernel<float,5>",
+                     "kernel": "mali_kernel<float, CRD> (column-resident MALI, FP32 sweep)",
                      "peak_note": "FP32 FMA peak = %d SMs x 128 lanes x 2 x %.0f MHz (median SM clock "
                                   "sampled during the timed region)" % (nsm, sm_mhz)},
         "e2e": e2e,
