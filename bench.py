@@ -41,13 +41,18 @@ METRIC = "converged columns/s to max|dn/n|<1e-3"
 # FP32 operations per formal-solver point (one depth x lambda x mu, both
 # sweep directions): thread-level FP32 operations of the column kernel
 # (2 x FFMA + FADD + FMUL, predicated-on threads) counted by ncu on 608 cube
-# columns x 3 iterations, divided by their points; re-counted whenever the
-# kernel changes
-FLOP_PER_PT = 271
-# DRAM bytes (read + write) per column of the column kernel, from the same ncu
-# capture (18.65 MB for 608 columns): the column's inputs and results, once
-# per column (the iterations stay on chip), so a launch moves this per column
-DRAM_BYTES_PER_COLUMN = 18.6455e6 / 608
+# columns x 12 iterations (about the iterations a column takes from the
+# learned guess), divided by their points; re-counted whenever the kernel
+# changes
+FLOP_PER_PT = 191.3
+# DRAM bytes (read + write) per column-iteration of the column kernel, from
+# the same ncu capture (12.77 GB for 608 x 12): the line-profile cache read
+# back every iteration (1.57 MB), its build once per column and the column's
+# inputs and results
+DRAM_BYTES_PER_COLUMN_ITERATION = (11.533787e9 + 1.232767e9) / (608 * 12)
+# warp instructions per column-iteration, same capture: the issue-slot view of
+# the same kernel (4 schedulers per SM, one warp instruction per cycle each)
+WARP_INST_PER_COLUMN_ITERATION = 24616860192 / (608 * 12)
 
 
 def _peaks():
@@ -468,10 +473,14 @@ def run_gpu(args):
         "rerun_columns_per_step": rescued / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
-                     "traffic": DRAM_BYTES_PER_COLUMN * (ncol + rescued / args.steps),
-                     "traffic_note": "bytes per launch: ncu DRAM bytes per column on the 608-column case "
-                                     "x columns of one launch (each column read and written once)",
+                     "traffic": DRAM_BYTES_PER_COLUMN_ITERATION * iters / args.steps,
+                     "traffic_note": "bytes per launch: ncu DRAM bytes per column-iteration on the "
+                                     "608-column x 12-iteration case x column-iterations of one launch",
                      "kernel": "mali_kernel<float, CRD> (column-resident MALI, FP32 sweep)",
+                     "issue_slots": {"achieved": WARP_INST_PER_COLUMN_ITERATION * iters / kern_s,
+                                     "peak": nsm * 4 * sm_mhz * 1e6, "unit": "warp instructions/s",
+                                     "frac": WARP_INST_PER_COLUMN_ITERATION * iters / kern_s
+                                             / (nsm * 4 * sm_mhz * 1e6)},
                      "peak_note": "FP32 FMA peak = %d SMs x 128 lanes x 2 x %.0f MHz (median SM clock "
                                   "sampled during the timed region)" % (nsm, sm_mhz)},
         "e2e": e2e,
@@ -486,7 +495,8 @@ def run_gpu(args):
 
 
 def run_ncu_case(args):
-    """Small fixed case for ncu captures: 608 columns of the cube, 3 iterations."""
+    """Small fixed case for ncu captures: 608 columns of the cube, a fixed
+    number of iterations (--ncu-iters)."""
     import __graft_entry__
     __graft_entry__.build()
     import paper_1411_1079_gb300 as rh
@@ -494,8 +504,9 @@ def run_ncu_case(args):
     ctx = rh.Context(0)
     ctx.setup_atom(rh_synth.hydrogen_like_atom())
     ctx.load_columns(rh_synth.subset(cube, slice(0, args.ncu_columns)))
-    s = ctx.iterate(maxiter=3, tol=0.0, precision=args.ncu_precision)
-    print(json.dumps({"ncu_case": True, "columns": args.ncu_columns, "seconds": s["seconds"]}))
+    s = ctx.iterate(maxiter=args.ncu_iters, tol=0.0, precision=args.ncu_precision)
+    print(json.dumps({"ncu_case": True, "columns": args.ncu_columns, "iterations": args.ncu_iters,
+                      "seconds": s["seconds"]}))
 
 
 def main():
@@ -511,6 +522,7 @@ def main():
                     help="columns of the plain FP64 LTE-start comparison (0: skip)")
     ap.add_argument("--ncu-columns", type=int, default=608)
     ap.add_argument("--ncu-precision", type=int, default=1)
+    ap.add_argument("--ncu-iters", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

@@ -96,6 +96,8 @@ struct rh_ctx {
     double *prd_nu_d = nullptr, *prd_w_d = nullptr;
     void *prd_scr = nullptr;
     size_t prd_cap = 0;
+    void *phic = nullptr;           // per-block profile cache of the column kernel
+    size_t phic_cap = 0;
     // start solutions: device copy of the continuum point lists
     int *sp_off_d = nullptr;
     double *sp_nu_d = nullptr, *sp_ce_d = nullptr;
@@ -423,6 +425,18 @@ int build_atom(rh_ctx *c, const rh_atom_desc *d)
     }
     da.macc = acc;
     da.nmap = nmap;
+    // profile-cache rows: one per line slot of every tile
+    da.nphi = 0;
+    for (int b = 0; b < a.ntile; ++b) {
+        DevTile &tl = da.tile[b];
+        for (int j = 0; j < RH_KMAX; ++j) tl.phi[j] = -1;
+        for (int j = 0; j < tl.K; ++j)
+            if (a.tr[tl.t[j]].kind == 0) {
+                da.phi_tile[da.nphi] = (int16_t)b;
+                da.phi_j[da.nphi] = (int8_t)j;
+                tl.phi[j] = da.nphi++;
+            }
+    }
     // partial redistribution
     {
         int np_lines = 0;
@@ -605,6 +619,27 @@ int ensure_prd(rh_ctx *c, int precision)
         c->prd_cap = want;
     }
     return RH_OK;
+}
+
+// Profile cache of the column kernel (as many blocks as the Ng history: 4 per SM)
+int ensure_phic(rh_ctx *c, int precision)
+{
+    const size_t want = mali_phic_bytes_per_block(c->da, c->ndep, precision) * (size_t)c->nsm * 4;
+    if (want && c->phic_cap < want) {
+        drop_graph(c);
+        dfree(c->phic);
+        c->phic = nullptr;
+        c->phic_cap = 0;
+        CK(cudaMalloc(&c->phic, want));
+        c->phic_cap = want;
+    }
+    return RH_OK;
+}
+
+void set_phic(const rh_ctx *c, IterLaunch &il)
+{
+    il.phic = c->phic;
+    il.phic_cap = c->phic_cap;
 }
 
 void set_prd(const rh_ctx *c, IterLaunch &il, double eps0)
@@ -937,6 +972,7 @@ void rh_destroy(rh_ctx *c)
     dfree(c->dtab_d);
     dfree(c->nghist);
     dfree(c->prd_scr);
+    dfree(c->phic);
     dfree(c->queue);
     dfree(c->badidx);
     dfree(c->colidx);
@@ -1135,6 +1171,8 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     if (r) return r;
     r = ensure_prd(c, o->precision);
     if (r) return r;
+    r = ensure_phic(c, o->precision);
+    if (r) return r;
     size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
     size_t want = per_block * (size_t)c->nsm * 4;
     if (c->nghist_cap < want) {
@@ -1161,6 +1199,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
         il.ctas_per_sm = c->tuned_ctas[o->precision];
     }
     set_prd(c, il, o->prd_eps0);
+    set_phic(c, il);
     float ms = 0;
     int grid = 0;
     char ebuf[256] = {0};
@@ -1535,6 +1574,8 @@ int rh_autotune(rh_ctx *c, int32_t precision, rh_tune_result *out)
     if (r) return r;
     r = ensure_prd(c, precision);
     if (r) return r;
+    r = ensure_phic(c, precision);
+    if (r) return r;
     const size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
     const size_t want = per_block * (size_t)c->nsm * 4;
     if (c->nghist_cap < want) {
@@ -1582,6 +1623,7 @@ int rh_autotune(rh_ctx *c, int32_t precision, rh_tune_result *out)
             il.nsm = c->nsm;
             il.nwork = S;
             set_prd(c, il, 0.0);
+            set_phic(c, il);
             double best = -1;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // first run: warm-up
                 float ms = 0;
@@ -1658,6 +1700,8 @@ int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
     if (r) return r;
     r = ensure_prd(c, prec);
     if (r) return r;
+    r = ensure_phic(c, prec);
+    if (r) return r;
     const size_t per_block = mali_nghist_bytes_per_block(c->da, c->ndep);
     const size_t want = per_block * (size_t)c->nsm * 4;
     if (c->nghist_cap < want) {
@@ -1691,6 +1735,7 @@ int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
         base.ctas_per_sm = c->tuned_ctas[prec];
     }
     set_prd(c, base, o->pass1.prd_eps0);
+    set_phic(c, base);
     const int bw_used = base.block_warps > 0 ? base.block_warps : (prec ? 8 : 4);
     const int ctas_max = mali_max_ctas_per_sm(c->da, c->ndep, prec, bw_used);
     const int ctas_used = base.ctas_per_sm > 0 ? std::min(base.ctas_per_sm, ctas_max) : ctas_max;

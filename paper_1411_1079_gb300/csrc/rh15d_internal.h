@@ -44,6 +44,7 @@ struct DevTile {
     int m;                        // accumulators of the tile = K (K + 1)
     int prd_slot;                 // slot j of a PRD line in the union, -1: none
     int pacc_off;                 // first plain-rate accumulator (2 per slot), PRD atoms only
+    int phi[RH_KMAX];             // line slot: its row of the profile cache; -1: continuum
 };
 
 // Everything the column kernel needs about the atom, passed by value as a
@@ -68,6 +69,11 @@ struct DevAtom {
     int prd_t[RH_MAXPRD];
     int prd_off[RH_MAXPRD + 1];
     int prd_koff[RH_MAXPRD + 1];
+    // profile cache: rows of line slots (tile, slot) whose Voigt profiles for
+    // every ray and depth the column kernel keeps per column in global scratch
+    int nphi;
+    int16_t phi_tile[RH_MAXTILE * RH_KMAX];
+    int8_t phi_j[RH_MAXTILE * RH_KMAX];
 };
 
 // Lane-table fields (structure of arrays, [field][npad]); per-slot fields are
@@ -578,6 +584,10 @@ struct IterLaunch {
     const double *prd_nu = nullptr, *prd_w = nullptr;   // [npp] frequency, quadrature weight
     void *prd_scr = nullptr;                  // per-block scratch (mali_prd_bytes_per_block)
     size_t prd_cap = 0;
+    // per-block profile cache (mali_phic_bytes_per_block); nullptr: the sweep
+    // evaluates the Voigt profiles itself
+    void *phic = nullptr;
+    size_t phic_cap = 0;
 };
 cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
                         const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
@@ -586,6 +596,7 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep);
 int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_warps);
 size_t mali_prd_bytes_per_block(const DevAtom &A, int ndep, int precision);
+size_t mali_phic_bytes_per_block(const DevAtom &A, int ndep, int precision);
 cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const void *lane_tab, int npad,
                                  const float4 *vtab, double nref, double *nghist, size_t nghist_cap, int *queue,
                                  const IterLaunch &o, cudaStream_t st, int *grid_out, char *err, size_t errn);

@@ -3,11 +3,14 @@
 // One thread block owns one column at a time and runs all of that column's
 // MALI iterations with the column's state in shared memory: populations
 // (FP64), collisional rates (FP64), per-depth atmosphere scalars, and the
-// rate accumulators.  Per iteration:
+// rate accumulators.  When it takes a column, the block evaluates the line
+// profiles of every line slot, ray and depth (they do not depend on the
+// populations) into a per-block cache in global memory.  Per iteration:
 //   1. warps take 32-wavelength tiles of the grid from a block-local queue;
-//      each lane owns one wavelength and, one angle mu at a time, sweeps depth
+//      each lane owns one wavelength and, two angles mu at a time, sweeps depth
 //      downward and then upward (linear short characteristics, intensity and
-//      local operator in registers); at every depth the lane forms its
+//      local operator in registers, profiles read from the cache one depth
+//      ahead); at every depth the lane forms its
 //      contributions to the preconditioned rate matrix (Rybicki & Hummer
 //      1992), the warp reduce-scatters them with shuffles, and one lane per
 //      value adds it to the tile's accumulator;
@@ -71,6 +74,9 @@ struct KParams {
     const double *prd_nu, *prd_w;
     char *prd_scr;
     size_t prd_stride;               // bytes of scratch per block
+    // profile cache (nullptr: the sweep evaluates the profiles itself)
+    char *phic;
+    size_t phic_stride;              // bytes of cache per block
 };
 
 // Per-block PRD scratch: in R, the redistribution kernels K [sum np^2][N] (per
@@ -89,6 +95,19 @@ __host__ __device__ inline size_t prd_bytes(const DevAtom &A, int N)
     r = (r + 255) & ~(size_t)255;
     return r + sizeof(double) * 2 * (size_t)A.nprd * N + 256;
 }
+// Per-block profile cache: the line profile phi (Voigt H(a, v) times its
+// normalisation and 1/Doppler width, v including the ray's Doppler shift)
+// of every line slot, ray and depth, [nphi][2 nmu][N][32 lanes] in R, ray
+// 2 m + d for angle m downward (d = 0) and upward (d = 1).  The profiles do
+// not depend on the populations, so a column builds them once and every
+// iteration reads them back instead of evaluating the Voigt function.
+template <typename R>
+__host__ __device__ inline size_t phic_bytes(const DevAtom &A, int N)
+{
+    const size_t r = sizeof(R) * (size_t)A.nphi * 2 * A.nmu * N * 32;
+    return (r + 255) & ~(size_t)255;
+}
+
 template <typename R>
 __device__ inline PrdScr<R> prd_carve(char *base, const DevAtom &A, int N)
 {
@@ -209,9 +228,8 @@ struct LaneC {
 template <typename R, int K>
 struct DepthC {
     R chibg, etabg, B, etac;
-    R Rs[K], Xs[K], nu_[K], chc[K], Uct[K], ad[K];
+    R Rs[K], Xs[K], nu_[K], chc[K], Uct[K];
     R rf[K];                   // partial redistribution: psi/phi of the slot (1 otherwise)
-    R ivth, vz;
 };
 
 template <typename R, int K, bool PRD = false>
@@ -238,11 +256,9 @@ __device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K>
             }
             d.chc[j] = 0;
             d.Uct[j] = 0;
-            d.ad[j] = s.ad[lc.sub[j] * N + k];
         } else {
             if constexpr (PRD) d.rf[j] = 1;
             d.Rs[j] = s.Gc[lc.sub[j] * N + k] * ex;
-            d.ad[j] = 0;
         }
         d.Xs[j] = nl - d.Rs[j] * d.nu_[j];
         if (!lc.isline[j]) {
@@ -251,24 +267,21 @@ __device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K>
             d.etac += d.nu_[j] * d.Uct[j];
         }
     }
-    d.ivth = s.ivth[k];
-    d.vz = s.vz[k];
 }
 
-// Opacity and emissivity for one ray direction (direction cosine muz);
-// per-slot profile phi, opacity chj and emissivity per upper-level
-// population U.
+// Opacity and emissivity for one ray at one depth from the line profiles pc
+// of its line slots; per-slot profile phi, opacity chj and emissivity per
+// upper-level population U.
 template <typename R, int K, bool PRD = false>
-__device__ __forceinline__ void angle_vals(const Smem<R> &s, const LaneC<R, K> &lc, const DepthC<R, K> &d, R muz,
-                                           R &chi, R &eta, R *phi, R *chj, R *U)
+__device__ __forceinline__ void angle_vals(const LaneC<R, K> &lc, const DepthC<R, K> &d, const R (&pc)[K], R &chi,
+                                           R &eta, R *phi, R *chj, R *U)
 {
     chi = d.chibg;
     R ea = d.etac;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         if (lc.isline[j]) {
-            R v = (lc.q[j] - muz * d.vz) * d.ivth;
-            R ph = voigt<R>(d.ad[j], v, s.vtab) * lc.pn[j] * d.ivth;
+            const R ph = pc[j];
             phi[j] = ph;
             chj[j] = lc.Vc[j] * ph * d.Xs[j];
             U[j] = lc.Uc[j] * ph;
@@ -325,9 +338,9 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 // and depth from the block's scratch), PRD lanes accumulate the angle-averaged
 // mean intensity J, and every slot also accumulates its plain rates (actual
 // intensity) cw I and cw R (E + I), for the PRD update.
-template <typename R, int K, bool PRD>
+template <typename R, int K, bool PRD, bool CACHE>
 __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane, R *prd_rho,
-                             R *prd_J, R *prd_plain)
+                             R *prd_J, R *prd_plain, const R *phc)
 {
     const int N = p.N;
     const DevTile &tl = A.tile[b];
@@ -355,6 +368,32 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
     lc.hm = lt[kLaneHm * npad + pi];
     lc.nu3s = lt[kLaneNu3 * npad + pi];
     lc.tw = lt[kLaneTw * npad + pi];
+    // line profiles of depth k, ray r (2 m + d) for the tile's line slots (0
+    // elsewhere): read from the column's cache (CACHE), or evaluated here (the
+    // same arithmetic as the cache's build)
+    const int nray = 2 * nmu;
+    // lane's element of each line slot's cache row (int: at most 288 rows x
+    // 32 rays x 4096 depths x 32 lanes < 2^31)
+    int poff[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) poff[j] = CACHE && lc.isline[j] ? tl.phi[j] * nray * N * kWarp + lane : 0;
+    auto load_ph = [&](int k, int r, R (&o)[K]) {
+        const int rk = (r * N + k) * kWarp;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if (!lc.isline[j]) {
+                o[j] = 0;
+            } else if constexpr (CACHE) {
+                o[j] = phc[poff[j] + rk];
+            } else {
+                const R mu = mu_of<R>(A, r >> 1);
+                const R muz = (r & 1) ? mu : -mu;
+                const R ivth = s.ivth[k];
+                const R v = (lc.q[j] - muz * s.vz[k]) * ivth;
+                o[j] = voigt<R>(s.ad[lc.sub[j] * N + k], v, s.vtab) * lc.pn[j] * ivth;
+            }
+        }
+    };
     constexpr int M = K * (K + 1);
     constexpr int MP = PRD ? M + 2 * K : M;        // with the plain rates
     constexpr int P = Pow2<MP>::v;
@@ -446,25 +485,32 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
             const R mu1 = mu_of<R>(A, m1), imu1 = imu_of<R>(A, m1), wb = wm2_of<R>(A, m1);
             for (int dir = 0; dir < 2; ++dir) {
                 const R z0 = dir == 0 ? -mu0 : mu0, z1 = dir == 0 ? -mu1 : mu1;
+                const int ra = 2 * m0 + dir, rb = 2 * m1 + dir;
                 const bool first = m0 == 0 && dir == 0;
                 R Ia, chipa = 0, Spa, Ib = 0, chipb = 0, Spb = 0;
                 {
                     const int k0 = dir == 0 ? 0 : N - 1;
                     R B2 = 0;
+                    R pc[K];
                     if (dir == 1) {
                         DepthC<R, K> d2;
                         depth_consts<R, K>(s, lc, N - 2, N, d2);
                         B2 = d2.B;
                         R phi[K], chj[K], U[K], eta;
-                        angle_vals<R, K>(s, lc, d2, z0, chipa, eta, phi, chj, U);
-                        if (two) angle_vals<R, K>(s, lc, d2, z1, chipb, eta, phi, chj, U);
+                        load_ph(N - 2, ra, pc);
+                        angle_vals<R, K>(lc, d2, pc, chipa, eta, phi, chj, U);
+                        if (two) {
+                            load_ph(N - 2, rb, pc);
+                            angle_vals<R, K>(lc, d2, pc, chipb, eta, phi, chj, U);
+                        }
                     }
                     DepthC<R, K> d;
                     depth_consts<R, K>(s, lc, k0, N, d);
                     R val[P];
                     {
                         R chi, eta, phi[K], chj[K], U[K];
-                        angle_vals<R, K>(s, lc, d, z0, chi, eta, phi, chj, U);
+                        load_ph(k0, ra, pc);
+                        angle_vals<R, K>(lc, d, pc, chi, eta, phi, chj, U);
                         const R ichi = rcp<R>(chi);
                         Ia = dir == 0 ? (R)0 : d.B + mu0 * (d.B - B2) * rcp<R>((R)0.5 * (chi + chipa) * s.dz[N - 2]);
                         chipa = chi;
@@ -473,7 +519,8 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                     }
                     if (two) {
                         R chi, eta, phi[K], chj[K], U[K];
-                        angle_vals<R, K>(s, lc, d, z1, chi, eta, phi, chj, U);
+                        load_ph(k0, rb, pc);
+                        angle_vals<R, K>(lc, d, pc, chi, eta, phi, chj, U);
                         const R ichi = rcp<R>(chi);
                         Ib = dir == 0 ? (R)0 : d.B + mu1 * (d.B - B2) * rcp<R>((R)0.5 * (chi + chipb) * s.dz[N - 2]);
                         chipb = chi;
@@ -482,15 +529,23 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                     }
                     flush(k0, val, first);
                 }
+                // cached profiles loaded one depth step ahead
+                R pa[K], pb[K];
+                load_ph(dir == 0 ? 1 : N - 2, ra, pa);
+                if (two) load_ph(dir == 0 ? 1 : N - 2, rb, pb);
                 for (int step = 1; step < N; ++step) {
                     const int k = dir == 0 ? step : N - 1 - step;
+                    const int kn = step + 1 < N ? (dir == 0 ? k + 1 : k - 1) : k;
+                    R na[K], nb[K];
+                    load_ph(kn, ra, na);
+                    if (two) load_ph(kn, rb, nb);
                     DepthC<R, K> d;
                     depth_consts<R, K>(s, lc, k, N, d);
                     const R dzk = dir == 0 ? s.dz[k - 1] : s.dz[k];
                     R val[P];
                     {
                         R chi, eta, phi[K], chj[K], U[K];
-                        angle_vals<R, K>(s, lc, d, z0, chi, eta, phi, chj, U);
+                        angle_vals<R, K>(lc, d, pa, chi, eta, phi, chj, U);
                         const R ichi = rcp<R>(chi);
                         const R S = eta * ichi;
                         R ome, wu, wo, omwo;
@@ -504,7 +559,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                     }
                     if (two) {
                         R chi, eta, phi[K], chj[K], U[K];
-                        angle_vals<R, K>(s, lc, d, z1, chi, eta, phi, chj, U);
+                        angle_vals<R, K>(lc, d, pb, chi, eta, phi, chj, U);
                         const R ichi = rcp<R>(chi);
                         const R S = eta * ichi;
                         R ome, wu, wo, omwo;
@@ -517,6 +572,11 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                                 true);
                     }
                     flush(k, val, first);
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        pa[j] = na[j];
+                        pb[j] = nb[j];
+                    }
                 }
             }
         }
@@ -527,9 +587,11 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
         const R mu = mu_of<R>(A, m), imu = imu_of<R>(A, m), wm2 = wm2_of<R>(A, m);
         for (int dir = 0; dir < 2; ++dir) {
             const R muz = dir == 0 ? -mu : mu;
+            const int ray = 2 * m + dir;
             const bool first = m == 0 && dir == 0;
             R I, chip = 0, Sp;
             {
+                R pc[K];
                 // boundary point: I = 0 at the top; at the bottom the diffusion
                 // condition, which needs chi and B one point up
                 const int k0 = dir == 0 ? 0 : N - 1;
@@ -539,12 +601,14 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                     depth_consts<R, K, PRD>(s, lc, N - 2, N, d2, rho_lane ? rho_lane[N - 2] : (R)1, tl.prd_slot);
                     B2 = d2.B;
                     R phi[K], chj[K], U[K], eta;
-                    angle_vals<R, K, PRD>(s, lc, d2, muz, chip, eta, phi, chj, U);
+                    load_ph(N - 2, ray, pc);
+                    angle_vals<R, K, PRD>(lc, d2, pc, chip, eta, phi, chj, U);
                 }
                 DepthC<R, K> d;
                 depth_consts<R, K, PRD>(s, lc, k0, N, d, rho_lane ? rho_lane[k0] : (R)1, tl.prd_slot);
                 R chi, eta, phi[K], chj[K], U[K];
-                angle_vals<R, K, PRD>(s, lc, d, muz, chi, eta, phi, chj, U);
+                load_ph(k0, ray, pc);
+                angle_vals<R, K, PRD>(lc, d, pc, chi, eta, phi, chj, U);
                 const R ichi = rcp<R>(chi);
                 if (dir == 0) {
                     I = 0;
@@ -558,14 +622,21 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
             }
             // rho of the lane's PRD point (global scratch) loaded one depth step ahead
             R rho_nx = (PRD && rho_lane) ? rho_lane[dir == 0 ? 1 : N - 2] : (R)1;
+            // cached profiles, like rho, loaded one depth step ahead
+            R pa[K];
+            load_ph(dir == 0 ? 1 : N - 2, ray, pa);
             for (int step = 1; step < N; ++step) {
                 const int k = dir == 0 ? step : N - 1 - step;
                 const R rho_k = rho_nx;
                 if (PRD && rho_lane && step + 1 < N) rho_nx = rho_lane[dir == 0 ? step + 1 : N - 2 - step];
+                R na[K];
+                load_ph(step + 1 < N ? (dir == 0 ? k + 1 : k - 1) : k, ray, na);
                 DepthC<R, K> d;
                 depth_consts<R, K, PRD>(s, lc, k, N, d, rho_k, tl.prd_slot);
                 R chi, eta, phi[K], chj[K], U[K];
-                angle_vals<R, K, PRD>(s, lc, d, muz, chi, eta, phi, chj, U);
+                angle_vals<R, K, PRD>(lc, d, pa, chi, eta, phi, chj, U);
+#pragma unroll
+                for (int j = 0; j < K; ++j) pa[j] = na[j];
                 const R ichi = rcp<R>(chi);
                 const R S = eta * ichi;
                 const R dzk = dir == 0 ? s.dz[k - 1] : s.dz[k];
@@ -584,14 +655,40 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
     }
 }
 
-template <typename R, bool PRD>
+template <typename R, bool PRD, bool CACHE>
 __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane,
-                                           R *prd_rho, R *prd_J, R *prd_plain)
+                                           R *prd_rho, R *prd_J, R *prd_plain, const R *phc)
 {
     switch (A.tile[b].K) {
-    case 1: sweep_tile_k<R, 1, PRD>(A, s, p, b, lane, prd_rho, prd_J, prd_plain); break;
-    case 2: sweep_tile_k<R, 2, PRD>(A, s, p, b, lane, prd_rho, prd_J, prd_plain); break;
-    default: sweep_tile_k<R, 3, PRD>(A, s, p, b, lane, prd_rho, prd_J, prd_plain); break;
+    case 1: sweep_tile_k<R, 1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_plain, phc); break;
+    case 2: sweep_tile_k<R, 2, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_plain, phc); break;
+    default: sweep_tile_k<R, 3, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_plain, phc); break;
+    }
+}
+
+// Fill the column's profile cache: warps take (row, ray) pairs, lanes their
+// wavelengths, and walk the depths (the same arithmetic as the uncached sweep).
+template <typename R>
+__device__ void build_profiles(const DevAtom &A, const Smem<R> &s, const KParams &p, R *phc)
+{
+    const int N = p.N, nray = 2 * A.nmu;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const R *lt = reinterpret_cast<const R *>(p.lane);
+    for (int w = threadIdx.x >> 5; w < A.nphi * nray; w += nw) {
+        const int row = w / nray, r = w - row * nray;
+        const int b = A.phi_tile[row], j = A.phi_j[row];
+        const int pi = b * kWarp + lane;
+        const R q = lt[(RH_NLANEF * j + 4) * p.npad + pi];
+        const R pn = lt[(RH_NLANEF * j + 5) * p.npad + pi];
+        const R mu = mu_of<R>(A, r >> 1);
+        const R muz = (r & 1) ? mu : -mu;
+        const R *ad = s.ad + (size_t)A.tr[A.tile[b].t[j]].sub * N;
+        R *o = phc + (size_t)w * N * kWarp + lane;
+        for (int k = 0; k < N; ++k) {
+            const R ivth = s.ivth[k];
+            const R v = (q - muz * s.vz[k]) * ivth;
+            o[(size_t)k * kWarp] = voigt<R>(ad[k], v, s.vtab) * pn * ivth;
+        }
     }
 }
 
@@ -684,7 +781,9 @@ __device__ int solve_depth(const DevAtom &A, const double *slotd, const float *s
     return 0;
 }
 
-template <typename R, bool PRD>
+// CACHE: line profiles from the per-block cache (p.phic, nullptr only for an
+// atom without lines); otherwise evaluated in the sweep
+template <typename R, bool PRD, bool CACHE>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) mali_kernel(const __grid_constant__ DevAtom A, const KParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
@@ -698,6 +797,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
     const int64_t nwork = p.nwork_d ? (int64_t)*p.nwork_d : p.nwork;
     PrdScr<R> ps{};
     if constexpr (PRD) ps = prd_carve<R>(p.prd_scr + (size_t)blockIdx.x * p.prd_stride, A, N);
+    R *phc = (CACHE && p.phic) ? reinterpret_cast<R *>(p.phic + (size_t)blockIdx.x * p.phic_stride) : nullptr;
     int64_t done = 0;
     for (;;) {
         __syncthreads();
@@ -740,6 +840,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
             }
         }
         for (int i = tid; i < N * 2 * A.ntr; i += blockDim.x) s.Cr[i] = p.Crate[(size_t)col * N * 2 * A.ntr + i];
+        if (phc) {
+            __syncthreads();   // the column's Doppler widths, velocities and damping
+            build_profiles<R>(A, s, p, phc);
+        }
         if constexpr (PRD) {
             // redistribution kernels of the column: K_ij = R(x_j, x_i) w_j / sum_j (.),
             // x in Doppler units of the depth (static frame), and the J-bar weights
@@ -814,7 +918,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 if (lane == 0) q = atomicAdd(&s.ibuf[1], 1);
                 q = __shfl_sync(0xffffffffu, q, 0);
                 if (q >= A.ntile) break;
-                sweep_tile<R, PRD>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.plain);
+                sweep_tile<R, PRD, CACHE>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.plain, phc);
             }
             __syncthreads();
             // ---- rate equations, one thread per depth
@@ -980,6 +1084,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
 
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep) { return sizeof(double) * 4 * A.nlev * ndep; }
 
+size_t mali_phic_bytes_per_block(const DevAtom &A, int ndep, int precision)
+{
+    return precision == 1 ? phic_bytes<float>(A, ndep) : phic_bytes<double>(A, ndep);
+}
+
 size_t mali_prd_bytes_per_block(const DevAtom &A, int ndep, int precision)
 {
     if (!A.nprd) return 0;
@@ -992,10 +1101,10 @@ int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_wa
     const void *fn;
     if (precision == 1) {
         sm = smem_bytes<float>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc);
-        fn = A.nprd ? (const void *)mali_kernel<float, true> : (const void *)mali_kernel<float, false>;
+        fn = A.nprd ? (const void *)mali_kernel<float, true, true> : (const void *)mali_kernel<float, false, true>;
     } else {
         sm = smem_bytes<double>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc);
-        fn = A.nprd ? (const void *)mali_kernel<double, true> : (const void *)mali_kernel<double, false>;
+        fn = A.nprd ? (const void *)mali_kernel<double, true, true> : (const void *)mali_kernel<double, false, true>;
     }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
     int per_sm = 0;
@@ -1005,10 +1114,15 @@ int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_wa
 
 template <typename R>
 static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps, int ctas_per_sm, int nsm, size_t cap,
-                            size_t prd_cap, cudaStream_t st, float *ms, char *err, size_t errn, int *grid_out)
+                            size_t prd_cap, size_t phic_cap, cudaStream_t st, float *ms, char *err, size_t errn,
+                            int *grid_out)
 {
     size_t sm = smem_bytes<R>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
-    auto kern = A.nprd ? mali_kernel<R, true> : mali_kernel<R, false>;
+    if (A.nphi && !p.phic) {
+        snprintf(err, errn, "no profile cache");
+        return cudaErrorInvalidValue;
+    }
+    auto kern = A.nprd ? mali_kernel<R, true, true> : mali_kernel<R, false, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int threads = block_warps * 32;
@@ -1025,6 +1139,7 @@ static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps,
     size_t per_block = mali_nghist_bytes_per_block(A, p.N);
     if ((size_t)grid * per_block > cap) grid = (int64_t)(cap / per_block);
     if (A.nprd && (size_t)grid * p.prd_stride > prd_cap) grid = (int64_t)(prd_cap / p.prd_stride);
+    if (p.phic && (size_t)grid * p.phic_stride > phic_cap) grid = (int64_t)(phic_cap / p.phic_stride);
     if (grid < 1) {
         snprintf(err, errn, "no scratch for the Ng history");
         return cudaErrorMemoryAllocation;
@@ -1095,15 +1210,18 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
     p.prd_w = o.prd_w;
     p.prd_scr = reinterpret_cast<char *>(o.prd_scr);
     p.prd_stride = A.nprd ? (o.precision == 1 ? prd_bytes<float>(A, c.ndep) : prd_bytes<double>(A, c.ndep)) : 0;
+    p.phic_stride = o.precision == 1 ? phic_bytes<float>(A, c.ndep) : phic_bytes<double>(A, c.ndep);
+    p.phic = (o.phic && p.phic_stride && p.phic_stride <= o.phic_cap) ? reinterpret_cast<char *>(o.phic) : nullptr;
     int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
     if (o.persistent) {
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
     }
     if (o.precision == 1)
-        return launch_t<float>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, o.prd_cap, st, ms_out, err, errn,
-                               grid_out);
-    return launch_t<double>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, o.prd_cap, st, ms_out, err, errn, grid_out);
+        return launch_t<float>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, o.prd_cap, o.phic_cap, st, ms_out, err,
+                               errn, grid_out);
+    return launch_t<double>(A, p, bw, o.ctas_per_sm, o.nsm, nghist_cap, o.prd_cap, o.phic_cap, st, ms_out, err, errn,
+                            grid_out);
 }
 
 }  // namespace rh
@@ -1165,16 +1283,27 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     p.prd_w = o.prd_w;
     p.prd_scr = reinterpret_cast<char *>(o.prd_scr);
     p.prd_stride = A.nprd ? (o.precision == 1 ? prd_bytes<float>(A, c.ndep) : prd_bytes<double>(A, c.ndep)) : 0;
+    p.phic_stride = o.precision == 1 ? phic_bytes<float>(A, c.ndep) : phic_bytes<double>(A, c.ndep);
+    p.phic = (o.phic && p.phic_stride && p.phic_stride <= o.phic_cap) ? reinterpret_cast<char *>(o.phic) : nullptr;
     const int bw = o.block_warps > 0 ? o.block_warps : (o.precision ? 8 : 4);
     const int threads = bw * 32;
     size_t sm;
     const void *fn;
+    // without a profile cache (callers that cannot allocate) the sweep
+    // evaluates the profiles; partial redistribution always has the cache
+    const bool cache = p.phic || !A.nphi;
+    if (!cache && A.nprd) {
+        snprintf(err, errn, "the partial-redistribution kernel needs the profile cache");
+        return cudaErrorInvalidValue;
+    }
     if (o.precision == 1) {
         sm = smem_bytes<float>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
-        fn = A.nprd ? (const void *)mali_kernel<float, true> : (const void *)mali_kernel<float, false>;
+        fn = A.nprd ? (const void *)mali_kernel<float, true, true>
+                    : (cache ? (const void *)mali_kernel<float, false, true> : (const void *)mali_kernel<float, false, false>);
     } else {
         sm = smem_bytes<double>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
-        fn = A.nprd ? (const void *)mali_kernel<double, true> : (const void *)mali_kernel<double, false>;
+        fn = A.nprd ? (const void *)mali_kernel<double, true, true>
+                    : (cache ? (const void *)mali_kernel<double, false, true> : (const void *)mali_kernel<double, false, false>);
     }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -1191,6 +1320,7 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     const size_t per_block = mali_nghist_bytes_per_block(A, p.N);
     if ((size_t)grid * per_block > nghist_cap) grid = (int64_t)(nghist_cap / per_block);
     if (A.nprd && (size_t)grid * p.prd_stride > o.prd_cap) grid = (int64_t)(o.prd_cap / p.prd_stride);
+    if (p.phic && (size_t)grid * p.phic_stride > o.phic_cap) grid = (int64_t)(o.phic_cap / p.phic_stride);
     if (grid < 1) {
         snprintf(err, errn, "Ng history of one column (%zu B) exceeds the scratch capacity (%zu B)", per_block,
                  nghist_cap);

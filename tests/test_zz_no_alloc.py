@@ -2,9 +2,15 @@
 memory while they solve (their memory belongs to their own pool, or they are
 capturing a stream into a graph, or they cannot afford the synchronisation of
 cudaMalloc).  It keeps its scratch in a static array inside the library and
-writes into buffers the caller owns.  Its results must match rh_iterate's on
-the same columns, on two calls in a row (the second call finds the scratch
-holding the first call's contents).  This file is collected last so that a
+writes into buffers the caller owns, and evaluates the line profiles in the
+sweep, where rh_iterate reads them from its per-column profile cache.  Its
+results must match rh_iterate's on the same columns, on two calls in a row
+(the second call finds the scratch holding the first call's contents).  In
+FP32 the two paths agree bit for bit, trajectory and stopping included.  In
+FP64 the two kernel instantiations may fuse multiply-adds of the Voigt
+function differently (1 ulp); Ng extrapolation amplifies such differences
+along a trajectory, so FP64 is compared on a fixed schedule without Ng, as
+the FP64 parity tests are.  This file is collected last so that a
 run stopping at the first failure has run every other test first."""
 import numpy as np
 import pytest
@@ -33,7 +39,10 @@ def test_noalloc_matches_rh_iterate_twice(precision):
     ctx = rh.Context(0)
     ctx.setup_atom(atom)
     ctx.load_columns(cols)
-    kw = dict(maxiter=120, tol=1e-3, precision=precision)
+    if precision == 1:
+        kw = dict(maxiter=120, tol=1e-3, precision=precision)
+    else:
+        kw = dict(maxiter=15, tol=0.0, ng_order=0, precision=precision)
     ref = ctx.iterate(**kw)
     n_ref, it_ref, st_ref, dm_ref = ctx.populations()
 
@@ -49,7 +58,7 @@ def test_noalloc_matches_rh_iterate_twice(precision):
         assert np.array_equal(it_out.cpu().numpy(), it_ref), call
         assert np.array_equal(st_out.cpu().numpy(), st_ref), call
         assert s["n_converged"] == ref["n_converged"] and s["iterations_total"] == ref["iterations_total"]
-        assert s["max_dn_final"] == pytest.approx(ref["max_dn_final"], rel=1e-12)
+        assert s["max_dn_final"] == pytest.approx(ref["max_dn_final"], rel=1e-12 if precision == 1 else 1e-6)
         n_out.fill_(-1.0)
         it_out.fill_(-1)
     # the context's own populations are untouched by the no-allocation call
