@@ -476,7 +476,7 @@ def run_gpu(args):
                      "traffic": DRAM_BYTES_PER_COLUMN_ITERATION * iters / args.steps,
                      "traffic_note": "bytes per launch: ncu DRAM bytes per column-iteration on the "
                                      "608-column x 12-iteration case x column-iterations of one launch",
-                     "kernel": "mali_kernel<float, CRD> (column-resident MALI, FP32 sweep)",
+                     "kernel": "mali_kernel<float, CRD, cached profiles> (column-resident MALI, FP32 sweep)",
                      "issue_slots": {"achieved": WARP_INST_PER_COLUMN_ITERATION * iters / kern_s,
                                      "peak": nsm * 4 * sm_mhz * 1e6, "unit": "warp instructions/s",
                                      "frac": WARP_INST_PER_COLUMN_ITERATION * iters / kern_s

@@ -615,6 +615,7 @@ int ensure_prd(rh_ctx *c, int precision)
     if (c->prd_cap < want) {
         drop_graph(c);
         dfree(c->prd_scr);
+        c->prd_cap = 0;
         CK(cudaMalloc(&c->prd_scr, want));
         c->prd_cap = want;
     }
@@ -1177,6 +1178,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     size_t want = per_block * (size_t)c->nsm * 4;
     if (c->nghist_cap < want) {
         dfree(c->nghist);
+        c->nghist_cap = 0;
         CK(cudaMalloc(&c->nghist, want));
         c->nghist_cap = want;
     }
@@ -1581,6 +1583,7 @@ int rh_autotune(rh_ctx *c, int32_t precision, rh_tune_result *out)
     if (c->nghist_cap < want) {
         drop_graph(c);
         dfree(c->nghist);
+        c->nghist_cap = 0;
         CK(cudaMalloc(&c->nghist, want));
         c->nghist_cap = want;
     }
@@ -1706,6 +1709,7 @@ int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
     const size_t want = per_block * (size_t)c->nsm * 4;
     if (c->nghist_cap < want) {
         dfree(c->nghist);
+        c->nghist_cap = 0;
         CK(cudaMalloc(&c->nghist, want));
         c->nghist_cap = want;
     }
