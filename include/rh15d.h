@@ -338,6 +338,20 @@ int rh_surrogate_loss_grad(rh_ctx *ctx, int64_t ncols, const int32_t *cols, doub
 /* Raw prediction ln(n/n*) [ncol][nlev][ndep] (host) for every loaded column. */
 int rh_surrogate_predict(rh_ctx *ctx, float *lnb_out);
 
+/* Checkpoint files of the network (host byte order, little-endian targets): */
+/* "RH15DMLP", uint32 version 1, int32 nin, hidden, nhidden, nout, int64     */
+/* nparam, the state (rh_surrogate_get_state's floats), and a 64-bit FNV-1a  */
+/* hash of the state bytes.  save: RH_ESTATE without a network, RH_EINVAL    */
+/* if the file cannot be written.  load: creates (or replaces) the network   */
+/* with the file's sizes and state; RH_ESTATE without loaded columns,        */
+/* RH_EINVAL for a missing, truncated or corrupted file or one made for      */
+/* another depth count or atom.  file_info: checks a file without a context */
+/* or GPU and returns its sizes {nin, hidden, nhidden, nout} and state       */
+/* length; RH_EINVAL with the reason in msg (optional, msg_len bytes).       */
+int rh_surrogate_save(rh_ctx *ctx, const char *path);
+int rh_surrogate_load(rh_ctx *ctx, const char *path);
+int rh_surrogate_file_info(const char *path, int32_t *sizes_out, int64_t *nparam_out, char *msg, size_t msg_len);
+
 /* ---------------------------------------------------------------------- */
 /* rh_iterate_noalloc -- the paper has no counterpart to this call; it      */
 /* exists for callers of this library that cannot allocate device memory    */

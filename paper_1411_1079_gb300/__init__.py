@@ -26,7 +26,7 @@ EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlam
            "rh_emergent_spectrum", "rh_iterate_noalloc", "rh_surrogate_init", "rh_surrogate_state_size",
            "rh_surrogate_get_state", "rh_surrogate_set_state", "rh_surrogate_train", "rh_surrogate_loss_grad",
            "rh_surrogate_predict", "rh_solve", "rh_autotune", "rh_start_populations",
-           "rh_emergent_stokes")
+           "rh_emergent_stokes", "rh_surrogate_save", "rh_surrogate_load", "rh_surrogate_file_info")
 
 MAX_RERUN = 4
 MAX_TUNE = 8
@@ -127,6 +127,9 @@ def lib(path: str | None = None):
         L.rh_surrogate_train.argtypes = [vp, C.POINTER(TrainOpts), C.POINTER(TrainStats)]
         L.rh_surrogate_loss_grad.argtypes = [vp, C.c_int64, _ip, C.POINTER(C.c_double), _fp]
         L.rh_surrogate_predict.argtypes = [vp, _fp]
+        L.rh_surrogate_save.argtypes = [vp, C.c_char_p]
+        L.rh_surrogate_load.argtypes = [vp, C.c_char_p]
+        L.rh_surrogate_file_info.argtypes = [C.c_char_p, _ip, C.POINTER(C.c_int64), C.c_char_p, C.c_size_t]
         _lib = L
     return _lib
 
@@ -152,6 +155,19 @@ class RhError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("rh error %d: %s" % (code, msg))
         self.code = code
+
+
+def surrogate_file_info(path) -> dict:
+    """rh_surrogate_file_info: check a network checkpoint file (no context,
+    no GPU); its sizes and state length, or RhError(RH_EINVAL, reason)."""
+    sizes = np.zeros(4, np.int32)
+    npar = C.c_int64()
+    msg = C.create_string_buffer(256)
+    rc = lib().rh_surrogate_file_info(os.fsencode(path), _i(sizes), C.byref(npar), msg, 256)
+    if rc:
+        raise RhError(rc, msg.value.decode())
+    return {"nin": int(sizes[0]), "hidden": int(sizes[1]), "nhidden": int(sizes[2]), "nout": int(sizes[3]),
+            "nparam": int(npar.value)}
 
 
 class Context:
@@ -339,6 +355,12 @@ class Context:
         self._check(self._lib.rh_surrogate_loss_grad(self._p, cols.size, _i(cols), C.byref(loss),
                                                      grad.ctypes.data_as(C.POINTER(C.c_float))))
         return loss.value, grad
+
+    def surrogate_save(self, path):
+        self._check(self._lib.rh_surrogate_save(self._p, os.fsencode(path)))
+
+    def surrogate_load(self, path):
+        self._check(self._lib.rh_surrogate_load(self._p, os.fsencode(path)))
 
     def surrogate_predict(self):
         out = np.zeros((self.ncol, self.nlev, self.ndep), np.float32)

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "rh15d_ckpt.h"
 #include "rh15d_internal.h"
 
 using namespace rh;
@@ -77,6 +78,7 @@ struct rh_ctx {
     // learned initial guess
     rh::Mlp *mlp = nullptr;
     int mlp_ndep = 0;
+    int mlp_hidden = 0, mlp_nhidden = 0;
     float *feat = nullptr, *tgt = nullptr, *lnb = nullptr;
     int64_t feat_cap = 0;
     int *idx_d = nullptr;
@@ -766,6 +768,8 @@ int rh_surrogate_init(rh_ctx *c, int32_t hidden, int32_t nhidden, uint64_t seed)
     c->mlp = nullptr;
     CK(mlp_create(&c->mlp, 4 * c->ndep, hidden, nhidden, c->da.nlev * c->ndep, seed));
     c->mlp_ndep = c->ndep;
+    c->mlp_hidden = hidden;
+    c->mlp_nhidden = nhidden;
     return RH_OK;
 }
 
@@ -900,6 +904,63 @@ int rh_surrogate_predict(rh_ctx *c, float *lnb_out)
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     cudaFree(save);
     if (e != cudaSuccess) return fail(c, RH_ECUDA, "rh_surrogate_predict: %s", cudaGetErrorString(e));
+    return RH_OK;
+}
+
+int rh_surrogate_save(rh_ctx *c, const char *path)
+{
+    if (!c || !path) return RH_EINVAL;
+    if (!c->mlp) return fail(c, RH_ESTATE, "rh_surrogate_save: no surrogate");
+    cudaSetDevice(c->dev);
+    std::vector<float> st((size_t)mlp_state_size(c->mlp));
+    CK(mlp_get_state(c->mlp, st.data()));
+    CkptSizes z;
+    z.nin = 4 * c->mlp_ndep;
+    z.hidden = c->mlp_hidden;
+    z.nhidden = c->mlp_nhidden;
+    z.nout = c->da.nlev * c->mlp_ndep;
+    if (ckpt_nparam(z) != (int64_t)st.size()) return fail(c, RH_EINVAL, "rh_surrogate_save: inconsistent network sizes");
+    const char *why = ckpt_write(path, z, st.data(), (int64_t)st.size());
+    if (why) return fail(c, RH_EINVAL, "rh_surrogate_save: %s: %s", path, why);
+    return RH_OK;
+}
+
+int rh_surrogate_load(rh_ctx *c, const char *path)
+{
+    if (!c || !path) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "rh_surrogate_load: load columns first (the network size follows ndep)");
+    CkptSizes z;
+    int64_t np = 0;
+    std::vector<float> st;
+    const char *why = ckpt_read(path, z, np, &st);
+    if (why) return fail(c, RH_EINVAL, "rh_surrogate_load: %s: %s", path, why);
+    if (z.nin != 4 * c->ndep || z.nout != c->da.nlev * c->ndep)
+        return fail(c, RH_EINVAL, "rh_surrogate_load: the checkpoint is for %d inputs and %d outputs, the loaded "
+                                  "columns need %d and %d", z.nin, z.nout, 4 * c->ndep, c->da.nlev * c->ndep);
+    int r = rh_surrogate_init(c, z.hidden, z.nhidden, 0);
+    if (r) return r;
+    if (mlp_state_size(c->mlp) != np) return fail(c, RH_EINVAL, "rh_surrogate_load: state length mismatch");
+    return rh_surrogate_set_state(c, st.data());
+}
+
+int rh_surrogate_file_info(const char *path, int32_t *sizes_out, int64_t *nparam_out, char *msg, size_t msg_len)
+{
+    if (msg && msg_len) msg[0] = 0;
+    if (!path) return RH_EINVAL;
+    CkptSizes z;
+    int64_t np = 0;
+    const char *why = ckpt_read(path, z, np, nullptr);
+    if (why) {
+        if (msg && msg_len) snprintf(msg, msg_len, "%s", why);
+        return RH_EINVAL;
+    }
+    if (sizes_out) {
+        sizes_out[0] = z.nin;
+        sizes_out[1] = z.hidden;
+        sizes_out[2] = z.nhidden;
+        sizes_out[3] = z.nout;
+    }
+    if (nparam_out) *nparam_out = np;
     return RH_OK;
 }
 
