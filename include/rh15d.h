@@ -26,6 +26,7 @@
 #ifndef RH15D_H
 #define RH15D_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

@@ -64,3 +64,12 @@ def test_library_missing_raises(tmp_path):
     finally:
         rh._lib = saved
         importlib.reload  # keep flake quiet
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/rh15d.h compiles as C99 on its own (no C++ or CUDA types)."""
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "rh15d.h"\nint main(void) { rh_ctx *c = 0; (void)c; return 0; }\n')
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
