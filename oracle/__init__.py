@@ -75,6 +75,7 @@ def lib():
         L.rho_rate_matrix.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int32, _dp]
         L.rho_collision_rates.argtypes = [C.c_void_p, C.c_int64, _dp]
         L.rho_escape_probabilities.argtypes = [C.c_void_p, C.c_int64, _dp, _dp]
+        L.rho_prd_kernel.argtypes = [C.c_void_p, C.c_int64, C.c_int32, _ip, _ip, _dp, _dp, _dp]
         L.rho_start_populations.argtypes = [C.c_void_p, C.c_int32]
         L.rho_emergent_spectrum.argtypes = [C.c_void_p, C.c_double, C.c_int64, _dp, _dp, C.c_int32]
         L.rho_electron_density.argtypes = [C.c_void_p, C.c_double, C.c_double]
@@ -332,6 +333,19 @@ class Oracle:
         e = np.zeros((self.ntr, self.ndep))
         self._check(self._lib.rho_escape_probabilities(self._p, col, _d(n), _d(e)))
         return e
+
+    def prd_kernel(self, col, q):
+        """Redistribution kernel of PRD line q in column col: grid indices
+        and quadrature weights of its points, K [ndep][np][np], f [ndep][np]."""
+        m = np.zeros(1, np.int32)
+        self._check(self._lib.rho_prd_kernel(self._p, col, q, _i(m), None, None, None, None))
+        n = int(m[0])
+        pts = np.zeros(n, np.int32)
+        w = np.zeros(n)
+        K = np.zeros((self.ndep, n, n))
+        f = np.zeros((self.ndep, n))
+        self._check(self._lib.rho_prd_kernel(self._p, col, q, _i(m), _i(pts), _d(w), _d(K), _d(f)))
+        return pts, w, K, f
 
     def start_populations(self, kind):
         """Write the start populations (0 LTE, 3 zero radiation, 4 escape

@@ -1686,6 +1686,33 @@ int rho_start_populations(rho_ctx *c, int32_t kind)
     return 0;
 }
 
+/* redistribution kernel of PRD line q (in the order of the atom's PRD lines)
+ * in column col, as the iteration builds it: *np_out = its points; with
+ * non-NULL outputs also their grid indices pts_out[np] (frequency order),
+ * quadrature weights w_out[np], K_out[N][np][np] and the J-bar weights
+ * f_out[N][np] */
+int rho_prd_kernel(rho_ctx *c, int64_t col, int32_t q, int32_t *np_out, int32_t *pts_out, double *w_out,
+                   double *K_out, double *f_out)
+{
+    const atom_t *a = &c->at;
+    if (col < 0 || col >= c->ncol) return fail(c, "column out of range");
+    if (q < 0 || q >= a->nprd_line) return fail(c, "no such PRD line");
+    const int m = a->prd_np[q], N = c->ndep;
+    if (np_out) *np_out = m;
+    if (!K_out && !f_out && !pts_out && !w_out) return 0;
+    for (int j = 0; j < m; ++j) {
+        if (pts_out) pts_out[j] = a->prd_pts[q][j];
+        if (w_out) w_out[j] = a->prd_w[q][j];
+    }
+    work_t w;
+    work_alloc(&w, a, N);
+    column_setup(c, col, &w);
+    if (K_out) memcpy(K_out, w.prdK[q], (size_t)N * m * m * sizeof(double));
+    if (f_out) memcpy(f_out, w.prdf[q], (size_t)N * m * sizeof(double));
+    work_free(&w);
+    return 0;
+}
+
 /* escape probabilities esc[t][k] of one column for populations n */
 int rho_escape_probabilities(rho_ctx *c, int64_t col, const double *n, double *esc_out)
 {
