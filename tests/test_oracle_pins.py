@@ -265,6 +265,7 @@ def test_collision_rates_two_published_forms(orc, column_oracle):
     T = rh_synth.chromosphere_column()["T"][0]
     info = o.atom_info()
     atom = rh_synth.hydrogen_like_atom()
+    branch = []
     for k in (5, 60):
         # van Regemorter in its original form (cgs): C_lu = 20.6 lambda^3 n_e T^-1/2 A_ul
         # (g_u/g_l) P(y) e^-y with lambda in cm -- independent of the Omega/8.63e-6 form
@@ -273,6 +274,14 @@ def test_collision_rates_two_published_forms(orc, column_oracle):
         P = max(0.2, 0.276 * np.exp(y) * exp1(y))
         ref = 20.6 * lam_cm ** 3 * (ne[0, k] * 1e-6) / np.sqrt(T[k]) * info["A"][0] * (8 / 2) * P * np.exp(-y)
         assert Cm[k, 0, 1] == pytest.approx(ref, rel=3e-3)
+        # the same for n = 4 -> 5 (y < 1: the 0.276 e^y E1(y) branch of P, not the 0.2 floor)
+        t45 = 9
+        lam_cm = sc.c / info["nu0"][t45] * 100
+        y = sc.h * info["nu0"][t45] / (sc.k * T[k])
+        P = max(0.2, 0.276 * np.exp(y) * exp1(y))
+        branch.append(P > 0.2)
+        ref = 20.6 * lam_cm ** 3 * (ne[0, k] * 1e-6) / np.sqrt(T[k]) * info["A"][t45] * (50 / 32) * P * np.exp(-y)
+        assert Cm[k, 3, 4] == pytest.approx(ref, rel=3e-3)
         # Seaton bound-free in cgs units
         u = sc.h * info["nu0"][10] / (sc.k * T[k])
         ref = 1.55e13 * (ne[0, k] * 1e-6) / np.sqrt(T[k]) * 0.1 * (atom["cont_alpha0"][0] * 1e4) * np.exp(-u) / u
@@ -280,6 +289,7 @@ def test_collision_rates_two_published_forms(orc, column_oracle):
         # detailed balance of the downward rates
         for (l, u_) in ((0, 1), (1, 3), (2, 5)):
             assert Cm[k, u_, l] / Cm[k, l, u_] == pytest.approx(ns[0, l, k] / ns[0, u_, k], rel=1e-12)
+    assert any(branch)
 
 
 def test_rate_matrix_columns_sum_to_zero(orc, column_oracle):
@@ -301,6 +311,82 @@ def _solve_stateq(A, nold, ntot):
         b[r] = ntot[k]
         out[:, k] = np.linalg.solve(M, b)
     return out
+
+
+def _planck(nu, T):
+    return 2 * sc.h * nu ** 3 / sc.c ** 2 / np.expm1(sc.h * nu / (sc.k * T))
+
+
+def test_radiative_rates_in_a_planck_field(orc, column_oracle):
+    """Every transition in a Planck field (mode 2, no Psi*): the radiative
+    rates reduce to quadratures of library functions on the oracle's grid.
+    Line: R_lu = B_lu B_nu0(T) sum_i w_i phi(nu_i) and R_ul = (A_ul + B_ul
+    B_nu0(T)) sum_i w_i phi(nu_i), phi = Re w(x + i a)/(sqrt(pi) dnu_D) from
+    scipy's Faddeeva function (static column, v_z = 0, so every ray sees the
+    same profile and the angle weights sum to one).  Continuum (Kramers,
+    alpha = alpha0 (nu0/nu)^3): R_lc = sum_i w_i 4 pi alpha B_nu/(h nu).
+    A factor on the angle or frequency weights, on the profile or on the
+    cross section's frequency law fails this."""
+    o = column_oracle
+    atom = rh_synth.hydrogen_like_atom()
+    T = rh_synth.chromosphere_column()["T"][0]
+    ns, _ = o.lte()
+    G = o.rate_matrix(0, ns[0], 2)
+    Cm = o.collision_rates(0)
+    info = o.atom_info()
+    g = o.grid()
+    N = len(T)
+    mass = atom["mass_amu"] * sc.atomic_mass
+    nline = len(atom["line_l"])
+
+    def points(t):
+        idx = [i for i in range(len(g["nu"])) if t in g["act"][i, :g["nact"][i]]]
+        w = np.array([g["wq"][i, list(g["act"][i, :g["nact"][i]]).index(t)] for i in idx])
+        return g["nu"][idx], w
+
+    for t in range(nline):
+        l, u = atom["line_l"][t], atom["line_u"][t]
+        nu, w = points(t)
+        for k in (0, 30, 81):
+            dnD = info["nu0"][t] / sc.c * np.sqrt(2 * sc.k * T[k] / mass)
+            s = k / (N - 1)
+            a = np.exp((1 - s) * np.log(atom["line_a_top"][t]) + s * np.log(atom["line_a_bot"][t]))
+            area = np.sum(w * wofz((nu - info["nu0"][t]) / dnD + 1j * a).real) / (np.sqrt(np.pi) * dnD)
+            B = _planck(info["nu0"][t], T[k])
+            assert G[k, u, l] - Cm[k, l, u] == pytest.approx(info["Blu"][t] * B * area, rel=1e-7), (t, k)
+            assert G[k, l, u] - Cm[k, u, l] == pytest.approx((info["A"][t] + info["Bul"][t] * B) * area,
+                                                             rel=1e-7), (t, k)
+    L = atom["nlev"]
+    for c, l in enumerate(atom["cont_l"]):
+        t = nline + c
+        nu, w = points(t)
+        alpha = atom["cont_alpha0"][c] * (info["nu0"][t] / nu) ** 3
+        for k in (0, 30, 81):
+            ref = np.sum(w * 4 * np.pi * alpha * _planck(nu, T[k]) / (sc.h * nu))
+            assert G[k, L - 1, l] - Cm[k, l, L - 1] == pytest.approx(ref, rel=1e-9), (t, k)
+
+
+def test_diffusion_limit_at_the_lower_boundary(orc):
+    """The lower boundary (diffusion approximation I = B + mu dB/dtau) in an
+    LTE column made optically thick at the bottom (n_H x 100): the upward
+    boundary rays and the downward rays that crossed the atmosphere cancel
+    to first order in the mean free path, so the continua's mean intensity
+    at the lowest point equals B to second order (observed <= 2e-9; the
+    opposite sign of the gradient term leaves a first-order 1e-5)."""
+    atom = rh_synth.hydrogen_like_atom()
+    cols = rh_synth.chromosphere_column()
+    cols["nH"] = cols["nH"] * 100.0
+    o = orc.Oracle()
+    o.setup_atom(atom)
+    o.load_columns(cols)
+    ns, _ = o.lte()
+    G1 = o.rate_matrix(0, ns[0], 1)       # intensity from the formal solution
+    G2 = o.rate_matrix(0, ns[0], 2)       # Planck field
+    Cm = o.collision_rates(0)
+    L, k = atom["nlev"], len(cols["T"][0]) - 1
+    for l in (1, 2, 3):                   # Balmer, Paschen and Brackett continua
+        r = (G1[k, L - 1, l] - Cm[k, l, L - 1]) / (G2[k, L - 1, l] - Cm[k, l, L - 1])
+        assert abs(r - 1) < 1e-7, (l, r)
 
 
 def test_detailed_balance_returns_lte(orc, column_oracle):
