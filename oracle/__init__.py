@@ -75,6 +75,8 @@ def lib():
         L.rho_rate_matrix.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int32, _dp]
         L.rho_collision_rates.argtypes = [C.c_void_p, C.c_int64, _dp]
         L.rho_escape_probabilities.argtypes = [C.c_void_p, C.c_int64, _dp, _dp]
+        L.rho_column_background.argtypes = [C.c_void_p, C.c_int64, _dp]
+        L.rho_prd_update_ratio.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int32, _dp]
         L.rho_prd_kernel.argtypes = [C.c_void_p, C.c_int64, C.c_int32, _ip, _ip, _dp, _dp, _dp]
         L.rho_start_populations.argtypes = [C.c_void_p, C.c_int32]
         L.rho_emergent_spectrum.argtypes = [C.c_void_p, C.c_double, C.c_int64, _dp, _dp, C.c_int32]
@@ -333,6 +335,22 @@ class Oracle:
         e = np.zeros((self.ntr, self.ndep))
         self._check(self._lib.rho_escape_probabilities(self._p, col, _d(n), _d(e)))
         return e
+
+    def column_background(self, col):
+        """Background opacity [nlambda][ndep] (m^-1) of column col on the grid."""
+        chi = np.zeros((self.nlambda, self.ndep))
+        self._check(self._lib.rho_column_background(self._p, col, _d(chi)))
+        return chi
+
+    def prd_update_ratio(self, col, n, q):
+        """One PRD update of line q from rho = 1 with populations n (no
+        switching, no under-relaxation): [ndep][np], points in frequency order."""
+        n = np.ascontiguousarray(n, dtype=np.float64)
+        m = np.zeros(1, np.int32)
+        self._check(self._lib.rho_prd_kernel(self._p, col, q, _i(m), None, None, None, None))
+        r = np.zeros((self.ndep, int(m[0])))
+        self._check(self._lib.rho_prd_update_ratio(self._p, col, _d(n), q, _d(r)))
+        return r
 
     def prd_kernel(self, col, q):
         """Redistribution kernel of PRD line q in column col: grid indices

@@ -1713,6 +1713,41 @@ int rho_prd_kernel(rho_ctx *c, int64_t col, int32_t q, int32_t *np_out, int32_t 
     return 0;
 }
 
+/* background opacity chi_c[nlam][N] (m^-1) of column col on the wavelength
+ * grid, as the iteration uses it: free-free, H- bound-free, stimulated
+ * emission, Thomson scattering */
+int rho_column_background(rho_ctx *c, int64_t col, double *chi_out)
+{
+    if (col < 0 || col >= c->ncol) return fail(c, "column out of range");
+    work_t w;
+    work_alloc(&w, &c->at, c->ndep);
+    column_setup(c, col, &w);
+    memcpy(chi_out, w.chic, sizeof(double) * c->at.nlam * c->ndep);
+    work_free(&w);
+    return 0;
+}
+
+/* One PRD update of line q in column col from rho = 1 with populations n
+ * and the formal solution they give, without switching or under-relaxation:
+ * r_out[N][np] = 1 + F (sum_j K_ij J_j / Jbar - 1), points in frequency order */
+int rho_prd_update_ratio(rho_ctx *c, int64_t col, const double *n, int32_t q, double *r_out)
+{
+    const atom_t *a = &c->at;
+    if (col < 0 || col >= c->ncol) return fail(c, "column out of range");
+    if (q < 0 || q >= a->nprd_line) return fail(c, "no such PRD line");
+    const int N = c->ndep, m = a->prd_np[q];
+    work_t w;
+    work_alloc(&w, a, N);
+    column_setup(c, col, &w);
+    rate_matrix(c, col, &w, n, 1);
+    prd_update(c, col, &w, n, 1, 0.0);
+    /* prd_update returns the mean of the previous rho (1) and the new value */
+    for (int k = 0; k < N; ++k)
+        for (int j = 0; j < m; ++j) r_out[(size_t)k * m + j] = 2.0 * w.rho[(size_t)a->prd_pts[q][j] * N + k] - 1.0;
+    work_free(&w);
+    return 0;
+}
+
 /* escape probabilities esc[t][k] of one column for populations n */
 int rho_escape_probabilities(rho_ctx *c, int64_t col, const double *n, double *esc_out)
 {
