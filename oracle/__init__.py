@@ -91,6 +91,10 @@ def lib():
         L.rho_stokes_sweep.restype = None
         L.rho_stokes_sweep.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp]
         L.rho_emergent_stokes.argtypes = [C.c_void_p, C.c_int32, C.c_double, _dp, _dp, _dp, C.c_int64, _dp, _dp]
+        L.rho_prd_switch_eps.restype = C.c_double
+        L.rho_prd_switch_eps.argtypes = [C.c_double, C.c_int32]
+        L.rho_crsw_factor.restype = C.c_double
+        L.rho_crsw_factor.argtypes = [C.c_double, C.c_int32]
     return _lib
 
 
@@ -154,6 +158,16 @@ def stokes_sweep(dtau, Kp, S, Ib):
     out = np.zeros(4)
     lib().rho_stokes_sweep(S.shape[0], _d(dtau), _d(Kp), _d(S), _d(Ib), _d(out))
     return out
+
+
+def prd_switch_eps(eps0, it):
+    """PRD switching factor eps of iteration it (Sect. 2.3, Eq. 1)."""
+    return lib().rho_prd_switch_eps(float(eps0), int(it))
+
+
+def crsw_factor(f0, it):
+    """Collisional-radiative switching factor of iteration it (Sect. 2.3)."""
+    return lib().rho_crsw_factor(float(f0), int(it))
 
 
 def expE1(y):
@@ -343,8 +357,9 @@ class Oracle:
         return chi
 
     def prd_update_ratio(self, col, n, q):
-        """One PRD update of line q from rho = 1 with populations n (no
-        switching, no under-relaxation): [ndep][np], points in frequency order."""
+        """One PRD update of line q from rho = 1 with populations n: the
+        plain ratio before switching and before the Jacobi step, [ndep][np],
+        points in frequency order."""
         n = np.ascontiguousarray(n, dtype=np.float64)
         m = np.zeros(1, np.int32)
         self._check(self._lib.rho_prd_kernel(self._p, col, q, _i(m), None, None, None, None))

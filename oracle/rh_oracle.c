@@ -15,9 +15,16 @@
  *     convergence on the maximum relative population change (1e-3).
  *   - Sect. 3.1 (pool mode): columns are handed out dynamically to workers
  *     (here: threads pulling column indices from a shared counter).
- * Readings where the paper is silent (formal-solver scheme, atom data,
- * background opacity, boundary conditions, Ng schedule) are listed in the
- * design notes and restated at each function.
+ * Readings where the paper is silent, each restated at the function that
+ * uses it: linear short characteristics (Olson & Kunasz 1987) as the formal
+ * solver; no incident radiation at the top and the diffusion approximation
+ * I = B + mu dB/dtau at the bottom; a hydrogen-like model atom (Kramers
+ * f-values and bound-free cross sections, van Regemorter and Seaton
+ * collisions); LTE H- bound-free, hydrogenic free-free and Thomson background;
+ * n_e fixed from Saha plus a metal floor; Ng of order 2 with uniform weights,
+ * delay 5, period 3; collisional-radiative switching by a decade per
+ * iteration; PRD switching eps = min(1, eps0 it^2); Ng and a Jacobi step on
+ * the PRD ratio rho.
  *
  * Parity status: every function is pinned by a test against closed forms,
  * limits or an independent library routine, except the overall multi-level
@@ -129,6 +136,11 @@ struct rho_ctx {
     int32_t *iters;
     uint8_t *status;
     double *dmax;
+    /* [ncol] per column the PRD kernels K and J-bar weights f of every PRD
+     * line, line after line ([N][np][np] then [N][np]); built by the first
+     * column_setup of the column and reused (they depend only on the atom
+     * and the column's temperatures) */
+    double **prdc;
 };
 typedef struct rho_ctx rho_ctx;
 
@@ -758,6 +770,11 @@ static void free_columns(rho_ctx *c)
 {
     free(c->z); free(c->T); free(c->nH); free(c->vz); free(c->ne); free(c->np);
     free(c->nstar); free(c->pops); free(c->iters); free(c->status); free(c->dmax);
+    if (c->prdc) {
+        for (int64_t col = 0; col < c->ncol; ++col) free(c->prdc[col]);
+        free(c->prdc);
+        c->prdc = NULL;
+    }
     c->z = c->T = c->nH = c->vz = c->ne = c->np = c->nstar = c->pops = c->dmax = NULL;
     c->iters = NULL;
     c->status = NULL;
@@ -838,6 +855,7 @@ int rho_load_columns(rho_ctx *c, int64_t ncol, int32_t ndep, const double *z, co
     c->ne = malloc(nd * 8); c->np = malloc(nd * 8);
     c->nstar = malloc(nd * L * 8); c->pops = malloc(nd * L * 8);
     c->iters = calloc(ncol, 4); c->status = malloc(ncol); c->dmax = calloc(ncol, 8);
+    if (c->at.nprd_line) c->prdc = calloc(ncol, sizeof(double *));
     memcpy(c->z, z, nd * 8); memcpy(c->T, T, nd * 8); memcpy(c->nH, nH, nd * 8); memcpy(c->vz, vz, nd * 8);
     for (int64_t col = 0; col < ncol; ++col) {
         c->status[col] = ST_NOTRUN;
@@ -903,6 +921,11 @@ typedef struct {
     /* partial redistribution */
     double *rho;      /* [nlam][N] psi/phi of the PRD line at each grid point (1 elsewhere) */
     double *Jp;       /* [nlam][N] angle-averaged mean intensity at the PRD points */
+    double *Dp;       /* [nlam][N] local derivative dJ/drho of the mean intensity at a PRD point
+                       * with respect to its own rho (through the line's emission, Psi*) */
+    double *U0;       /* [MAXACT][N] U of each active transition without the factor rho */
+    double *rplain;   /* [nlam][N] the last update's plain ratio r (before switching) */
+    double *rhist;    /* Ng history of rho at the PRD points [4][npt N], newest first */
     double *Pup, *Pdn;    /* [ntr][N] plain radiative rate coefficients (actual I, not I_eff) */
     double *prdK[MAXTR];   /* per PRD line [N][np][np]: normalised redistribution kernel */
     double *prdf[MAXTR];   /* per PRD line [N][np]: weights of J-bar */
@@ -929,6 +952,14 @@ static void work_alloc(work_t *w, const atom_t *a, int N)
     w->hist = malloc(4 * L * N * 8);
     w->rho = malloc(a->nlam * N * 8);
     w->Jp = malloc(a->nlam * N * 8);
+    w->Dp = malloc(a->nlam * N * 8);
+    w->U0 = malloc(MAXACT * N * 8);
+    w->rplain = malloc(a->nlam * N * 8);
+    {
+        size_t npt = 0;
+        for (int q = 0; q < a->nprd_line; ++q) npt += (size_t)a->prd_np[q];
+        w->rhist = malloc(4 * (npt > 0 ? npt : 1) * N * 8);
+    }
     w->Pup = malloc((size_t)a->ntr * N * 8);
     w->Pdn = malloc((size_t)a->ntr * N * 8);
     for (int64_t i = 0; i < a->nlam * N; ++i) w->rho[i] = 1.0;
@@ -946,6 +977,7 @@ static void work_free(work_t *w)
     free(w->Ieff); free(w->omlam); free(w->Sbg);
     free(w->Ut); free(w->hist);
     free(w->rho); free(w->Jp); free(w->Pup); free(w->Pdn);
+    free(w->Dp); free(w->U0); free(w->rplain); free(w->rhist);
     for (int q = 0; q < MAXTR; ++q) {
         if (w->prdK[q]) free(w->prdK[q]);
         if (w->prdf[q]) free(w->prdf[q]);
@@ -1049,6 +1081,17 @@ static void column_setup(const rho_ctx *c, int64_t col, work_t *w)
      * discrete normalisation makes a frequency-independent J give rho = 1),
      * and the weights of J-bar, f_j = H(a, x_j) w_j / sum (...); x in Doppler
      * units of the depth, static frame */
+    if (a->nprd_line && c->prdc && c->prdc[col]) {
+        const double *src = c->prdc[col];
+        for (int q = 0; q < a->nprd_line; ++q) {
+            size_t m = a->prd_np[q];
+            memcpy(w->prdK[q], src, sizeof(double) * N * m * m);
+            src += (size_t)N * m * m;
+            memcpy(w->prdf[q], src, sizeof(double) * N * m);
+            src += (size_t)N * m;
+        }
+        return;
+    }
     for (int q = 0; q < a->nprd_line; ++q) {
         int t = a->prd_t[q], m = a->prd_np[q];
         for (int k = 0; k < N; ++k) {
@@ -1073,26 +1116,84 @@ static void column_setup(const rho_ctx *c, int64_t col, work_t *w)
             }
         }
     }
+    if (a->nprd_line && c->prdc) {
+        size_t tot = 0;
+        for (int q = 0; q < a->nprd_line; ++q) tot += (size_t)N * a->prd_np[q] * (a->prd_np[q] + 1);
+        double *dst = malloc(sizeof(double) * tot);
+        if (dst) {
+            c->prdc[col] = dst;
+            for (int q = 0; q < a->nprd_line; ++q) {
+                size_t m = a->prd_np[q];
+                memcpy(dst, w->prdK[q], sizeof(double) * N * m * m);
+                dst += (size_t)N * m * m;
+                memcpy(dst, w->prdf[q], sizeof(double) * N * m);
+                dst += (size_t)N * m;
+            }
+        }
+    }
+}
+
+/* PRD switching (Sect. 2.3, Eq. 1): rho' = eps rho + (1 - eps).  The paper
+ * starts eps at a small eps0, raises it with the square of the iteration
+ * number until it reaches unity, and states that this takes about
+ * eps0^{-1/2} iterations; read as eps_it = min(1, eps0 it^2) for the rho that
+ * the formal solution of iteration it uses (eps_1 = eps0; the literal
+ * compounding product eps0 1^2 2^2 ... 3^2 would reach unity far sooner than
+ * eps0^{-1/2}).  eps0 <= 0 switches it off (eps = 1). */
+double rho_prd_switch_eps(double eps0, int32_t it)
+{
+    if (!(eps0 > 0.0)) return 1.0;
+    return fmin(1.0, eps0 * (double)it * (double)it);
+}
+
+/* Collisional-radiative switching (Sect. 2.3, after Hummer & Voels 1988):
+ * the collisional rates of iteration it are multiplied by
+ * max(1, f0 10^{-(it-1)}), so the first iteration uses f0 and the factor
+ * falls by a decade per iteration until it reaches unity (the paper gives
+ * only the range of f0, 10 to 1e5, and "decreased until it reaches unity").
+ * f0 <= 1 switches it off. */
+double rho_crsw_factor(double f0, int32_t it)
+{
+    if (!(f0 > 1.0)) return 1.0;
+    double f = f0 * pow(10.0, -(double)(it - 1));
+    return f > 1.0 ? f : 1.0;
 }
 
 /* rho = psi/phi of every PRD line after a solve (Uitenbroek 2001, Eq. 14,
  * angle-averaged, coherent scattering in the atom's frame, gamma = 1):
- *   rho_i = 1 + F [sum_j K_ij J_j / Jbar - 1],  Jbar = sum_j f_j J_j,
+ *   r_i = 1 + F [sum_j K_ij J_j / Jbar - 1],  Jbar = sum_j f_j J_j,
  *   F = n_l R_lu / sum_k n_k P_ku,
  * the fraction of the upper level's supply that is absorption in the line,
  * with the actual (not preconditioned) radiative rates of the formal solution
  * just done plus collisions and the populations of the next iteration; at
  * statistical equilibrium sum_k n_k P_ku = n_u P_u and R_lu = B_lu Jbar, the
- * usual n_l B_lu (sum K J - Jbar)/(n_u P_u), and F in [0, 1] keeps rho >= 0
- * on the way there.  Then PRD switching (Eq. 1) rho' = eps rho + (1 - eps),
- * eps = min(1, eps0 it^2) for the next iteration it (eps0 <= 0: eps = 1),
- * and the new rho is the mean of rho' and the previous rho (under-relaxation:
- * the plain lagged update diverged without Ng on thick Lyman alpha wings). */
-static void prd_update(const rho_ctx *c, int64_t col, work_t *w, const double *n, int it_next, double eps0)
+ * usual n_l B_lu (sum K J - Jbar)/(n_u P_u), and F in [0, 1] keeps r >= 0.
+ * PRD switching (Eq. 1): r' = eps r + (1 - eps), eps = rho_prd_switch_eps(eps0,
+ * it_next) for the iteration it_next that uses the new rho.
+ *
+ * The map rho -> r' is iterated with the formal solution in between: in
+ * optically thick wings, where the redistribution is coherent, that is a
+ * Lambda iteration on the scattered light and converges at the pace of one.
+ * With Ng acceleration (jacobi = 1) the update takes one Jacobi (diagonal
+ * Newton) step,
+ *   rho_new = rho + (r' - rho) / max(1 - eps g_ii, RHO_JACOBI_FLOOR),
+ *   g_ii = d r_i / d rho_i = F D_i (K_ii - f_i sum_j K_ij J_j / Jbar) / Jbar,
+ * D_i = dJ_i/drho_i the local derivative of the mean intensity through the
+ * line's own emission (Psi*, accumulated in rate_matrix): the ALI idea applied
+ * to rho.  The floor bounds the step at 50 times the plain one where the
+ * local derivative nears unity; Ng acceleration of the rho sequence (Sect.
+ * 2.3: Ng "both for the Lambda-iterations and the PRD iterations", applied by
+ * the caller) controls the oscillating mode of the coupled update.  Without
+ * Ng (jacobi = 0) the plain update is damped instead, rho_new = (rho + r')/2:
+ * undamped, it oscillates and diverges in thick Lyman alpha wings.  Either
+ * way the fixed point is rho = r'. */
+#define RHO_JACOBI_FLOOR 0.02
+static void prd_update(const rho_ctx *c, int64_t col, work_t *w, const double *n, int it_next, double eps0,
+                       int jacobi)
 {
     const atom_t *a = &c->at;
     int N = c->ndep, L = a->nlev;
-    double eps = eps0 > 0.0 ? fmin(1.0, eps0 * (double)it_next * (double)it_next) : 1.0;
+    double eps = rho_prd_switch_eps(eps0, it_next);
     (void)col;
     for (int q = 0; q < a->nprd_line; ++q) {
         int t = a->prd_t[q], m = a->prd_np[q], l = a->tl[t], u = a->tu[t];
@@ -1110,15 +1211,35 @@ static void prd_update(const rho_ctx *c, int64_t col, work_t *w, const double *n
             double jbar = 0.0;
             for (int j = 0; j < m; ++j) jbar += f[j] * w->Jp[(size_t)a->prd_pts[q][j] * N + k];
             for (int i = 0; i < m; ++i) {
+                size_t gi = (size_t)a->prd_pts[q][i] * N + k;
                 double sr = 0.0;
                 for (int j = 0; j < m; ++j) sr += K[i * m + j] * w->Jp[(size_t)a->prd_pts[q][j] * N + k];
                 double r = 1.0 + F * (sr / jbar - 1.0);
-                /* under-relaxed by 1/2: the lagged update alone diverged without Ng */
-                double *rp = &w->rho[(size_t)a->prd_pts[q][i] * N + k];
-                *rp = 0.5 * *rp + 0.5 * (eps * r + (1.0 - eps));
+                w->rplain[gi] = r;
+                double den = 2.0;
+                if (jacobi) {
+                    double g = F * (K[i * m + i] - f[i] * sr / jbar) * w->Dp[gi] / jbar;
+                    den = 1.0 - eps * g;
+                    if (den < RHO_JACOBI_FLOOR) den = RHO_JACOBI_FLOOR;
+                }
+                w->rho[gi] += ((eps * r + (1.0 - eps)) - w->rho[gi]) / den;
             }
         }
     }
+}
+
+/* rho of every PRD point and depth gathered into (dir 0) or scattered from
+ * (dir 1) one vector, lines and points in order, depth fastest */
+static void rho_vector(const atom_t *a, int N, double *rho, double *v, int dir)
+{
+    size_t p = 0;
+    for (int q = 0; q < a->nprd_line; ++q)
+        for (int i = 0; i < a->prd_np[q]; ++i)
+            for (int k = 0; k < N; ++k, ++p) {
+                double *r = rho + (size_t)a->prd_pts[q][i] * N + k;
+                if (dir == 0) v[p] = *r;
+                else *r = v[p];
+            }
 }
 
 /* per-transition V_lu, V_ul, U_ul and chi_t on all depths for grid point i, ray (m,d) */
@@ -1131,6 +1252,7 @@ static void transition_coeffs(const rho_ctx *c, int64_t col, const work_t *w, co
     for (int s = 0; s < a->nact[i]; ++s) {
         int t = a->act[i * MAXACT + s], l = a->tl[t], u = a->tu[t];
         double *Vlu = w->Vlu + s * N, *Vul = w->Vul + s * N, *U = w->Ut + s * N, *ch = w->chit + s * N;
+        double *U0 = w->U0 + s * N;
         if (a->kind[t] == 0) {
             const double *p = w->prof + (((size_t)a->prof_slot[i * MAXACT + s] * a->nmu + m) * 2 + d) * N;
             double h4 = HPLANCK * nu / (4.0 * PI_D);
@@ -1140,7 +1262,8 @@ static void transition_coeffs(const rho_ctx *c, int64_t col, const work_t *w, co
                 double r = a->prd[t] ? w->rho[i * N + k] : 1.0;
                 Vlu[k] = h4 * a->Blu[t] * p[k];
                 Vul[k] = a->g[l] / a->g[u] * Vlu[k] * r;
-                U[k] = h4 * a->A[t] * p[k] * r;
+                U0[k] = h4 * a->A[t] * p[k];
+                U[k] = U0[k] * r;
             }
         } else {
             double r = a->nu0[t] / nu;
@@ -1151,6 +1274,7 @@ static void transition_coeffs(const rho_ctx *c, int64_t col, const work_t *w, co
                 Vlu[k] = alpha;
                 Vul[k] = G * w->ex[i * N + k] * alpha;
                 U[k] = tw * Vul[k];
+                U0[k] = U[k];
             }
         }
         for (int k = 0; k < N; ++k) ch[k] = n[l * N + k] * Vlu[k] - n[u * N + k] * Vul[k];
@@ -1214,6 +1338,7 @@ static void rate_matrix(const rho_ctx *c, int64_t col, work_t *w, const double *
     memset(G, 0, sizeof(double) * N * L * L);
     if (a->nprd_line) {
         memset(w->Jp, 0, sizeof(double) * a->nlam * N);
+        memset(w->Dp, 0, sizeof(double) * a->nlam * N);
         memset(w->Pup, 0, sizeof(double) * a->ntr * N);
         memset(w->Pdn, 0, sizeof(double) * a->ntr * N);
     }
@@ -1225,8 +1350,19 @@ static void rate_matrix(const rho_ctx *c, int64_t col, work_t *w, const double *
             for (int d = 0; d < 2; ++d) {
                 transition_coeffs(c, col, w, n, i, m, d);
                 if (mode != 2) formal_ray(c, col, w, n, i, m, d);
-                if (prd_pt && mode != 2)
+                if (prd_pt && mode != 2) {
                     for (int k = 0; k < N; ++k) w->Jp[i * N + k] += 0.5 * a->wmu[m] * w->I[k];
+                    /* dI_k/drho_k = Psi*_k n_u U0_k of the PRD line (its emission
+                     * is the only term of S that rho multiplies; stimulated
+                     * emission in chi is left out of this derivative) */
+                    for (int s = 0; s < a->nact[i]; ++s) {
+                        int t = a->act[i * MAXACT + s];
+                        if (!a->prd[t]) continue;
+                        for (int k = 0; k < N; ++k)
+                            w->Dp[i * N + k] += 0.5 * a->wmu[m] * (w->lam[k] / w->chi[k]) *
+                                                n[a->tu[t] * N + k] * w->U0[s * N + k];
+                    }
+                }
                 for (int k = 0; k < N; ++k) {
                     double psi = (mode == 0) ? w->lam[k] / w->chi[k] : 0.0;
                     double Ieff = (mode == 2) ? 0.0 : (mode == 0 ? w->Ieff[k] : w->I[k]);
@@ -1509,7 +1645,9 @@ static void iterate_column(rho_ctx *c, int64_t col, const rho_iter_opts *o, work
     memcpy(Cbase, w->C, sizeof(double) * N * L * L);
     if (o->start == 0)
         memcpy(n, c->nstar + (size_t)col * nv, nv * 8);
-    int hcount = 0, it = 0, status = ST_MAXITER;
+    int hcount = 0, rcount = 0, it = 0, status = ST_MAXITER;
+    size_t nrv = 0;   /* length of the rho vector (PRD points x depths) */
+    for (int q = 0; q < a->nprd_line; ++q) nrv += (size_t)a->prd_np[q] * N;
     double dmax = INFINITY;
     for (int64_t q = 0; q < a->nlam * N; ++q) w->rho[q] = 1.0;   /* PRD starts as CRD */
     if (o->start == 3 || o->start == 4) {
@@ -1525,10 +1663,8 @@ static void iterate_column(rho_ctx *c, int64_t col, const rho_iter_opts *o, work
         }
     }
     for (it = 1; it <= o->maxiter; ++it) {
-        /* collisional-radiative switching (Hummer & Voels 1988): C scaled by
-         * max(1, f0 10^{-(it-1)}) */
-        double fcr = o->crsw_init > 1.0 ? o->crsw_init * pow(10.0, -(it - 1)) : 1.0;
-        if (fcr < 1.0) fcr = 1.0;
+        /* collisional-radiative switching (Hummer & Voels 1988) */
+        double fcr = rho_crsw_factor(o->crsw_init, it);
         for (int q = 0; q < N * L * L; ++q) w->C[q] = Cbase[q] * fcr;
         rate_matrix(c, col, w, n, 0);
         int st = stateq(c, col, w, n, nnew);
@@ -1563,7 +1699,29 @@ static void iterate_column(rho_ctx *c, int64_t col, const rho_iter_opts *o, work
         }
         memcpy(n, nnew, nv * 8);
         if (converged) { status = ST_CONV; break; }
-        if (a->nprd_line) prd_update(c, col, w, n, it + 1, o->prd_eps0);
+        if (a->nprd_line) {
+            prd_update(c, col, w, n, it + 1, o->prd_eps0, o->ng_order == 2);
+            /* Ng acceleration of the PRD iterations (Sect. 2.3), on the rho
+             * vector with its own history and the populations' schedule; an
+             * extrapolation with a negative rho is rejected */
+            memmove(w->rhist + nrv, w->rhist, 3 * nrv * 8);
+            rho_vector(a, N, w->rho, w->rhist, 0);
+            if (rcount < 4) ++rcount;
+            if (o->ng_order == 2 && it >= o->ng_delay && rcount >= 4 && (it - o->ng_delay) % o->ng_period == 0) {
+                double *acc = malloc(nrv * 8);
+                if (!ng2_w(nrv, w->rhist, w->rhist + nrv, w->rhist + 2 * nrv, w->rhist + 3 * nrv, acc, 0)) {
+                    int ok = 1;
+                    for (size_t q = 0; q < nrv; ++q)
+                        if (!(isfinite(acc[q]) && acc[q] >= 0.0)) { ok = 0; break; }
+                    if (ok) {
+                        memcpy(w->rhist, acc, nrv * 8);
+                        rho_vector(a, N, w->rho, acc, 1);
+                        rcount = 1;
+                    }
+                }
+                free(acc);
+            }
+        }
     }
     if (it > o->maxiter) it = o->maxiter;
     c->iters[col] = it;
@@ -1728,7 +1886,8 @@ int rho_column_background(rho_ctx *c, int64_t col, double *chi_out)
 }
 
 /* One PRD update of line q in column col from rho = 1 with populations n
- * and the formal solution they give, without switching or under-relaxation:
+ * and the formal solution they give, the plain ratio before switching and
+ * before the Jacobi step:
  * r_out[N][np] = 1 + F (sum_j K_ij J_j / Jbar - 1), points in frequency order */
 int rho_prd_update_ratio(rho_ctx *c, int64_t col, const double *n, int32_t q, double *r_out)
 {
@@ -1740,10 +1899,9 @@ int rho_prd_update_ratio(rho_ctx *c, int64_t col, const double *n, int32_t q, do
     work_alloc(&w, a, N);
     column_setup(c, col, &w);
     rate_matrix(c, col, &w, n, 1);
-    prd_update(c, col, &w, n, 1, 0.0);
-    /* prd_update returns the mean of the previous rho (1) and the new value */
+    prd_update(c, col, &w, n, 1, 0.0, 0);
     for (int k = 0; k < N; ++k)
-        for (int j = 0; j < m; ++j) r_out[(size_t)k * m + j] = 2.0 * w.rho[(size_t)a->prd_pts[q][j] * N + k] - 1.0;
+        for (int j = 0; j < m; ++j) r_out[(size_t)k * m + j] = w.rplain[(size_t)a->prd_pts[q][j] * N + k];
     work_free(&w);
     return 0;
 }

@@ -868,6 +868,27 @@ def _prd_atom(prd=True):
     return a
 
 
+_PRD_ORACLES = {}
+
+
+def _prd_run(orc, prd, cols, **kw):
+    """Iterate the PRD (or CRD) test atom on cols from LTE; one oracle per
+    atom and column set, so its redistribution kernels are built once."""
+    key = (prd, id(cols))
+    if key not in _PRD_ORACLES:
+        o = orc.Oracle()
+        o.setup_atom(_prd_atom(prd))
+        o.load_columns(cols)
+        _PRD_ORACLES[key] = (o, cols)
+    o = _PRD_ORACLES[key][0]
+    o.iterate(**kw)
+    return o.populations()
+
+
+_COL16 = rh_synth.chromosphere_column(ndep=16)
+_CUBE32 = rh_synth.subset(rh_synth.chromosphere_cube(nx=16, ny=16, ndep=32, seed=3), [0, 5])
+
+
 def test_prd_emission_profile_is_non_negative(orc):
     """One PRD update (Sect. 2.3, after Uitenbroek 2001, Eq. 14) from the
     converged CRD populations of the chromosphere column, without switching
@@ -912,16 +933,151 @@ def test_prd_reduces_to_crd_when_collisions_dominate(orc):
 
 
 def test_prd_converges_and_differs_from_crd(orc):
-    cols = rh_synth.subset(rh_synth.chromosphere_cube(nx=16, ny=16, ndep=32, seed=3), [0, 5])
     res = {}
     for prd in (False, True):
-        o = orc.Oracle()
-        o.setup_atom(_prd_atom(prd))
-        o.load_columns(cols)
-        o.iterate(maxiter=400, tol=1e-3)
-        n, it, st, _ = o.populations()
+        n, it, st, _ = _prd_run(orc, prd, _CUBE32, maxiter=400, tol=1e-3)
         assert np.all(st == 0), (prd, st)
         res[prd] = n
         # conservation holds with PRD too
-        assert np.allclose(n.sum(axis=1), cols["nH"], rtol=1e-12)
+        assert np.allclose(n.sum(axis=1), _CUBE32["nH"], rtol=1e-12)
     assert np.max(np.abs(res[True] / res[False] - 1)) > 1e-2
+
+
+# ---------------------------------------------------------------- switching schedules (Sect. 2.3)
+def test_prd_switching_schedule(orc):
+    """PRD switching (Eq. 1): eps starts at eps0 and reaches unity after
+    about eps0^{-1/2} iterations, the count the paper states; it never
+    decreases, and eps0 <= 0 leaves PRD unswitched (eps = 1)."""
+    for eps0 in (0.05, 0.02, 0.003, 0.3):
+        eps = [orc.prd_switch_eps(eps0, it) for it in range(1, 60)]
+        assert eps[0] == eps0
+        first = 1 + next(i for i, e in enumerate(eps) if e == 1.0)
+        assert first == int(np.ceil(eps0 ** -0.5))
+        assert all(b >= a for a, b in zip(eps, eps[1:]))
+        assert 0 < min(eps) and max(eps) == 1.0
+    assert orc.prd_switch_eps(0.0, 1) == 1.0 and orc.prd_switch_eps(-1.0, 3) == 1.0
+
+
+def test_collisional_radiative_switching_schedule(orc):
+    """CR switching: the first iteration multiplies the collisional rates by
+    f0, the factor falls until it reaches unity (after log10 f0 decades) and
+    stays there; f0 <= 1 is off."""
+    for f0, n1 in ((1e3, 4), (1e5, 6), (10.0, 2)):
+        f = [orc.crsw_factor(f0, it) for it in range(1, 12)]
+        assert f[0] == f0
+        assert all(b <= a for a, b in zip(f, f[1:])) and min(f) == 1.0
+        assert 1 + next(i for i, v in enumerate(f) if v == 1.0) == n1
+    assert orc.crsw_factor(1.0, 1) == 1.0 and orc.crsw_factor(0.5, 2) == 1.0
+
+
+def _collision_matrix(Cm):
+    """Rate-matrix form of the collisional rates C[k][p][q] (p -> q): entry
+    [q][p] = C_pq, diagonal minus the column sum."""
+    A = np.transpose(Cm, (0, 2, 1)).copy()
+    L = A.shape[1]
+    for q in range(L):
+        A[:, q, q] = 0.0
+    A[:, range(L), range(L)] = -A.sum(axis=1)
+    return A
+
+
+def _solve_rate_equations(A, nold, nH):
+    """Statistical equilibrium A n = 0 with sum_i n_i = n_H at every depth,
+    as the least-squares solution of the stacked system (no row is dropped,
+    so no row choice enters), unknowns scaled by the old populations."""
+    N, L, _ = A.shape
+    out = np.zeros((L, N))
+    for k in range(N):
+        s = nold[:, k]
+        M = np.vstack([A[k] * s[None, :], s[None, :]])
+        rhs = np.zeros(L + 1)
+        rhs[-1] = nH[k]
+        rs = np.max(np.abs(M), axis=1)
+        y = np.linalg.lstsq(M / rs[:, None], rhs / rs, rcond=None)[0]
+        out[:, k] = y * s
+    return out
+
+
+def test_crsw_iterations_use_the_scaled_collisions(orc):
+    """CR switching with f0 = 1e3: the first iteration is the preconditioned
+    rate equations at the LTE start with C x 1e3, the second the same at the
+    first iterate with C x 1e2 (rate matrix of the oracle, collisions scaled
+    and rate equations solved here)."""
+    cols = rh_synth.chromosphere_column()
+    o = orc.Oracle()
+    o.setup_atom(rh_synth.hydrogen_like_atom())
+    o.load_columns(cols)
+    nH = cols["nH"][0]
+    Cm = _collision_matrix(o.collision_rates(0))
+    ns, _ = o.lte()
+    prev = ns[0]
+    for it, f in ((1, 1e3), (2, 1e2)):
+        o.load_columns(cols)
+        o.iterate(maxiter=it, tol=0.0, ng_order=0, crsw_init=1e3)
+        n_it = o.populations()[0][0]
+        A = o.rate_matrix(0, prev, 0) + (f - 1.0) * Cm
+        ref = _solve_rate_equations(A, prev, nH)
+        assert np.max(np.abs(n_it / ref - 1)) < 1e-9, it
+        # unscaled collisions give a different iterate
+        ref1 = _solve_rate_equations(o.rate_matrix(0, prev, 0), prev, nH)
+        assert np.max(np.abs(n_it / ref1 - 1)) > 1e-3
+        prev = n_it
+
+
+def test_crsw_keeps_the_fixed_point(orc):
+    """Converged to 1e-12 with and without CR switching (f0 = 1e3, with and
+    without Ng), the populations agree to 1e-10."""
+    cols = rh_synth.subset(rh_synth.chromosphere_cube(nx=16, ny=16, seed=3), [0, 6, 7])
+    res = []
+    for f0, ng in ((1.0, 2), (1e3, 0), (1e3, 2)):
+        o = orc.Oracle()
+        o.setup_atom(rh_synth.hydrogen_like_atom())
+        o.load_columns(cols)
+        o.iterate(maxiter=3000, tol=1e-12, crsw_init=f0, ng_order=ng)
+        n, it, st, _ = o.populations()
+        assert np.all(st == 0)
+        res.append(n)
+    for n in res[1:]:
+        assert np.max(np.abs(n / res[0] - 1)) < 1e-10
+
+
+def test_prd_switching_zero_eps_is_crd(orc):
+    """Eq. 1 with eps = 0 gives psi = phi, complete redistribution: with eps0
+    = 1e-300 every iterate equals the CRD iterate bit for bit, with and
+    without Ng."""
+    for ng in (0, 2):
+        for it in (2, 9):
+            a = _prd_run(orc, True, _COL16, maxiter=it, tol=0.0, ng_order=ng, prd_eps0=1e-300)[0]
+            b = _prd_run(orc, False, _COL16, maxiter=it, tol=0.0, ng_order=ng)[0]
+            assert np.array_equal(a, b), (ng, it)
+
+
+def test_prd_switching_applies_to_the_iteration_that_uses_rho(orc):
+    """The first rho comes from the formal solution of iteration 1 and is
+    used by iteration 2, whose eps is eps0 2^2: eps0 = 1/4 switches nothing,
+    so every iterate equals the unswitched one bit for bit, and eps0 = 0.2
+    (eps_2 = 0.8) does not."""
+    for ng in (0, 2):
+        for it in (2, 3, 8):
+            a = _prd_run(orc, True, _COL16, maxiter=it, tol=0.0, ng_order=ng, prd_eps0=0.25)[0]
+            b = _prd_run(orc, True, _COL16, maxiter=it, tol=0.0, ng_order=ng, prd_eps0=0.0)[0]
+            c = _prd_run(orc, True, _COL16, maxiter=it, tol=0.0, ng_order=ng, prd_eps0=0.2)[0]
+            assert np.array_equal(a, b), (ng, it)
+            if it > 2:
+                assert np.max(np.abs(c / b - 1)) > 1e-9, (ng, it)
+
+
+def test_prd_switching_and_ng_keep_the_fixed_point(orc):
+    """Switching, Ng on the PRD ratio and its Jacobi step change the path,
+    not the fixed point: converged to 1e-11 with eps0 = 0, with eps0 = 0.05
+    and with another Ng schedule, the populations agree to 1e-10; the PRD
+    iteration reaches 1e-11 in a few hundred iterations."""
+    ref = None
+    for kw in (dict(prd_eps0=0.0), dict(prd_eps0=0.05), dict(prd_eps0=0.0, ng_delay=8, ng_period=4)):
+        n, it, st, _ = _prd_run(orc, True, _CUBE32, maxiter=1500, tol=1e-11, **kw)
+        assert np.all(st == 0), kw
+        assert np.all(it < 1000), (kw, it)
+        if ref is None:
+            ref = n
+        else:
+            assert np.max(np.abs(n / ref - 1)) < 1e-10, kw
