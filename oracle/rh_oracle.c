@@ -1037,6 +1037,118 @@ static double line_profile(const atom_t *a, int t, double nu, double T, double v
     return rho_voigt(adamp, v) / (sqrt(PI_D) * dnuD);
 }
 
+/* Partial redistribution: the redistribution kernel of PRD line q at depth k
+ * of column col on the line's points, K[i][j] = R(x_j, x_i) w_j / sum_j (...)
+ * (the discrete normalisation makes a frequency-independent J give rho = 1),
+ * and the weights of J-bar, f_j = H(a, x_j) w_j / sum (...); x in Doppler
+ * units of the depth, static frame.  R is symmetric in its arguments, so
+ * each unordered pair is evaluated once. */
+static void prd_kernel_depth(const rho_ctx *c, int64_t col, int q, int k, double *K, double *f)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep, t = a->prd_t[q], m = a->prd_np[q];
+    double T = c->T[col * N + k];
+    double dnuD = a->nu0[t] / CLIGHT * sqrt(2.0 * KBOLTZ * T / a->mass);
+    double ad = damping(a, t, k, N);
+    double fs = 0.0;
+    for (int j = 0; j < m; ++j) {
+        double xj = (a->nu[a->prd_pts[q][j]] - a->nu0[t]) / dnuD;
+        f[j] = rho_voigt(ad, xj) * a->prd_w[q][j];
+        fs += f[j];
+    }
+    for (int j = 0; j < m; ++j) f[j] /= fs;
+    for (int i = 0; i < m; ++i) {
+        double xi = (a->nu[a->prd_pts[q][i]] - a->nu0[t]) / dnuD;
+        for (int j = i; j < m; ++j) {
+            double xj = (a->nu[a->prd_pts[q][j]] - a->nu0[t]) / dnuD;
+            double r = rho_r2a(ad, xj, xi);
+            K[i * m + j] = r * a->prd_w[q][j];
+            K[j * m + i] = r * a->prd_w[q][i];
+        }
+    }
+    for (int i = 0; i < m; ++i) {
+        double rs = 0.0;
+        for (int j = 0; j < m; ++j) rs += K[i * m + j];
+        for (int j = 0; j < m; ++j) K[i * m + j] /= rs;
+    }
+}
+
+/* offsets of line q's kernel and weights inside a column's cache entry */
+static size_t prd_cache_koff(const atom_t *a, int N, int q)
+{
+    size_t off = 0;
+    for (int p = 0; p < q; ++p) off += (size_t)N * a->prd_np[p] * (a->prd_np[p] + 1);
+    return off;
+}
+
+static double *prd_cache_alloc(const rho_ctx *c, int64_t col)
+{
+    const atom_t *a = &c->at;
+    if (!c->prdc) return NULL;
+    if (!c->prdc[col]) c->prdc[col] = malloc(sizeof(double) * prd_cache_koff(a, c->ndep, a->nprd_line));
+    return c->prdc[col];
+}
+
+/* build the cache entry of one column (one thread) */
+static void prd_cache_column(const rho_ctx *c, int64_t col)
+{
+    const atom_t *a = &c->at;
+    int N = c->ndep;
+    double *e = prd_cache_alloc(c, col);
+    if (!e) return;
+    for (int q = 0; q < a->nprd_line; ++q) {
+        size_t m = a->prd_np[q];
+        double *K = e + prd_cache_koff(a, N, q), *f = K + (size_t)N * m * m;
+        for (int k = 0; k < N; ++k) prd_kernel_depth(c, col, q, k, K + (size_t)k * m * m, f + (size_t)k * m);
+    }
+}
+
+/* build the cache entries of every column that has none, in parallel over
+ * (column, line, depth) */
+typedef struct {
+    const rho_ctx *c;
+    const int64_t *cols;   /* the columns to build */
+    int64_t ntask, next;
+    pthread_mutex_t mu;
+} kpool_t;
+
+static void *kpool_worker(void *arg)
+{
+    kpool_t *p = arg;
+    const rho_ctx *c = p->c;
+    const atom_t *a = &c->at;
+    int N = c->ndep, nq = a->nprd_line;
+    for (;;) {
+        pthread_mutex_lock(&p->mu);
+        int64_t tk = p->next++;
+        pthread_mutex_unlock(&p->mu);
+        if (tk >= p->ntask) break;
+        int64_t col = p->cols[tk / ((int64_t)nq * N)];
+        int q = (int)(tk / N % nq), k = (int)(tk % N);
+        size_t m = a->prd_np[q];
+        double *K = c->prdc[col] + prd_cache_koff(a, N, q), *f = K + (size_t)N * m * m;
+        prd_kernel_depth(c, col, q, k, K + (size_t)k * m * m, f + (size_t)k * m);
+    }
+    return NULL;
+}
+
+static void prd_cache_build(rho_ctx *c, int nthreads)
+{
+    const atom_t *a = &c->at;
+    if (!a->nprd_line || !c->prdc) return;
+    int64_t *cols = malloc(sizeof(int64_t) * c->ncol), n = 0;
+    for (int64_t col = 0; col < c->ncol; ++col)
+        if (!c->prdc[col] && prd_cache_alloc(c, col)) cols[n++] = col;
+    if (n) {
+        kpool_t p = {c, cols, n * a->nprd_line * c->ndep, 0, PTHREAD_MUTEX_INITIALIZER};
+        pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+        for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, kpool_worker, &p);
+        for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+        free(th);
+    }
+    free(cols);
+}
+
 static void column_setup(const rho_ctx *c, int64_t col, work_t *w)
 {
     const atom_t *a = &c->at;
@@ -1076,13 +1188,12 @@ static void column_setup(const rho_ctx *c, int64_t col, work_t *w)
         for (int l = 0; l < L; ++l) ns[l] = c->nstar[((size_t)col * L + l) * N + k];
         collision_rates(a, T[k], ne[k], ns, w->C + (size_t)k * L * L);
     }
-    /* partial redistribution: per PRD line and depth the redistribution
-     * kernel on the line's points, K[i][j] = R(x_j, x_i) w_j / sum_j (...) (the
-     * discrete normalisation makes a frequency-independent J give rho = 1),
-     * and the weights of J-bar, f_j = H(a, x_j) w_j / sum (...); x in Doppler
-     * units of the depth, static frame */
-    if (a->nprd_line && c->prdc && c->prdc[col]) {
-        const double *src = c->prdc[col];
+    /* partial redistribution: the kernels of every PRD line and depth
+     * (prd_kernel_depth), from the column's cache entry */
+    if (!a->nprd_line) return;
+    if (!(c->prdc && c->prdc[col])) prd_cache_column(c, col);
+    const double *src = c->prdc ? c->prdc[col] : NULL;
+    if (src) {
         for (int q = 0; q < a->nprd_line; ++q) {
             size_t m = a->prd_np[q];
             memcpy(w->prdK[q], src, sizeof(double) * N * m * m);
@@ -1090,46 +1201,11 @@ static void column_setup(const rho_ctx *c, int64_t col, work_t *w)
             memcpy(w->prdf[q], src, sizeof(double) * N * m);
             src += (size_t)N * m;
         }
-        return;
-    }
-    for (int q = 0; q < a->nprd_line; ++q) {
-        int t = a->prd_t[q], m = a->prd_np[q];
-        for (int k = 0; k < N; ++k) {
-            double dnuD = a->nu0[t] / CLIGHT * sqrt(2.0 * KBOLTZ * T[k] / a->mass);
-            double ad = damping(a, t, k, N);
-            double *K = w->prdK[q] + (size_t)k * m * m, *f = w->prdf[q] + (size_t)k * m;
-            double fs = 0.0;
-            for (int j = 0; j < m; ++j) {
-                double xj = (a->nu[a->prd_pts[q][j]] - a->nu0[t]) / dnuD;
-                f[j] = rho_voigt(ad, xj) * a->prd_w[q][j];
-                fs += f[j];
-            }
-            for (int j = 0; j < m; ++j) f[j] /= fs;
-            for (int i = 0; i < m; ++i) {
-                double xi = (a->nu[a->prd_pts[q][i]] - a->nu0[t]) / dnuD, rs = 0.0;
-                for (int j = 0; j < m; ++j) {
-                    double xj = (a->nu[a->prd_pts[q][j]] - a->nu0[t]) / dnuD;
-                    K[i * m + j] = rho_r2a(ad, xj, xi) * a->prd_w[q][j];
-                    rs += K[i * m + j];
-                }
-                for (int j = 0; j < m; ++j) K[i * m + j] /= rs;
-            }
-        }
-    }
-    if (a->nprd_line && c->prdc) {
-        size_t tot = 0;
-        for (int q = 0; q < a->nprd_line; ++q) tot += (size_t)N * a->prd_np[q] * (a->prd_np[q] + 1);
-        double *dst = malloc(sizeof(double) * tot);
-        if (dst) {
-            c->prdc[col] = dst;
-            for (int q = 0; q < a->nprd_line; ++q) {
-                size_t m = a->prd_np[q];
-                memcpy(dst, w->prdK[q], sizeof(double) * N * m * m);
-                dst += (size_t)N * m * m;
-                memcpy(dst, w->prdf[q], sizeof(double) * N * m);
-                dst += (size_t)N * m;
-            }
-        }
+    } else {
+        for (int q = 0; q < a->nprd_line; ++q)
+            for (int k = 0; k < N; ++k)
+                prd_kernel_depth(c, col, q, k, w->prdK[q] + (size_t)k * a->prd_np[q] * a->prd_np[q],
+                                 w->prdf[q] + (size_t)k * a->prd_np[q]);
     }
 }
 
@@ -1773,6 +1849,7 @@ int rho_iterate(rho_ctx *c, const rho_iter_opts *o, rho_iter_stats *st, int32_t 
     if (nthreads < 1) nthreads = 1;
     struct timespec t0, t1;
     clock_gettime(CLOCK_MONOTONIC, &t0);
+    prd_cache_build(c, nthreads);
     pool_t p = {c, o, 0, PTHREAD_MUTEX_INITIALIZER, 0.0};
     pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
     for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, pool_worker, &p);
