@@ -81,19 +81,21 @@ struct KParams {
 
 // Per-block PRD scratch: in R, the redistribution kernels K [sum np^2][N] (per
 // line [k][i][j]), then per PRD point [npp][N] the J-bar weights f, the mean
-// intensity J and rho, then the plain-rate accumulators [pacc][N]; in FP64
-// the supply fraction F and J-bar per line [nprd][N].
+// intensity J, rho and D = dJ/drho (the derivative of J through the line's own
+// emission), then the plain-rate accumulators [pacc][N]; in FP64 the supply
+// fraction F and J-bar per line [nprd][N], then the Ng history of rho
+// [4][npp][N] (newest first).
 template <typename R>
 struct PrdScr {
-    R *K, *f, *J, *rho, *plain;
-    double *F, *Jbar;
+    R *K, *f, *J, *rho, *D, *plain;
+    double *F, *Jbar, *hist;
 };
 template <typename R>
 __host__ __device__ inline size_t prd_bytes(const DevAtom &A, int N)
 {
-    size_t r = sizeof(R) * ((size_t)A.prd_koff[A.nprd] * N + 3 * (size_t)A.npp * N + (size_t)A.pacc * N);
+    size_t r = sizeof(R) * ((size_t)A.prd_koff[A.nprd] * N + 4 * (size_t)A.npp * N + (size_t)A.pacc * N);
     r = (r + 255) & ~(size_t)255;
-    return r + sizeof(double) * 2 * (size_t)A.nprd * N + 256;
+    return r + sizeof(double) * (2 * (size_t)A.nprd * N + 4 * (size_t)A.npp * N) + 256;
 }
 // Per-block profile cache: the line profile phi (Voigt H(a, v) times its
 // normalisation and 1/Doppler width, v including the ray's Doppler shift)
@@ -121,11 +123,14 @@ __device__ inline PrdScr<R> prd_carve(char *base, const DevAtom &A, int N)
     r += (size_t)A.npp * N;
     q.rho = r;
     r += (size_t)A.npp * N;
+    q.D = r;
+    r += (size_t)A.npp * N;
     q.plain = r;
     r += (size_t)A.pacc * N;
     size_t off = (reinterpret_cast<size_t>(r) + 255) & ~(size_t)255;
     q.F = reinterpret_cast<double *>(off);
     q.Jbar = q.F + (size_t)A.nprd * N;
+    q.hist = q.Jbar + (size_t)A.nprd * N;
     return q;
 }
 
@@ -340,7 +345,7 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 // intensity) cw I and cw R (E + I), for the PRD update.
 template <typename R, int K, bool PRD, bool CACHE>
 __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane, R *prd_rho,
-                             R *prd_J, R *prd_plain, const R *phc)
+                             R *prd_J, R *prd_D, R *prd_plain, const R *phc)
 {
     const int N = p.N;
     const DevTile &tl = A.tile[b];
@@ -458,8 +463,16 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 val[M + 2 * j + 1] = cw * d.Rs[j] * (lc.E[j] + Ik);
             }
             // fire-and-forget reductions (zeroed before the sweep): one lane per
-            // location, adding in program order, so the sum is deterministic
-            if (pp >= 0) atomicAdd(prd_J + (size_t)pp * N + k, wm2 * Ik);
+            // location, adding in program order, so the sum is deterministic;
+            // D = dJ/drho through the PRD line's own emission, Psi* n_u U0
+            if (pp >= 0) {
+                R e0 = 0;
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+                    if (j == tl.prd_slot) e0 = d.nu_[j] * lc.Uc[j] * phi[j];
+                atomicAdd(prd_J + (size_t)pp * N + k, wm2 * Ik);
+                atomicAdd(prd_D + (size_t)pp * N + k, wm2 * psi * e0);
+            }
         }
 #pragma unroll
         for (int a = MP; a < P; ++a) val[a] = 0;
@@ -657,12 +670,12 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
 
 template <typename R, bool PRD, bool CACHE>
 __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane,
-                                           R *prd_rho, R *prd_J, R *prd_plain, const R *phc)
+                                           R *prd_rho, R *prd_J, R *prd_D, R *prd_plain, const R *phc)
 {
     switch (A.tile[b].K) {
-    case 1: sweep_tile_k<R, 1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_plain, phc); break;
-    case 2: sweep_tile_k<R, 2, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_plain, phc); break;
-    default: sweep_tile_k<R, 3, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_plain, phc); break;
+    case 1: sweep_tile_k<R, 1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
+    case 2: sweep_tile_k<R, 2, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
+    default: sweep_tile_k<R, 3, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
     }
 }
 
@@ -899,14 +912,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
             double v = start == 0 ? p.nstar[(size_t)col * LN + i] : p.pops[(size_t)col * LN + i];
             s.n[i] = v;
         }
-        int hcount = 0, hpos = 0;
+        int hcount = 0, hpos = 0, rcount = 0, rpos = 0;
         status = RH_COL_MAXITER;
         dmax = 1e300;
         for (it = 1; it <= maxiter; ++it) {
             double fcr = crsw > 1.0 ? fmax(1.0, crsw * pow(10.0, -(double)(it - 1))) : 1.0;
             for (int i = tid; i < LN; i += blockDim.x) s.nr[i] = (R)(s.n[i] * p.inv_nref);
             if constexpr (PRD) {
-                for (int i = tid; i < A.npp * N; i += blockDim.x) ps.J[i] = 0;
+                for (int i = tid; i < A.npp * N; i += blockDim.x) {
+                    ps.J[i] = 0;
+                    ps.D[i] = 0;
+                }
                 for (int i = tid; i < A.pacc * N; i += blockDim.x) ps.plain[i] = 0;
             }
             if (tid == 0) s.ibuf[1] = 0;
@@ -918,7 +934,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 if (lane == 0) q = atomicAdd(&s.ibuf[1], 1);
                 q = __shfl_sync(0xffffffffu, q, 0);
                 if (q >= A.ntile) break;
-                sweep_tile<R, PRD, CACHE>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.plain, phc);
+                sweep_tile<R, PRD, CACHE>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.D, ps.plain, phc);
             }
             __syncthreads();
             // ---- rate equations, one thread per depth
@@ -1010,10 +1026,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
             }
             if constexpr (PRD) {
                 // rho for the next iteration (Uitenbroek 2001, Eq. 14, angle-averaged,
-                // gamma = 1): rho = 1 + F (sum_j K_ij J_j / Jbar - 1), F = n_l R_lu /
+                // gamma = 1): r = 1 + F (sum_j K_ij J_j / Jbar - 1), F = n_l R_lu /
                 // (supply of the upper level) with the plain rates of this formal
                 // solution and the collisions, n the next iteration's populations;
-                // PRD switching (Eq. 1) and under-relaxation by 1/2
+                // PRD switching (Eq. 1) r' = eps r + (1 - eps), eps = min(1, eps0
+                // it^2) of the iteration that uses it
                 const double eps =
                     p.prd_eps0 > 0.0 ? fmin(1.0, p.prd_eps0 * (double)(it + 1) * (double)(it + 1)) : 1.0;
                 for (int e = tid; e < A.nprd * N; e += blockDim.x) {
@@ -1044,6 +1061,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                     ps.Jbar[e] = jb;
                 }
                 __syncthreads();
+                // with Ng: one Jacobi step rho += (r' - rho) / max(1 - eps g_ii, 0.02),
+                // g_ii = dr_i/drho_i = F D_i (K_ii - f_i sum_j K_ij J_j / Jbar) / Jbar,
+                // and Ng on the rho sequence; without Ng: rho = (rho + r') / 2
+                const bool jac = ng_order == 2;
+                rpos = (rpos + 3) & 3;
+                double *rh0 = ps.hist + (size_t)rpos * A.npp * N;
                 for (int e = tid; e < A.npp * N; e += blockDim.x) {
                     const int pp = e / N, k = e % N;
                     int q = 0;
@@ -1052,8 +1075,66 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                     const R *Krow = ps.K + (size_t)A.prd_koff[q] * N + ((size_t)k * np + i) * np;
                     double sr = 0.0;
                     for (int j = 0; j < np; ++j) sr += (double)Krow[j] * (double)ps.J[(size_t)(off + j) * N + k];
-                    const double r = 1.0 + ps.F[q * N + k] * (sr / ps.Jbar[q * N + k] - 1.0);
-                    ps.rho[e] = (R)(0.5 * (double)ps.rho[e] + 0.5 * (eps * r + (1.0 - eps)));
+                    const double jb = ps.Jbar[q * N + k], F = ps.F[q * N + k];
+                    const double r = 1.0 + F * (sr / jb - 1.0);
+                    double den = 2.0;
+                    if (jac) {
+                        const double g = F * ((double)Krow[i] - (double)ps.f[e] * sr / jb) * (double)ps.D[e] / jb;
+                        den = fmax(1.0 - eps * g, 0.02);
+                    }
+                    const double rn = (double)ps.rho[e] + ((eps * r + (1.0 - eps)) - (double)ps.rho[e]) / den;
+                    ps.rho[e] = (R)rn;
+                    rh0[e] = (double)ps.rho[e];
+                }
+                __syncthreads();
+                if (rcount < 4) ++rcount;
+                if (jac && it >= p.ng_delay && rcount >= 4 && (it - p.ng_delay) % p.ng_period == 0) {
+                    const int RV = A.npp * N;
+                    const double *x0 = rh0, *x1 = ps.hist + (size_t)((rpos + 1) & 3) * RV,
+                                 *x2 = ps.hist + (size_t)((rpos + 2) & 3) * RV,
+                                 *x3 = ps.hist + (size_t)((rpos + 3) & 3) * RV;
+                    for (int v = tid; v < kNgLanes; v += blockDim.x) {
+                        double q5[5] = {0, 0, 0, 0, 0};
+                        for (int i = v; i < RV; i += kNgLanes) {
+                            double d0 = x0[i] - x1[i], d1 = x1[i] - x2[i], d2 = x2[i] - x3[i];
+                            double pq = d0 - d1, qq = d0 - d2;
+                            q5[0] += pq * pq;
+                            q5[1] += pq * qq;
+                            q5[2] += qq * qq;
+                            q5[3] += d0 * pq;
+                            q5[4] += d0 * qq;
+                        }
+                        for (int j = 0; j < 5; ++j) s.red[j * kNgLanes + v] = q5[j];
+                    }
+                    __syncthreads();
+                    if (tid < 5) {
+                        double t = 0.0;
+                        for (int i = 0; i < kNgLanes; ++i) t += s.red[tid * kNgLanes + i];
+                        s.red[5 * kNgLanes + tid] = t;
+                    }
+                    __syncthreads();
+                    const double a11 = s.red[5 * kNgLanes + 0], a12 = s.red[5 * kNgLanes + 1],
+                                 a22 = s.red[5 * kNgLanes + 2], b1 = s.red[5 * kNgLanes + 3],
+                                 b2 = s.red[5 * kNgLanes + 4];
+                    __syncthreads();
+                    const double det = a11 * a22 - a12 * a12;
+                    if (fabs(det) > 0.0 && isfinite(det)) {
+                        const double ca = (b1 * a22 - b2 * a12) / det, cb = (a11 * b2 - a12 * b1) / det;
+                        int okl = 1;
+                        for (int i = tid; i < RV; i += blockDim.x) {
+                            const double v = (1.0 - ca - cb) * x0[i] + ca * x1[i] + cb * x2[i];
+                            if (!(isfinite(v) && v >= 0.0)) okl = 0;
+                        }
+                        const double ok = -block_max(-(double)okl, s.red);
+                        if (ok > 0.5) {
+                            for (int i = tid; i < RV; i += blockDim.x) {
+                                const double v = (1.0 - ca - cb) * x0[i] + ca * x1[i] + cb * x2[i];
+                                ps.rho[i] = (R)v;
+                                rh0[i] = (double)ps.rho[i];
+                            }
+                            rcount = 1;
+                        }
+                    }
                 }
                 __syncthreads();
             }
