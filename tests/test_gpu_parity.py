@@ -339,3 +339,52 @@ def test_emergent_stokes_zero_field_equals_scalar(rh, atom, cols, stokes_case):
         I = g.emergent_spectrum(1.0, lam, precision=precision)
         assert rel(st[..., 0], I) < tol
         assert np.max(np.abs(st[..., 1:])) == 0.0
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_fp64_crsw_fixed_schedule_matches_oracle(rh, orc, atom, cols, persistent):
+    """Collisional-radiative switching (Sect. 2.3), f0 = 1e3: the FP64 GPU
+    iterates equal the oracle's within 1e-9 on an identical schedule without
+    Ng, through the iterations where the factor falls (1e3, 1e2, 10, 1)."""
+    g, o = _pair(rh, orc, atom, cols)
+    for it in (1, 2, 6):
+        g.load_columns(cols)
+        o.load_columns(cols)
+        g.iterate(maxiter=it, tol=0.0, precision=0, persistent=persistent, ng_order=0, crsw_init=1e3)
+        o.iterate(maxiter=it, tol=0.0, ng_order=0, crsw_init=1e3)
+        assert rel(g.populations()[0], o.populations()[0]) < FP64_TOL, it
+    # the switched schedule differs from the plain one
+    g.load_columns(cols)
+    g.iterate(maxiter=2, tol=0.0, precision=0, ng_order=0)
+    o.load_columns(cols)
+    o.iterate(maxiter=2, tol=0.0, ng_order=0, crsw_init=1e3)
+    assert rel(g.populations()[0], o.populations()[0]) > 1e-3
+
+
+@pytest.fixture(scope="module")
+def cols128():
+    """Cube columns of 128 heights (the full-run height count)."""
+    return rh_synth.subset(rh_synth.chromosphere_cube(nx=16, ny=16, ndep=128, seed=5), [0, 37, 101, 200])
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_fp64_128_depths_matches_oracle(rh, orc, atom, cols128, persistent):
+    g, o = _pair(rh, orc, atom, cols128)
+    for it in (2, 20):
+        g.load_columns(cols128)
+        o.load_columns(cols128)
+        g.iterate(maxiter=it, tol=0.0, precision=0, persistent=persistent, ng_order=0)
+        o.iterate(maxiter=it, tol=0.0, ng_order=0)
+        assert rel(g.populations()[0], o.populations()[0]) < FP64_TOL, it
+
+
+def test_mixed_128_depths_fixed_point(rh, orc, atom, cols128):
+    g, o = _pair(rh, orc, atom, cols128)
+    o.iterate(maxiter=1000, tol=1e-9)
+    no, _, sto, _ = o.populations()
+    g.iterate(maxiter=1000, tol=1e-6, precision=1)
+    ng, _, stg, _ = g.populations()
+    assert np.all(sto == 0) and np.all(stg == 0)
+    assert rel(ng, no) < POP_TOL_MIXED
+    lam = np.concatenate([np.linspace(121.45e-9, 121.7e-9, 26), np.linspace(656.1e-9, 656.5e-9, 21)])
+    assert rel(g.emergent_spectrum(1.0, lam, precision=1), o.emergent_spectrum(1.0, lam)) < INT_TOL_MIXED
