@@ -145,7 +145,7 @@ typedef struct {
     int64_t iterations_total;      /* sum over the processed columns of formal solutions */
     double seconds;                /* device time of the iteration kernel */
     double pts;                    /* depth x lambda x mu points solved */
-    double max_dn_final;           /* max over columns of the last max |dn/n| */
+    double max_dn_final;           /* max over columns of the last max |dn/n| (NaN entries skipped) */
     int64_t guess_fallback_depths; /* start = 1: depths whose prediction fell back to LTE */
     double guess_seconds;          /* start = 1: time of the prediction (included in seconds) */
 } rh_iter_stats;
@@ -180,6 +180,10 @@ int rh_emergent_stokes(rh_ctx *ctx, int32_t line, double g_eff, const double *B_
 /* Start solutions (Sect. 2.3: "LTE populations, zero radiation, and ...     */
 /* escape probability iterations"), written into the current populations of */
 /* every loaded column (iterate from them with start = 2).  kind 0: LTE.     */
+/* kind 1, the learned guess of start = 1 (no counterpart in the paper): the */
+/* network's ln b per level and depth, n = e^{ln b} n* renormalised per      */
+/* depth to sum n = n_H, LTE at a depth with a non-finite prediction;        */
+/* RH_ESTATE without a network for the loaded depth count.                   */
 /* kind 3, zero radiation: the rate equations with J = 0 -- radiative rates  */
 /* are spontaneous only (A_ul; for a continuum the recombination            */
 /* 4 pi sum w (2 h nu^3/c^2) alpha (n*_l/n*_c) e^{-h nu/kT} / (h nu) over its */
@@ -354,37 +358,55 @@ int rh_surrogate_load(rh_ctx *ctx, const char *path);
 int rh_surrogate_file_info(const char *path, int32_t *sizes_out, int64_t *nparam_out, char *msg, size_t msg_len);
 
 /* ---------------------------------------------------------------------- */
+/* Measured fused multiply-add rate of a device (no counterpart in the      */
+/* paper: the denominator of the column kernel's roofline).  precision 1    */
+/* FP32, 0 FP64.  Every thread of 4 x 256-thread blocks per SM runs 16      */
+/* independent chains x <- a x + b; after a calibration launch one launch   */
+/* of about `seconds` (0 < seconds <= 10) is timed with CUDA events, and    */
+/* flop_s_out = 2 x FMAs / its time (seconds_out, optional: that time).     */
+/* Allocates a 2 KB device buffer and a stream for the call.  The caller's  */
+/* current device is restored.  RH_EINVAL for bad arguments, RH_ECUDA.      */
+int rh_fma_peak(int32_t device, int32_t precision, double seconds, double *flop_s_out, double *seconds_out);
+
+/* ---------------------------------------------------------------------- */
 /* rh_iterate_noalloc -- the paper has no counterpart to this call; it      */
 /* exists for callers of this library that cannot allocate device memory    */
 /* while they solve: programs that hand all GPU memory to their own pool or  */
-/* budget (a framework allocator that must see every byte), code running    */
-/* while a CUDA stream is being captured into a graph, and latency-bound     */
-/* loops that cannot afford the device-wide synchronisation cudaMalloc and   */
-/* cudaFree imply.  Such a caller creates the context, sets the atom and     */
+/* budget (a framework allocator that must see every byte), and latency-     */
+/* bound loops that cannot afford the device-wide synchronisation cudaMalloc */
+/* and cudaFree imply.  Such a caller creates the context, sets the atom and */
 /* loads the columns once during start-up (those calls do allocate), and     */
 /* later calls this function as often as it likes.                           */
 /*                                                                           */
 /* It runs the same iteration as rh_iterate over every loaded column         */
-/* (only_unconverged must be 0) and writes the results to caller-owned       */
-/* DEVICE buffers: n_out [ncol][nlev][ndep] (with start = 2 it is also read  */
-/* as the starting populations), iters_out [ncol], status_out [ncol]         */
-/* (RH_COL_*), dmax_out [ncol].  It calls no cudaMalloc, cudaFree or other   */
-/* allocating routine: its scratch (work-queue counter, result counters,     */
-/* the wavelength table in the iteration's precision and the Ng history of   */
-/* the resident blocks) is one statically sized 9 MiB device array inside   */
-/* the library, which every GPU that loads the library holds until the      */
-/* process exits.  A problem whose Ng history for one column exceeds that    */
-/* array (4 x nlev x ndep doubles > ~8 MiB; cannot happen within the limits  */
-/* of rh_load_columns and rh_setup_atom) is rejected with RH_EINVAL; a       */
-/* smaller array only lowers the number of resident blocks.                  */
-/* The first call on each device looks the array's address up (so make that */
-/* first call before starting any stream capture).  All calls, from every    */
-/* context and thread, share the one array: the counters are cleared at the  */
-/* start of each call, and calls whose GPU work overlaps (other streams,     */
-/* other threads) race on it and must be serialised by the caller.  The call */
-/* returns after the work has finished on the context's stream; stats_out    */
-/* (optional, host) reports wall-clock seconds.  Returns RH_OK, RH_ENOTCONV,  */
-/* RH_EINVAL, RH_ESTATE or RH_ECUDA as rh_iterate does.                      */
+/* (only_unconverged must be 0; atoms with PRD lines are refused, their      */
+/* redistribution scratch is allocated) and writes the results to           */
+/* caller-owned DEVICE buffers of the context's device: n_out               */
+/* [ncol][nlev][ndep] (with start = 2 it is also read as the starting       */
+/* populations), iters_out [ncol], status_out [ncol] (RH_COL_*), dmax_out    */
+/* [ncol].  A pointer that is not device (or managed) memory of that device  */
+/* is refused with RH_EINVAL; their sizes cannot be checked here and must    */
+/* hold the counts above.  It calls no cudaMalloc, cudaFree or other         */
+/* allocating routine: its device scratch (work-queue counter, result       */
+/* counters, the wavelength table in the iteration's precision and the Ng   */
+/* history of the resident blocks) is one statically sized 9 MiB device     */
+/* array inside the library, which every GPU that loads the library holds    */
+/* until the process exits, and the wavelength table is staged through two   */
+/* static host arrays of the library.  A problem whose Ng history for one    */
+/* column exceeds the device array (4 x nlev x ndep doubles > ~8 MiB; cannot */
+/* happen within the limits of rh_load_columns and rh_setup_atom) is        */
+/* rejected with RH_EINVAL; a smaller array only lowers the number of        */
+/* resident blocks.  The first call on each device looks the array's         */
+/* address up, so make that first call before starting any stream capture.  */
+/* Every call, from every context and thread, shares the device and host     */
+/* arrays and keeps its counters' last contents (they are cleared at the     */
+/* start of each call); calls whose GPU work overlapped would race on them.  */
+/* The library holds a lock for the whole call and returns only after the    */
+/* call's GPU work has finished on the context's stream, so calls from       */
+/* several host threads of one process run one after another.  The caller's  */
+/* current device is restored on return.  stats_out (optional, host)         */
+/* reports wall-clock seconds, and max_dn_final as rh_iterate does.  Returns  */
+/* RH_OK, RH_ENOTCONV, RH_EINVAL, RH_ESTATE or RH_ECUDA as rh_iterate does.   */
 int rh_iterate_noalloc(rh_ctx *ctx, const rh_iter_opts *opts, double *n_out, int32_t *iters_out,
                        uint8_t *status_out, double *dmax_out, rh_iter_stats *stats_out);
 

@@ -26,7 +26,8 @@ EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlam
            "rh_emergent_spectrum", "rh_iterate_noalloc", "rh_surrogate_init", "rh_surrogate_state_size",
            "rh_surrogate_get_state", "rh_surrogate_set_state", "rh_surrogate_train", "rh_surrogate_loss_grad",
            "rh_surrogate_predict", "rh_solve", "rh_autotune", "rh_start_populations",
-           "rh_emergent_stokes", "rh_surrogate_save", "rh_surrogate_load", "rh_surrogate_file_info")
+           "rh_emergent_stokes", "rh_surrogate_save", "rh_surrogate_load", "rh_surrogate_file_info",
+           "rh_fma_peak")
 
 MAX_RERUN = 4
 MAX_TUNE = 8
@@ -130,6 +131,7 @@ def lib(path: str | None = None):
         L.rh_surrogate_save.argtypes = [vp, C.c_char_p]
         L.rh_surrogate_load.argtypes = [vp, C.c_char_p]
         L.rh_surrogate_file_info.argtypes = [C.c_char_p, _ip, C.POINTER(C.c_int64), C.c_char_p, C.c_size_t]
+        L.rh_fma_peak.argtypes = [C.c_int32, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -149,6 +151,17 @@ def _ptr(x):
     if hasattr(x, "data_ptr"):
         return C.c_void_p(x.data_ptr())
     return C.c_void_p(x.ctypes.data)
+
+
+def fma_peak(device: int = 0, precision: int = 1, seconds: float = 0.5) -> dict:
+    """rh_fma_peak: measured FMA rate of the device (FP32: precision 1, FP64:
+    0), FLOP/s, and the timed launch's duration."""
+    f = C.c_double()
+    t = C.c_double()
+    rc = lib().rh_fma_peak(device, precision, seconds, C.byref(f), C.byref(t))
+    if rc:
+        raise RhError(rc, "rh_fma_peak failed")
+    return {"flop_s": f.value, "seconds": t.value}
 
 
 class RhError(RuntimeError):
@@ -182,6 +195,8 @@ class Context:
             msg = self._lib.rh_last_error(p).decode() if p else "rh_create failed"
             raise RhError(rc, msg)
         self._keep = None
+        self.device = device
+        self.ncol = 0
 
     def close(self):
         if getattr(self, "_p", None):
@@ -371,8 +386,26 @@ class Context:
                         ng_delay=5, ng_period=3, start=0, precision=1, persistent=1, block_warps=0,
                         crsw_init=1.0) -> dict:
         """rh_iterate_noalloc: results into caller-owned CUDA tensors (float64
-        [ncol][nlev][ndep], int32 [ncol], uint8 [ncol], float64 [ncol]); the
-        library allocates nothing during the call."""
+        [ncol][nlev][ndep], int32 [ncol], uint8 [ncol], float64 [ncol]) on the
+        context's device, contiguous; the library allocates nothing during the
+        call.  Anything else is refused here, before the call."""
+        if not self.ncol:          # nothing loaded: the library reports RH_ESTATE
+            want = ()
+        else:
+            want = ((n_out, "float64", self.ncol * self.nlev * self.ndep, "n_out"),
+                    (iters_out, "int32", self.ncol, "iters_out"), (status_out, "uint8", self.ncol, "status_out"),
+                    (dmax_out, "float64", self.ncol, "dmax_out"))
+        for t, dt, numel, name in want:
+            if not (hasattr(t, "is_cuda") and t.is_cuda):
+                raise ValueError("%s must be a CUDA tensor" % name)
+            if t.device.index != self.device:
+                raise ValueError("%s is on cuda:%s, the context on cuda:%d" % (name, t.device.index, self.device))
+            if str(t.dtype) != "torch." + dt:
+                raise ValueError("%s must be %s, got %s" % (name, dt, t.dtype))
+            if not t.is_contiguous():
+                raise ValueError("%s must be contiguous" % name)
+            if t.numel() < numel:
+                raise ValueError("%s holds %d elements, needs %d" % (name, t.numel(), numel))
         o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
                      ng_period=ng_period, start=start, precision=precision, persistent=persistent,
                      block_warps=block_warps, crsw_init=crsw_init, only_unconverged=0)

@@ -9,7 +9,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librh15d_gpu.so")
-SOURCES = ["rh15d_host.cu", "rh15d_setup.cu", "rh15d_mali.cu", "rh15d_mlp.cu"]
+SOURCES = ["rh15d_host.cu", "rh15d_setup.cu", "rh15d_mali.cu", "rh15d_mlp.cu", "rh15d_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

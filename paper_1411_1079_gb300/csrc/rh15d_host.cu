@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <random>
 #include <string>
 #include <vector>
@@ -1294,7 +1295,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
         else if (s[i] == RH_COL_MAXITER) S.n_maxiter++;
         else S.n_failed++;
         if (done[i]) S.iterations_total += it[i];
-        if (i == 0 || dm[i] > S.max_dn_final) S.max_dn_final = dm[i];
+        if (dm[i] > S.max_dn_final) S.max_dn_final = dm[i];   // NaN entries skipped
     }
     S.pts = (double)S.iterations_total * c->ndep * (double)c->ha.nu.size() * c->ha.nmu;
     if (st) *st = S;
@@ -1612,11 +1613,20 @@ int rh_start_populations(rh_ctx *c, int32_t kind)
 {
     if (!c) return RH_EINVAL;
     if (!c->ncol) return fail(c, RH_ESTATE, "rh_start_populations: no columns loaded");
-    if (kind != 0 && kind != 3 && kind != 4) return fail(c, RH_EINVAL, "rh_start_populations: kind 0, 3 or 4");
+    if (kind != 0 && kind != 1 && kind != 3 && kind != 4)
+        return fail(c, RH_EINVAL, "rh_start_populations: kind 0, 1, 3 or 4");
     cudaSetDevice(c->dev);
     const size_t nv = (size_t)c->ncol * c->ndep * c->da.nlev;
     if (kind == 0) {
         CK(cudaMemcpyAsync(c->ca.pops, c->ca.nstar, nv * 8, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemsetAsync(c->ca.status, RH_COL_NOTRUN, c->ncol, c->st));
+    } else if (kind == 1) {
+        if (!c->mlp || c->mlp_ndep != c->ndep)
+            return fail(c, RH_ESTATE, "rh_start_populations: kind 1 needs a surrogate for %d depths", c->ndep);
+        drop_graph(c);   // network buffers may be (re)allocated
+        int r = ensure_mlp_buffers(c);
+        if (r) return r;
+        CK(mlp_predict_apply(c->mlp, c->ca, c->da.nlev, c->feat, c->lnb, c->nfb_d, c->st));
         CK(cudaMemsetAsync(c->ca.status, RH_COL_NOTRUN, c->ncol, c->st));
     } else {
         int r = ensure_start_tables(c);
@@ -1913,9 +1923,31 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 // device address of the scratch array, looked up once per device (host code
 // may not use the symbol itself as an address)
 void *g_noalloc_dev_ptr[kNoallocMaxDev];
-// host staging of the lane table (static: no heap allocation per call)
+// host staging of the lane table (static: no heap allocation per call),
+// shared by every call; the lock serialises calls from several host threads
+// while they fill it and hand it to cudaMemcpyAsync (which has copied a
+// pageable source out by the time it returns)
 double g_noalloc_lane64[(size_t)kLaneFields * RH_MAXTILE * 32];
 float g_noalloc_lane32[(size_t)kLaneFields * RH_MAXTILE * 32];
+std::mutex g_noalloc_mutex;
+
+// restores the caller's current device when the call returns
+struct DeviceRestore {
+    int dev = -1;
+    DeviceRestore() { if (cudaGetDevice(&dev) != cudaSuccess) dev = -1; }
+    ~DeviceRestore() { if (dev >= 0) cudaSetDevice(dev); }
+};
+
+// 1 if p is device (or managed) memory of device dev
+bool noalloc_device_pointer(const void *p, int dev)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
 
 __global__ void noalloc_count_kernel(int64_t ncol, const int32_t *iters, const uint8_t *status,
                                      unsigned long long *cnt)
@@ -1927,6 +1959,8 @@ __global__ void noalloc_count_kernel(int64_t ncol, const int32_t *iters, const u
     atomicAdd(&cnt[3], (unsigned long long)iters[i]);
 }
 
+// max over columns of dmax (NaN entries skipped, as in rh_iterate; the
+// column kernel writes none); the kernel writes only values >= 0
 __global__ void noalloc_max_kernel(int64_t ncol, const double *dmax, unsigned long long *out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1950,7 +1984,16 @@ extern "C" int rh_iterate_noalloc(rh_ctx *c, const rh_iter_opts *o, double *n_ou
         return fail(c, RH_EINVAL, "rh_iterate_noalloc: invalid options (only_unconverged is not supported here)");
     if (c->da.nprd) return fail(c, RH_EINVAL, "rh_iterate_noalloc: atoms with PRD lines need scratch; use rh_iterate");
     if (c->dev < 0 || c->dev >= kNoallocMaxDev) return fail(c, RH_EINVAL, "rh_iterate_noalloc: device index too large");
+    DeviceRestore restore_device;
     CK(cudaSetDevice(c->dev));
+    {
+        const void *bufs[4] = {n_out, iters_out, status_out, dmax_out};
+        const char *names[4] = {"n_out", "iters_out", "status_out", "dmax_out"};
+        for (int i = 0; i < 4; ++i)
+            if (!noalloc_device_pointer(bufs[i], c->dev))
+                return fail(c, RH_EINVAL, "rh_iterate_noalloc: %s is not device memory of device %d", names[i],
+                            c->dev);
+    }
     // once per device, with the device current: the scratch array's address
     if (!g_noalloc_dev_ptr[c->dev]) {
         void *ptr = nullptr;
@@ -1971,6 +2014,7 @@ extern "C" int rh_iterate_noalloc(rh_ctx *c, const rh_iter_opts *o, double *n_ou
     // the lane table in the iteration's precision, populations scaled by n_ref
     const int np = c->ha.npad;
     const size_t nl = (size_t)kLaneFields * np;
+    std::lock_guard<std::mutex> staging_lock(g_noalloc_mutex);
     for (size_t i = 0; i < nl; ++i) g_noalloc_lane64[i] = c->lane_master[i];
     for (int j = 0; j < RH_KMAX; ++j)
         for (int f : {1, 2})
