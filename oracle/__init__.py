@@ -91,6 +91,8 @@ def lib():
         L.rho_stokes_sweep.restype = None
         L.rho_stokes_sweep.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp]
         L.rho_emergent_stokes.argtypes = [C.c_void_p, C.c_int32, C.c_double, _dp, _dp, _dp, C.c_int64, _dp, _dp]
+        L.rho_regrid.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+        L.rho_get_columns.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
         L.rho_prd_switch_eps.restype = C.c_double
         L.rho_prd_switch_eps.argtypes = [C.c_double, C.c_int32]
         L.rho_crsw_factor.restype = C.c_double
@@ -121,6 +123,11 @@ class IterOpts(C.Structure):
     _fields_ = [("maxiter", C.c_int32), ("tol", C.c_double), ("ng_order", C.c_int32),
                 ("ng_delay", C.c_int32), ("ng_period", C.c_int32), ("start", C.c_int32),
                 ("crsw_init", C.c_double), ("prd_eps0", C.c_double)]
+
+
+class GridOpts(C.Structure):
+    _fields_ = [("dlog_colden", C.c_double), ("dlnT", C.c_double), ("dvz", C.c_double),
+                ("spacing_factor", C.c_double), ("z_top", C.c_double), ("use_z_top", C.c_int32)]
 
 
 class IterStats(C.Structure):
@@ -303,6 +310,20 @@ class Oracle:
             nep = _d(ne)
         self._check(self._lib.rho_load_columns(self._p, ncol, ndep, _d(z), _d(T), nep, _d(nH), _d(vz)))
         self.ncol, self.ndep = ncol, ndep
+
+    def regrid(self, ndep_out, dlog_colden=0.1, dlnT=0.02, dvz=1e3, spacing_factor=4.0, z_top=None):
+        """Depth-grid optimisation (Sect. 2.3) of every loaded column onto
+        ndep_out points; z_top (m) removes the layers above it."""
+        o = GridOpts(dlog_colden=dlog_colden, dlnT=dlnT, dvz=dvz, spacing_factor=spacing_factor,
+                     z_top=0.0 if z_top is None else z_top, use_z_top=0 if z_top is None else 1)
+        self._check(self._lib.rho_regrid(self._p, ndep_out, C.byref(o)))
+        self.ndep = ndep_out
+
+    def columns(self):
+        """The loaded atmosphere: dict of z, T, nH, vz [ncol][ndep]."""
+        out = {k: np.zeros((self.ncol, self.ndep)) for k in ("z", "T", "nH", "vz")}
+        self._check(self._lib.rho_get_columns(self._p, _d(out["z"]), _d(out["T"]), _d(out["nH"]), _d(out["vz"])))
+        return out
 
     def electron_density(self, T, nH):
         return float(self._lib.rho_electron_density(self._p, float(T), float(nH)))

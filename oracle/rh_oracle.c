@@ -874,6 +874,145 @@ int rho_load_columns(rho_ctx *c, int64_t ncol, int32_t ndep, const double *z, co
     return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Depth-grid optimisation (Sect. 2.3): the atmosphere of every column is
+ * interpolated onto a grid that places more points where the temperature,
+ * the velocity or the optical depth change fastest, optionally without the
+ * layers above a height z_top.  The paper gives no formula; this reading:
+ *   - optical depth is represented by the hydrogen column density N_H(z) =
+ *     int_z^top n_H dz' (the continuum opacity scales with it), integrated
+ *     exactly for n_H exponential between grid points, with n_H(z_0) H_0
+ *     above the top point (H_0 the scale height of the top two points);
+ *   - the monitor s(z) grows between neighbouring points by
+ *       ds = sqrt((d log10 N_H / dN)^2 + (d ln T / dT)^2 + (d v_z / dv)^2
+ *                 + (dz / dz_max)^2),
+ *     dz_max = spacing_factor x (column height / (ndep_out - 1)) so that no
+ *     step exceeds spacing_factor times the uniform one;
+ *   - the new points are equidistant in s (equal monitor increments), the
+ *     first and last at the column's ends; T and v_z are interpolated
+ *     linearly in z, ln n_H and ln n_e linearly in z (exact for exponential
+ *     profiles), along the piecewise-linear path of the old grid;
+ *   - z_top (use_z_top != 0): the column above z_top is removed, its new top
+ *     point at z_top itself.
+ * n_e is interpolated (not recomputed), then LTE populations and rates are
+ * rebuilt on the new grid by loading the new columns. */
+typedef struct {
+    double dlog_colden;     /* dN: resolution scale of log10 N_H (dex) */
+    double dlnT;            /* dT: of ln T */
+    double dvz;             /* dv: of v_z (m/s) */
+    double spacing_factor;  /* largest step in units of the uniform step */
+    double z_top;           /* m */
+    int32_t use_z_top;
+} rho_grid_opts;
+
+/* one column: input zi..nei [N], output zo..neo [M]; returns nonzero on bad
+ * options for this column (z_top outside it) */
+static int regrid_column(int N, const double *zi, const double *Ti, const double *nHi, const double *vzi,
+                         const double *nei, int M, const rho_grid_opts *o, double *zo, double *To, double *nHo,
+                         double *vzo, double *neo)
+{
+    /* truncation at z_top: the kept part of the column, top point first */
+    double *z = malloc(N * 8), *T = malloc(N * 8), *lnH = malloc(N * 8), *v = malloc(N * 8), *lne = malloc(N * 8);
+    double *s = malloc(N * 8), *col = malloc(N * 8);
+    int n = 0, k0 = 0, rc = 0;
+    if (o->use_z_top && o->z_top < zi[0]) {
+        if (!(o->z_top > zi[N - 1])) { rc = 1; goto done; }   /* the cut must leave a layer */
+        while (zi[k0] > o->z_top) ++k0;                        /* first point at or below z_top */
+        if (zi[k0] < o->z_top) {
+            double t = (o->z_top - zi[k0 - 1]) / (zi[k0] - zi[k0 - 1]);
+            z[0] = o->z_top;
+            T[0] = Ti[k0 - 1] + t * (Ti[k0] - Ti[k0 - 1]);
+            lnH[0] = log(nHi[k0 - 1]) + t * (log(nHi[k0]) - log(nHi[k0 - 1]));
+            v[0] = vzi[k0 - 1] + t * (vzi[k0] - vzi[k0 - 1]);
+            lne[0] = log(nei[k0 - 1]) + t * (log(nei[k0]) - log(nei[k0 - 1]));
+            n = 1;
+        }
+    }
+    for (int k = k0; k < N; ++k, ++n) {
+        z[n] = zi[k];
+        T[n] = Ti[k];
+        lnH[n] = log(nHi[k]);
+        v[n] = vzi[k];
+        lne[n] = log(nei[k]);
+    }
+    /* hydrogen column density from the top */
+    {
+        double r = lnH[1] - lnH[0];
+        double H0 = r > 1e-12 ? (z[0] - z[1]) / r : (z[0] - z[1]);
+        col[0] = exp(lnH[0]) * H0;
+        for (int k = 0; k + 1 < n; ++k) {
+            double dz = z[k] - z[k + 1], a = exp(lnH[k]), b = exp(lnH[k + 1]), d = lnH[k + 1] - lnH[k];
+            col[k + 1] = col[k] + (fabs(d) > 1e-12 ? dz * (b - a) / d : dz * a);
+        }
+    }
+    {
+        double dzmax = o->spacing_factor * (z[0] - z[n - 1]) / (M - 1);
+        s[0] = 0.0;
+        for (int k = 0; k + 1 < n; ++k) {
+            double a1 = log10(col[k + 1] / col[k]) / o->dlog_colden;
+            double a2 = log(T[k + 1] / T[k]) / o->dlnT;
+            double a3 = (v[k + 1] - v[k]) / o->dvz;
+            double a4 = (z[k] - z[k + 1]) / dzmax;
+            s[k + 1] = s[k] + sqrt(a1 * a1 + a2 * a2 + a3 * a3 + a4 * a4);
+        }
+    }
+    for (int j = 0, k = 0; j < M; ++j) {
+        if (j == M - 1) {
+            zo[j] = z[n - 1]; To[j] = T[n - 1]; nHo[j] = exp(lnH[n - 1]); vzo[j] = v[n - 1]; neo[j] = exp(lne[n - 1]);
+            break;
+        }
+        double sj = s[n - 1] * j / (M - 1);
+        while (k + 2 < n && s[k + 1] < sj) ++k;
+        double t = (sj - s[k]) / (s[k + 1] - s[k]);
+        zo[j] = z[k] + t * (z[k + 1] - z[k]);
+        To[j] = T[k] + t * (T[k + 1] - T[k]);
+        nHo[j] = exp(lnH[k] + t * (lnH[k + 1] - lnH[k]));
+        vzo[j] = v[k] + t * (v[k + 1] - v[k]);
+        neo[j] = exp(lne[k] + t * (lne[k + 1] - lne[k]));
+    }
+done:
+    free(z); free(T); free(lnH); free(v); free(lne); free(s); free(col);
+    return rc;
+}
+
+int rho_regrid(rho_ctx *c, int32_t ndep_out, const rho_grid_opts *o)
+{
+    if (!c->ncol) return fail(c, "no columns loaded"), 4;
+    if (ndep_out < 2 || !o || !(o->dlog_colden > 0) || !(o->dlnT > 0) || !(o->dvz > 0) ||
+        !(o->spacing_factor >= 1.0))
+        return fail(c, "invalid regrid options");
+    int64_t nc = c->ncol;
+    int N = c->ndep, M = ndep_out;
+    size_t nd = (size_t)nc * M;
+    double *z = malloc(nd * 8), *T = malloc(nd * 8), *nH = malloc(nd * 8), *vz = malloc(nd * 8), *ne = malloc(nd * 8);
+    int bad = -1;
+    for (int64_t col = 0; col < nc && bad < 0; ++col)
+        if (regrid_column(N, c->z + col * N, c->T + col * N, c->nH + col * N, c->vz + col * N, c->ne + col * N, M, o,
+                          z + col * M, T + col * M, nH + col * M, vz + col * M, ne + col * M))
+            bad = (int)col;
+    int rc = 0;
+    if (bad >= 0) {
+        char m[160];
+        snprintf(m, sizeof m, "z_top leaves fewer than two points of column %d", bad);
+        rc = fail(c, m);
+    } else {
+        rc = rho_load_columns(c, nc, M, z, T, ne, nH, vz);
+    }
+    free(z); free(T); free(nH); free(vz); free(ne);
+    return rc;
+}
+
+/* the loaded atmosphere [ncol][ndep] (any output may be NULL) */
+int rho_get_columns(const rho_ctx *c, double *z, double *T, double *nH, double *vz)
+{
+    size_t nd = (size_t)c->ncol * c->ndep;
+    if (z) memcpy(z, c->z, nd * 8);
+    if (T) memcpy(T, c->T, nd * 8);
+    if (nH) memcpy(nH, c->nH, nd * 8);
+    if (vz) memcpy(vz, c->vz, nd * 8);
+    return 0;
+}
+
 int rho_get_lte(const rho_ctx *c, double *nstar, double *ne)
 {
     size_t nd = (size_t)c->ncol * c->ndep;
