@@ -177,6 +177,33 @@ int rh_emergent_stokes(rh_ctx *ctx, int32_t line, double g_eff, const double *B_
                        int32_t precision, int32_t on_device);
 
 /* ---------------------------------------------------------------------- */
+/* ---------------------------------------------------------------------- */
+/* Depth-grid optimisation (Sect. 2.3: the atmosphere of each column is      */
+/* interpolated onto a grid with more points where temperature, velocity or  */
+/* optical depth change fastest, optionally without the upper layers).  The  */
+/* paper gives no formula; this library's reading: every loaded column is    */
+/* replaced by ndep_out points (2..4096) equidistant in the monitor s, whose */
+/* step between neighbouring points is                                       */
+/*   sqrt((d log10 N_H / dlog_colden)^2 + (d ln T / dlnT)^2                   */
+/*        + (d v_z / dvz)^2 + (d z / dz_max)^2),                              */
+/* N_H(z) the hydrogen column density above z (the optical-depth proxy; n_H   */
+/* H at the top point, H the scale height of the top two points, plus the   */
+/* exact integral of an exponential n_H between points), dz_max =           */
+/* spacing_factor x column height / (ndep_out - 1).  The ends of the column  */
+/* are kept; with use_z_top the layers above z_top (m) are removed first,    */
+/* the new top point at z_top.  T and v_z are interpolated linearly, n_H and */
+/* n_e logarithmically in height; then the columns are loaded as by          */
+/* rh_load_columns (LTE populations, rates; populations reset).  Typical     */
+/* scales: 0.1 dex, 0.02, 1000 m/s, 4.  RH_EINVAL for bad options or a      */
+/* z_top at or below a column's bottom (naming the first such column).      */
+typedef struct {
+    double dlog_colden, dlnT, dvz, spacing_factor, z_top;
+    int32_t use_z_top;
+} rh_grid_opts;
+int rh_regrid(rh_ctx *ctx, int32_t ndep_out, const rh_grid_opts *opts);
+/* The loaded atmosphere [ncol][ndep] into host buffers (any may be NULL). */
+int rh_get_columns(rh_ctx *ctx, double *z_out, double *T_out, double *nH_out, double *vz_out);
+
 /* Start solutions (Sect. 2.3: "LTE populations, zero radiation, and ...     */
 /* escape probability iterations"), written into the current populations of */
 /* every loaded column (iterate from them with start = 2).  kind 0: LTE.     */

@@ -27,7 +27,7 @@ EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlam
            "rh_surrogate_get_state", "rh_surrogate_set_state", "rh_surrogate_train", "rh_surrogate_loss_grad",
            "rh_surrogate_predict", "rh_solve", "rh_autotune", "rh_start_populations",
            "rh_emergent_stokes", "rh_surrogate_save", "rh_surrogate_load", "rh_surrogate_file_info",
-           "rh_fma_peak")
+           "rh_fma_peak", "rh_regrid", "rh_get_columns")
 
 MAX_RERUN = 4
 MAX_TUNE = 8
@@ -42,6 +42,11 @@ class AtomDesc(C.Structure):
                 ("cont_nlambda", _ip), ("cont_ratio", _dp),
                 ("mass_amu", C.c_double), ("T_ref", C.c_double), ("nmu", C.c_int32),
                 ("metal_floor", C.c_double), ("line_prd", _ip)]
+
+
+class GridOpts(C.Structure):
+    _fields_ = [("dlog_colden", C.c_double), ("dlnT", C.c_double), ("dvz", C.c_double),
+                ("spacing_factor", C.c_double), ("z_top", C.c_double), ("use_z_top", C.c_int32)]
 
 
 class IterOpts(C.Structure):
@@ -131,6 +136,8 @@ def lib(path: str | None = None):
         L.rh_surrogate_save.argtypes = [vp, C.c_char_p]
         L.rh_surrogate_load.argtypes = [vp, C.c_char_p]
         L.rh_surrogate_file_info.argtypes = [C.c_char_p, _ip, C.POINTER(C.c_int64), C.c_char_p, C.c_size_t]
+        L.rh_regrid.argtypes = [vp, C.c_int32, C.POINTER(GridOpts)]
+        L.rh_get_columns.argtypes = [vp, _dp, _dp, _dp, _dp]
         L.rh_fma_peak.argtypes = [C.c_int32, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
     return _lib
@@ -326,9 +333,23 @@ class Context:
 
     START_LTE, START_LEARNED, START_CURRENT, START_ZERO_RADIATION, START_ESCAPE = 0, 1, 2, 3, 4
 
+    def regrid(self, ndep_out, dlog_colden=0.1, dlnT=0.02, dvz=1e3, spacing_factor=4.0, z_top=None):
+        """rh_regrid: depth-grid optimisation of every loaded column onto
+        ndep_out points; z_top (m) removes the layers above it."""
+        o = GridOpts(dlog_colden=dlog_colden, dlnT=dlnT, dvz=dvz, spacing_factor=spacing_factor,
+                     z_top=0.0 if z_top is None else z_top, use_z_top=0 if z_top is None else 1)
+        self._check(self._lib.rh_regrid(self._p, ndep_out, C.byref(o)))
+        self.ndep = int(ndep_out)
+
+    def columns(self):
+        """The loaded atmosphere: dict of z, T, nH, vz [ncol][ndep]."""
+        out = {k: np.zeros((self.ncol, self.ndep)) for k in ("z", "T", "nH", "vz")}
+        self._check(self._lib.rh_get_columns(self._p, _d(out["z"]), _d(out["T"]), _d(out["nH"]), _d(out["vz"])))
+        return out
+
     def start_populations(self, kind):
-        """rh_start_populations: write the LTE (0), zero-radiation (3) or
-        escape-probability (4) start into the current populations."""
+        """rh_start_populations: write the LTE (0), learned (1), zero-radiation
+        (3) or escape-probability (4) start into the current populations."""
         self._check(self._lib.rh_start_populations(self._p, kind))
 
     def autotune(self, precision=1) -> dict:

@@ -1328,6 +1328,62 @@ int rh_get_lte(rh_ctx *c, double *nstar_out, double *ne_out)
     return RH_OK;
 }
 
+int rh_get_columns(rh_ctx *c, double *z_out, double *T_out, double *nH_out, double *vz_out)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "no columns loaded");
+    cudaSetDevice(c->dev);
+    CK(cudaStreamSynchronize(c->st));
+    const size_t nd = (size_t)c->ncol * c->ndep * 8;
+    if (z_out) CK(cudaMemcpy(z_out, c->ca.z, nd, cudaMemcpyDeviceToHost));
+    if (T_out) CK(cudaMemcpy(T_out, c->ca.T, nd, cudaMemcpyDeviceToHost));
+    if (nH_out) CK(cudaMemcpy(nH_out, c->ca.nH, nd, cudaMemcpyDeviceToHost));
+    if (vz_out) CK(cudaMemcpy(vz_out, c->ca.vz, nd, cudaMemcpyDeviceToHost));
+    return RH_OK;
+}
+
+int rh_regrid(rh_ctx *c, int32_t ndep_out, const rh_grid_opts *o)
+{
+    if (!c) return RH_EINVAL;
+    if (!c->ncol) return fail(c, RH_ESTATE, "rh_regrid: no columns loaded");
+    if (!o || ndep_out < 2 || ndep_out > 4096 || !(o->dlog_colden > 0) || !(o->dlnT > 0) || !(o->dvz > 0) ||
+        !(o->spacing_factor >= 1.0) || !std::isfinite(o->spacing_factor) || (o->use_z_top && !std::isfinite(o->z_top)))
+        return fail(c, RH_EINVAL, "rh_regrid: invalid options");
+    cudaSetDevice(c->dev);
+    const int64_t nc = c->ncol;
+    const size_t nout = (size_t)nc * ndep_out * 8;
+    double *buf = nullptr, *srow = nullptr;
+    unsigned long long *bad = nullptr;
+    CK(cudaMalloc(&buf, 5 * nout));
+    cudaError_t e = cudaMalloc(&srow, (size_t)nc * c->ndep * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        cudaFree(srow);
+        return fail(c, RH_ENOMEM, "rh_regrid: %s", cudaGetErrorString(e));
+    }
+    double *zo = buf, *To = zo + nout / 8, *nHo = To + nout / 8, *vzo = nHo + nout / 8, *neo = vzo + nout / 8;
+    RegridParams g{o->dlog_colden, o->dlnT, o->dvz, o->spacing_factor, o->z_top, o->use_z_top ? 1 : 0};
+    unsigned long long hbad = ~0ull;
+    e = cudaMemcpyAsync(bad, &hbad, sizeof hbad, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = launch_regrid(c->ca, ndep_out, g, srow, zo, To, nHo, vzo, neo, bad, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    int r = RH_OK;
+    if (e != cudaSuccess) {
+        r = fail(c, RH_ECUDA, "rh_regrid: %s", cudaGetErrorString(e));
+    } else if (hbad != ~0ull) {
+        r = fail(c, RH_EINVAL, "rh_regrid: z_top leaves no layer in column %llu", hbad);
+    } else {
+        // the new columns replace the old ones (copied; LTE set-up on the new grid)
+        r = rh_load_columns(c, nc, ndep_out, zo, To, neo, nHo, vzo, 1);
+    }
+    cudaFree(buf);
+    cudaFree(srow);
+    cudaFree(bad);
+    return r;
+}
+
 int rh_set_populations(rh_ctx *c, const double *n_in)
 {
     if (!c || !n_in) return RH_EINVAL;
@@ -1681,8 +1737,12 @@ int rh_autotune(rh_ctx *c, int32_t precision, rh_tune_result *out)
     rh_tune_result R;
     memset(&R, 0, sizeof R);
     R.sample_columns = S;
-    const int bws[3] = {precision ? 4 : 2, precision ? 8 : 4, 8};
-    const int nbw = precision ? 2 : 3;
+    // warps per column block: a block's warps share the 32-wavelength tiles of
+    // its column, so counts that divide the tile count into nearly whole
+    // rounds (19 tiles: 7 warps fill 19 of 21 warp-slots, 8 warps 19 of 24)
+    // leave fewer warps idle at the end of the sweep
+    const int bws[4] = {precision ? 4 : 2, precision ? 6 : 4, precision ? 7 : 8, 8};
+    const int nbw = precision ? 4 : 3;
     for (int ib = 0; ib < nbw && e == cudaSuccess; ++ib) {
         const int maxc = mali_max_ctas_per_sm(c->da, N, precision, bws[ib]);
         for (int ct = 1; ct <= std::min(maxc, 2) && R.ncand < RH_MAX_TUNE; ++ct) {

@@ -607,6 +607,13 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
 constexpr int kStartEscapeIterations = 3;
 cudaError_t launch_start(const DevAtom &A, const ColumnArrays &c, int kind, const int *sp_off, const double *sp_nu,
                          const double *sp_ce, cudaStream_t st);
+// depth-grid optimisation: monitor scales and the optional top cut
+struct RegridParams {
+    double dN, dT, dv, spacing, z_top;
+    int use_z_top;
+};
+cudaError_t launch_regrid(const ColumnArrays &c, int M, const RegridParams &g, double *srow, double *zo, double *To,
+                          double *nHo, double *vzo, double *neo, unsigned long long *bad, cudaStream_t st);
 // emergent spectrum: per requested wavelength j, up to RH_SPEC_ACT transitions
 // with constants spec[(j * RH_SPEC_ACT + s) * RH_SPEC_F + f]
 #define RH_SPEC_ACT 8

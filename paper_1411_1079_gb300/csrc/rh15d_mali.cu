@@ -80,20 +80,23 @@ struct KParams {
 };
 
 // Per-block PRD scratch: in R, the redistribution kernels K [sum np^2][N] (per
-// line [k][i][j]), then per PRD point [npp][N] the J-bar weights f, the mean
-// intensity J, rho and D = dJ/drho (the derivative of J through the line's own
-// emission), then the plain-rate accumulators [pacc][N]; in FP64 the supply
-// fraction F and J-bar per line [nprd][N], then the Ng history of rho
-// [4][npp][N] (newest first).
+// line [k][j][i] = K_ij: transposed, so that the threads of a warp, which own
+// consecutive points i, read consecutive addresses), then per PRD point
+// [npp][N] the J-bar weights f, the mean intensity J, rho, D = dJ/drho (the
+// derivative of J through the line's own emission) and the reduced frequency
+// x of the point at each depth, per line [nprd][N] the damping a, then the
+// plain-rate accumulators [pacc][N]; in FP64 the supply fraction F and J-bar
+// per line [nprd][N], then the Ng history of rho [4][npp][N] (newest first).
 template <typename R>
 struct PrdScr {
-    R *K, *f, *J, *rho, *D, *plain;
+    R *K, *f, *J, *rho, *D, *x, *a, *plain;
     double *F, *Jbar, *hist;
 };
 template <typename R>
 __host__ __device__ inline size_t prd_bytes(const DevAtom &A, int N)
 {
-    size_t r = sizeof(R) * ((size_t)A.prd_koff[A.nprd] * N + 4 * (size_t)A.npp * N + (size_t)A.pacc * N);
+    size_t r = sizeof(R) * ((size_t)A.prd_koff[A.nprd] * N + 5 * (size_t)A.npp * N + (size_t)A.nprd * N +
+                            (size_t)A.pacc * N);
     r = (r + 255) & ~(size_t)255;
     return r + sizeof(double) * (2 * (size_t)A.nprd * N + 4 * (size_t)A.npp * N) + 256;
 }
@@ -125,6 +128,10 @@ __device__ inline PrdScr<R> prd_carve(char *base, const DevAtom &A, int N)
     r += (size_t)A.npp * N;
     q.D = r;
     r += (size_t)A.npp * N;
+    q.x = r;
+    r += (size_t)A.npp * N;
+    q.a = r;
+    r += (size_t)A.nprd * N;
     q.plain = r;
     r += (size_t)A.pacc * N;
     size_t off = (reinterpret_cast<size_t>(r) + 255) & ~(size_t)255;
@@ -860,44 +867,61 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
         if constexpr (PRD) {
             // redistribution kernels of the column: K_ij = R(x_j, x_i) w_j / sum_j (.),
             // x in Doppler units of the depth (static frame), and the J-bar weights
-            // f_j = H(a, x_j) w_j / sum_j (.)
-            for (int q = 0; q < A.nprd; ++q) {
+            // f_j = H(a, x_j) w_j / sum_j (.); x and a per point and depth first
+            for (int e = tid; e < A.npp * N; e += blockDim.x) {
+                const int pp = e / N, k = e % N;
+                int q = 0;
+                while (pp >= A.prd_off[q + 1]) ++q;
                 const DevTrans &tr = A.tr[A.prd_t[q]];
-                const int off = A.prd_off[q], np = A.prd_off[q + 1] - off;
+                const double dnuD = tr.nu0 / kC * sqrt(2.0 * kK * p.T[cN + k] / A.mass);
+                ps.x[e] = (R)((p.prd_nu[pp] - tr.nu0) / dnuD);
+            }
+            for (int e = tid; e < A.nprd * N; e += blockDim.x) {
+                const int q = e / N, k = e % N;
+                const DevTrans &tr = A.tr[A.prd_t[q]];
+                const double sk = N > 1 ? (double)k / (N - 1) : 0.0;
+                ps.a[e] = (R)exp((1.0 - sk) * tr.ln_atop + sk * tr.ln_abot);
+            }
+            __syncthreads();
+            for (int q = 0; q < A.nprd; ++q) {
+                const int off = A.prd_off[q], np = A.prd_off[q + 1] - off, npair = np * (np + 1) / 2;
                 R *Kq = ps.K + (size_t)A.prd_koff[q] * N;
-                // R is symmetric: one evaluation per unordered pair (j >= i)
-                for (int e = tid; e < np * np * N; e += blockDim.x) {
-                    const int k = e / (np * np), r = e % (np * np), i = r / np, j = r % np;
-                    if (j < i) continue;
-                    const double T = p.T[cN + k], sk = N > 1 ? (double)k / (N - 1) : 0.0;
-                    const double dnuD = tr.nu0 / kC * sqrt(2.0 * kK * T / A.mass);
-                    const double a = exp((1.0 - sk) * tr.ln_atop + sk * tr.ln_abot);
-                    const double xi = (p.prd_nu[off + i] - tr.nu0) / dnuD, xj = (p.prd_nu[off + j] - tr.nu0) / dnuD;
-                    const R rv = r2a_dev<R>((R)a, (R)xj, (R)xi);
-                    Kq[e] = rv * (R)p.prd_w[off + j];
-                    Kq[(size_t)k * np * np + (size_t)j * np + i] = rv * (R)p.prd_w[off + i];
+                // R is symmetric: one evaluation per unordered pair (i <= j), pairs
+                // numbered row by row, p = i np - i (i - 1) / 2 + (j - i)
+                for (int e = tid; e < npair * N; e += blockDim.x) {
+                    const int k = e / npair, pr = e % npair;
+                    int i = (int)((2.0f * np + 1.0f - sqrtf((2.0f * np + 1.0f) * (2.0f * np + 1.0f) - 8.0f * pr)) * 0.5f);
+                    while (i > 0 && i * np - i * (i - 1) / 2 > pr) --i;
+                    while ((i + 1) * np - (i + 1) * i / 2 <= pr) ++i;
+                    const int j = i + pr - (i * np - i * (i - 1) / 2);
+                    const R ak = ps.a[q * N + k];
+                    const R rv = r2a_dev<R>(ak, ps.x[(size_t)(off + j) * N + k], ps.x[(size_t)(off + i) * N + k]);
+                    Kq[((size_t)k * np + j) * np + i] = rv * (R)p.prd_w[off + j];     // K_ij
+                    Kq[((size_t)k * np + i) * np + j] = rv * (R)p.prd_w[off + i];     // K_ji
                 }
             }
             __syncthreads();
             for (int q = 0; q < A.nprd; ++q) {
-                const DevTrans &tr = A.tr[A.prd_t[q]];
                 const int off = A.prd_off[q], np = A.prd_off[q + 1] - off;
                 R *Kq = ps.K + (size_t)A.prd_koff[q] * N;
                 for (int e = tid; e < np * N; e += blockDim.x) {
-                    R *row = Kq + (size_t)e * np;          // e = k np + i
-                    double sr = 0.0;
-                    for (int j = 0; j < np; ++j) sr += (double)row[j];
-                    for (int j = 0; j < np; ++j) row[j] = (R)((double)row[j] / sr);
+                    const int k = e / np, i = e % np;
+                    R *col = Kq + (size_t)k * np * np + i;                    // K_ij at col[j np]
+                    R sr = 0;
+                    for (int j = 0; j < np; ++j) sr += col[(size_t)j * np];
+                    const R inv = (R)1 / sr;
+                    for (int j = 0; j < np; ++j) col[(size_t)j * np] *= inv;
                 }
                 for (int k = tid; k < N; k += blockDim.x) {
-                    const double T = p.T[cN + k], sk = N > 1 ? (double)k / (N - 1) : 0.0;
-                    const double dnuD = tr.nu0 / kC * sqrt(2.0 * kK * T / A.mass);
-                    const double a = exp((1.0 - sk) * tr.ln_atop + sk * tr.ln_abot);
-                    double fs = 0.0;
-                    for (int j = 0; j < np; ++j) fs += voigt_f64(a, (p.prd_nu[off + j] - tr.nu0) / dnuD) * p.prd_w[off + j];
-                    for (int j = 0; j < np; ++j)
-                        ps.f[(size_t)(off + j) * N + k] =
-                            (R)(voigt_f64(a, (p.prd_nu[off + j] - tr.nu0) / dnuD) * p.prd_w[off + j] / fs);
+                    const R ak = ps.a[q * N + k];
+                    R fs = 0;
+                    for (int j = 0; j < np; ++j) {
+                        const R v = voigt<R>(ak, ps.x[(size_t)(off + j) * N + k], s.vtab) * (R)p.prd_w[off + j];
+                        ps.f[(size_t)(off + j) * N + k] = v;
+                        fs += v;
+                    }
+                    const R inv = (R)1 / fs;
+                    for (int j = 0; j < np; ++j) ps.f[(size_t)(off + j) * N + k] *= inv;
                 }
             }
         }
@@ -1055,10 +1079,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                     }
                     ps.F[e] = s.n[l * N + k] * up_line / in;
                     const int off = A.prd_off[q], np = A.prd_off[q + 1] - off;
-                    double jb = 0.0;
-                    for (int j = 0; j < np; ++j)
-                        jb += (double)ps.f[(size_t)(off + j) * N + k] * (double)ps.J[(size_t)(off + j) * N + k];
-                    ps.Jbar[e] = jb;
+                    R jb = 0;
+                    for (int j = 0; j < np; ++j) jb += ps.f[(size_t)(off + j) * N + k] * ps.J[(size_t)(off + j) * N + k];
+                    ps.Jbar[e] = (double)jb;
                 }
                 __syncthreads();
                 // with Ng: one Jacobi step rho += (r' - rho) / max(1 - eps g_ii, 0.02),
@@ -1067,24 +1090,27 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 const bool jac = ng_order == 2;
                 rpos = (rpos + 3) & 3;
                 double *rh0 = ps.hist + (size_t)rpos * A.npp * N;
-                for (int e = tid; e < A.npp * N; e += blockDim.x) {
-                    const int pp = e / N, k = e % N;
-                    int q = 0;
-                    while (pp >= A.prd_off[q + 1]) ++q;
-                    const int off = A.prd_off[q], np = A.prd_off[q + 1] - off, i = pp - off;
-                    const R *Krow = ps.K + (size_t)A.prd_koff[q] * N + ((size_t)k * np + i) * np;
-                    double sr = 0.0;
-                    for (int j = 0; j < np; ++j) sr += (double)Krow[j] * (double)ps.J[(size_t)(off + j) * N + k];
-                    const double jb = ps.Jbar[q * N + k], F = ps.F[q * N + k];
-                    const double r = 1.0 + F * (sr / jb - 1.0);
-                    double den = 2.0;
-                    if (jac) {
-                        const double g = F * ((double)Krow[i] - (double)ps.f[e] * sr / jb) * (double)ps.D[e] / jb;
-                        den = fmax(1.0 - eps * g, 0.02);
+                // threads own (depth, point) with the point fastest: K_ij of
+                // consecutive points i at consecutive addresses, J_j shared
+                for (int q = 0; q < A.nprd; ++q) {
+                    const int off = A.prd_off[q], np = A.prd_off[q + 1] - off;
+                    const R *Kq = ps.K + (size_t)A.prd_koff[q] * N;
+                    for (int e = tid; e < np * N; e += blockDim.x) {
+                        const int k = e / np, i = e % np, pe = (off + i) * N + k;
+                        const R *col = Kq + (size_t)k * np * np + i;
+                        R sr = 0;
+                        for (int j = 0; j < np; ++j) sr += col[(size_t)j * np] * ps.J[(size_t)(off + j) * N + k];
+                        const R jb = (R)ps.Jbar[q * N + k], F = (R)ps.F[q * N + k], ep = (R)eps;
+                        const R r = (R)1 + F * (sr / jb - (R)1);
+                        R den = 2;
+                        if (jac) {
+                            const R g = F * (col[(size_t)i * np] - ps.f[pe] * sr / jb) * ps.D[pe] / jb;
+                            den = (R)1 - ep * g;
+                            den = den > (R)0.02 ? den : (R)0.02;
+                        }
+                        ps.rho[pe] += ((ep * r + ((R)1 - ep)) - ps.rho[pe]) / den;
+                        rh0[pe] = (double)ps.rho[pe];
                     }
-                    const double rn = (double)ps.rho[e] + ((eps * r + (1.0 - eps)) - (double)ps.rho[e]) / den;
-                    ps.rho[e] = (R)rn;
-                    rh0[e] = (double)ps.rho[e];
                 }
                 __syncthreads();
                 if (rcount < 4) ++rcount;

@@ -519,6 +519,102 @@ __global__ void stokes_kernel(const __grid_constant__ DevAtom A, ColumnArrays c,
     for (int i = 0; i < 4; ++i) o[i] = (double)I[i];
 }
 
+// Depth-grid optimisation (Sect. 2.3), one thread per column, FP64.  The
+// column -- after the optional cut at z_top, whose new top point is
+// interpolated (T, v_z linearly, n_H and n_e logarithmically in height) -- is
+// walked twice: first the monitor s (cumulative, into the scratch row of the
+// column), whose step between neighbours is the root sum of squares of the
+// step in log10 of the hydrogen column density over dN, in ln T over dT, in
+// v_z over dv and in height over spacing x (height / (M - 1)); the column
+// density above each point is n_H H at the top (H the scale height of the
+// top two points) plus the exact integral of an exponential n_H between
+// points.  Then M points at equal steps of s from the top to the bottom,
+// each interpolated on its segment of the old grid.
+__global__ void regrid_kernel(int64_t ncol, int N, int M, const double *z, const double *T, const double *nH,
+                              const double *vz, const double *ne, RegridParams g, double *srow, double *zo,
+                              double *To, double *nHo, double *vzo, double *neo, unsigned long long *bad)
+{
+    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const double *cz = z + col * N, *cT = T + col * N, *cn = nH + col * N, *cv = vz + col * N, *ce = ne + col * N;
+    double *sc = srow + col * N;
+    // the kept column: an optional interpolated top point, then old points k0..N-1
+    int k0 = 0;
+    bool top = false;
+    double tz = 0, tT = 0, tln = 0, tv = 0, tle = 0;
+    if (g.use_z_top && g.z_top < cz[0]) {
+        if (!(g.z_top > cz[N - 1])) {
+            atomicMin(bad, (unsigned long long)col);
+            return;
+        }
+        while (cz[k0] > g.z_top) ++k0;
+        if (cz[k0] < g.z_top) {
+            const double f = (g.z_top - cz[k0 - 1]) / (cz[k0] - cz[k0 - 1]);
+            top = true;
+            tz = g.z_top;
+            tT = cT[k0 - 1] + f * (cT[k0] - cT[k0 - 1]);
+            tln = log(cn[k0 - 1]) + f * (log(cn[k0]) - log(cn[k0 - 1]));
+            tv = cv[k0 - 1] + f * (cv[k0] - cv[k0 - 1]);
+            tle = log(ce[k0 - 1]) + f * (log(ce[k0]) - log(ce[k0 - 1]));
+        }
+    }
+    const int n = N - k0 + (top ? 1 : 0);
+    auto at = [&](int i, double &zz, double &tt, double &ln, double &vv, double &le) {
+        if (top && i == 0) {
+            zz = tz; tt = tT; ln = tln; vv = tv; le = tle;
+            return;
+        }
+        const int k = k0 + i - (top ? 1 : 0);
+        zz = cz[k]; tt = cT[k]; ln = log(cn[k]); vv = cv[k]; le = log(ce[k]);
+    };
+    double z0, T0, l0, v0, e0, z1, T1, l1, v1, e1;
+    at(0, z0, T0, l0, v0, e0);
+    at(1, z1, T1, l1, v1, e1);
+    double zb, Tb, lb, vb, eb;
+    at(n - 1, zb, Tb, lb, vb, eb);
+    const double dzs = g.spacing * (z0 - zb) / (M - 1);
+    // monitor
+    double Ncol = exp(l0) * ((l1 - l0) > 1e-12 ? (z0 - z1) / (l1 - l0) : (z0 - z1));
+    sc[0] = 0.0;
+    for (int i = 0; i + 1 < n; ++i) {
+        if (i > 0) {
+            z0 = z1; T0 = T1; l0 = l1; v0 = v1;
+            at(i + 1, z1, T1, l1, v1, e1);
+        }
+        const double dz = z0 - z1, dl = l1 - l0;
+        const double seg = fabs(dl) > 1e-12 ? dz * (exp(l1) - exp(l0)) / dl : dz * exp(l0);
+        const double N1 = Ncol + seg;
+        const double q1 = log10(N1 / Ncol) / g.dN, q2 = log(T1 / T0) / g.dT, q3 = (v1 - v0) / g.dv, q4 = dz / dzs;
+        sc[i + 1] = sc[i] + sqrt(q1 * q1 + q2 * q2 + q3 * q3 + q4 * q4);
+        Ncol = N1;
+    }
+    // new points
+    const double stot = sc[n - 1];
+    int i = 0;
+    double za, Ta, la, va, ea, zc, Tc, lc, vc, ec;
+    at(0, za, Ta, la, va, ea);
+    at(1, zc, Tc, lc, vc, ec);
+    for (int j = 0; j < M; ++j) {
+        const int64_t o = col * M + j;
+        if (j == M - 1) {
+            zo[o] = zb; To[o] = Tb; nHo[o] = exp(lb); vzo[o] = vb; neo[o] = exp(eb);
+            break;
+        }
+        const double sj = stot * j / (M - 1);
+        while (i + 2 < n && sc[i + 1] < sj) {
+            ++i;
+            za = zc; Ta = Tc; la = lc; va = vc; ea = ec;
+            at(i + 1, zc, Tc, lc, vc, ec);
+        }
+        const double f = (sj - sc[i]) / (sc[i + 1] - sc[i]);
+        zo[o] = za + f * (zc - za);
+        To[o] = Ta + f * (Tc - Ta);
+        nHo[o] = exp(la + f * (lc - la));
+        vzo[o] = va + f * (vc - va);
+        neo[o] = exp(ea + f * (ec - ea));
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_lte_setup(const DevAtom &A, const ColumnArrays &c, int ne_given, cudaStream_t st)
@@ -573,6 +669,14 @@ cudaError_t launch_spectrum(const DevAtom &A, const ColumnArrays &c, double mu, 
         spectrum_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(A, c, mu, nlam, nu_d, nact_d, act_d, spec_d, out);
     else
         spectrum_kernel<double><<<(unsigned)blocks, threads, 0, st>>>(A, c, mu, nlam, nu_d, nact_d, act_d, spec_d, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_regrid(const ColumnArrays &c, int M, const RegridParams &g, double *srow, double *zo, double *To,
+                          double *nHo, double *vzo, double *neo, unsigned long long *bad, cudaStream_t st)
+{
+    regrid_kernel<<<(unsigned)((c.ncol + 127) / 128), 128, 0, st>>>(c.ncol, c.ndep, M, c.z, c.T, c.nH, c.vz, c.ne, g,
+                                                                   srow, zo, To, nHo, vzo, neo, bad);
     return cudaGetLastError();
 }
 

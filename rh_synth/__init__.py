@@ -52,13 +52,15 @@ def hydrogen_like_atom(nbound: int = 5,
                        nmu: int = 5,
                        T_ref: float = 5000.0,
                        metal_floor: float = 1e-4,
-                       prd_lines=()) -> dict:
+                       prd_lines=(),
+                       prd_nlambda: int = 0) -> dict:
     """Atom description of the H-like model atom (arrays are numpy, SI units).
 
     Level index i = n - 1 for bound levels, the continuum is the last level.
     With the defaults the wavelength grid has 4*64 + 6*32 + 5*32 = 608 points.
     ``prd_lines``: (lower n, upper n) pairs treated in partial redistribution,
-    e.g. ((1, 2), (1, 3)) for Lyman alpha and beta.
+    e.g. ((1, 2), (1, 3)) for Lyman alpha and beta; ``prd_nlambda`` > 0 gives
+    those lines that many wavelength points instead of their default.
     """
     nlev = nbound + 1
     E = np.array([E_RYD_EV * (1.0 - 1.0 / n ** 2) for n in range(1, nbound + 1)]
@@ -70,7 +72,10 @@ def hydrogen_like_atom(nbound: int = 5,
             ll.append(n - 1)
             lu.append(m - 1)
             f.append(kramers_f(n, m))
-            nl.append(lyman_nlambda if n == 1 else line_nlambda)
+            if prd_nlambda > 0 and (n, m) in tuple(prd_lines):
+                nl.append(prd_nlambda)
+            else:
+                nl.append(lyman_nlambda if n == 1 else line_nlambda)
     nline = len(ll)
     cont_l = list(range(nbound))
     alpha0 = [7.91e-22 * n for n in range(1, nbound + 1)]

@@ -388,3 +388,42 @@ def test_mixed_128_depths_fixed_point(rh, orc, atom, cols128):
     assert rel(ng, no) < POP_TOL_MIXED
     lam = np.concatenate([np.linspace(121.45e-9, 121.7e-9, 26), np.linspace(656.1e-9, 656.5e-9, 21)])
     assert rel(g.emergent_spectrum(1.0, lam, precision=1), o.emergent_spectrum(1.0, lam)) < INT_TOL_MIXED
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(z_top=2.0e6, dlnT=0.05, spacing_factor=2.0)])
+def test_regrid_matches_oracle(rh, orc, atom, cols, kw):
+    """Depth-grid optimisation (Sect. 2.3) onto 100 points: the GPU's new
+    atmosphere and its LTE set-up equal the oracle's within 1e-12, and a
+    fixed FP64 schedule on the new grid within 1e-9."""
+    g, o = _pair(rh, orc, atom, cols)
+    g.regrid(100, **kw)
+    o.regrid(100, **kw)
+    cg, co = g.columns(), o.columns()
+    for k in ("z", "T", "nH"):
+        assert rel(cg[k], co[k]) < 1e-12, k
+    assert np.max(np.abs(cg["vz"] - co["vz"])) < 1e-9
+    if "z_top" in kw:
+        assert np.all(cg["z"][:, 0] == kw["z_top"])
+    ns_g, ne_g = g.lte()
+    ns_o, ne_o = o.lte()
+    assert rel(ne_g, ne_o) < 1e-12 and rel(ns_g, ns_o) < 1e-12
+    g.iterate(maxiter=6, tol=0.0, precision=0, ng_order=0)
+    o.iterate(maxiter=6, tol=0.0, ng_order=0)
+    assert rel(g.populations()[0], o.populations()[0]) < FP64_TOL
+
+
+def test_regrid_cube_solves(rh, atom):
+    """A 4096-column cube optimised onto 100 points converges everywhere
+    (mixed precision, rh_solve), with particle conservation."""
+    cube = rh_synth.subset(rh_synth.chromosphere_cube(nx=64, ny=64, seed=21), slice(0, 4096))
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    g.load_columns(cube)
+    g.regrid(100)
+    s = g.solve(precision=1)
+    assert s["n_converged"] == 4096, s
+    n = g.populations()[0]
+    assert np.allclose(n.sum(axis=1), g.columns()["nH"], rtol=1e-12)
+    with pytest.raises(rh.RhError) as e:
+        g.regrid(50, z_top=-1.0e6)
+    assert e.value.code == rh.RH_EINVAL
