@@ -385,6 +385,19 @@ int rh_surrogate_load(rh_ctx *ctx, const char *path);
 int rh_surrogate_file_info(const char *path, int32_t *sizes_out, int64_t *nparam_out, char *msg, size_t msg_len);
 
 /* ---------------------------------------------------------------------- */
+/* Shared-memory layout of the column kernel (no counterpart in the paper;  */
+/* a host computation that needs no GPU, for checking the layout): the byte  */
+/* offsets of its 17 regions in carve order (populations, new populations,   */
+/* collisional rates, reduction scratch, rate accumulators, 7 per-depth      */
+/* arrays, continuum factors, damping, populations in the working precision, */
+/* Voigt table, block counters) and the carve's end in offsets_out[0..17],   */
+/* and the bytes the launch allocates in bytes_out (the same function sizes  */
+/* and carves, so the two are equal).  macc: rate accumulators per depth.   */
+/* RH_EINVAL for sizes outside the library's limits.                        */
+int rh_column_smem_layout(int32_t precision, int32_t nlev, int32_t ndep, int32_t ntr, int32_t ncont, int32_t nline,
+                          int32_t macc, size_t *offsets_out, size_t *bytes_out);
+
+/* ---------------------------------------------------------------------- */
 /* Measured fused multiply-add rate of a device (no counterpart in the      */
 /* paper: the denominator of the column kernel's roofline).  precision 1    */
 /* FP32, 0 FP64.  Every thread of 4 x 256-thread blocks per SM runs 16      */

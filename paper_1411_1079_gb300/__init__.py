@@ -27,7 +27,7 @@ EXPORTS = ("rh_create", "rh_destroy", "rh_last_error", "rh_setup_atom", "rh_nlam
            "rh_surrogate_get_state", "rh_surrogate_set_state", "rh_surrogate_train", "rh_surrogate_loss_grad",
            "rh_surrogate_predict", "rh_solve", "rh_autotune", "rh_start_populations",
            "rh_emergent_stokes", "rh_surrogate_save", "rh_surrogate_load", "rh_surrogate_file_info",
-           "rh_fma_peak", "rh_regrid", "rh_get_columns")
+           "rh_fma_peak", "rh_regrid", "rh_get_columns", "rh_column_smem_layout")
 
 MAX_RERUN = 4
 MAX_TUNE = 8
@@ -138,6 +138,7 @@ def lib(path: str | None = None):
         L.rh_surrogate_file_info.argtypes = [C.c_char_p, _ip, C.POINTER(C.c_int64), C.c_char_p, C.c_size_t]
         L.rh_regrid.argtypes = [vp, C.c_int32, C.POINTER(GridOpts)]
         L.rh_get_columns.argtypes = [vp, _dp, _dp, _dp, _dp]
+        L.rh_column_smem_layout.argtypes = [C.c_int32] * 7 + [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         L.rh_fma_peak.argtypes = [C.c_int32, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
     return _lib
@@ -158,6 +159,17 @@ def _ptr(x):
     if hasattr(x, "data_ptr"):
         return C.c_void_p(x.data_ptr())
     return C.c_void_p(x.ctypes.data)
+
+
+def column_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc):
+    """rh_column_smem_layout (host only): ([18] region offsets in carve
+    order, the carve's end last; allocated bytes)."""
+    off = (C.c_size_t * 18)()
+    b = C.c_size_t()
+    rc = lib().rh_column_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc, off, C.byref(b))
+    if rc:
+        raise RhError(rc, "rh_column_smem_layout: invalid sizes")
+    return list(off), b.value
 
 
 def fma_peak(device: int = 0, precision: int = 1, seconds: float = 0.5) -> dict:

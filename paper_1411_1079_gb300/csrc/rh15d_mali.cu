@@ -154,46 +154,77 @@ struct Smem {
     int *ibuf;                 // [8]
 };
 
+// Byte offsets of the regions of the block's dynamic shared memory.  The one
+// function both sizes the allocation (host) and carves it (device), so the
+// two cannot disagree: a layout whose carve ends past the allocated size
+// (regions reserved by the carve but dropped from the size) writes outside
+// the block's shared memory.
+struct SmemLayout {
+    size_t n, nn, Cr, red, slot, dz, ivth, vz, hkT, kff, nhm, thom, Gc, ad, nr, vtab, ibuf, end;
+};
+template <typename R>
+__host__ __device__ inline SmemLayout smem_layout(int L, int N, int ntr, int ncont, int nline, int macc)
+{
+    SmemLayout o;
+    size_t b = 0;
+    o.n = b;
+    b += sizeof(double) * (size_t)L * N;
+    o.nn = b;
+    b += sizeof(double) * (size_t)L * N;
+    o.Cr = b;
+    b += sizeof(double) * (size_t)N * 2 * ntr;
+    o.red = b;
+    b += sizeof(double) * kRedDoubles;
+    o.slot = b;
+    b += sizeof(R) * (size_t)macc * N;
+    size_t *one[7] = {&o.dz, &o.ivth, &o.vz, &o.hkT, &o.kff, &o.nhm, &o.thom};
+    for (int i = 0; i < 7; ++i) {
+        *one[i] = b;
+        b += sizeof(R) * (size_t)N;
+    }
+    o.Gc = b;
+    b += sizeof(R) * (size_t)ncont * N;
+    o.ad = b;
+    b += sizeof(R) * (size_t)nline * N;
+    o.nr = b;
+    b += sizeof(R) * (size_t)L * N;
+    b = (b + 15) & ~(size_t)15;                    // float4 table: 16-byte aligned
+    o.vtab = b;
+    b += sizeof(float4) * (RH_VT_N + 1);
+    o.ibuf = b;
+    b += sizeof(int) * 8;
+    o.end = b;
+    return o;
+}
+
 template <typename R>
 __host__ __device__ size_t smem_bytes(int L, int N, int ntr, int ncont, int nline, int macc)
 {
-    size_t b = 0;
-    b += sizeof(double) * (2 * L * N + (size_t)N * 2 * ntr);
-    b += sizeof(R) * ((size_t)macc * N + 7 * N + (size_t)ncont * N + (size_t)nline * N + (size_t)L * N);
-    b += sizeof(float4) * (RH_VT_N + 1) + 16;
-    b += sizeof(double) * kRedDoubles + sizeof(int) * 8 + 64;
-    return b;
+    return smem_layout<R>(L, N, ntr, ncont, nline, macc).end;
 }
 
 template <typename R>
 __device__ Smem<R> carve(char *base, int L, int N, int ntr, int ncont, int nline, int macc)
 {
+    const SmemLayout o = smem_layout<R>(L, N, ntr, ncont, nline, macc);
     Smem<R> s;
-    double *d = reinterpret_cast<double *>(base);
-    s.n = d;
-    d += L * N;
-    s.nn = d;
-    d += L * N;
-    s.Cr = d;
-    d += N * 2 * ntr;
-    s.red = d;
-    d += kRedDoubles;
-    R *r = reinterpret_cast<R *>(d);
-    s.slot = r;
-    r += macc * N;
-    s.dz = r; r += N;
-    s.ivth = r; r += N;
-    s.vz = r; r += N;
-    s.hkT = r; r += N;
-    s.kff = r; r += N;
-    s.nhm = r; r += N;
-    s.thom = r; r += N;
-    s.Gc = r; r += ncont * N;
-    s.ad = r; r += nline * N;
-    s.nr = r; r += L * N;
-    size_t off = (reinterpret_cast<size_t>(r) + 15) & ~(size_t)15;
-    s.vtab = reinterpret_cast<float4 *>(off);
-    s.ibuf = reinterpret_cast<int *>(s.vtab + RH_VT_N + 1);
+    s.n = reinterpret_cast<double *>(base + o.n);
+    s.nn = reinterpret_cast<double *>(base + o.nn);
+    s.Cr = reinterpret_cast<double *>(base + o.Cr);
+    s.red = reinterpret_cast<double *>(base + o.red);
+    s.slot = reinterpret_cast<R *>(base + o.slot);
+    s.dz = reinterpret_cast<R *>(base + o.dz);
+    s.ivth = reinterpret_cast<R *>(base + o.ivth);
+    s.vz = reinterpret_cast<R *>(base + o.vz);
+    s.hkT = reinterpret_cast<R *>(base + o.hkT);
+    s.kff = reinterpret_cast<R *>(base + o.kff);
+    s.nhm = reinterpret_cast<R *>(base + o.nhm);
+    s.thom = reinterpret_cast<R *>(base + o.thom);
+    s.Gc = reinterpret_cast<R *>(base + o.Gc);
+    s.ad = reinterpret_cast<R *>(base + o.ad);
+    s.nr = reinterpret_cast<R *>(base + o.nr);
+    s.vtab = reinterpret_cast<float4 *>(base + o.vtab);
+    s.ibuf = reinterpret_cast<int *>(base + o.ibuf);
     return s;
 }
 
@@ -1190,6 +1221,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
 }  // namespace
 
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep) { return sizeof(double) * 4 * A.nlev * ndep; }
+
+// the column kernel's shared-memory layout for the given sizes: its byte
+// offsets in carve order and the allocated size (host computation only)
+int mali_smem_layout(int precision, int L, int N, int ntr, int ncont, int nline, int macc, size_t *offsets, int noff,
+                     size_t *bytes)
+{
+    const SmemLayout o = precision == 1 ? smem_layout<float>(L, N, ntr, ncont, nline, macc)
+                                        : smem_layout<double>(L, N, ntr, ncont, nline, macc);
+    const size_t v[18] = {o.n, o.nn, o.Cr, o.red, o.slot, o.dz, o.ivth, o.vz, o.hkT, o.kff, o.nhm, o.thom, o.Gc,
+                          o.ad, o.nr, o.vtab, o.ibuf, o.end};
+    for (int i = 0; i < noff && i < 18; ++i) offsets[i] = v[i];
+    *bytes = precision == 1 ? smem_bytes<float>(L, N, ntr, ncont, nline, macc)
+                            : smem_bytes<double>(L, N, ntr, ncont, nline, macc);
+    return 18;
+}
 
 size_t mali_phic_bytes_per_block(const DevAtom &A, int ndep, int precision)
 {
