@@ -55,6 +55,57 @@ DRAM_BYTES_PER_COLUMN_ITERATION = (11.533787e9 + 1.232767e9) / (608 * 12)
 WARP_INST_PER_COLUMN_ITERATION = 24616860192 / (608 * 12)
 
 
+def algorithmic_flop_per_pt(atom, nu):
+    """Algorithmic FP32 operations per formal-solver point of the mixed-
+    precision column kernel, counted from its source in the units of the ncu
+    count (2 x FMA + ADD + MUL; the MUFU exponentials and reciprocals are
+    counted apart), for the transitions actually active at each wavelength
+    (no padding lanes, no inactive slots of a tile's union) and the
+    optically thick branch of the SC weights (one exponential per step; the
+    Taylor branch of thin steps is an accuracy choice).  Per depth, ray and
+    direction, with n_l lines and n_c continua active (K = n_l + n_c):
+      depth terms (x, e^-x, 1-e^-x, chi_bg, B, eta_bg)     11 + 2 n_l + 7 n_c,
+          shared by the two angles of a pass (5 angles: 3 passes);
+      opacities of the ray (chi, eta)                      1 + 6 n_l + 1 n_c;
+      SC step (dtau, weights, I, I_eff, Psi*, S)            19;
+      rate terms per active line (continuum)               10 (9) + (K - 1)
+          (+ 2 + (K - 1) cross terms when K > 1, + (2 + (K - 1)) sums into
+          the pass's registers for the second angle of a pass);
+      warp reduce-scatter of P = 2^ceil(log2 K(K+1)) values  P - 1 + 5 - log2 P
+          per pass.
+    Both directions count once per point."""
+    h, c, k = 6.62607015e-34, 2.99792458e8, 1.380649e-23
+    E = np.asarray(atom["E_J"])
+    vD = np.sqrt(2 * k * atom["T_ref"] / (atom["mass_amu"] * 1.66053906660e-27))
+    ranges = []
+    for l, u, q in zip(atom["line_l"], atom["line_u"], atom["line_qwing"]):
+        nu0 = (E[u] - E[l]) / h
+        ranges.append((nu0 * (1 - q * vD / c), nu0 * (1 + q * vD / c), 0))
+    for l, r in zip(atom["cont_l"], atom["cont_ratio"]):
+        nue = (E[-1] - E[l]) / h
+        ranges.append((nue, r * nue, 1))
+    nmu = atom["nmu"]
+    npass = (nmu + 1) // 2
+    share = npass / nmu                      # depth terms and reductions per ray
+    second = (nmu - npass) / nmu             # rays that sum into a pass's registers
+    tot = 0.0
+    mufu = 0.0
+    for f in nu:
+        act = [kind for lo, hi, kind in ranges if lo * (1 - 1e-13) <= f <= hi * (1 + 1e-13)]
+        nl = act.count(0)
+        nc = act.count(1)
+        K = max(nl + nc, 1)
+        P = 1 << int(np.ceil(np.log2(K * (K + 1))))
+        dc = (11 + 2 * nl + 7 * nc) * share
+        av = 1 + 6 * nl + nc
+        st = 19
+        ct = 10 * nl + 9 * nc + K * (K - 1) + (K * (2 + (K - 1)) if K > 1 else 0) + K * (2 + (K - 1)) * second
+        fl = (P - 1 + 5 - np.log2(P)) * share
+        tot += 2 * (dc + av + st + ct + fl)
+        mufu += 2 * (2 * share + 3)          # e^-x, rcp(1 - e^-x); rcp(chi), e^-dtau, rcp(dtau)
+    return tot / len(nu), mufu / len(nu)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -175,6 +226,41 @@ def cpu_baseline(cube, seconds_target=15.0):
                       "strategy, %d threads, %.1f s; %d converged" % (n1, cores, dt, conv)}
 
 
+def true_error(cube, n_gpu, nsample=32, seed=2024):
+    """The headline solve's error against the oracle's tight fixed point on
+    a seeded sample of columns: the 1e-3 stopping criterion does not bound
+    the true error when the iteration's spectral radius is near one."""
+    import oracle
+    cores = os.cpu_count() or 1
+    idx = np.sort(np.random.default_rng(seed).choice(cube["T"].shape[0], nsample, replace=False))
+    o = oracle.Oracle()
+    o.setup_atom(rh_synth.hydrogen_like_atom())
+    o.load_columns(rh_synth.subset(cube, idx))
+    t0 = time.perf_counter()
+    o.iterate(maxiter=2000, tol=1e-9, nthreads=cores)
+    no, _, sto, _ = o.populations()
+    ok = sto == oracle.ST_CONV
+    d = np.abs(n_gpu[idx] / no - 1).max(axis=(1, 2))[ok]
+    return {"max_rel_dn": float(d.max()) if d.size else None, "median_rel_dn": float(np.median(d)) if d.size else None,
+            "columns_above_1e-3": int((d > 1e-3).sum()), "columns": int(ok.sum()),
+            "reference": "oracle (FP64) converged to max|dn/n| < 1e-9 on %d seeded columns, %d threads, %.1f s"
+                         % (nsample, cores, time.perf_counter() - t0)}
+
+
+def measured_peaks(rh, local):
+    """FP32 and FP64 FMA rates of this GPU (rh_fma_peak), each with the
+    median SM clock sampled while it ran."""
+    out = {}
+    for name, prec in (("fp32", 1), ("fp64", 0)):
+        rh.fma_peak(local, prec, 0.05)                      # warm-up
+        with ClockSampler(local) as clk:
+            r = rh.fma_peak(local, prec, 1.0)
+        c = clk.summary()
+        out[name] = {"tflops": r["flop_s"] / 1e12, "seconds": r["seconds"], "sm_mhz": c.get("sm_mhz"),
+                     "reasons": c.get("reasons")}
+    return out
+
+
 def oracle_two_pass(o, cols, cores):
     """The oracle with the same two passes as the GPU run; returns converged count."""
     import oracle
@@ -229,6 +315,105 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_full_config(rh, torch, local, stream, ncol, train_cols, seed=5678, fp64_columns=0, oracle_columns=0):
+    """The full-run configuration: 512x512 columns of 128 heights (the
+    first ncol of that cube), Lyman alpha and beta in angle-averaged PRD with
+    200 frequencies each (880 wavelengths), solved from the learned guess in
+    mixed precision (a network trained on train_cols CRD-converged columns of
+    a disjoint 128-height cube), then the FP32 Zeeman Stokes spectrum of H
+    alpha (400 wavelengths, mu = 1, seeded field).  One step each, timed on
+    the device."""
+    t_all = time.perf_counter()
+    patom = rh_synth.hydrogen_like_atom(prd_lines=((1, 2), (1, 3)), prd_nlambda=200)
+    catom = dict(patom)
+    catom["line_prd"] = patom["line_prd"] * 0
+    nd = 128
+    c = rh.Context(local, stream=stream.cuda_stream)
+    c.setup_atom(catom)
+    train = rh_synth.chromosphere_cube(256, 256, nd, seed=TRAIN_SEED + 17)
+    if train_cols < 65536:
+        train = rh_synth.subset(train, slice(0, train_cols))
+    c.load_columns(train)
+    c.solve(precision=1)
+    c.surrogate_init(hidden=512, nhidden=3, seed=0)
+    tr = c.surrogate_train(epochs=TRAIN_EPOCHS, batch=512, lr=2e-3, seed=1)
+    state = c.surrogate_state()
+    del c
+    full = rh_synth.chromosphere_cube(512, 512, nd, seed=seed)
+    cube = full if ncol >= 512 * 512 else rh_synth.subset(full, slice(0, ncol))
+    del full
+    dev = {k: torch.from_numpy(v).to("cuda") for k, v in cube.items()}
+    p = rh.Context(local, stream=stream.cuda_stream)
+    p.setup_atom(patom)
+    p.load_columns(dev, on_device=True)
+    p.surrogate_init(hidden=512, nhidden=3, seed=0)
+    p.surrogate_set_state(state)
+    opts = dict(maxiter=MAXITER, tol=TOL, precision=1, start=1, prd_eps0=0.05)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s = p.solve(**opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n_gpu = p.populations()[0]
+    # Stokes H alpha after convergence
+    rng_f = np.random.default_rng(seed + 1)
+    Bc, thc, chc = rng_f.uniform(0.0, 0.2, ncol), np.arccos(rng_f.uniform(-1.0, 1.0, ncol)), rng_f.uniform(0, 2 * np.pi, ncol)
+    fld = [torch.from_numpy(np.repeat(x[:, None], nd, axis=1)).to("cuda") for x in (Bc, thc, chc)]
+    ha = [i for i, (l, u) in enumerate(zip(patom["line_l"], patom["line_u"])) if (l, u) == (1, 2)][0]
+    nu_ha = (patom["E_J"][2] - patom["E_J"][1]) / 6.62607015e-34
+    lam = 2.99792458e8 / nu_ha + np.linspace(-2e-10, 2e-10, 400)
+    iquv = torch.empty((ncol, lam.size, 4), dtype=torch.float64, device="cuda")
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    p.emergent_stokes(ha, 1.5, *fld, lam, precision=1, out=iquv)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    st_ms = s0.elapsed_time(s1)
+    out = {"workload": "%d columns of the 512x512 synthetic chromosphere cube (seed %d), 128 heights, H-like atom "
+                       "with Lyman alpha and beta in angle-averaged PRD (R_II-A, 200 frequencies each; 880 "
+                       "wavelengths), learned start, mixed precision, tol 1e-3; then the FP32 H alpha Zeeman "
+                       "Stokes spectrum (400 wavelengths)" % (ncol, seed),
+           "columns": ncol, "value": ncol / ((ms + st_ms) / 1e3), "unit": "columns/s",
+           "solve": {"ms": ms, "converged": s["n_converged"], "iterations_per_column": s["iterations_total"] / ncol,
+                     "rerun_columns": s["rerun_columns"], "columns_per_s": ncol / (ms / 1e3)},
+           "stokes": {"ms": st_ms, "columns_per_s": ncol / (st_ms / 1e3),
+                      "max_abs_V_over_I": float((iquv[..., 3].abs() / iquv[..., 0]).max())},
+           "learned_start": {"train_columns": train_cols, "loss_last_epoch": tr["loss_last_epoch"],
+                             "trained_on": "CRD-converged 128-height columns of a disjoint cube"}}
+    if fp64_columns > 0:
+        idx = np.sort(np.random.default_rng(99).choice(ncol, min(fp64_columns, ncol), replace=False))
+        q = rh.Context(local, stream=stream.cuda_stream)
+        q.setup_atom(patom)
+        q.load_columns(rh_synth.subset(cube, idx))
+        t0 = time.perf_counter()
+        sq = q.iterate(maxiter=MAXITER, tol=TOL, precision=0, prd_eps0=0.05)
+        dt = time.perf_counter() - t0
+        out["lte_start_fp64"] = {"value": sq["n_converged"] / dt, "unit": "columns/s", "columns": len(idx),
+                                 "converged": sq["n_converged"], "iterations_per_column": sq["iterations_total"] / len(idx),
+                                 "seconds": dt, "sample": "plain FP64 GPU MALI from LTE, one pass"}
+    if oracle_columns > 0:
+        import oracle
+        idx = np.sort(np.random.default_rng(2024).choice(ncol, min(oracle_columns, ncol), replace=False))
+        o = oracle.Oracle()
+        o.setup_atom(patom)
+        o.load_columns(rh_synth.subset(cube, idx))
+        t0 = time.perf_counter()
+        o.iterate(maxiter=3000, tol=1e-8, prd_eps0=0.05, nthreads=os.cpu_count() or 1)
+        no, _, sto, _ = o.populations()
+        ok = sto == oracle.ST_CONV
+        d = np.abs(n_gpu[idx] / no - 1).max(axis=(1, 2))[ok]
+        out["true_error"] = {"max_rel_dn": float(d.max()) if d.size else None,
+                             "median_rel_dn": float(np.median(d)) if d.size else None, "columns": int(ok.sum()),
+                             "reference": "oracle converged to 1e-8 on %d seeded columns, %.0f s"
+                                          % (len(idx), time.perf_counter() - t0)}
+    out["wall_s"] = time.perf_counter() - t_all
+    return out
+
+
 def run_gpu(args):
     import torch
     import __graft_entry__
@@ -248,6 +433,7 @@ def run_gpu(args):
     ctx = rh.Context(local, stream=stream.cuda_stream)
     atom = rh_synth.hydrogen_like_atom()
     ctx.setup_atom(atom)
+    alg_flop, alg_mufu = algorithmic_flop_per_pt(atom, ctx.grid())
     # learned initial guess: converge a disjoint cube from LTE, train on it (untimed)
     t0 = time.perf_counter()
     ctx.load_columns(rh_synth.chromosphere_cube(NX, NY, NDEP, seed=seeds["train"]))
@@ -258,6 +444,7 @@ def run_gpu(args):
                   "epochs": TRAIN_EPOCHS, "loss_first_epoch": tr["loss_first_epoch"],
                   "loss_last_epoch": tr["loss_last_epoch"], "train_seconds": tr["seconds"],
                   "data_generation_seconds": time.perf_counter() - t0 - tr["seconds"]}
+    peaks_meas = measured_peaks(rh, local)
     dev = {k: torch.from_numpy(v).to("cuda") for k, v in cube.items()}
     ctx.load_columns(dev, on_device=True)
     opts = dict(maxiter=MAXITER, tol=TOL, precision=1, persistent=1, start=1)
@@ -295,6 +482,7 @@ def run_gpu(args):
         barrier()
         torch.cuda.profiler.stop()
     ms = e0.elapsed_time(e1)
+    n_headline = ctx.populations()[0] if rank == 0 and not args.no_cpu_baseline else None
     # the same solve from LTE, for comparison (one step)
     lte_opts = dict(opts, start=0)
     barrier()
@@ -417,9 +605,10 @@ def run_gpu(args):
     # plain FP64 MALI from LTE on a random sample of the cube (FP64 arithmetic is
     # slow on this part: one column per SM keeps the run under a minute)
     fp64 = None
-    if args.fp64_columns > 0:
+    nsm_dev = torch.cuda.get_device_properties(local).multi_processor_count
+    if args.fp64_columns_per_sm > 0:
         rng = np.random.default_rng(99)
-        idx = np.sort(rng.choice(ncol, size=min(args.fp64_columns, ncol), replace=False))
+        idx = np.sort(rng.choice(ncol, size=min(args.fp64_columns_per_sm * nsm_dev, ncol), replace=False))
         ctx.load_columns(rh_synth.subset(cube, idx))
         barrier()
         t_f = time.perf_counter()
@@ -429,18 +618,36 @@ def run_gpu(args):
         fp64 = {"value": s_f["n_converged"] / f_s, "unit": "columns/s", "columns": len(idx),
                 "converged": s_f["n_converged"], "seconds": f_s,
                 "iterations_per_column": s_f["iterations_total"] / len(idx),
-                "sample": "%d random columns of the cube, LTE start, FP64 throughout, one pass" % len(idx)}
+                "formal_solver_pts_per_s": s_f["pts"] / s_f["seconds"],
+                "roofline": {"bound": "alu", "achieved": s_f["pts"] * alg_flop / s_f["seconds"] / 1e12,
+                             "peak": peaks_meas["fp64"]["tflops"], "unit": "TFLOP/s",
+                             "frac": s_f["pts"] * alg_flop / s_f["seconds"] / 1e12
+                                     / peaks_meas["fp64"]["tflops"],
+                             "flop_per_pt": alg_flop,
+                             "peak_note": "measured FP64 FMA rate (rh_fma_peak) of this GPU; the same "
+                                          "algorithmic operation count as the FP32 sweep (FP64 exponentials, "
+                                          "divisions and reciprocals run as FMA sequences on top); ncu: FP64 "
+                                          "pipe 80 % busy (profiles/mali_kernel_fp64_152col.md)"},
+                "sample": "%d random columns of the cube (%d per SM), LTE start, FP64 throughout, one pass"
+                          % (len(idx), len(idx) // nsm_dev)}
 
+    full_run = None
+    if args.full_run_columns > 0:
+        full_run = run_full_config(rh, torch, local, stream, args.full_run_columns, args.full_run_train,
+                                   oracle_columns=0 if args.no_cpu_baseline else args.full_run_oracle)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     peaks = _peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # FP32 lanes x 2 flop per FMA x clock (152 SMs, 128 FP32 lanes each)
-    nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    peak_tflops = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = pts * FLOP_PER_PT / kern_s / 1e12
+    nsm = nsm_dev
+    # measured FP32 FMA rate, scaled from the clock it ran at to the median
+    # clock of the timed region
+    p32 = peaks_meas["fp32"]
+    peak_tflops = p32["tflops"] * (sm_mhz / p32["sm_mhz"] if p32.get("sm_mhz") else 1.0)
+    achieved = pts * alg_flop / kern_s / 1e12
+    achieved_exec = pts * FLOP_PER_PT / kern_s / 1e12
     pts_s = pts / kern_s
     line = {
         "metric": METRIC, "value": value, "unit": "columns/s", "n_gpus": ws, "steps": args.steps,
@@ -463,6 +670,7 @@ def run_gpu(args):
         "lte_start_fp64": fp64,
         "other_starts": other,
         "cube_512": big,
+        "full_run": full_run,
         "stokes": stokes,
         "prd": prd,
         "surrogate": train_info,
@@ -473,6 +681,15 @@ def run_gpu(args):
         "rerun_columns_per_step": rescued / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
+                     "flop_per_pt": alg_flop,
+                     "flop_note": "algorithmic FP32 operations per point (2 x FMA + ADD + MUL) counted from the "
+                                  "sweep's source for the transitions active at each wavelength, thick-layer SC "
+                                  "branch (bench.algorithmic_flop_per_pt); plus %.1f MUFU operations" % alg_mufu,
+                     "executed": {"flop_per_pt": FLOP_PER_PT, "achieved": achieved_exec,
+                                  "frac": achieved_exec / peak_tflops,
+                                  "note": "thread-level FP32 operations executed (ncu, 608 columns x 12 "
+                                          "iterations): padding, both SC branches where a warp diverges, inactive "
+                                          "slots of a tile's transition union, the profile build"},
                      "traffic": DRAM_BYTES_PER_COLUMN_ITERATION * iters / args.steps,
                      "traffic_note": "bytes per launch: ncu DRAM bytes per column-iteration on the "
                                      "608-column x 12-iteration case x column-iterations of one launch",
@@ -481,13 +698,17 @@ def run_gpu(args):
                                      "peak": nsm * 4 * sm_mhz * 1e6, "unit": "warp instructions/s",
                                      "frac": WARP_INST_PER_COLUMN_ITERATION * iters / kern_s
                                              / (nsm * 4 * sm_mhz * 1e6)},
-                     "peak_note": "FP32 FMA peak = %d SMs x 128 lanes x 2 x %.0f MHz (median SM clock "
-                                  "sampled during the timed region)" % (nsm, sm_mhz)},
+                     "peak_note": "measured FP32 FMA rate (rh_fma_peak: %.1f TFLOP/s at %s MHz) scaled to the "
+                                  "median SM clock of the timed region (%.0f MHz); nominal 152 x 128 x 2 x clock "
+                                  "= %.1f TFLOP/s" % (p32["tflops"], p32.get("sm_mhz"), sm_mhz,
+                                                      nsm * 256 * sm_mhz * 1e-6)},
+        "measured_peaks": peaks_meas,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
+        line["true_error"] = true_error(cube, n_headline)
         line["cpu_baseline"] = cpu_baseline(cube)
     print(json.dumps(line), flush=True)
     if dist:
@@ -495,18 +716,46 @@ def run_gpu(args):
 
 
 def run_ncu_case(args):
-    """Small fixed case for ncu captures: 608 columns of the cube, a fixed
-    number of iterations (--ncu-iters)."""
+    """Small fixed cases for ncu captures (columns of the 256x256 cube):
+    crd -- the column kernel, --ncu-iters iterations from LTE;
+    prd -- the same with Lyman alpha and beta in PRD (64 points each);
+    stokes -- the H alpha Zeeman Stokes spectrum (400 wavelengths) after a
+              few iterations;
+    mlp -- one training epoch of the learned-guess network (BF16 GEMMs)."""
     import __graft_entry__
     __graft_entry__.build()
     import paper_1411_1079_gb300 as rh
     cube = rh_synth.chromosphere_cube(NX, NY, NDEP, seed=1234)
+    sub = rh_synth.subset(cube, slice(0, args.ncu_columns))
     ctx = rh.Context(0)
-    ctx.setup_atom(rh_synth.hydrogen_like_atom())
-    ctx.load_columns(rh_synth.subset(cube, slice(0, args.ncu_columns)))
-    s = ctx.iterate(maxiter=args.ncu_iters, tol=0.0, precision=args.ncu_precision)
-    print(json.dumps({"ncu_case": True, "columns": args.ncu_columns, "iterations": args.ncu_iters,
-                      "seconds": s["seconds"]}))
+    kind = args.ncu_kind
+    atom = rh_synth.hydrogen_like_atom(prd_lines=((1, 2), (1, 3))) if kind == "prd" else \
+        rh_synth.hydrogen_like_atom()
+    ctx.setup_atom(atom)
+    ctx.load_columns(sub)
+    out = {"ncu_case": kind, "columns": args.ncu_columns, "precision": args.ncu_precision}
+    if kind in ("crd", "prd"):
+        s = ctx.iterate(maxiter=args.ncu_iters, tol=0.0, precision=args.ncu_precision,
+                        prd_eps0=0.05 if kind == "prd" else 0.0)
+        out.update(iterations=args.ncu_iters, seconds=s["seconds"], pts=s["pts"])
+    elif kind == "stokes":
+        ctx.iterate(maxiter=args.ncu_iters, tol=0.0, precision=1)
+        ncol = args.ncu_columns
+        rng = np.random.default_rng(2024)
+        fld = [np.repeat(x[:, None], NDEP, axis=1) for x in
+               (rng.uniform(0.0, 0.2, ncol), np.arccos(rng.uniform(-1.0, 1.0, ncol)), rng.uniform(0, 2 * np.pi, ncol))]
+        ha = [i for i, (l, u) in enumerate(zip(atom["line_l"], atom["line_u"])) if (l, u) == (1, 2)][0]
+        nu_ha = (atom["E_J"][2] - atom["E_J"][1]) / 6.62607015e-34
+        lam = 2.99792458e8 / nu_ha + np.linspace(-2e-10, 2e-10, 400)
+        t0 = time.perf_counter()
+        ctx.emergent_stokes(ha, 1.5, *fld, lam, precision=args.ncu_precision)
+        out.update(nlambda=400, seconds=time.perf_counter() - t0)
+    elif kind == "mlp":
+        ctx.solve(precision=1)                    # converged columns to learn from
+        ctx.surrogate_init(hidden=512, nhidden=3, seed=0)
+        t = ctx.surrogate_train(epochs=1, batch=512, lr=2e-3, seed=1)
+        out.update(seconds=t["seconds"])
+    print(json.dumps(out))
 
 
 def main():
@@ -518,9 +767,18 @@ def main():
                     help="skip the one-step 512x512 cube measurement")
     ap.add_argument("--prd-columns", type=int, default=4096,
                     help="columns of the partial-redistribution timing (0: skip)")
-    ap.add_argument("--fp64-columns", type=int, default=152,
-                    help="columns of the plain FP64 LTE-start comparison (0: skip)")
+    ap.add_argument("--full-run-columns", type=int, default=1216,
+                    help="columns of the full-run configuration (512x512 x 128 heights, PRD Lyman alpha/beta at "
+                         "200 frequencies, Stokes) to solve; 262144 = the whole cube (0: skip)")
+    ap.add_argument("--full-run-train", type=int, default=8192,
+                    help="CRD-converged 128-height columns the full run's network is trained on")
+    ap.add_argument("--full-run-oracle", type=int, default=0,
+                    help="full-run columns compared with the oracle (its 200-point PRD kernels take minutes "
+                         "per column to build on the host; 0: skip)")
+    ap.add_argument("--fp64-columns-per-sm", type=int, default=3,
+                    help="columns per SM of the plain FP64 LTE-start comparison (0: skip)")
     ap.add_argument("--ncu-columns", type=int, default=608)
+    ap.add_argument("--ncu-kind", default="crd", choices=["crd", "prd", "stokes", "mlp"])
     ap.add_argument("--ncu-precision", type=int, default=1)
     ap.add_argument("--ncu-iters", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)

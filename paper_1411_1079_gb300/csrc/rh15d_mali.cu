@@ -98,7 +98,8 @@ __host__ __device__ inline size_t prd_bytes(const DevAtom &A, int N)
     size_t r = sizeof(R) * ((size_t)A.prd_koff[A.nprd] * N + 5 * (size_t)A.npp * N + (size_t)A.nprd * N +
                             (size_t)A.pacc * N);
     r = (r + 255) & ~(size_t)255;
-    return r + sizeof(double) * (2 * (size_t)A.nprd * N + 4 * (size_t)A.npp * N) + 256;
+    r += sizeof(double) * (2 * (size_t)A.nprd * N + 4 * (size_t)A.npp * N) + 256;
+    return (r + 255) & ~(size_t)255;   // every block's scratch 256-byte aligned (float4 loads of K)
 }
 // Per-block profile cache: the line profile phi (Voigt H(a, v) times its
 // normalisation and 1/Doppler width, v including the ray's Doppler shift)
@@ -766,9 +767,9 @@ __device__ int solve_depth(const DevAtom &A, const double *slotd, const float *s
     double G[RH_MAXLEV * RH_MAXLEV];
     for (int i = 0; i < L * L; ++i) G[i] = 0.0;
     for (int e = 0; e < A.nmap; ++e) {
-        int a = A.map_acc[e];
-        double v = slotd ? slotd[a * N + k] : (double)slotf[a * N + k];
-        G[A.map_row[e] * L + A.map_col[e]] += A.map_sign[e] * v;
+        const int a = A.map_acc[e];
+        const double v = slotd ? slotd[a * N + k] : (double)slotf[a * N + k];
+        G[A.map_row[e] * L + A.map_col[e]] += A.map_sign[e] > 0 ? v : -v;   // signs are +-1
     }
     const double *Ck = Cr + (size_t)k * 2 * A.ntr;
     for (int t = 0; t < A.ntr; ++t) {
@@ -817,16 +818,19 @@ __device__ int solve_depth(const DevAtom &A, const double *slotd, const float *s
             b[c] = b[piv];
             b[piv] = t;
         }
+        // one reciprocal per pivot (kept for the back substitution)
+        const double ip = 1.0 / G[c * L + c];
+        G[c * L + c] = ip;
         for (int rr = c + 1; rr < L; ++rr) {
-            double f = G[rr * L + c] / G[c * L + c];
-            for (int q = c; q < L; ++q) G[rr * L + q] -= f * G[c * L + q];
+            const double f = G[rr * L + c] * ip;
+            for (int q = c + 1; q < L; ++q) G[rr * L + q] -= f * G[c * L + q];
             b[rr] -= f * b[c];
         }
     }
     for (int c = L - 1; c >= 0; --c) {
         double s = b[c];
         for (int q = c + 1; q < L; ++q) s -= G[c * L + q] * b[q];
-        b[c] = s / G[c * L + c];
+        b[c] = s * G[c * L + c];
     }
     for (int l = 0; l < L; ++l) nn[l * N + k] = b[l] * sc[l];
     return 0;
@@ -1122,25 +1126,81 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 rpos = (rpos + 3) & 3;
                 double *rh0 = ps.hist + (size_t)rpos * A.npp * N;
                 // threads own (depth, point) with the point fastest: K_ij of
-                // consecutive points i at consecutive addresses, J_j shared
+                // consecutive points i at consecutive addresses, J_j shared.  In
+                // FP32, with np a multiple of 4, a thread owns four consecutive
+                // points and streams K as float4 with eight rows in flight (the
+                // sum is memory-latency-bound otherwise); the sums run over j in
+                // the same order either way.
                 for (int q = 0; q < A.nprd; ++q) {
                     const int off = A.prd_off[q], np = A.prd_off[q + 1] - off;
                     const R *Kq = ps.K + (size_t)A.prd_koff[q] * N;
-                    for (int e = tid; e < np * N; e += blockDim.x) {
-                        const int k = e / np, i = e % np, pe = (off + i) * N + k;
-                        const R *col = Kq + (size_t)k * np * np + i;
-                        R sr = 0;
-                        for (int j = 0; j < np; ++j) sr += col[(size_t)j * np] * ps.J[(size_t)(off + j) * N + k];
-                        const R jb = (R)ps.Jbar[q * N + k], F = (R)ps.F[q * N + k], ep = (R)eps;
-                        const R r = (R)1 + F * (sr / jb - (R)1);
-                        R den = 2;
-                        if (jac) {
-                            const R g = F * (col[(size_t)i * np] - ps.f[pe] * sr / jb) * ps.D[pe] / jb;
-                            den = (R)1 - ep * g;
-                            den = den > (R)0.02 ? den : (R)0.02;
+                    const bool vec = sizeof(R) == 4 && (np & 3) == 0 && (A.prd_koff[q] & 3) == 0;
+                    const int G = vec ? 4 : 1, ng = np / G;
+                    for (int e = tid; e < ng * N; e += blockDim.x) {
+                        const int k = e / ng, i0 = (e % ng) * G;
+                        const R *col = Kq + (size_t)k * np * np + i0;
+                        const R *Jk = ps.J + (size_t)off * N + k;
+                        R sr[4] = {0, 0, 0, 0};
+                        if constexpr (sizeof(R) == 4) {
+                            if (vec) {
+                                float4 acc[2] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};
+                                int j = 0;
+                                for (; j + 8 <= np; j += 8) {
+                                    float4 kv[8];
+                                    float jv[8];
+#pragma unroll
+                                    for (int u = 0; u < 8; ++u) {
+                                        kv[u] = *reinterpret_cast<const float4 *>(col + (size_t)(j + u) * np);
+                                        jv[u] = Jk[(size_t)(j + u) * N];
+                                    }
+#pragma unroll
+                                    for (int u = 0; u < 8; ++u) {
+                                        float4 &a4 = acc[u & 1];
+                                        a4.x += kv[u].x * jv[u];
+                                        a4.y += kv[u].y * jv[u];
+                                        a4.z += kv[u].z * jv[u];
+                                        a4.w += kv[u].w * jv[u];
+                                    }
+                                }
+                                for (; j < np; ++j) {
+                                    const float4 kv = *reinterpret_cast<const float4 *>(col + (size_t)j * np);
+                                    const float jv = Jk[(size_t)j * N];
+                                    acc[0].x += kv.x * jv;
+                                    acc[0].y += kv.y * jv;
+                                    acc[0].z += kv.z * jv;
+                                    acc[0].w += kv.w * jv;
+                                }
+                                sr[0] = acc[0].x + acc[1].x;
+                                sr[1] = acc[0].y + acc[1].y;
+                                sr[2] = acc[0].z + acc[1].z;
+                                sr[3] = acc[0].w + acc[1].w;
+                            }
                         }
-                        ps.rho[pe] += ((ep * r + ((R)1 - ep)) - ps.rho[pe]) / den;
-                        rh0[pe] = (double)ps.rho[pe];
+                        if (!vec) {
+                            // eight independent partial sums, added in a fixed order
+                            R part[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                            int j = 0;
+                            for (; j + 8 <= np; j += 8) {
+#pragma unroll
+                                for (int u = 0; u < 8; ++u)
+                                    part[u] += col[(size_t)(j + u) * np] * Jk[(size_t)(j + u) * N];
+                            }
+                            for (; j < np; ++j) part[0] += col[(size_t)j * np] * Jk[(size_t)j * N];
+                            sr[0] = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
+                        }
+                        const R jb = (R)ps.Jbar[q * N + k], F = (R)ps.F[q * N + k], ep = (R)eps;
+                        for (int g = 0; g < G; ++g) {
+                            const int i = i0 + g, pe = (off + i) * N + k;
+                            const R r = (R)1 + F * (sr[g] / jb - (R)1);
+                            R den = 2;
+                            if (jac) {
+                                const R gi = F * (Kq[((size_t)k * np + i) * np + i] - ps.f[pe] * sr[g] / jb) * ps.D[pe] / jb;
+                                den = (R)1 - ep * gi;
+                                den = den > (R)0.02 ? den : (R)0.02;
+                            }
+                            ps.rho[pe] += ((ep * r + ((R)1 - ep)) - ps.rho[pe]) / den;
+                            rh0[pe] = (double)ps.rho[pe];
+                        }
                     }
                 }
                 __syncthreads();

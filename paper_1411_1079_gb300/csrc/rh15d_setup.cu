@@ -519,6 +519,165 @@ __global__ void stokes_kernel(const __grid_constant__ DevAtom A, ColumnArrays c,
     for (int i = 0; i < 4; ++i) o[i] = (double)I[i];
 }
 
+// FP32 Zeeman Stokes spectrum, one block per column (grid-stride): the
+// quantities that depend on depth only -- background coefficients, Doppler
+// widths, populations (divided by kStokesNref so that every product stays in
+// FP32 range), continuum LTE ratios, the polarised line's opacity factor,
+// source function, damping, Zeeman splitting and field geometry -- are formed
+// once per depth in FP64 and stored in shared memory in FP32; then every
+// thread sweeps its wavelengths with FP32 opacities, profiles and the same
+// DELO-linear step as stokes_kernel.  Layout of the shared arrays: kSF fields
+// [field][N], then the populations [L][N] and continuum ratios [ncont][N].
+constexpr double kStokesNref = 1e20;
+constexpr int kSF = 16;
+enum { SF_HKT, SF_KFF, SF_NHM, SF_THOM, SF_IVTH, SF_VZ, SF_DZ, SF_SK, SF_KL, SF_SL, SF_A0, SF_VB, SF_S2, SF_CT, SF_C2,
+       SF_SN2 };
+__global__ void __launch_bounds__(128) stokes32_kernel(const __grid_constant__ DevAtom A, ColumnArrays c, int t0,
+                                                       double geff, const double *Bf, const double *thf,
+                                                       const double *azf, int64_t nlam, const double *nu_d,
+                                                       const int *nact_d, const int *act_d, const double *spec,
+                                                       const float4 *vtab_g, const float4 *dtab_g, double *out)
+{
+    extern __shared__ __align__(16) float sf[];
+    __shared__ float4 tabs[2 * (RH_VT_N + 1)];
+    const float4 *vtab = tabs, *dtab = tabs + (RH_VT_N + 1);
+    for (int i = threadIdx.x; i <= RH_VT_N; i += blockDim.x) {
+        tabs[i] = vtab_g[i];
+        tabs[RH_VT_N + 1 + i] = dtab_g[i];
+    }
+    const int N = c.ndep, L = A.nlev;
+    float *pop = sf + (size_t)kSF * N;            // [L][N] populations / kStokesNref
+    float *gc = pop + (size_t)L * N;              // [ncont][N] n*_l / n*_u
+    const DevTrans &tr0 = A.tr[t0];
+    const double e2 = kQ * kQ / (4.0 * kPi * kEps0);
+    const double Cff = e2 * e2 * e2 * 4.0 / (3.0 * kMe * kH * kC) * sqrt(2.0 * kPi / (3.0 * kK * kMe));
+    const double nuB = geff * kQ / (4.0 * kPi * kMe);
+    const double h40 = kH * tr0.nu0 / (4.0 * kPi);
+    for (int64_t col = blockIdx.x; col < c.ncol; col += gridDim.x) {
+        __syncthreads();
+        const size_t cN = (size_t)col * N;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            const double T = c.T[cN + k], ne = c.ne[cN + k];
+            const double vth = sqrt(2.0 * kK * T / A.mass);
+            const double lam3 = pow(kH * kH / (2.0 * kPi * kMe * kK * T), 1.5);
+            const double sk = N > 1 ? (double)k / (N - 1) : 0.0;
+            sf[SF_HKT * N + k] = (float)(kH / (kK * T));
+            sf[SF_KFF * N + k] = (float)(Cff * ne * c.np[cN + k] / sqrt(T) / kNuRef3);
+            sf[SF_NHM * N + k] = (float)(0.25 * c.nstar[((size_t)col * L + 0) * N + k] * ne * lam3 *
+                                         exp(0.754 * kQ / (kK * T)));
+            sf[SF_THOM * N + k] = (float)(kSigmaT * ne);
+            sf[SF_IVTH * N + k] = (float)(1.0 / vth);
+            sf[SF_VZ * N + k] = (float)c.vz[cN + k];
+            sf[SF_DZ * N + k] = (float)(k < N - 1 ? fabs(c.z[cN + k] - c.z[cN + k + 1]) : 0.0);
+            sf[SF_SK * N + k] = (float)sk;
+            const double nl0 = c.pops[((size_t)col * L + tr0.l) * N + k];
+            const double nu0 = c.pops[((size_t)col * L + tr0.u) * N + k];
+            const double dnuD = tr0.nu0 * vth / kC;
+            sf[SF_KL * N + k] = (float)((nl0 * tr0.Blu - nu0 * tr0.Bul) * h40 / (kSqrtPi * dnuD));
+            sf[SF_SL * N + k] = (float)(nu0 * tr0.A / (nl0 * tr0.Blu - nu0 * tr0.Bul));
+            sf[SF_A0 * N + k] = (float)exp((1.0 - sk) * tr0.ln_atop + sk * tr0.ln_abot);
+            sf[SF_VB * N + k] = (float)(nuB * Bf[cN + k] / dnuD);
+            const double th = thf[cN + k], az = azf[cN + k];
+            sf[SF_S2 * N + k] = (float)(sin(th) * sin(th));
+            sf[SF_CT * N + k] = (float)cos(th);
+            sf[SF_C2 * N + k] = (float)cos(2.0 * az);
+            sf[SF_SN2 * N + k] = (float)sin(2.0 * az);
+            for (int l = 0; l < L; ++l)
+                pop[l * N + k] = (float)(c.pops[((size_t)col * L + l) * N + k] / kStokesNref);
+            for (int t = 0; t < A.ntr; ++t) {
+                const DevTrans &tr = A.tr[t];
+                if (tr.kind != 0)
+                    gc[tr.sub * N + k] = (float)(c.nstar[((size_t)col * L + tr.l) * N + k] /
+                                                 c.nstar[((size_t)col * L + tr.u) * N + k]);
+            }
+        }
+        __syncthreads();
+        for (int64_t j = threadIdx.x; j < nlam; j += blockDim.x) {
+            const double nud = nu_d[j];
+            const float nu = (float)nud;
+            const int na = nact_d[j];
+            const float hm = (float)hminus_sigma(kC / nud);
+            const float tw = (float)(2.0 * kH * nud * nud * nud / (kC * kC));
+            const float nu3s = (float)(kNuRef3 / (nud * nud * nud));
+            const float q0 = (float)(kC * ((nud - tr0.nu0) / tr0.nu0));
+            const float hr = (float)(nud / tr0.nu0);             // h4(nu) / h4(nu0)
+            float I[4] = {0, 0, 0, 0}, Ku[6], Su[4], eIu = 0, Bu = 0;
+            for (int step = 0; step < N; ++step) {
+                const int k = N - 1 - step;
+                const float x = nu * sf[SF_HKT * N + k];
+                const float ex = __expf(-x), omex = 1.0f - ex;
+                float chi = (sf[SF_KFF * N + k] * nu3s + sf[SF_NHM * N + k] * hm) * omex + sf[SF_THOM * N + k];
+                const float B = tw * ex / omex;
+                float eta = chi * B;
+                const float ivth = sf[SF_IVTH * N + k], vz = sf[SF_VZ * N + k], sk = sf[SF_SK * N + k];
+                for (int s2i = 0; s2i < na; ++s2i) {
+                    const int t = act_d[j * RH_SPEC_ACT + s2i];
+                    if (t == t0) continue;
+                    const DevTrans &tr = A.tr[t];
+                    const double *f = spec + ((size_t)j * RH_SPEC_ACT + s2i) * RH_SPEC_F;
+                    const float nl = pop[tr.l * N + k], nuu = pop[tr.u * N + k];
+                    if (tr.kind == 0) {
+                        const float a = __expf((1.0f - sk) * (float)tr.ln_atop + sk * (float)tr.ln_abot);
+                        const float v = ((float)f[3] - vz) * ivth;
+                        const float ph = voigt_f32(a, v, vtab) * (float)(f[4] * kStokesNref) * ivth;
+                        const float Vlu = (float)f[0] * ph;
+                        chi += nl * Vlu - nuu * ((float)f[2] * Vlu);
+                        eta += nuu * ((float)f[1] * ph);
+                    } else {
+                        const float G = gc[tr.sub * N + k] * ex;
+                        const float al = (float)(f[0] * kStokesNref);
+                        chi += nl * al - nuu * G * al;
+                        eta += nuu * G * (float)(f[1] * kStokesNref);
+                    }
+                }
+                const float v = (q0 - vz) * ivth;
+                float Hz[3], Lz[3];
+                zeeman_profiles<float>(sf[SF_A0 * N + k], v, sf[SF_VB * N + k], vtab, dtab, Hz, Lz);
+                const float s2 = sf[SF_S2 * N + k], ct = sf[SF_CT * N + k];
+                const float c2 = sf[SF_C2 * N + k], sn2 = sf[SF_SN2 * N + k];
+                const float hk = 0.5f * sf[SF_KL * N + k] * hr, Sl = sf[SF_SL * N + k];
+                const float lI = hk * (Hz[1] * s2 + 0.5f * (Hz[0] + Hz[2]) * (1.0f + ct * ct));
+                const float lq = hk * (Hz[1] - 0.5f * (Hz[0] + Hz[2])) * s2;
+                const float lV = hk * (Hz[2] - Hz[0]) * ct;
+                const float rq = hk * (Lz[1] - 0.5f * (Lz[0] + Lz[2])) * s2;
+                const float rV = hk * (Lz[2] - Lz[0]) * ct;
+                const float eI = chi + lI;
+                const float ie = 1.0f / eI;
+                const float e6[6] = {lq * c2, lq * sn2, lV, rq * c2, rq * sn2, rV};
+                float Ko[6], So[4];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) Ko[i] = e6[i] * ie;
+                So[0] = (eta + Sl * lI) * ie;
+                So[1] = Sl * e6[0] * ie;
+                So[2] = Sl * e6[1] * ie;
+                So[3] = Sl * e6[2] * ie;
+                if (step == 0) {
+                    eIu = eI;
+                    Bu = B;
+                } else {
+                    if (step == 1) {
+                        // diffusion condition at the bottom point (vertical optical depth)
+                        const float dtv = 0.5f * (eI + eIu) * sf[SF_DZ * N + N - 2];
+                        I[0] = Bu + (Bu - B) / dtv;
+                    }
+                    const float dtau = 0.5f * (eI + eIu) * sf[SF_DZ * N + k];
+                    float ome, wu, wo;
+                    sc_weights(dtau, ome, wu, wo);
+                    delo_step<float>(ome, wu, wo, Ku, Ko, Su, So, I);
+                    eIu = eI;
+                }
+#pragma unroll
+                for (int i = 0; i < 6; ++i) Ku[i] = Ko[i];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) Su[i] = So[i];
+            }
+            double *o = out + ((size_t)col * nlam + j) * 4;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) o[i] = (double)I[i];
+        }
+    }
+}
+
 // Depth-grid optimisation (Sect. 2.3), one thread per column, FP64.  The
 // column -- after the optional cut at z_top, whose new top point is
 // interpolated (T, v_z linearly, n_H and n_e logarithmically in height) -- is
@@ -648,7 +807,23 @@ cudaError_t launch_stokes(const DevAtom &A, const ColumnArrays &c, int t0, doubl
     if (n == 0) return cudaSuccess;
     int threads = 128;
     int64_t blocks = (n + threads - 1) / threads;
-    if (precision == 1)
+    // FP32: depth-only quantities once per column in shared memory (fits for
+    // every depth count up to the limit below; larger columns use the
+    // per-wavelength kernel)
+    const size_t sm32 = sizeof(float) * (size_t)c.ndep * (kSF + A.nlev + A.ncont);
+    if (precision == 1 && sm32 <= 160 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(stokes32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
+        if (e != cudaSuccess) return e;
+        int dev = 0, nsm = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stokes32_kernel, 128, sm32);
+        if (e != cudaSuccess) return e;
+        int64_t g = (int64_t)(per > 0 ? per : 1) * nsm;
+        if (g > c.ncol) g = c.ncol;
+        stokes32_kernel<<<(unsigned)g, 128, sm32, st>>>(A, c, t0, geff, B_T, theta, chi, nlam, nu_d, nact_d, act_d,
+                                                        spec_d, vtab, dtab, out);
+    } else if (precision == 1)
         stokes_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(A, c, t0, geff, B_T, theta, chi, nlam, nu_d, nact_d,
                                                                  act_d, spec_d, vtab, dtab, out);
     else
