@@ -715,6 +715,28 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_full(args):
+    """The full-run configuration on the whole 512x512 cube (one step),
+    with the plain FP64 GPU MALI timed on a sample beside it and sampled
+    columns compared with the oracle; one JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1411_1079_gb300 as rh
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    with ClockSampler(0) as clk:
+        r = run_full_config(rh, torch, 0, stream, 512 * 512, args.full_run_train,
+                            fp64_columns=args.full_run_fp64, oracle_columns=args.full_run_oracle)
+    line = {"metric": METRIC, "value": r["value"], "unit": "columns/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": r["solve"]["ms"] + r["stokes"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": r["workload"], "ndep": 128, "nlambda": 880, "nmu": 5,
+                       "l2": "working set > L2 (inputs larger than L2)", "parallelism": "dp1 (independent columns)"},
+            "full_run": r, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_ncu_case(args):
     """Small fixed cases for ncu captures (columns of the 256x256 cube):
     crd -- the column kernel, --ncu-iters iterations from LTE;
@@ -770,6 +792,10 @@ def main():
     ap.add_argument("--full-run-columns", type=int, default=1216,
                     help="columns of the full-run configuration (512x512 x 128 heights, PRD Lyman alpha/beta at "
                          "200 frequencies, Stokes) to solve; 262144 = the whole cube (0: skip)")
+    ap.add_argument("--full-run", action="store_true",
+                    help="only the full-run configuration on the whole 512x512 cube (tens of minutes)")
+    ap.add_argument("--full-run-fp64", type=int, default=152,
+                    help="columns of the plain FP64 comparison in --full-run")
     ap.add_argument("--full-run-train", type=int, default=8192,
                     help="CRD-converged 128-height columns the full run's network is trained on")
     ap.add_argument("--full-run-oracle", type=int, default=0,
@@ -789,6 +815,8 @@ def main():
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args)
+    elif args.full_run:
+        run_full(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -1189,7 +1189,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                             sr[0] = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
                         }
                         const R jb = (R)ps.Jbar[q * N + k], F = (R)ps.F[q * N + k], ep = (R)eps;
-                        for (int g = 0; g < G; ++g) {
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            if (g >= G) break;
                             const int i = i0 + g, pe = (off + i) * N + k;
                             const R r = (R)1 + F * (sr[g] / jb - (R)1);
                             R den = 2;
