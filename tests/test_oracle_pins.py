@@ -1081,3 +1081,24 @@ def test_prd_switching_and_ng_keep_the_fixed_point(orc):
             ref = n
         else:
             assert np.max(np.abs(n / ref - 1)) < 1e-10, kw
+
+
+def test_redistribution_function_tail_bound(orc):
+    """R_II-A(x', x) <= erfc(|x - x'|/2): integrated by parts, R is erfc(u)
+    times two Lorentzians of total area 2 pi, averaged over u >= |x - x'|/2
+    with weight 1/(2 pi).  The GPU rules drop the pairs beyond u0 = 5 (FP32)
+    and 6 (FP64), where the bound is 1.5e-12 and 2e-17; the bound is also
+    nearly reached (within a factor 10) where one Lorentzian centre lies at
+    the lower limit, so it is the right scale for the cut."""
+    from scipy.special import erfc
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for _ in range(400):
+        a = 10 ** rng.uniform(-3.5, -1.5)
+        x = rng.uniform(-30, 30)
+        xp = x + rng.uniform(-14, 14)
+        u0 = abs(x - xp) / 2
+        r = orc.r2a(a, xp, x)
+        assert r <= erfc(u0) * (1 + 1e-9) + 1e-300, (a, x, xp, r, erfc(u0))
+        worst = max(worst, r / erfc(u0))
+    assert worst > 0.1
