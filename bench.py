@@ -44,15 +44,15 @@ METRIC = "converged columns/s to max|dn/n|<1e-3"
 # columns x 12 iterations (about the iterations a column takes from the
 # learned guess), divided by their points; re-counted whenever the kernel
 # changes
-FLOP_PER_PT = 191.3
+FLOP_PER_PT = 181.6
 # DRAM bytes (read + write) per column-iteration of the column kernel, from
-# the same ncu capture (12.77 GB for 608 x 12): the line-profile cache read
+# the same ncu capture (12.74 GB for 608 x 12): the line-profile cache read
 # back every iteration (1.57 MB), its build once per column and the column's
 # inputs and results
-DRAM_BYTES_PER_COLUMN_ITERATION = (11.533787e9 + 1.232767e9) / (608 * 12)
+DRAM_BYTES_PER_COLUMN_ITERATION = (11.510031e9 + 1.231854e9) / (608 * 12)
 # warp instructions per column-iteration, same capture: the issue-slot view of
 # the same kernel (4 schedulers per SM, one warp instruction per cycle each)
-WARP_INST_PER_COLUMN_ITERATION = 24616860192 / (608 * 12)
+WARP_INST_PER_COLUMN_ITERATION = 15015163046 / (608 * 12)
 
 
 def algorithmic_flop_per_pt(atom, nu):
@@ -373,6 +373,8 @@ def run_full_config(rh, torch, local, stream, ncol, train_cols, seed=5678, fp64_
     s1.record(stream)
     torch.cuda.synchronize()
     st_ms = s0.elapsed_time(s1)
+    conv_cols = torch.from_numpy(np.where(p.populations()[2] == 0)[0]).to("cuda")
+    vi = (iquv[..., 3].abs() / iquv[..., 0]).amax(dim=1)
     out = {"workload": "%d columns of the 512x512 synthetic chromosphere cube (seed %d), 128 heights, H-like atom "
                        "with Lyman alpha and beta in angle-averaged PRD (R_II-A, 200 frequencies each; 880 "
                        "wavelengths), learned start, mixed precision, tol 1e-3; then the FP32 H alpha Zeeman "
@@ -381,7 +383,8 @@ def run_full_config(rh, torch, local, stream, ncol, train_cols, seed=5678, fp64_
            "solve": {"ms": ms, "converged": s["n_converged"], "iterations_per_column": s["iterations_total"] / ncol,
                      "rerun_columns": s["rerun_columns"], "columns_per_s": ncol / (ms / 1e3)},
            "stokes": {"ms": st_ms, "columns_per_s": ncol / (st_ms / 1e3),
-                      "max_abs_V_over_I": float((iquv[..., 3].abs() / iquv[..., 0]).max())},
+                      "max_abs_V_over_I_converged": float(vi[conv_cols].max()) if conv_cols.numel() else None,
+                      "columns_with_abs_V_above_I": int((vi > 1).sum())},
            "learned_start": {"train_columns": train_cols, "loss_last_epoch": tr["loss_last_epoch"],
                              "trained_on": "CRD-converged 128-height columns of a disjoint cube"}}
     if fp64_columns > 0:

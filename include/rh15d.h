@@ -387,10 +387,11 @@ int rh_surrogate_file_info(const char *path, int32_t *sizes_out, int64_t *nparam
 /* ---------------------------------------------------------------------- */
 /* Shared-memory layout of the column kernel (no counterpart in the paper;  */
 /* a host computation that needs no GPU, for checking the layout): the byte  */
-/* offsets of its 17 regions in carve order (populations, new populations,   */
-/* collisional rates, reduction scratch, rate accumulators, 7 per-depth      */
-/* arrays, continuum factors, damping, populations in the working precision, */
-/* Voigt table, block counters) and the carve's end in offsets_out[0..17],   */
+/* offsets of its 14 regions in carve order (populations, new populations,   */
+/* collisional rates, reduction scratch, rate accumulators, 3 per-depth      */
+/* arrays, the per-depth background block [ndep][4], continuum factors,      */
+/* damping, populations in the working precision, Voigt table, block         */
+/* counters) and the carve's end in offsets_out[0..14],                      */
 /* and the bytes the launch allocates in bytes_out (the same function sizes  */
 /* and carves, so the two are equal).  macc: rate accumulators per depth.   */
 /* RH_EINVAL for sizes outside the library's limits.                        */
@@ -420,7 +421,12 @@ int rh_fma_peak(int32_t device, int32_t precision, double seconds, double *flop_
 /*                                                                           */
 /* It runs the same iteration as rh_iterate over every loaded column         */
 /* (only_unconverged must be 0; atoms with PRD lines are refused, their      */
-/* redistribution scratch is allocated) and writes the results to           */
+/* redistribution scratch is allocated).  The line profiles come from the    */
+/* context's profile cache when an earlier rh_iterate or rh_solve on the     */
+/* context allocated it -- the results are then bit for bit those of         */
+/* rh_iterate with the same options -- and are otherwise evaluated inside    */
+/* the sweep, which agrees with the cached sweep to FP32 rounding (the two   */
+/* kernels' multiply-adds may be fused differently).  It writes results to  */
 /* caller-owned DEVICE buffers of the context's device: n_out               */
 /* [ncol][nlev][ndep] (with start = 2 it is also read as the starting       */
 /* populations), iters_out [ncol], status_out [ncol] (RH_COL_*), dmax_out    */

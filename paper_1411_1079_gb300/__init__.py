@@ -162,9 +162,9 @@ def _ptr(x):
 
 
 def column_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc):
-    """rh_column_smem_layout (host only): ([18] region offsets in carve
+    """rh_column_smem_layout (host only): ([15] region offsets in carve
     order, the carve's end last; allocated bytes)."""
-    off = (C.c_size_t * 18)()
+    off = (C.c_size_t * 15)()
     b = C.c_size_t()
     rc = lib().rh_column_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc, off, C.byref(b))
     if rc:
@@ -289,7 +289,7 @@ class Context:
 
     def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True, start=0,
               ng_order=2, ng_delay=5, ng_period=3, use_graph=1, autotune=1, fused_rerun=1,
-              prd_eps0=0.0) -> dict:
+              prd_eps0=0.0, rungs=None) -> dict:
         """rh_solve: every column from LTE (start=0), the learned guess
         (start=1), the current populations (start=2), zero radiation (3) or
         escape probabilities (4) with Ng acceleration, then the columns that
@@ -298,14 +298,20 @@ class Context:
         (x1e3, x1e5, then x1e7) and without Ng (the paper's two-stage
         strategy): by the column kernel itself as
         soon as a column fails (fused_rerun=1) or as separate passes over a
-        device-selected list; the sequence is replayed as a CUDA graph."""
+        device-selected list; the sequence is replayed as a CUDA graph.
+        rungs: the re-run ladder as (collisional-radiative factor, Ng on)
+        pairs, at most MAX_RERUN of them, in place of the default."""
         o = SolveOpts()
         o.pass1 = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay, ng_period=ng_period,
                            start=start, precision=precision, persistent=persistent, block_warps=block_warps,
                            crsw_init=1.0, only_unconverged=0, prd_eps0=prd_eps0)
         # the ladder: from a start other than LTE, first LTE with the same
         # options; then stronger and stronger switching without Ng
-        rungs = ([(1.0, 1)] if start != 0 else []) + [(f, 0) for f in self.RERUN_CRSW]
+        if rungs is None:
+            rungs = ([(1.0, 1)] if start != 0 else []) + [(f, 0) for f in self.RERUN_CRSW]
+        rungs = [(float(f), int(bool(ng))) for f, ng in rungs]
+        if len(rungs) > len(o.rerun_crsw) or any(not f >= 1.0 for f, _ in rungs):
+            raise ValueError("rungs: at most %d pairs with factors >= 1" % len(o.rerun_crsw))
         o.nrerun = len(rungs) if rescue else 0
         o.rerun_maxiter = maxiter
         for i, (f, ng) in enumerate(rungs[:o.nrerun]):

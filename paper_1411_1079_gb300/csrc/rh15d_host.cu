@@ -1334,7 +1334,7 @@ int rh_column_smem_layout(int32_t precision, int32_t nlev, int32_t ndep, int32_t
     if ((precision != 0 && precision != 1) || nlev < 2 || nlev > RH_MAXLEV || ndep < 2 || ndep > 4096 || ntr < 1 ||
         ntr > RH_MAXTR || ncont < 0 || nline < 0 || macc < 1 || !offsets_out || !bytes_out)
         return RH_EINVAL;
-    mali_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc, offsets_out, 18, bytes_out);
+    mali_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc, offsets_out, 15, bytes_out);
     return RH_OK;
 }
 
@@ -2114,6 +2114,10 @@ extern "C" int rh_iterate_noalloc(rh_ctx *c, const rh_iter_opts *o, double *n_ou
     il.nsm = c->nsm;
     il.colidx = nullptr;
     il.nwork = c->ncol;
+    // the context's line-profile cache, when an earlier rh_iterate or rh_solve
+    // allocated it (then this call runs the very kernel rh_iterate runs);
+    // without it the sweep evaluates the profiles itself
+    set_phic(c, il);
     int grid = 0;
     char ebuf[256] = {0};
     const std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();

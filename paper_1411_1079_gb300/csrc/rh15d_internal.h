@@ -314,23 +314,34 @@ __host__ inline void voigt_coeffs(double v, double &h1, double &d1, double &h3, 
 // Voigt function, FP32, branch-free: the expansion above with H1 and H3 from
 // a cubic-Hermite table on a uniform grid in t = 1/(1+|v|) in (0, 1]
 // (tab[i] = {H1, h dH1/dt, H3, h dH3/dt} at t_i = i h, h = 1/RH_VT_N).
+//
+// Every rounding step is an explicit intrinsic (fused multiply-adds where they
+// are wanted, __f*_rn elsewhere): the compiler may not contract or split them,
+// so the result does not depend on the code the function is inlined into.
+// Hermite basis: h00 = f^2 (2f - 3) + 1, h01 = f^2 (3 - 2f), h10 = f (f - 1)^2,
+// h11 = f^2 (f - 1).
 __device__ __forceinline__ float voigt_f32(float a, float v, const float4 *__restrict__ tab)
 {
-    float av = fabsf(v);
-    float v2 = av * av;
-    float g = __expf(-v2);
-    float t = rcp_f32(1.0f + av);
-    float x = t * (float)RH_VT_N;
-    int i = min((int)x, RH_VT_N - 1);
-    float f = x - (float)i;
-    float4 p0 = tab[i], p1 = tab[i + 1];
-    float f2 = f * f, f3 = f2 * f;
-    float h00 = 2.0f * f3 - 3.0f * f2 + 1.0f, h10 = f3 - 2.0f * f2 + f, h01 = 3.0f * f2 - 2.0f * f3, h11 = f3 - f2;
-    float H1 = h00 * p0.x + h10 * p0.y + h01 * p1.x + h11 * p1.y;
-    float H3 = h00 * p0.z + h10 * p0.w + h01 * p1.z + h11 * p1.w;
-    float a2 = a * a;
-    float gpoly = 1.0f + a2 * (1.0f - 2.0f * v2) + a2 * a2 * (0.66666667f * v2 * v2 - 2.0f * v2 + 0.5f);
-    return g * gpoly + a * (H1 + a2 * H3);
+    const float av = fabsf(v);
+    const float v2 = __fmul_rn(av, av);
+    const float g = __expf(-v2);
+    const float t = rcp_f32(__fadd_rn(1.0f, av));
+    const float x = __fmul_rn(t, (float)RH_VT_N);
+    const int i = min((int)x, RH_VT_N - 1);
+    const float f = __fsub_rn(x, (float)i);
+    const float4 p0 = tab[i], p1 = tab[i + 1];
+    const float f2 = __fmul_rn(f, f), fm1 = __fsub_rn(f, 1.0f);
+    const float h00 = __fmaf_rn(f2, __fmaf_rn(2.0f, f, -3.0f), 1.0f);
+    const float h01 = __fmul_rn(f2, __fmaf_rn(-2.0f, f, 3.0f));
+    const float h10 = __fmul_rn(f, __fmul_rn(fm1, fm1));
+    const float h11 = __fmul_rn(f2, fm1);
+    const float H1 = __fmaf_rn(h00, p0.x, __fmaf_rn(h10, p0.y, __fmaf_rn(h01, p1.x, __fmul_rn(h11, p1.y))));
+    const float H3 = __fmaf_rn(h00, p0.z, __fmaf_rn(h10, p0.w, __fmaf_rn(h01, p1.z, __fmul_rn(h11, p1.w))));
+    const float a2 = __fmul_rn(a, a);
+    // 1 + a^2 (1 - 2 v^2) + a^4 (2/3 v^4 - 2 v^2 + 1/2)
+    const float q4 = __fmaf_rn(v2, __fmaf_rn(0.66666667f, v2, -2.0f), 0.5f);
+    const float gpoly = __fmaf_rn(__fmul_rn(a2, a2), q4, __fmaf_rn(a2, __fmaf_rn(-2.0f, v2, 1.0f), 1.0f));
+    return __fmaf_rn(g, gpoly, __fmul_rn(a, __fmaf_rn(a2, H3, H1)));
 }
 
 __device__ __forceinline__ float disp_f32(float a, float v, const float4 *__restrict__ tab)

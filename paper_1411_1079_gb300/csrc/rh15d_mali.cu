@@ -146,7 +146,8 @@ template <typename R>
 struct Smem {
     double *n, *nn, *Cr;       // [L*N], [L*N], [N][2*ntr]
     R *slot;                   // [macc][N]
-    R *dz, *ivth, *vz, *hkT, *kff, *nhm, *thom;   // [N]
+    R *dz, *ivth, *vz;         // [N]
+    R *bg;                     // [N][4]: h/kT, free-free, H- density, Thomson (one vector load per depth)
     R *Gc;                     // [ncont][N]
     R *ad;                     // [nline][N] damping
     R *nr;                     // [L][N] populations in R
@@ -161,7 +162,7 @@ struct Smem {
 // (regions reserved by the carve but dropped from the size) writes outside
 // the block's shared memory.
 struct SmemLayout {
-    size_t n, nn, Cr, red, slot, dz, ivth, vz, hkT, kff, nhm, thom, Gc, ad, nr, vtab, ibuf, end;
+    size_t n, nn, Cr, red, slot, dz, ivth, vz, bg, Gc, ad, nr, vtab, ibuf, end;
 };
 template <typename R>
 __host__ __device__ inline SmemLayout smem_layout(int L, int N, int ntr, int ncont, int nline, int macc)
@@ -178,11 +179,14 @@ __host__ __device__ inline SmemLayout smem_layout(int L, int N, int ntr, int nco
     b += sizeof(double) * kRedDoubles;
     o.slot = b;
     b += sizeof(R) * (size_t)macc * N;
-    size_t *one[7] = {&o.dz, &o.ivth, &o.vz, &o.hkT, &o.kff, &o.nhm, &o.thom};
-    for (int i = 0; i < 7; ++i) {
+    size_t *one[3] = {&o.dz, &o.ivth, &o.vz};
+    for (int i = 0; i < 3; ++i) {
         *one[i] = b;
         b += sizeof(R) * (size_t)N;
     }
+    b = (b + 15) & ~(size_t)15;                    // vector loads of the background block
+    o.bg = b;
+    b += sizeof(R) * 4 * (size_t)N;
     o.Gc = b;
     b += sizeof(R) * (size_t)ncont * N;
     o.ad = b;
@@ -217,10 +221,7 @@ __device__ Smem<R> carve(char *base, int L, int N, int ntr, int ncont, int nline
     s.dz = reinterpret_cast<R *>(base + o.dz);
     s.ivth = reinterpret_cast<R *>(base + o.ivth);
     s.vz = reinterpret_cast<R *>(base + o.vz);
-    s.hkT = reinterpret_cast<R *>(base + o.hkT);
-    s.kff = reinterpret_cast<R *>(base + o.kff);
-    s.nhm = reinterpret_cast<R *>(base + o.nhm);
-    s.thom = reinterpret_cast<R *>(base + o.thom);
+    s.bg = reinterpret_cast<R *>(base + o.bg);
     s.Gc = reinterpret_cast<R *>(base + o.Gc);
     s.ad = reinterpret_cast<R *>(base + o.ad);
     s.nr = reinterpret_cast<R *>(base + o.nr);
@@ -235,6 +236,24 @@ template <>
 __device__ __forceinline__ float voigt<float>(float a, float v, const float4 *tab) { return voigt_f32(a, v, tab); }
 template <>
 __device__ __forceinline__ double voigt<double>(double a, double v, const float4 *) { return voigt_f64(a, v); }
+
+// Line profile phi(k, ray) of one wavelength: the Doppler shift of the ray,
+// the Voigt function and the normalisation, with every rounding step fixed by
+// intrinsics.  The cache build and the in-sweep evaluation both call this, and
+// the compiler may not fuse or split its operations differently in the two
+// places, so cached and uncached sweeps give the same bits.
+__device__ __forceinline__ float line_phi(float q, float muz, float vz, float ivth, float a, float pn,
+                                          const float4 *tab)
+{
+    const float v = __fmul_rn(__fmaf_rn(-muz, vz, q), ivth);
+    return __fmul_rn(__fmul_rn(voigt<float>(a, v, tab), pn), ivth);
+}
+__device__ __forceinline__ double line_phi(double q, double muz, double vz, double ivth, double a, double pn,
+                                           const float4 *tab)
+{
+    const double v = __dmul_rn(__fma_rn(-muz, vz, q), ivth);
+    return __dmul_rn(__dmul_rn(voigt<double>(a, v, tab), pn), ivth);
+}
 
 template <typename R> __device__ __forceinline__ R rcp(R x);
 template <> __device__ __forceinline__ float rcp<float>(float x) { return rcp_f32(x); }
@@ -260,6 +279,18 @@ template <typename R> __device__ __forceinline__ R wm2_of(const DevAtom &A, int 
 template <> __device__ __forceinline__ float wm2_of<float>(const DevAtom &A, int m) { return A.wm2f[m]; }
 template <> __device__ __forceinline__ double wm2_of<double>(const DevAtom &A, int m) { return 0.5 * A.wmu[m]; }
 
+// four consecutive values of a 16-byte aligned shared array
+__device__ __forceinline__ void load4(const float *p, float &a, float &b, float &c, float &d)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void load4(const double *p, double &a, double &b, double &c, double &d)
+{
+    const double2 u = reinterpret_cast<const double2 *>(p)[0], v = reinterpret_cast<const double2 *>(p)[1];
+    a = u.x; b = u.y; c = v.x; d = v.y;
+}
+
 // Per-lane constants of one tile with K transitions in its union.
 template <typename R, int K>
 struct LaneC {
@@ -280,10 +311,12 @@ template <typename R, int K, bool PRD = false>
 __device__ __forceinline__ void depth_consts(const Smem<R> &s, const LaneC<R, K> &lc, int k, int N, DepthC<R, K> &d,
                                              R rho_k = (R)1, int prd_slot = -1)
 {
-    R x = lc.nu * s.hkT[k];
+    R hkT, kff, nhm, thom;
+    load4(s.bg + 4 * k, hkT, kff, nhm, thom);
+    R x = lc.nu * hkT;
     R ex = rexp<R>(-x);
     R omex = one_m_exp<R>(x, ex);
-    d.chibg = (s.kff[k] * lc.nu3s + s.nhm[k] * lc.hm) * omex + s.thom[k];
+    d.chibg = (kff * lc.nu3s + nhm * lc.hm) * omex + thom;
     d.B = lc.tw * ex * rcp<R>(omex);
     d.etabg = d.chibg * d.B;
     d.etac = 0;
@@ -382,7 +415,10 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 // and depth from the block's scratch), PRD lanes accumulate the angle-averaged
 // mean intensity J, and every slot also accumulates its plain rates (actual
 // intensity) cw I and cw R (E + I), for the PRD update.
-template <typename R, int K, bool PRD, bool CACHE>
+// NL >= 0: the tile's first NL slots are lines and the rest continua (the
+// host orders the transitions lines first), known at compile time so the
+// per-slot kind tests fold away; NL < 0: the kinds are read at run time.
+template <typename R, int K, int NL, bool PRD, bool CACHE>
 __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane, R *prd_rho,
                              R *prd_J, R *prd_D, R *prd_plain, const R *phc)
 {
@@ -403,7 +439,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
         lc.q[j] = lt[(RH_NLANEF * j + 4) * npad + pi];
         lc.pn[j] = lt[(RH_NLANEF * j + 5) * npad + pi];
         lc.grat[j] = lt[(RH_NLANEF * j + 6) * npad + pi];
-        lc.isline[j] = tr.kind == 0;
+        lc.isline[j] = NL >= 0 ? j < NL : tr.kind == 0;
         lc.lo[j] = tr.l;
         lc.up[j] = tr.u;
         lc.sub[j] = tr.sub;
@@ -431,10 +467,8 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 o[j] = phc[poff[j] + rk];
             } else {
                 const R mu = mu_of<R>(A, r >> 1);
-                const R muz = (r & 1) ? mu : -mu;
-                const R ivth = s.ivth[k];
-                const R v = (lc.q[j] - muz * s.vz[k]) * ivth;
-                o[j] = voigt<R>(s.ad[lc.sub[j] * N + k], v, s.vtab) * lc.pn[j] * ivth;
+                o[j] = line_phi(lc.q[j], (r & 1) ? mu : -mu, s.vz[k], s.ivth[k], s.ad[lc.sub[j] * N + k], lc.pn[j],
+                                s.vtab);
             }
         }
     };
@@ -478,20 +512,16 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
         }
     };
     // reduce the warp's contributions and add them to the tile's accumulators
-    auto flush = [&](int k, R (&val)[P], bool first) {
+    auto flush = [&](int k, R (&val)[P]) {
 #pragma unroll
         for (int a = MP; a < P; ++a) val[a] = 0;
         const R t = reduce_scatter<P>(val, lane);
-        if (writer && widx < M) {
-            R *sl = slot + widx * N + k;
-            if (first) *sl = t;
-            else *sl += t;
-        }
+        if (writer && widx < M) slot[widx * N + k] += t;   // zeroed before the sweep
     };
 
     // contributions of one depth point to the tile's accumulators
     auto emit = [&](int k, const DepthC<R, K> &d, const R (&phi)[K], const R (&chj)[K], const R (&U)[K], R ichi,
-                    R wo, R omwo, R psi, R Ieff, R Ik, R wm2, bool first) {
+                    R wo, R omwo, R psi, R Ieff, R Ik, R wm2) {
         R val[P];
         contrib(d, phi, chj, U, ichi, wo, omwo, psi, Ieff, wm2, val, false);
         if constexpr (PRD) {
@@ -516,11 +546,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
 #pragma unroll
         for (int a = MP; a < P; ++a) val[a] = 0;
         const R t = reduce_scatter<P>(val, lane);
-        if (writer && widx < M) {
-            R *sl = slot + widx * N + k;
-            if (first) *sl = t;
-            else *sl += t;
-        }
+        if (writer && widx < M) slot[widx * N + k] += t;   // zeroed before the sweep
         if constexpr (PRD) {
             if (writer && widx >= M && widx < MP) atomicAdd(plain + (widx - M) * N + k, t);
         }
@@ -538,7 +564,6 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
             for (int dir = 0; dir < 2; ++dir) {
                 const R z0 = dir == 0 ? -mu0 : mu0, z1 = dir == 0 ? -mu1 : mu1;
                 const int ra = 2 * m0 + dir, rb = 2 * m1 + dir;
-                const bool first = m0 == 0 && dir == 0;
                 R Ia, chipa = 0, Spa, Ib = 0, chipb = 0, Spb = 0;
                 {
                     const int k0 = dir == 0 ? 0 : N - 1;
@@ -579,7 +604,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                         Spb = eta * ichi;
                         contrib(d, phi, chj, U, ichi, (R)0, (R)1, (R)0, Ib, wb, val, true);
                     }
-                    flush(k0, val, first);
+                    flush(k0, val);
                 }
                 // cached profiles loaded one depth step ahead
                 R pa[K], pb[K];
@@ -623,7 +648,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                         contrib(d, phi, chj, U, ichi, wo, omwo, wo * ichi, base + wo * (d.etabg * ichi), wb, val,
                                 true);
                     }
-                    flush(k, val, first);
+                    flush(k, val);
 #pragma unroll
                     for (int j = 0; j < K; ++j) {
                         pa[j] = na[j];
@@ -640,7 +665,6 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
         for (int dir = 0; dir < 2; ++dir) {
             const R muz = dir == 0 ? -mu : mu;
             const int ray = 2 * m + dir;
-            const bool first = m == 0 && dir == 0;
             R I, chip = 0, Sp;
             {
                 R pc[K];
@@ -670,7 +694,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 }
                 chip = chi;
                 Sp = eta * ichi;
-                emit(k0, d, phi, chj, U, ichi, (R)0, (R)1, (R)0, I, I, wm2, first);
+                emit(k0, d, phi, chj, U, ichi, (R)0, (R)1, (R)0, I, I, wm2);
             }
             // rho of the lane's PRD point (global scratch) loaded one depth step ahead
             R rho_nx = (PRD && rho_lane) ? rho_lane[dir == 0 ? 1 : N - 2] : (R)1;
@@ -701,7 +725,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 const R psi = wo * ichi;
                 chip = chi;
                 Sp = S;
-                emit(k, d, phi, chj, U, ichi, wo, omwo, psi, Ieff, I, wm2, first);
+                emit(k, d, phi, chj, U, ichi, wo, omwo, psi, Ieff, I, wm2);
             }
         }
     }
@@ -711,10 +735,32 @@ template <typename R, bool PRD, bool CACHE>
 __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane,
                                            R *prd_rho, R *prd_J, R *prd_D, R *prd_plain, const R *phc)
 {
-    switch (A.tile[b].K) {
-    case 1: sweep_tile_k<R, 1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
-    case 2: sweep_tile_k<R, 2, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
-    default: sweep_tile_k<R, 3, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
+    const DevTile &tl = A.tile[b];
+    if constexpr (sizeof(R) == 4 && !PRD) {
+        // the FP32 CRD instantiations (with and without the profile cache, so
+        // that the two keep the same arithmetic): one tile kernel per
+        // (transitions, lines)
+        int nl = 0;
+        for (int j = 0; j < tl.K; ++j) nl += A.tr[tl.t[j]].kind == 0;
+#define RH_TILE(K_, NL_) sweep_tile_k<R, K_, NL_, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc)
+        switch (tl.K * 4 + nl) {
+        case 4: RH_TILE(1, 0); break;
+        case 5: RH_TILE(1, 1); break;
+        case 8: RH_TILE(2, 0); break;
+        case 9: RH_TILE(2, 1); break;
+        case 10: RH_TILE(2, 2); break;
+        case 12: RH_TILE(3, 0); break;
+        case 13: RH_TILE(3, 1); break;
+        case 14: RH_TILE(3, 2); break;
+        default: RH_TILE(3, 3); break;
+        }
+#undef RH_TILE
+    } else {
+        switch (tl.K) {
+        case 1: sweep_tile_k<R, 1, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
+        case 2: sweep_tile_k<R, 2, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
+        default: sweep_tile_k<R, 3, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
+        }
     }
 }
 
@@ -736,11 +782,7 @@ __device__ void build_profiles(const DevAtom &A, const Smem<R> &s, const KParams
         const R muz = (r & 1) ? mu : -mu;
         const R *ad = s.ad + (size_t)A.tr[A.tile[b].t[j]].sub * N;
         R *o = phc + (size_t)w * N * kWarp + lane;
-        for (int k = 0; k < N; ++k) {
-            const R ivth = s.ivth[k];
-            const R v = (q - muz * s.vz[k]) * ivth;
-            o[(size_t)k * kWarp] = voigt<R>(ad[k], v, s.vtab) * pn * ivth;
-        }
+        for (int k = 0; k < N; ++k) o[(size_t)k * kWarp] = line_phi(q, muz, s.vz[k], s.ivth[k], ad[k], pn, s.vtab);
     }
 }
 
@@ -875,14 +917,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
             double vth = sqrt(2.0 * kK * T / A.mass);
             s.ivth[k] = (R)(1.0 / vth);
             s.vz[k] = (R)p.vz[cN + k];
-            s.hkT[k] = (R)(kH / (kK * T));
+            s.bg[4 * k + 0] = (R)(kH / (kK * T));
             double e2 = kQ * kQ / (4.0 * kPi * kEps0);
             double Cff = e2 * e2 * e2 * 4.0 / (3.0 * kMe * kH * kC) * sqrt(2.0 * kPi / (3.0 * kK * kMe));
-            s.kff[k] = (R)(Cff * ne * p.np[cN + k] / sqrt(T) / kNuRef3);
+            s.bg[4 * k + 1] = (R)(Cff * ne * p.np[cN + k] / sqrt(T) / kNuRef3);
             double n1 = p.nstar[((size_t)col * L + 0) * N + k];
             double lam3 = pow(kH * kH / (2.0 * kPi * kMe * kK * T), 1.5);
-            s.nhm[k] = (R)(0.25 * n1 * ne * lam3 * exp(0.754 * kQ / (kK * T)));
-            s.thom[k] = (R)(kSigmaT * ne);
+            s.bg[4 * k + 2] = (R)(0.25 * n1 * ne * lam3 * exp(0.754 * kQ / (kK * T)));
+            s.bg[4 * k + 3] = (R)(kSigmaT * ne);
             double sk = N > 1 ? (double)k / (N - 1) : 0.0;
             for (int t = 0; t < A.ntr; ++t) {
                 const DevTrans &tr = A.tr[t];
@@ -977,6 +1019,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
         for (it = 1; it <= maxiter; ++it) {
             double fcr = crsw > 1.0 ? fmax(1.0, crsw * pow(10.0, -(double)(it - 1))) : 1.0;
             for (int i = tid; i < LN; i += blockDim.x) s.nr[i] = (R)(s.n[i] * p.inv_nref);
+            for (int i = tid; i < A.macc * N; i += blockDim.x) s.slot[i] = 0;
             if constexpr (PRD) {
                 for (int i = tid; i < A.npp * N; i += blockDim.x) {
                     ps.J[i] = 0;
@@ -1291,12 +1334,12 @@ int mali_smem_layout(int precision, int L, int N, int ntr, int ncont, int nline,
 {
     const SmemLayout o = precision == 1 ? smem_layout<float>(L, N, ntr, ncont, nline, macc)
                                         : smem_layout<double>(L, N, ntr, ncont, nline, macc);
-    const size_t v[18] = {o.n, o.nn, o.Cr, o.red, o.slot, o.dz, o.ivth, o.vz, o.hkT, o.kff, o.nhm, o.thom, o.Gc,
-                          o.ad, o.nr, o.vtab, o.ibuf, o.end};
-    for (int i = 0; i < noff && i < 18; ++i) offsets[i] = v[i];
+    const size_t v[15] = {o.n, o.nn, o.Cr, o.red, o.slot, o.dz, o.ivth, o.vz, o.bg, o.Gc, o.ad, o.nr, o.vtab, o.ibuf,
+                          o.end};
+    for (int i = 0; i < noff && i < 15; ++i) offsets[i] = v[i];
     *bytes = precision == 1 ? smem_bytes<float>(L, N, ntr, ncont, nline, macc)
                             : smem_bytes<double>(L, N, ntr, ncont, nline, macc);
-    return 18;
+    return 15;
 }
 
 size_t mali_phic_bytes_per_block(const DevAtom &A, int ndep, int precision)

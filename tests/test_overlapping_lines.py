@@ -5,14 +5,18 @@ continuum, so 32-wavelength tiles of the grid hold two or three lines: the
 cross terms between lines and the per-line profile rows of the column
 kernel's cache are exercised.  FP64: identical schedule without Ng against
 the oracle, within 1e-9 per column.  FP32: the cached profiles (rh_iterate)
-against the profiles evaluated in the sweep (rh_iterate_noalloc), equal to
-rounding of the same arithmetic."""
+against the profiles evaluated in the sweep (rh_iterate_noalloc on a context
+that never allocated the cache).  The profile arithmetic is the same in both
+to the bit; the two kernels may fuse the sweep's other multiply-adds
+differently, so they agree to FP32 rounding: FP32_SWEEP_TOL = 32 u (u =
+2^-24), against 2.4 u seen after three iterations."""
 import numpy as np
 import pytest
 
 import rh_synth
 
 FP64_TOL = 1e-9
+FP32_SWEEP_TOL = 32 * 2.0 ** -24
 QWING = 1000.0        # line half-width in reference Doppler widths
 
 
@@ -64,17 +68,20 @@ def test_fp32_cached_profiles_equal_profiles_in_sweep(atom, cols):
 
     import paper_1411_1079_gb300 as rh
     rh.build()
-    ctx = rh.Context(0)
-    ctx.setup_atom(atom)
-    ctx.load_columns(cols)
     kw = dict(maxiter=3, tol=0.0, ng_order=0, precision=1)
-    ctx.iterate(**kw)
-    n_ref = ctx.populations()[0]
+    cached = rh.Context(0)
+    cached.setup_atom(atom)
+    cached.load_columns(cols)
+    cached.iterate(**kw)
+    n_ref = cached.populations()[0]
+    fresh = rh.Context(0)          # no rh_iterate yet: no profile cache
+    fresh.setup_atom(atom)
+    fresh.load_columns(cols)
     ncol, ndep = cols["T"].shape
     n_out = torch.zeros((ncol, atom["nlev"], ndep), dtype=torch.float64, device="cuda")
     it_out = torch.zeros(ncol, dtype=torch.int32, device="cuda")
     st_out = torch.zeros(ncol, dtype=torch.uint8, device="cuda")
     dm_out = torch.zeros(ncol, dtype=torch.float64, device="cuda")
-    ctx.iterate_noalloc(n_out, it_out, st_out, dm_out, **kw)
+    fresh.iterate_noalloc(n_out, it_out, st_out, dm_out, **kw)
     torch.cuda.synchronize()
-    assert float(np.max(np.abs(n_out.cpu().numpy() / n_ref - 1))) < FP64_TOL
+    assert float(np.max(np.abs(n_out.cpu().numpy() / n_ref - 1))) < FP32_SWEEP_TOL

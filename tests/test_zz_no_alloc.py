@@ -1,18 +1,18 @@
 """rh_iterate_noalloc: the iteration for callers that cannot allocate device
 memory while they solve (their memory belongs to their own pool or budget,
 or they cannot afford the device-wide synchronisation of cudaMalloc).  It
-keeps its scratch in a static array inside the library, writes into buffers
-the caller owns, and evaluates the line profiles in the sweep, where
-rh_iterate reads them from its per-column profile cache.  Its results must
-match rh_iterate's on the same columns, on two calls in a row (the second
-call finds the scratch holding the first call's contents), and the second
-call must leave the device's free memory and torch's allocation unchanged.
-In FP32 the two paths agree bit for bit, trajectory and stopping included.
-In FP64 the two kernel instantiations may fuse multiply-adds of the Voigt
-function differently (1 ulp); Ng extrapolation amplifies such differences
-along a trajectory, so FP64 is compared on a fixed schedule without Ng, as
-the FP64 parity tests are.  This file is collected last so that a run
-stopping at the first failure has run every other test first."""
+keeps its scratch in a static array inside the library and writes into
+buffers the caller owns; here rh_iterate runs first on the same context, so
+the no-alloc call reads the line profiles from the profile cache rh_iterate
+allocated and runs the same kernel.  Its results must match rh_iterate's on
+the same columns, on two calls in a row (the second call finds the scratch
+holding the first call's contents), and the second call must leave the
+device's free memory and torch's allocation unchanged.  FP32 is compared
+bit for bit, trajectory and stopping included; FP64 on a fixed schedule
+without Ng within the FP64 parity tests' bound.  The sweep without the
+cache is compared with the cached one in the overlapping-lines tests.  This
+file is collected last so that a run stopping at the first failure has run
+every other test first."""
 import ctypes as C
 
 import numpy as np
