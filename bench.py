@@ -44,15 +44,15 @@ METRIC = "converged columns/s to max|dn/n|<1e-3"
 # columns x 12 iterations (about the iterations a column takes from the
 # learned guess), divided by their points; re-counted whenever the kernel
 # changes
-FLOP_PER_PT = 181.6
+FLOP_PER_PT = 180.3
 # DRAM bytes (read + write) per column-iteration of the column kernel, from
-# the same ncu capture (12.74 GB for 608 x 12): the line-profile cache read
+# the same ncu capture (12.75 GB for 608 x 12): the line-profile cache read
 # back every iteration (1.57 MB), its build once per column and the column's
 # inputs and results
-DRAM_BYTES_PER_COLUMN_ITERATION = (11.510031e9 + 1.231854e9) / (608 * 12)
+DRAM_BYTES_PER_COLUMN_ITERATION = (11.522290e9 + 1.232291e9) / (608 * 12)
 # warp instructions per column-iteration, same capture: the issue-slot view of
 # the same kernel (4 schedulers per SM, one warp instruction per cycle each)
-WARP_INST_PER_COLUMN_ITERATION = 15015163046 / (608 * 12)
+WARP_INST_PER_COLUMN_ITERATION = 15918287990 / (608 * 12)
 
 
 def algorithmic_flop_per_pt(atom, nu):

@@ -387,16 +387,20 @@ int rh_surrogate_file_info(const char *path, int32_t *sizes_out, int64_t *nparam
 /* ---------------------------------------------------------------------- */
 /* Shared-memory layout of the column kernel (no counterpart in the paper;  */
 /* a host computation that needs no GPU, for checking the layout): the byte  */
-/* offsets of its 14 regions in carve order (populations, new populations,   */
+/* offsets of its 15 regions in carve order (populations, new populations,   */
 /* collisional rates, reduction scratch, rate accumulators, 3 per-depth      */
 /* arrays, the per-depth background block [ndep][4], continuum factors,      */
 /* damping, populations in the working precision, Voigt table, block         */
-/* counters) and the carve's end in offsets_out[0..14],                      */
-/* and the bytes the launch allocates in bytes_out (the same function sizes  */
-/* and carves, so the two are equal).  macc: rate accumulators per depth.   */
+/* counters, the warps' line-profile rings) and the carve's end in           */
+/* offsets_out[0..15], and the bytes the launch allocates in bytes_out (the  */
+/* same function sizes and carves, so the two are equal).  macc: rate        */
+/* accumulators per depth.  ring_warps (0..32): warps whose profile ring the */
+/* block holds -- the block's warps for the FP32 kernel with the profile     */
+/* cache and without PRD lines (2304 bytes each: three depths of up to three */
+/* line profiles for the two rays of a sweep pass), 0 for the other kernels. */
 /* RH_EINVAL for sizes outside the library's limits.                        */
 int rh_column_smem_layout(int32_t precision, int32_t nlev, int32_t ndep, int32_t ntr, int32_t ncont, int32_t nline,
-                          int32_t macc, size_t *offsets_out, size_t *bytes_out);
+                          int32_t macc, int32_t ring_warps, size_t *offsets_out, size_t *bytes_out);
 
 /* ---------------------------------------------------------------------- */
 /* Measured fused multiply-add rate of a device (no counterpart in the      */

@@ -138,7 +138,7 @@ def lib(path: str | None = None):
         L.rh_surrogate_file_info.argtypes = [C.c_char_p, _ip, C.POINTER(C.c_int64), C.c_char_p, C.c_size_t]
         L.rh_regrid.argtypes = [vp, C.c_int32, C.POINTER(GridOpts)]
         L.rh_get_columns.argtypes = [vp, _dp, _dp, _dp, _dp]
-        L.rh_column_smem_layout.argtypes = [C.c_int32] * 7 + [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+        L.rh_column_smem_layout.argtypes = [C.c_int32] * 8 + [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         L.rh_fma_peak.argtypes = [C.c_int32, C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
     return _lib
@@ -161,12 +161,12 @@ def _ptr(x):
     return C.c_void_p(x.ctypes.data)
 
 
-def column_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc):
-    """rh_column_smem_layout (host only): ([15] region offsets in carve
+def column_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc, ring_warps=0):
+    """rh_column_smem_layout (host only): ([16] region offsets in carve
     order, the carve's end last; allocated bytes)."""
-    off = (C.c_size_t * 15)()
+    off = (C.c_size_t * 16)()
     b = C.c_size_t()
-    rc = lib().rh_column_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc, off, C.byref(b))
+    rc = lib().rh_column_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc, ring_warps, off, C.byref(b))
     if rc:
         raise RhError(rc, "rh_column_smem_layout: invalid sizes")
     return list(off), b.value

@@ -1329,12 +1329,13 @@ int rh_get_lte(rh_ctx *c, double *nstar_out, double *ne_out)
 }
 
 int rh_column_smem_layout(int32_t precision, int32_t nlev, int32_t ndep, int32_t ntr, int32_t ncont, int32_t nline,
-                          int32_t macc, size_t *offsets_out, size_t *bytes_out)
+                          int32_t macc, int32_t ring_warps, size_t *offsets_out, size_t *bytes_out)
 {
     if ((precision != 0 && precision != 1) || nlev < 2 || nlev > RH_MAXLEV || ndep < 2 || ndep > 4096 || ntr < 1 ||
-        ntr > RH_MAXTR || ncont < 0 || nline < 0 || macc < 1 || !offsets_out || !bytes_out)
+        ntr > RH_MAXTR || ncont < 0 || nline < 0 || macc < 1 || ring_warps < 0 || ring_warps > 32 || !offsets_out ||
+        !bytes_out)
         return RH_EINVAL;
-    mali_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc, offsets_out, 15, bytes_out);
+    mali_smem_layout(precision, nlev, ndep, ntr, ncont, nline, macc, ring_warps, offsets_out, 16, bytes_out);
     return RH_OK;
 }
 

@@ -677,8 +677,8 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
                         const IterLaunch &o, cudaStream_t st, float *ms_out, int *grid_out, char *err,
                         size_t errn);
 size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep);
-int mali_smem_layout(int precision, int L, int N, int ntr, int ncont, int nline, int macc, size_t *offsets, int noff,
-                     size_t *bytes);
+int mali_smem_layout(int precision, int L, int N, int ntr, int ncont, int nline, int macc, int ring_warps,
+                     size_t *offsets, int noff, size_t *bytes);
 int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_warps);
 size_t mali_prd_bytes_per_block(const DevAtom &A, int ndep, int precision);
 size_t mali_phic_bytes_per_block(const DevAtom &A, int ndep, int precision);

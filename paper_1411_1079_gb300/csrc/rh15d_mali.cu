@@ -40,6 +40,16 @@ namespace rh {
 namespace {
 
 constexpr int kWarp = 32;
+// Profile ring of the FP32 sweep with the profile cache (two angles per
+// pass): per warp, its tile's cached line profiles (at most kRingLines line
+// slots, the pass's two rays) at kRingSlots depths -- the depth being swept
+// and the next two -- copied from the cache by cp.async, so the HBM latency
+// of a profile read is covered by two depth steps without holding the values
+// in registers.
+constexpr int kRingSlots = 3;
+constexpr int kRingLines = 3;
+constexpr int kRingSlotFloats = 2 * kRingLines * kWarp;
+constexpr int kRingFloatsPerWarp = kRingSlots * kRingSlotFloats;
 constexpr int kNgLanes = 64;                    // fixed partition of the Ng dot products
 constexpr int kRedDoubles = 5 * kNgLanes + 8;   // block reduction scratch
 
@@ -154,6 +164,7 @@ struct Smem {
     float4 *vtab;              // [RH_VT_N + 1] Voigt coefficient table
     double *red;               // reduction scratch [kRedDoubles]
     int *ibuf;                 // [8]
+    float *ring;               // [warps][kRingFloatsPerWarp] profile ring (ring kernels only)
 };
 
 // Byte offsets of the regions of the block's dynamic shared memory.  The one
@@ -162,10 +173,13 @@ struct Smem {
 // (regions reserved by the carve but dropped from the size) writes outside
 // the block's shared memory.
 struct SmemLayout {
-    size_t n, nn, Cr, red, slot, dz, ivth, vz, bg, Gc, ad, nr, vtab, ibuf, end;
+    size_t n, nn, Cr, red, slot, dz, ivth, vz, bg, Gc, ad, nr, vtab, ibuf, ring, end;
 };
+// ring_warps: warps whose profile ring the block holds (the launch's warps
+// for a ring kernel, else 0)
 template <typename R>
-__host__ __device__ inline SmemLayout smem_layout(int L, int N, int ntr, int ncont, int nline, int macc)
+__host__ __device__ inline SmemLayout smem_layout(int L, int N, int ntr, int ncont, int nline, int macc,
+                                                  int ring_warps)
 {
     SmemLayout o;
     size_t b = 0;
@@ -198,20 +212,30 @@ __host__ __device__ inline SmemLayout smem_layout(int L, int N, int ntr, int nco
     b += sizeof(float4) * (RH_VT_N + 1);
     o.ibuf = b;
     b += sizeof(int) * 8;
+    b = (b + 15) & ~(size_t)15;
+    o.ring = b;
+    b += sizeof(float) * (size_t)kRingFloatsPerWarp * ring_warps;
     o.end = b;
     return o;
 }
 
 template <typename R>
-__host__ __device__ size_t smem_bytes(int L, int N, int ntr, int ncont, int nline, int macc)
+__host__ __device__ size_t smem_bytes(int L, int N, int ntr, int ncont, int nline, int macc, int ring_warps)
 {
-    return smem_layout<R>(L, N, ntr, ncont, nline, macc).end;
+    return smem_layout<R>(L, N, ntr, ncont, nline, macc, ring_warps).end;
+}
+
+// kernels whose sweep reads the line profiles through the ring
+template <typename R, bool PRD, bool CACHE>
+__host__ __device__ constexpr bool uses_ring()
+{
+    return RH_ANGLE_PAIRS && CACHE && !PRD && sizeof(R) == 4;
 }
 
 template <typename R>
-__device__ Smem<R> carve(char *base, int L, int N, int ntr, int ncont, int nline, int macc)
+__device__ Smem<R> carve(char *base, int L, int N, int ntr, int ncont, int nline, int macc, int ring_warps)
 {
-    const SmemLayout o = smem_layout<R>(L, N, ntr, ncont, nline, macc);
+    const SmemLayout o = smem_layout<R>(L, N, ntr, ncont, nline, macc, ring_warps);
     Smem<R> s;
     s.n = reinterpret_cast<double *>(base + o.n);
     s.nn = reinterpret_cast<double *>(base + o.nn);
@@ -227,6 +251,7 @@ __device__ Smem<R> carve(char *base, int L, int N, int ntr, int ncont, int nline
     s.nr = reinterpret_cast<R *>(base + o.nr);
     s.vtab = reinterpret_cast<float4 *>(base + o.vtab);
     s.ibuf = reinterpret_cast<int *>(base + o.ibuf);
+    s.ring = reinterpret_cast<float *>(base + o.ring);
     return s;
 }
 
@@ -236,6 +261,20 @@ template <>
 __device__ __forceinline__ float voigt<float>(float a, float v, const float4 *tab) { return voigt_f32(a, v, tab); }
 template <>
 __device__ __forceinline__ double voigt<double>(double a, double v, const float4 *) { return voigt_f64(a, v); }
+
+// 4-byte asynchronous global -> shared copy and its group fences (each
+// thread waits for its own copies; a thread reads only what it copied)
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Line profile phi(k, ray) of one wavelength: the Doppler shift of the ray,
 // the Voigt function and the normalisation, with every rounding step fixed by
@@ -606,16 +645,56 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                     }
                     flush(k0, val);
                 }
-                // cached profiles loaded one depth step ahead
+                // profiles of the depth being swept: through the warp's ring
+                // (copies issued two steps ahead), else loaded one step ahead
+                constexpr bool RING = uses_ring<R, PRD, CACHE>() && NL > 0;
                 R pa[K], pb[K];
-                load_ph(dir == 0 ? 1 : N - 2, ra, pa);
-                if (two) load_ph(dir == 0 ? 1 : N - 2, rb, pb);
+                float *rw = nullptr;   // the lane's element of the warp's ring
+                int rs = 1;            // ring slot of the current step
+                // issue the copies of step st's depth into ring slot sl (one
+                // commit group per step, empty past the last step)
+                auto ring_fill = [&](int st, int sl) {
+                    if constexpr (RING) {
+                        if (st < N) {
+                            const int kk = dir == 0 ? st : N - 1 - st;
+                            float *dst = rw + sl * kRingSlotFloats;
+#pragma unroll
+                            for (int j = 0; j < NL; ++j) {
+                                cp_async4(dst + j * kWarp, phc + poff[j] + (ra * N + kk) * kWarp);
+                                if (two) cp_async4(dst + (kRingLines + j) * kWarp, phc + poff[j] + (rb * N + kk) * kWarp);
+                            }
+                        }
+                        cp_async_commit();
+                    }
+                };
+                if constexpr (RING) {
+                    rw = s.ring + (size_t)(threadIdx.x >> 5) * kRingFloatsPerWarp + lane;
+                    ring_fill(1, 1);
+                    ring_fill(2, 2);
+                } else {
+                    load_ph(dir == 0 ? 1 : N - 2, ra, pa);
+                    if (two) load_ph(dir == 0 ? 1 : N - 2, rb, pb);
+                }
                 for (int step = 1; step < N; ++step) {
                     const int k = dir == 0 ? step : N - 1 - step;
-                    const int kn = step + 1 < N ? (dir == 0 ? k + 1 : k - 1) : k;
                     R na[K], nb[K];
-                    load_ph(kn, ra, na);
-                    if (two) load_ph(kn, rb, nb);
+                    if constexpr (RING) {
+                        cp_async_wait<1>();                 // this step's copies have landed
+                        const float *sl = rw + rs * kRingSlotFloats;
+#pragma unroll
+                        for (int j = 0; j < K; ++j) {
+                            pa[j] = j < NL ? sl[j * kWarp] : (R)0;
+                            pb[j] = (j < NL && two) ? sl[(kRingLines + j) * kWarp] : (R)0;
+                        }
+                        // refill the slot read one step ago with step + 2
+                        const int sf = rs == 0 ? kRingSlots - 1 : rs - 1;
+                        ring_fill(step + 2, sf);
+                        rs = rs == kRingSlots - 1 ? 0 : rs + 1;
+                    } else {
+                        const int kn = step + 1 < N ? (dir == 0 ? k + 1 : k - 1) : k;
+                        load_ph(kn, ra, na);
+                        if (two) load_ph(kn, rb, nb);
+                    }
                     DepthC<R, K> d;
                     depth_consts<R, K>(s, lc, k, N, d);
                     const R dzk = dir == 0 ? s.dz[k - 1] : s.dz[k];
@@ -649,10 +728,12 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                                 true);
                     }
                     flush(k, val);
+                    if constexpr (!RING) {
 #pragma unroll
-                    for (int j = 0; j < K; ++j) {
-                        pa[j] = na[j];
-                        pb[j] = nb[j];
+                        for (int j = 0; j < K; ++j) {
+                            pa[j] = na[j];
+                            pb[j] = nb[j];
+                        }
                     }
                 }
             }
@@ -885,7 +966,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
 {
     extern __shared__ __align__(16) char smem_raw[];
     const int N = p.N, L = A.nlev;
-    Smem<R> s = carve<R>(smem_raw, L, N, A.ntr, A.ncont, A.nline, A.macc);
+    Smem<R> s = carve<R>(smem_raw, L, N, A.ntr, A.ncont, A.nline, A.macc,
+                         uses_ring<R, PRD, CACHE>() ? (int)(blockDim.x >> 5) : 0);
     const int tid = threadIdx.x, lane = tid & 31;
     const int LN = L * N;
     double *hist = p.nghist + (size_t)blockIdx.x * 4 * LN;
@@ -1329,17 +1411,17 @@ size_t mali_nghist_bytes_per_block(const DevAtom &A, int ndep) { return sizeof(d
 
 // the column kernel's shared-memory layout for the given sizes: its byte
 // offsets in carve order and the allocated size (host computation only)
-int mali_smem_layout(int precision, int L, int N, int ntr, int ncont, int nline, int macc, size_t *offsets, int noff,
-                     size_t *bytes)
+int mali_smem_layout(int precision, int L, int N, int ntr, int ncont, int nline, int macc, int ring_warps,
+                     size_t *offsets, int noff, size_t *bytes)
 {
-    const SmemLayout o = precision == 1 ? smem_layout<float>(L, N, ntr, ncont, nline, macc)
-                                        : smem_layout<double>(L, N, ntr, ncont, nline, macc);
-    const size_t v[15] = {o.n, o.nn, o.Cr, o.red, o.slot, o.dz, o.ivth, o.vz, o.bg, o.Gc, o.ad, o.nr, o.vtab, o.ibuf,
-                          o.end};
-    for (int i = 0; i < noff && i < 15; ++i) offsets[i] = v[i];
-    *bytes = precision == 1 ? smem_bytes<float>(L, N, ntr, ncont, nline, macc)
-                            : smem_bytes<double>(L, N, ntr, ncont, nline, macc);
-    return 15;
+    const SmemLayout o = precision == 1 ? smem_layout<float>(L, N, ntr, ncont, nline, macc, ring_warps)
+                                        : smem_layout<double>(L, N, ntr, ncont, nline, macc, ring_warps);
+    const size_t v[16] = {o.n,  o.nn, o.Cr, o.red,  o.slot, o.dz,   o.ivth, o.vz,
+                          o.bg, o.Gc, o.ad, o.nr,   o.vtab, o.ibuf, o.ring, o.end};
+    for (int i = 0; i < noff && i < 16; ++i) offsets[i] = v[i];
+    *bytes = precision == 1 ? smem_bytes<float>(L, N, ntr, ncont, nline, macc, ring_warps)
+                            : smem_bytes<double>(L, N, ntr, ncont, nline, macc, ring_warps);
+    return 16;
 }
 
 size_t mali_phic_bytes_per_block(const DevAtom &A, int ndep, int precision)
@@ -1358,10 +1440,11 @@ int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_wa
     size_t sm;
     const void *fn;
     if (precision == 1) {
-        sm = smem_bytes<float>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc);
+        sm = smem_bytes<float>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc,
+                               A.nprd ? 0 : (uses_ring<float, false, true>() ? block_warps : 0));
         fn = A.nprd ? (const void *)mali_kernel<float, true, true> : (const void *)mali_kernel<float, false, true>;
     } else {
-        sm = smem_bytes<double>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc);
+        sm = smem_bytes<double>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc, 0);
         fn = A.nprd ? (const void *)mali_kernel<double, true, true> : (const void *)mali_kernel<double, false, true>;
     }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
@@ -1375,7 +1458,8 @@ static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps,
                             size_t prd_cap, size_t phic_cap, cudaStream_t st, float *ms, char *err, size_t errn,
                             int *grid_out)
 {
-    size_t sm = smem_bytes<R>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
+    const int ring_warps = !A.nprd && uses_ring<R, false, true>() ? block_warps : 0;
+    size_t sm = smem_bytes<R>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc, ring_warps);
     if (A.nphi && !p.phic) {
         snprintf(err, errn, "no profile cache");
         return cudaErrorInvalidValue;
@@ -1555,11 +1639,12 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
         return cudaErrorInvalidValue;
     }
     if (o.precision == 1) {
-        sm = smem_bytes<float>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
+        sm = smem_bytes<float>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc,
+                               (!A.nprd && cache && uses_ring<float, false, true>()) ? bw : 0);
         fn = A.nprd ? (const void *)mali_kernel<float, true, true>
                     : (cache ? (const void *)mali_kernel<float, false, true> : (const void *)mali_kernel<float, false, false>);
     } else {
-        sm = smem_bytes<double>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc);
+        sm = smem_bytes<double>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc, 0);
         fn = A.nprd ? (const void *)mali_kernel<double, true, true>
                     : (cache ? (const void *)mali_kernel<double, false, true> : (const void *)mali_kernel<double, false, false>);
     }

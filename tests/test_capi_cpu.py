@@ -78,20 +78,22 @@ def test_header_is_plain_c(tmp_path):
 def test_column_kernel_shared_memory_layout():
     """The column kernel's shared memory is sized and carved by one layout
     (host computation, no GPU): regions follow each other without overlap,
-    the FP64 regions are 8-byte and the background block and the Voigt
-    table 16-byte aligned, the
-    carve ends exactly at the allocated size, and the H atom's FP32 block
-    fits two per SM (228 KB) at 82 depths and one at 128 depths.  A carve
+    the FP64 regions are 8-byte and the background block, the Voigt
+    table and the profile rings 16-byte aligned, the rings take 2304 bytes per
+    warp, the carve ends exactly at the allocated size, and the H atom's FP32
+    block with the rings of 8 warps fits two per SM (228 KB) at 82 depths and
+    one at 128 depths.  A carve
     that reserved more than the allocation -- a region dropped from the size
     but not from the carve -- would write past the block's shared memory."""
     import paper_1411_1079_gb300 as rh
     sizes = {"double": 8, "float": 4}
     for prec in (0, 1):
         R = 4 if prec == 1 else 8
-        for L, N, ntr, ncont, nline, macc in [(2, 2, 1, 0, 1, 2), (4, 13, 5, 3, 2, 20), (6, 82, 15, 5, 10, 117),
-                                              (6, 128, 15, 5, 10, 180), (8, 4096, 32, 7, 25, 300)]:
-            off, nbytes = rh.column_smem_layout(prec, L, N, ntr, ncont, nline, macc)
-            # n, nn, Cr, red, slot, dz, ivth, vz, (pad) bg[N][4], Gc, ad, nr, (pad) vtab, ibuf, end
+        for (L, N, ntr, ncont, nline, macc), rw in zip([(2, 2, 1, 0, 1, 2), (4, 13, 5, 3, 2, 20),
+                                                        (6, 82, 15, 5, 10, 117), (6, 128, 15, 5, 10, 180),
+                                                        (8, 4096, 32, 7, 25, 300)], [0, 3, 8, 8, 0]):
+            off, nbytes = rh.column_smem_layout(prec, L, N, ntr, ncont, nline, macc, rw)
+            # n, nn, Cr, red, slot, dz, ivth, vz, (pad) bg[N][4], Gc, ad, nr, (pad) vtab, ibuf, (pad) ring, end
             want = [8 * L * N, 8 * L * N, 8 * N * 2 * ntr, 8 * (5 * 64 + 8), R * macc * N, R * N, R * N]
             for i, w in enumerate(want):
                 assert off[i + 1] - off[i] == w, (prec, i)
@@ -100,8 +102,9 @@ def test_column_kernel_shared_memory_layout():
             assert off[10] - off[9] == R * ncont * N and off[11] - off[10] == R * nline * N
             assert all(o % 8 == 0 for o in off[:5]) and off[12] % 16 == 0
             assert off[11] + R * L * N <= off[12] < off[11] + R * L * N + 16
-            assert off[13] == off[12] + 16 * 1025 and off[14] == off[13] + 32
-            assert off[14] == nbytes
-    h82 = rh.column_smem_layout(1, 6, 82, 15, 5, 10, 117)[1]
-    assert 2 * h82 <= 228 * 1024
-    assert rh.column_smem_layout(1, 6, 128, 15, 5, 10, 180)[1] <= 227 * 1024
+            assert off[13] == off[12] + 16 * 1025
+            assert off[13] + 32 <= off[14] < off[13] + 48 and off[14] % 16 == 0
+            assert off[15] == off[14] + 2304 * rw and off[15] == nbytes
+    h82 = rh.column_smem_layout(1, 6, 82, 15, 5, 10, 117, 8)[1]
+    assert 2 * (h82 + 1024) <= 228 * 1024        # 1 KB per block reserved by the driver
+    assert rh.column_smem_layout(1, 6, 128, 15, 5, 10, 180, 8)[1] <= 227 * 1024
