@@ -315,14 +315,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_full_config(rh, torch, local, stream, ncol, train_cols, seed=5678, fp64_columns=0, oracle_columns=0):
+def run_full_config(rh, torch, local, stream, ncol, train_cols, seed=5678, fp64_columns=0, oracle_columns=0,
+                    hybrid=1, save_sample=0, sample_path=None):
     """The full-run configuration: 512x512 columns of 128 heights (the
-    first ncol of that cube), Lyman alpha and beta in angle-averaged PRD with
-    200 frequencies each (880 wavelengths), solved from the learned guess in
-    mixed precision (a network trained on train_cols CRD-converged columns of
-    a disjoint 128-height cube), then the FP32 Zeeman Stokes spectrum of H
-    alpha (400 wavelengths, mu = 1, seeded field).  One step each, timed on
-    the device."""
+    first ncol of that cube), Lyman alpha and beta in PRD with 200
+    frequencies each (880 wavelengths) -- R_II-A angle-averaged in the frame
+    of the moving gas (the hybrid scheme, hybrid=1; the columns move at up
+    to 10 km/s) or in the static frame (hybrid=0) -- solved from the learned
+    guess in mixed precision (a network trained on train_cols CRD-converged
+    columns of a disjoint 128-height cube), then the FP32 Zeeman Stokes
+    spectrum of H alpha (400 wavelengths, mu = 1, seeded field).  One step
+    each, timed on the device."""
     t_all = time.perf_counter()
     patom = rh_synth.hydrogen_like_atom(prd_lines=((1, 2), (1, 3)), prd_nlambda=200)
     catom = dict(patom)
@@ -348,7 +351,7 @@ def run_full_config(rh, torch, local, stream, ncol, train_cols, seed=5678, fp64_
     p.load_columns(dev, on_device=True)
     p.surrogate_init(hidden=512, nhidden=3, seed=0)
     p.surrogate_set_state(state)
-    opts = dict(maxiter=MAXITER, tol=TOL, precision=1, start=1, prd_eps0=0.05)
+    opts = dict(maxiter=MAXITER, tol=TOL, precision=1, start=1, prd_eps0=0.05, prd_hybrid=hybrid)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -375,13 +378,19 @@ def run_full_config(rh, torch, local, stream, ncol, train_cols, seed=5678, fp64_
     st_ms = s0.elapsed_time(s1)
     conv_cols = torch.from_numpy(np.where(p.populations()[2] == 0)[0]).to("cuda")
     vi = (iquv[..., 3].abs() / iquv[..., 0]).amax(dim=1)
+    st_all = p.populations()[2]
     out = {"workload": "%d columns of the 512x512 synthetic chromosphere cube (seed %d), 128 heights, H-like atom "
-                       "with Lyman alpha and beta in angle-averaged PRD (R_II-A, 200 frequencies each; 880 "
+                       "with Lyman alpha and beta in PRD (R_II-A, %s, 200 frequencies each; 880 "
                        "wavelengths), learned start, mixed precision, tol 1e-3; then the FP32 H alpha Zeeman "
-                       "Stokes spectrum (400 wavelengths)" % (ncol, seed),
+                       "Stokes spectrum (400 wavelengths)"
+                       % (ncol, seed, "angle-averaged in the frame of the moving gas (hybrid)" if hybrid
+                          else "angle-averaged in the static frame"),
            "columns": ncol, "value": ncol / ((ms + st_ms) / 1e3), "unit": "columns/s",
            "solve": {"ms": ms, "converged": s["n_converged"], "iterations_per_column": s["iterations_total"] / ncol,
-                     "rerun_columns": s["rerun_columns"], "columns_per_s": ncol / (ms / 1e3)},
+                     "rerun_columns": s["rerun_columns"], "pass_columns": s["pass_columns"],
+                     "not_converged": {"maxiter": int((st_all == 1).sum()), "non_finite": int((st_all == 2).sum()),
+                                       "singular": int((st_all == 3).sum())},
+                     "columns_per_s": ncol / (ms / 1e3)},
            "stokes": {"ms": st_ms, "columns_per_s": ncol / (st_ms / 1e3),
                       "max_abs_V_over_I_converged": float(vi[conv_cols].max()) if conv_cols.numel() else None,
                       "columns_with_abs_V_above_I": int((vi > 1).sum())},
@@ -393,11 +402,21 @@ def run_full_config(rh, torch, local, stream, ncol, train_cols, seed=5678, fp64_
         q.setup_atom(patom)
         q.load_columns(rh_synth.subset(cube, idx))
         t0 = time.perf_counter()
-        sq = q.iterate(maxiter=MAXITER, tol=TOL, precision=0, prd_eps0=0.05)
+        sq = q.iterate(maxiter=3 * MAXITER, tol=TOL, precision=0, prd_eps0=0.05, prd_hybrid=hybrid)
         dt = time.perf_counter() - t0
         out["lte_start_fp64"] = {"value": sq["n_converged"] / dt, "unit": "columns/s", "columns": len(idx),
                                  "converged": sq["n_converged"], "iterations_per_column": sq["iterations_total"] / len(idx),
-                                 "seconds": dt, "sample": "plain FP64 GPU MALI from LTE, one pass"}
+                                 "seconds": dt, "sample": "plain FP64 GPU MALI from LTE, one pass of up to %d "
+                                                          "iterations" % (3 * MAXITER)}
+    if save_sample > 0 and sample_path:
+        # seeded columns' GPU results, for the oracle comparison on a host
+        # (--full-run-compare): the oracle's 200-point kernels take minutes
+        # per column to build
+        idx = np.sort(np.random.default_rng(2024).choice(ncol, min(save_sample, ncol), replace=False))
+        p_all = p.populations()
+        np.savez(sample_path, idx=idx, n=p_all[0][idx], status=p_all[2][idx], iters=p_all[1][idx], seed=seed,
+                 ncol=ncol, hybrid=hybrid)
+        out["saved_sample"] = {"path": sample_path, "columns": int(len(idx))}
     if oracle_columns > 0:
         import oracle
         idx = np.sort(np.random.default_rng(2024).choice(ncol, min(oracle_columns, ncol), replace=False))
@@ -405,7 +424,7 @@ def run_full_config(rh, torch, local, stream, ncol, train_cols, seed=5678, fp64_
         o.setup_atom(patom)
         o.load_columns(rh_synth.subset(cube, idx))
         t0 = time.perf_counter()
-        o.iterate(maxiter=3000, tol=1e-8, prd_eps0=0.05, nthreads=os.cpu_count() or 1)
+        o.iterate(maxiter=3000, tol=1e-8, prd_eps0=0.05, prd_hybrid=hybrid, nthreads=os.cpu_count() or 1)
         no, _, sto, _ = o.populations()
         ok = sto == oracle.ST_CONV
         d = np.abs(n_gpu[idx] / no - 1).max(axis=(1, 2))[ok]
@@ -602,8 +621,21 @@ def run_gpu(args):
         npc = len(psub["T"])
         prd = {"value": npc / dt_p, "unit": "columns/s", "columns": npc, "converged": s_p["n_converged"],
                "iterations_per_column": s_p["iterations_total"] / npc,
-               "lines": "Lyman alpha and beta, 64 wavelengths each, R_II-A, PRD switching eps0 = 0.05",
+               "lines": "Lyman alpha and beta, 64 wavelengths each, R_II-A in the static frame, PRD switching "
+                        "eps0 = 0.05",
                "precision": "fp32 formal solution/rates/redistribution, fp64 rate equations/Ng"}
+        # the same columns with the redistribution in the frame of the moving gas
+        pctx.load_columns(psub)
+        pctx.solve(maxiter=MAXITER, tol=TOL, precision=1, prd_eps0=0.05, prd_hybrid=1)
+        pctx.load_columns(psub)
+        barrier()
+        t_p = time.perf_counter()
+        s_h = pctx.solve(maxiter=MAXITER, tol=TOL, precision=1, prd_eps0=0.05, prd_hybrid=1)
+        barrier()
+        dt_h = time.perf_counter() - t_p
+        prd["hybrid"] = {"value": npc / dt_h, "unit": "columns/s", "converged": s_h["n_converged"],
+                         "iterations_per_column": s_h["iterations_total"] / npc,
+                         "scheme": "R_II-A angle-averaged in the frame of the moving gas (hybrid)"}
 
     # plain FP64 MALI from LTE on a random sample of the cube (FP64 arithmetic is
     # slow on this part: one column per SM keeps the run under a minute)
@@ -730,7 +762,8 @@ def run_full(args):
     stream = torch.cuda.current_stream()
     with ClockSampler(0) as clk:
         r = run_full_config(rh, torch, 0, stream, 512 * 512, args.full_run_train,
-                            fp64_columns=args.full_run_fp64, oracle_columns=args.full_run_oracle)
+                            fp64_columns=args.full_run_fp64, oracle_columns=args.full_run_oracle,
+                            save_sample=args.full_run_save, sample_path=args.full_run_sample_path)
     line = {"metric": METRIC, "value": r["value"], "unit": "columns/s", "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": r["solve"]["ms"] + r["stokes"]["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -738,6 +771,32 @@ def run_full(args):
                        "l2": "working set > L2 (inputs larger than L2)", "parallelism": "dp1 (independent columns)"},
             "full_run": r, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
+
+
+def run_full_compare(args):
+    """True error of a full run's saved columns (--full-run-save) against
+    the oracle converged to 1e-8 on this host's cores; one JSON line."""
+    import oracle
+    z = np.load(args.full_run_compare)
+    idx, ncol, seed, hyb = z["idx"], int(z["ncol"]), int(z["seed"]), int(z["hybrid"])
+    patom = rh_synth.hydrogen_like_atom(prd_lines=((1, 2), (1, 3)), prd_nlambda=200)
+    full = rh_synth.chromosphere_cube(512, 512, 128, seed=seed)
+    cube = full if ncol >= 512 * 512 else rh_synth.subset(full, slice(0, ncol))
+    o = oracle.Oracle()
+    o.setup_atom(patom)
+    o.load_columns(rh_synth.subset(cube, idx))
+    t0 = time.perf_counter()
+    o.iterate(maxiter=3000, tol=1e-8, prd_eps0=0.05, prd_hybrid=hyb, nthreads=os.cpu_count() or 1)
+    no, ito, sto, _ = o.populations()
+    ok = (sto == oracle.ST_CONV) & (z["status"] == 0)
+    d = np.abs(z["n"] / no - 1).max(axis=(1, 2))
+    print(json.dumps({"true_error": {"max_rel_dn": float(d[ok].max()) if ok.any() else None,
+                                     "median_rel_dn": float(np.median(d[ok])) if ok.any() else None,
+                                     "per_column": [float(x) for x in d], "columns": [int(i) for i in idx],
+                                     "oracle_iterations": [int(i) for i in ito],
+                                     "gpu_iterations": [int(i) for i in z["iters"]],
+                                     "reference": "oracle converged to 1e-8, %.0f s on %d host threads"
+                                                  % (time.perf_counter() - t0, os.cpu_count() or 1)}}), flush=True)
 
 
 def run_ncu_case(args):
@@ -804,6 +863,11 @@ def main():
     ap.add_argument("--full-run-oracle", type=int, default=0,
                     help="full-run columns compared with the oracle (its 200-point PRD kernels take minutes "
                          "per column to build on the host; 0: skip)")
+    ap.add_argument("--full-run-save", type=int, default=0,
+                    help="seeded full-run columns whose GPU results --full-run writes to --full-run-sample-path")
+    ap.add_argument("--full-run-sample-path", default="full_run_sample.npz")
+    ap.add_argument("--full-run-compare", default=None,
+                    help="a saved full-run sample: compare it with the oracle on this host (no GPU)")
     ap.add_argument("--fp64-columns-per-sm", type=int, default=3,
                     help="columns per SM of the plain FP64 LTE-start comparison (0: skip)")
     ap.add_argument("--ncu-columns", type=int, default=608)
@@ -816,7 +880,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.ncu_case:
+    if args.full_run_compare:
+        run_full_compare(args)
+    elif args.ncu_case:
         run_ncu_case(args)
     elif args.full_run:
         run_full(args)

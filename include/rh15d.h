@@ -137,6 +137,14 @@ typedef struct {
                              options); converged columns are left untouched */
     double prd_eps0;      /* PRD switching (Eq. 1): rho' = eps rho + (1 - eps), eps = min(1, eps0 it^2);
                              <= 0: off (eps = 1).  Atoms with PRD lines only */
+    int32_t prd_hybrid;   /* PRD lines: 0 angle-averaged redistribution in the static frame; 1 the
+                             hybrid approximation of angle-dependent PRD in moving atmospheres
+                             (Sect. 2.1): rho is computed in the frame of the moving gas from the
+                             gas-frame mean intensity J_f(nu) = sum over rays (w_mu/2)
+                             I(nu + nu0 mu_z v_z / c), and each ray emits with rho_f(nu - nu0
+                             mu_z v_z / c); both transfers interpolate linearly in frequency over
+                             the line's points, constant beyond its ends.  Without velocities the
+                             two are the same scheme */
 } rh_iter_opts;
 
 typedef struct {

@@ -122,7 +122,7 @@ class AtomDesc(C.Structure):
 class IterOpts(C.Structure):
     _fields_ = [("maxiter", C.c_int32), ("tol", C.c_double), ("ng_order", C.c_int32),
                 ("ng_delay", C.c_int32), ("ng_period", C.c_int32), ("start", C.c_int32),
-                ("crsw_init", C.c_double), ("prd_eps0", C.c_double)]
+                ("crsw_init", C.c_double), ("prd_eps0", C.c_double), ("prd_hybrid", C.c_int32)]
 
 
 class GridOpts(C.Structure):
@@ -348,9 +348,10 @@ class Oracle:
         self._check(self._lib.rho_set_populations(self._p, _d(n)))
 
     def iterate(self, maxiter=500, tol=1e-3, ng_order=2, ng_delay=5, ng_period=3, start=0,
-                crsw_init=1.0, nthreads=None, prd_eps0=0.0):
+                crsw_init=1.0, nthreads=None, prd_eps0=0.0, prd_hybrid=0):
         o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
-                     ng_period=ng_period, start=start, crsw_init=crsw_init, prd_eps0=prd_eps0)
+                     ng_period=ng_period, start=start, crsw_init=crsw_init, prd_eps0=prd_eps0,
+                     prd_hybrid=prd_hybrid)
         s = IterStats()
         if nthreads is None:
             nthreads = os.cpu_count() or 1

@@ -24,7 +24,9 @@
  * n_e fixed from Saha plus a metal floor; Ng of order 2 with uniform weights,
  * delay 5, period 3; collisional-radiative switching by a decade per
  * iteration; PRD switching eps = min(1, eps0 it^2); Ng and a Jacobi step on
- * the PRD ratio rho.
+ * the PRD ratio rho; for the hybrid PRD option (Sect. 2.1), the gas-frame
+ * mean intensity and ratio transferred between frames by linear
+ * interpolation in frequency over the line's points, constant beyond them.
  *
  * Parity status: every function is pinned by a test against closed forms,
  * limits or an independent library routine, except the overall multi-level
@@ -85,6 +87,8 @@ typedef struct {
     int32_t start;      /* 0 LTE, 2 user populations, 3 zero radiation, 4 escape probability */
     double crsw_init;   /* collisional-radiative switching start factor; <=1 off */
     double prd_eps0;    /* PRD switching (Eq. 1): eps = min(1, eps0 it^2); <= 0: off (eps = 1) */
+    int32_t prd_hybrid; /* 0: angle-averaged in the static frame; 1: the hybrid approximation of
+                         * angle-dependent PRD in moving atmospheres (Sect. 2.1) */
 } rho_iter_opts;
 
 typedef struct {
@@ -1066,6 +1070,10 @@ typedef struct {
     double *rplain;   /* [nlam][N] the last update's plain ratio r (before switching) */
     double *rhist;    /* Ng history of rho at the PRD points [4][npt N], newest first */
     double *Pup, *Pdn;    /* [ntr][N] plain radiative rate coefficients (actual I, not I_eff) */
+    double *Iray;     /* [2 nmu][nlam][N] intensity of each ray at the PRD points (hybrid PRD) */
+    double *Dray;     /* [2 nmu][nlam][N] each ray's dI/drho through the line's own emission */
+    const double *vz; /* the column's vertical velocity (hybrid PRD) */
+    int hybrid;       /* 1: rho in the fluid frame (hybrid PRD) */
     double *prdK[MAXTR];   /* per PRD line [N][np][np]: normalised redistribution kernel */
     double *prdf[MAXTR];   /* per PRD line [N][np]: weights of J-bar */
 } work_t;
@@ -1101,6 +1109,8 @@ static void work_alloc(work_t *w, const atom_t *a, int N)
     }
     w->Pup = malloc((size_t)a->ntr * N * 8);
     w->Pdn = malloc((size_t)a->ntr * N * 8);
+    w->Iray = a->nprd_line ? malloc((size_t)2 * a->nmu * a->nlam * N * 8) : NULL;
+    w->Dray = a->nprd_line ? calloc((size_t)2 * a->nmu * a->nlam * N, 8) : NULL;
     for (int64_t i = 0; i < a->nlam * N; ++i) w->rho[i] = 1.0;
     for (int q = 0; q < a->nprd_line; ++q) {
         w->prdK[q] = malloc((size_t)N * a->prd_np[q] * a->prd_np[q] * 8);
@@ -1115,7 +1125,7 @@ static void work_free(work_t *w)
     free(w->dtau); free(w->I); free(w->lam); free(w->chit); free(w->Vlu); free(w->Vul);
     free(w->Ieff); free(w->omlam); free(w->Sbg);
     free(w->Ut); free(w->hist);
-    free(w->rho); free(w->Jp); free(w->Pup); free(w->Pdn);
+    free(w->rho); free(w->Jp); free(w->Pup); free(w->Pdn); free(w->Iray); free(w->Dray);
     free(w->Dp); free(w->U0); free(w->rplain); free(w->rhist);
     for (int q = 0; q < MAXTR; ++q) {
         if (w->prdK[q]) free(w->prdK[q]);
@@ -1374,6 +1384,127 @@ double rho_crsw_factor(double f0, int32_t it)
     return f > 1.0 ? f : 1.0;
 }
 
+/* Hybrid approximation of angle-dependent PRD in moving atmospheres (Sect.
+ * 2.1, Leenaarts et al. 2012): the redistribution is angle-averaged in the
+ * frame of the moving gas, where the atmosphere is locally static.  A photon
+ * of observer-frame frequency nu travelling with direction cosine mu_z has
+ * the frequency nu - nu0 mu_z v_z / c in the gas (the same shift the line
+ * profile carries), so
+ *   J_f(nu_i) = sum over rays (w_mu / 2) I_ray(nu_i + nu0 mu_z v_z / c),
+ * the mean intensity at the line's points in the gas frame, replaces J in
+ * the update of rho (which is then rho_f, a function of the gas-frame
+ * frequency), and the ray (mu_z) at observer frequency nu emits with
+ * rho_f(nu - nu0 mu_z v_z / c).  Both transfers are linear interpolations
+ * in frequency over the line's points, held constant beyond its first and
+ * last point.  Without velocity every shifted frequency is a grid point and
+ * the scheme is the static-frame one exactly. */
+
+/* v at frequency nu by linear interpolation over PRD line q's points (sorted
+ * by increasing frequency) at depth k; v[pt * N + k] holds the value at grid
+ * point pt */
+static double prd_interp(const atom_t *a, int q, int N, int k, const double *v, double nu)
+{
+    const int m = a->prd_np[q];
+    const int *pt = a->prd_pts[q];
+    if (nu <= a->nu[pt[0]]) return v[(size_t)pt[0] * N + k];
+    if (nu >= a->nu[pt[m - 1]]) return v[(size_t)pt[m - 1] * N + k];
+    int lo = 0, hi = m - 1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (a->nu[pt[mid]] <= nu) lo = mid;
+        else hi = mid;
+    }
+    double na = a->nu[pt[lo]], nb = a->nu[pt[hi]];
+    if (!(nb > na)) return v[(size_t)pt[lo] * N + k];
+    double t = (nu - na) / (nb - na);
+    return (1.0 - t) * v[(size_t)pt[lo] * N + k] + t * v[(size_t)pt[hi] * N + k];
+}
+
+/* PRD line of transition t (-1: none) */
+static int prd_line_of(const atom_t *a, int t)
+{
+    for (int q = 0; q < a->nprd_line; ++q)
+        if (a->prd_t[q] == t) return q;
+    return -1;
+}
+
+/* the bracket of frequency nu among PRD line q's points: interpolation
+ * between points lo and hi = lo + 1 with weight t on hi, or lo = hi with
+ * t = 0 beyond the line's first or last point (prd_interp's rule) */
+static void prd_bracket(const atom_t *a, int q, double nu, int *lo_out, int *hi_out, double *t_out)
+{
+    const int m = a->prd_np[q];
+    const int *pt = a->prd_pts[q];
+    if (nu <= a->nu[pt[0]] || nu >= a->nu[pt[m - 1]]) {
+        *lo_out = *hi_out = nu <= a->nu[pt[0]] ? 0 : m - 1;
+        *t_out = 0.0;
+        return;
+    }
+    int lo = 0, hi = m - 1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (a->nu[pt[mid]] <= nu) lo = mid;
+        else hi = mid;
+    }
+    *lo_out = lo;
+    *hi_out = hi;
+    *t_out = (nu - a->nu[pt[lo]]) / (a->nu[pt[hi]] - a->nu[pt[lo]]);
+}
+
+/* weight of point i of PRD line q in the interpolation at frequency nu */
+static double prd_weight(const atom_t *a, int q, int i, double nu)
+{
+    int lo, hi;
+    double t;
+    prd_bracket(a, q, nu, &lo, &hi, &t);
+    if (lo == hi) return lo == i ? 1.0 : 0.0;
+    return (lo == i ? 1.0 - t : 0.0) + (hi == i ? t : 0.0);
+}
+
+/* the hybrid scheme's local derivative of J_f at point i with respect to
+ * rho_f at the same point, through the line's own emission: J_f(i) takes
+ * ray r's intensity at nu_i + s_r (s_r = nu0 mu_z v_z / c) from the points
+ * j around it (weights c_j), and the ray emits at point j with rho_f
+ * interpolated at nu_j - s_r, where point i has the weight e_ij; with dr_j
+ * = dI_r(nu_j)/drho there (Psi* n_u U0),
+ *   D_f(i) = sum over rays (w_mu / 2) sum_j c_j dr_j e_ij. */
+static void prd_fluid_D(const atom_t *a, const work_t *w, int q, int N, int k, double *Dl)
+{
+    const int t = a->prd_t[q], m = a->prd_np[q];
+    const int *pt = a->prd_pts[q];
+    for (int i = 0; i < m; ++i) Dl[i] = 0.0;
+    for (int mu = 0; mu < a->nmu; ++mu)
+        for (int d = 0; d < 2; ++d) {
+            const double muz = d == 0 ? -a->mu[mu] : a->mu[mu];
+            const double sh = a->nu0[t] * muz * w->vz[k] / CLIGHT;
+            const double *dr = w->Dray + (size_t)(mu * 2 + d) * a->nlam * N;
+            for (int i = 0; i < m; ++i) {
+                int lo, hi;
+                double tt;
+                prd_bracket(a, q, a->nu[pt[i]] + sh, &lo, &hi, &tt);
+                double s = (1.0 - tt) * dr[(size_t)pt[lo] * N + k] * prd_weight(a, q, i, a->nu[pt[lo]] - sh);
+                if (hi != lo) s += tt * dr[(size_t)pt[hi] * N + k] * prd_weight(a, q, i, a->nu[pt[hi]] - sh);
+                Dl[i] += 0.5 * a->wmu[mu] * s;
+            }
+        }
+}
+
+/* gas-frame mean intensity of PRD line q at depth k at its points (Jl[m]);
+ * rays in the order the formal solution accumulates the static-frame J */
+static void prd_fluid_J(const atom_t *a, const work_t *w, int q, int N, int k, double *Jl)
+{
+    const int t = a->prd_t[q], m = a->prd_np[q];
+    for (int i = 0; i < m; ++i) Jl[i] = 0.0;
+    for (int mu = 0; mu < a->nmu; ++mu)
+        for (int d = 0; d < 2; ++d) {
+            const double muz = d == 0 ? -a->mu[mu] : a->mu[mu];
+            const double sh = a->nu0[t] * muz * w->vz[k] / CLIGHT;
+            const double *Ir = w->Iray + (size_t)(mu * 2 + d) * a->nlam * N;
+            for (int i = 0; i < m; ++i)
+                Jl[i] += 0.5 * a->wmu[mu] * prd_interp(a, q, N, k, Ir, a->nu[a->prd_pts[q][i]] + sh);
+        }
+}
+
 /* rho = psi/phi of every PRD line after a solve (Uitenbroek 2001, Eq. 14,
  * angle-averaged, coherent scattering in the atom's frame, gamma = 1):
  *   r_i = 1 + F [sum_j K_ij J_j / Jbar - 1],  Jbar = sum_j f_j J_j,
@@ -1412,8 +1543,20 @@ static void prd_update(const rho_ctx *c, int64_t col, work_t *w, const double *n
     (void)col;
     for (int q = 0; q < a->nprd_line; ++q) {
         int t = a->prd_t[q], m = a->prd_np[q], l = a->tl[t], u = a->tu[t];
+        double *Jl = malloc(sizeof(double) * m), *Dl = malloc(sizeof(double) * m);
         for (int k = 0; k < N; ++k) {
             const double *K = w->prdK[q] + (size_t)k * m * m, *f = w->prdf[q] + (size_t)k * m;
+            /* the mean intensity at the line's points: static frame, or the
+             * gas frame for the hybrid scheme */
+            if (w->hybrid) {
+                prd_fluid_J(a, w, q, N, k, Jl);
+                if (jacobi) prd_fluid_D(a, w, q, N, k, Dl);
+            } else {
+                for (int j = 0; j < m; ++j) {
+                    Jl[j] = w->Jp[(size_t)a->prd_pts[q][j] * N + k];
+                    Dl[j] = w->Dp[(size_t)a->prd_pts[q][j] * N + k];
+                }
+            }
             /* supply of the upper level: radiative (plain) and collisional */
             double in = 0.0;
             for (int t2 = 0; t2 < a->ntr; ++t2) {
@@ -1424,22 +1567,24 @@ static void prd_update(const rho_ctx *c, int64_t col, work_t *w, const double *n
                 if (p != u) in += n[p * N + k] * w->C[(size_t)k * L * L + p * L + u];
             double F = n[l * N + k] * w->Pup[(size_t)t * N + k] / in;
             double jbar = 0.0;
-            for (int j = 0; j < m; ++j) jbar += f[j] * w->Jp[(size_t)a->prd_pts[q][j] * N + k];
+            for (int j = 0; j < m; ++j) jbar += f[j] * Jl[j];
             for (int i = 0; i < m; ++i) {
                 size_t gi = (size_t)a->prd_pts[q][i] * N + k;
                 double sr = 0.0;
-                for (int j = 0; j < m; ++j) sr += K[i * m + j] * w->Jp[(size_t)a->prd_pts[q][j] * N + k];
+                for (int j = 0; j < m; ++j) sr += K[i * m + j] * Jl[j];
                 double r = 1.0 + F * (sr / jbar - 1.0);
                 w->rplain[gi] = r;
                 double den = 2.0;
                 if (jacobi) {
-                    double g = F * (K[i * m + i] - f[i] * sr / jbar) * w->Dp[gi] / jbar;
+                    double g = F * (K[i * m + i] - f[i] * sr / jbar) * Dl[i] / jbar;
                     den = 1.0 - eps * g;
                     if (den < RHO_JACOBI_FLOOR) den = RHO_JACOBI_FLOOR;
                 }
                 w->rho[gi] += ((eps * r + (1.0 - eps)) - w->rho[gi]) / den;
             }
         }
+        free(Jl);
+        free(Dl);
     }
 }
 
@@ -1471,10 +1616,13 @@ static void transition_coeffs(const rho_ctx *c, int64_t col, const work_t *w, co
         if (a->kind[t] == 0) {
             const double *p = w->prof + (((size_t)a->prof_slot[i * MAXACT + s] * a->nmu + m) * 2 + d) * N;
             double h4 = HPLANCK * nu / (4.0 * PI_D);
+            const int q = (a->prd[t] && w->hybrid) ? prd_line_of(a, t) : -1;
+            const double muz = d == 0 ? -a->mu[m] : a->mu[m];
             for (int k = 0; k < N; ++k) {
                 /* partial redistribution: emission and stimulated emission
-                 * with psi = rho phi */
+                 * with psi = rho phi (hybrid: rho of the gas-frame frequency) */
                 double r = a->prd[t] ? w->rho[i * N + k] : 1.0;
+                if (q >= 0) r = prd_interp(a, q, N, k, w->rho, nu - a->nu0[t] * muz * w->vz[k] / CLIGHT);
                 Vlu[k] = h4 * a->Blu[t] * p[k];
                 Vul[k] = a->g[l] / a->g[u] * Vlu[k] * r;
                 U0[k] = h4 * a->A[t] * p[k];
@@ -1567,15 +1715,18 @@ static void rate_matrix(const rho_ctx *c, int64_t col, work_t *w, const double *
                 if (mode != 2) formal_ray(c, col, w, n, i, m, d);
                 if (prd_pt && mode != 2) {
                     for (int k = 0; k < N; ++k) w->Jp[i * N + k] += 0.5 * a->wmu[m] * w->I[k];
+                    memcpy(w->Iray + ((size_t)(m * 2 + d) * a->nlam + i) * N, w->I, sizeof(double) * N);
                     /* dI_k/drho_k = Psi*_k n_u U0_k of the PRD line (its emission
                      * is the only term of S that rho multiplies; stimulated
                      * emission in chi is left out of this derivative) */
                     for (int s = 0; s < a->nact[i]; ++s) {
                         int t = a->act[i * MAXACT + s];
                         if (!a->prd[t]) continue;
-                        for (int k = 0; k < N; ++k)
-                            w->Dp[i * N + k] += 0.5 * a->wmu[m] * (w->lam[k] / w->chi[k]) *
-                                                n[a->tu[t] * N + k] * w->U0[s * N + k];
+                        double *dr = w->Dray + ((size_t)(m * 2 + d) * a->nlam + i) * N;
+                        for (int k = 0; k < N; ++k) {
+                            dr[k] = (w->lam[k] / w->chi[k]) * n[a->tu[t] * N + k] * w->U0[s * N + k];
+                            w->Dp[i * N + k] += 0.5 * a->wmu[m] * dr[k];
+                        }
                     }
                 }
                 for (int k = 0; k < N; ++k) {
@@ -1857,6 +2008,8 @@ static void iterate_column(rho_ctx *c, int64_t col, const rho_iter_opts *o, work
     double *n = c->pops + (size_t)col * nv;
     double *nnew = malloc(nv * 8), *Cbase = malloc(sizeof(double) * N * L * L);
     column_setup(c, col, w);
+    w->hybrid = o->prd_hybrid != 0;
+    w->vz = c->vz + col * N;
     memcpy(Cbase, w->C, sizeof(double) * N * L * L);
     if (o->start == 0)
         memcpy(n, c->nstar + (size_t)col * nv, nv * 8);

@@ -53,7 +53,8 @@ class IterOpts(C.Structure):
     _fields_ = [("maxiter", C.c_int32), ("tol", C.c_double), ("ng_order", C.c_int32),
                 ("ng_delay", C.c_int32), ("ng_period", C.c_int32), ("start", C.c_int32),
                 ("precision", C.c_int32), ("persistent", C.c_int32), ("block_warps", C.c_int32),
-                ("crsw_init", C.c_double), ("only_unconverged", C.c_int32), ("prd_eps0", C.c_double)]
+                ("crsw_init", C.c_double), ("only_unconverged", C.c_int32), ("prd_eps0", C.c_double),
+                ("prd_hybrid", C.c_int32)]
 
 
 class IterStats(C.Structure):
@@ -246,6 +247,7 @@ class Context:
         self._check(self._lib.rh_setup_atom(self._p, C.byref(d)))
         self.nlev = a["nlev"]
         self.nmu = a["nmu"]
+        self.has_prd = bool("line_prd" in a and np.any(a["line_prd"]))
 
     @property
     def nlambda(self) -> int:
@@ -272,11 +274,11 @@ class Context:
 
     def iterate(self, maxiter=500, tol=1e-3, ng_order=2, ng_delay=5, ng_period=3, start=0,
                 precision=1, persistent=1, block_warps=0, crsw_init=1.0, only_unconverged=0,
-                prd_eps0=0.0) -> dict:
+                prd_eps0=0.0, prd_hybrid=0) -> dict:
         o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
                      ng_period=ng_period, start=start, precision=precision, persistent=persistent,
                      block_warps=block_warps, crsw_init=crsw_init, only_unconverged=only_unconverged,
-                     prd_eps0=prd_eps0)
+                     prd_eps0=prd_eps0, prd_hybrid=prd_hybrid)
         s = IterStats()
         rc = self._check(self._lib.rh_iterate(self._p, C.byref(o), C.byref(s)), allow=(RH_ENOTCONV,))
         out = {f: getattr(s, f) for f, _ in IterStats._fields_}
@@ -286,10 +288,13 @@ class Context:
     # Sect. 2.3: run all columns with an aggressive choice of options, then
     # re-run the columns that did not converge with other options.
     RERUN_CRSW = (1e3, 1e5, 1e7)
+    # with PRD lines the rungs keep Ng (its Jacobi step on rho): the damped
+    # rho update without it diverges on strongly moving columns
+    RERUN_CRSW_PRD = (1e3, 1e5)
 
     def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True, start=0,
               ng_order=2, ng_delay=5, ng_period=3, use_graph=1, autotune=1, fused_rerun=1,
-              prd_eps0=0.0, rungs=None) -> dict:
+              prd_eps0=0.0, rungs=None, prd_hybrid=0, rerun_maxiter=None) -> dict:
         """rh_solve: every column from LTE (start=0), the learned guess
         (start=1), the current populations (start=2), zero radiation (3) or
         escape probabilities (4) with Ng acceleration, then the columns that
@@ -299,21 +304,30 @@ class Context:
         strategy): by the column kernel itself as
         soon as a column fails (fused_rerun=1) or as separate passes over a
         device-selected list; the sequence is replayed as a CUDA graph.
-        rungs: the re-run ladder as (collisional-radiative factor, Ng on)
-        pairs, at most MAX_RERUN of them, in place of the default."""
+        With PRD lines the default ladder keeps Ng in every rung (LTE, then
+        switching x1e3 and x1e5) and re-runs take up to 3 x maxiter
+        iterations.  rungs: the re-run ladder as (collisional-radiative
+        factor, Ng on) pairs, at most MAX_RERUN of them, in place of the
+        default; rerun_maxiter: the re-runs' iteration limit."""
         o = SolveOpts()
         o.pass1 = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay, ng_period=ng_period,
                            start=start, precision=precision, persistent=persistent, block_warps=block_warps,
-                           crsw_init=1.0, only_unconverged=0, prd_eps0=prd_eps0)
+                           crsw_init=1.0, only_unconverged=0, prd_eps0=prd_eps0, prd_hybrid=prd_hybrid)
         # the ladder: from a start other than LTE, first LTE with the same
         # options; then stronger and stronger switching without Ng
+        prd = getattr(self, "has_prd", False)
         if rungs is None:
-            rungs = ([(1.0, 1)] if start != 0 else []) + [(f, 0) for f in self.RERUN_CRSW]
+            if prd:
+                rungs = ([(1.0, 1)] if start != 0 else []) + [(f, 1) for f in self.RERUN_CRSW_PRD]
+            else:
+                rungs = ([(1.0, 1)] if start != 0 else []) + [(f, 0) for f in self.RERUN_CRSW]
+        if rerun_maxiter is None:
+            rerun_maxiter = 3 * maxiter if prd else maxiter
         rungs = [(float(f), int(bool(ng))) for f, ng in rungs]
         if len(rungs) > len(o.rerun_crsw) or any(not f >= 1.0 for f, _ in rungs):
             raise ValueError("rungs: at most %d pairs with factors >= 1" % len(o.rerun_crsw))
         o.nrerun = len(rungs) if rescue else 0
-        o.rerun_maxiter = maxiter
+        o.rerun_maxiter = int(rerun_maxiter)
         for i, (f, ng) in enumerate(rungs[:o.nrerun]):
             o.rerun_crsw[i] = f
             o.rerun_ng[i] = ng

@@ -488,6 +488,7 @@ int build_atom(rh_ctx *c, const rh_atom_desc *d)
                 a.prd_w.push_back(a.wq[gi][it - a.act[gi].begin()]);
             }
             const int npq = (int)pts.size();
+            if (npq < 2) return fail(c, RH_EINVAL, "a PRD line needs at least two wavelength points");
             da.prd_off[q + 1] = da.prd_off[q] + npq;
             da.prd_koff[q + 1] = da.prd_koff[q] + npq * npq;
         }
@@ -646,9 +647,10 @@ void set_phic(const rh_ctx *c, IterLaunch &il)
     il.phic_cap = c->phic_cap;
 }
 
-void set_prd(const rh_ctx *c, IterLaunch &il, double eps0)
+void set_prd(const rh_ctx *c, IterLaunch &il, double eps0, int hybrid)
 {
     il.prd_eps0 = eps0;
+    il.prd_hybrid = hybrid;
     il.lane_prd = c->lane_prd_d;
     il.prd_nu = c->prd_nu_d;
     il.prd_w = c->prd_w_d;
@@ -1164,7 +1166,8 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     if (o->maxiter < 1 || !(o->tol >= 0) || (o->ng_order != 0 && o->ng_order != 2) ||
         (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) || (o->precision != 0 && o->precision != 1) ||
         (o->start < 0 || o->start > 4) || o->block_warps < 0 || o->block_warps > 8 ||
-        (o->only_unconverged != 0 && o->only_unconverged != 1) || !std::isfinite(o->prd_eps0))
+        (o->only_unconverged != 0 && o->only_unconverged != 1) || !std::isfinite(o->prd_eps0) ||
+        (o->prd_hybrid != 0 && o->prd_hybrid != 1))
         return fail(c, RH_EINVAL, "rh_iterate: invalid options");
     cudaSetDevice(c->dev);
     int start = o->start;
@@ -1262,7 +1265,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
         il.block_warps = c->tuned_bw[o->precision];
         il.ctas_per_sm = c->tuned_ctas[o->precision];
     }
-    set_prd(c, il, o->prd_eps0);
+    set_prd(c, il, o->prd_eps0, o->prd_hybrid);
     set_phic(c, il);
     float ms = 0;
     int grid = 0;
@@ -1560,7 +1563,8 @@ bool valid_iter_opts(const rh_iter_opts *o)
 {
     return o->maxiter >= 1 && o->tol >= 0 && (o->ng_order == 0 || o->ng_order == 2) &&
            !(o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) && (o->precision == 0 || o->precision == 1) &&
-           o->start >= 0 && o->start <= 4 && o->block_warps >= 0 && o->block_warps <= 8;
+           o->start >= 0 && o->start <= 4 && o->block_warps >= 0 && o->block_warps <= 8 &&
+           std::isfinite(o->prd_eps0) && (o->prd_hybrid == 0 || o->prd_hybrid == 1);
 }
 
 // everything the enqueued sequence depends on, compared byte-wise
@@ -1767,7 +1771,7 @@ int rh_autotune(rh_ctx *c, int32_t precision, rh_tune_result *out)
             il.start = 0;
             il.nsm = c->nsm;
             il.nwork = S;
-            set_prd(c, il, 0.0);
+            set_prd(c, il, 0.0, 0);
             set_phic(c, il);
             double best = -1;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // first run: warm-up
@@ -1880,7 +1884,7 @@ int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
         base.block_warps = c->tuned_bw[prec];
         base.ctas_per_sm = c->tuned_ctas[prec];
     }
-    set_prd(c, base, o->pass1.prd_eps0);
+    set_prd(c, base, o->pass1.prd_eps0, o->pass1.prd_hybrid);
     set_phic(c, base);
     const int bw_used = base.block_warps > 0 ? base.block_warps : (prec ? 8 : 4);
     const int ctas_max = mali_max_ctas_per_sm(c->da, c->ndep, prec, bw_used);

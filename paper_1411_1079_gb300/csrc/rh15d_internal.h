@@ -663,6 +663,7 @@ struct IterLaunch {
     unsigned long long *rung_its = nullptr;   // [1 + nrung] formal solutions per pass / rung
     // partial redistribution (atoms with PRD lines)
     double prd_eps0 = 0.0;                    // PRD switching eps = min(1, eps0 it^2); <= 0: off
+    int prd_hybrid = 0;                       // 1: rho in the frame of the moving gas (hybrid PRD)
     const int *lane_prd = nullptr;            // [npad] PRD point of each lane, -1: none
     const double *prd_nu = nullptr, *prd_w = nullptr;   // [npp] frequency, quadrature weight
     void *prd_scr = nullptr;                  // per-block scratch (mali_prd_bytes_per_block)

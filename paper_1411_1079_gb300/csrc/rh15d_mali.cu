@@ -80,6 +80,7 @@ struct KParams {
     unsigned long long *rung_its;    // [1 + nrung] formal solutions of the pass and of each rung
     // partial redistribution
     double prd_eps0;
+    int prd_hybrid;                  // 1: rho in the frame of the moving gas
     const int *lane_prd;
     const double *prd_nu, *prd_w;
     char *prd_scr;
@@ -95,18 +96,31 @@ struct KParams {
 // [npp][N] the J-bar weights f, the mean intensity J, rho, D = dJ/drho (the
 // derivative of J through the line's own emission) and the reduced frequency
 // x of the point at each depth, per line [nprd][N] the damping a, then the
-// plain-rate accumulators [pacc][N]; in FP64 the supply fraction F and J-bar
-// per line [nprd][N], then the Ng history of rho [4][npp][N] (newest first).
+// plain-rate accumulators [pacc][N], the intensity of every ray at the PRD
+// points [2 nmu][npp][N] (ray 2 m + d) followed by each ray's dI/drho there
+// through the line's own emission [2 nmu][npp][N] (the hybrid scheme's
+// gas-frame J and D are interpolated from them) and each ray's rho at the
+// points [2 nmu][npp][N] (the hybrid scheme's gas-frame rho at the ray's
+// gas-frame frequency, filled once per iteration), the hybrid scheme's
+// interpolation tables of the column [2 nmu][npp][N] each (they depend on
+// its velocities only; brackets as int in R-sized slots): for J_f at point
+// i the bracket j and weight t of q_i + mu_z v_z and the weights e0, e1 of
+// point i in the ray's rho at points j and j + 1, for the ray's rho at
+// point p the bracket and weight of q_p - mu_z v_z; and the points'
+// frequencies in velocity units c (nu - nu0) / nu0 [npp].  In FP64 the
+// supply fraction F and J-bar per line [nprd][N], then the Ng history of rho
+// [4][npp][N] (newest first).
 template <typename R>
 struct PrdScr {
-    R *K, *f, *J, *rho, *D, *x, *a, *plain;
+    R *K, *f, *J, *rho, *D, *x, *a, *plain, *Iray, *ht, *he0, *he1, *rt, *q;
+    int *hj, *rj;
     double *F, *Jbar, *hist;
 };
 template <typename R>
 __host__ __device__ inline size_t prd_bytes(const DevAtom &A, int N)
 {
     size_t r = sizeof(R) * ((size_t)A.prd_koff[A.nprd] * N + 5 * (size_t)A.npp * N + (size_t)A.nprd * N +
-                            (size_t)A.pacc * N);
+                            (size_t)A.pacc * N + 18 * (size_t)A.nmu * A.npp * N + (size_t)A.npp);
     r = (r + 255) & ~(size_t)255;
     r += sizeof(double) * (2 * (size_t)A.nprd * N + 4 * (size_t)A.npp * N) + 256;
     return (r + 255) & ~(size_t)255;   // every block's scratch 256-byte aligned (float4 loads of K)
@@ -145,6 +159,23 @@ __device__ inline PrdScr<R> prd_carve(char *base, const DevAtom &A, int N)
     r += (size_t)A.nprd * N;
     q.plain = r;
     r += (size_t)A.pacc * N;
+    q.Iray = r;
+    r += 6 * (size_t)A.nmu * A.npp * N;   // intensities, dI/drho, then rho per ray
+    const size_t nt = 2 * (size_t)A.nmu * A.npp * N;
+    q.hj = reinterpret_cast<int *>(r);
+    r += nt;
+    q.ht = r;
+    r += nt;
+    q.he0 = r;
+    r += nt;
+    q.he1 = r;
+    r += nt;
+    q.rj = reinterpret_cast<int *>(r);
+    r += nt;
+    q.rt = r;
+    r += nt;
+    q.q = r;
+    r += (size_t)A.npp;
     size_t off = (reinterpret_cast<size_t>(r) + 255) & ~(size_t)255;
     q.F = reinterpret_cast<double *>(off);
     q.Jbar = q.F + (size_t)A.nprd * N;
@@ -314,6 +345,10 @@ template <> __device__ __forceinline__ double mu_of<double>(const DevAtom &A, in
 template <typename R> __device__ __forceinline__ R imu_of(const DevAtom &A, int m);
 template <> __device__ __forceinline__ float imu_of<float>(const DevAtom &A, int m) { return A.imuf[m]; }
 template <> __device__ __forceinline__ double imu_of<double>(const DevAtom &A, int m) { return 1.0 / A.mu[m]; }
+// a product rounded on its own (never fused into a following addition)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename R> __device__ __forceinline__ R wm2_of(const DevAtom &A, int m);
 template <> __device__ __forceinline__ float wm2_of<float>(const DevAtom &A, int m) { return A.wm2f[m]; }
 template <> __device__ __forceinline__ double wm2_of<double>(const DevAtom &A, int m) { return 0.5 * A.wmu[m]; }
@@ -457,9 +492,12 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 // NL >= 0: the tile's first NL slots are lines and the rest continua (the
 // host orders the transitions lines first), known at compile time so the
 // per-slot kind tests fold away; NL < 0: the kinds are read at run time.
+// prd_I (hybrid PRD only, else nullptr): the rays' intensities at the PRD
+// points and then their dI/drho, written here, and then the rays' rho,
+// read here; prd_q: the points' frequencies in velocity units.
 template <typename R, int K, int NL, bool PRD, bool CACHE>
 __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane, R *prd_rho,
-                             R *prd_J, R *prd_D, R *prd_plain, const R *phc)
+                             R *prd_J, R *prd_D, R *prd_plain, R *prd_I, const R *prd_q, const R *phc)
 {
     const int N = p.N;
     const DevTile &tl = A.tile[b];
@@ -521,11 +559,14 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
     int pp = -1;                                   // PRD point of the lane
     const R *rho_lane = nullptr;
     R *plain = nullptr;
+    bool hyb = false;                              // hybrid PRD at this lane
     if constexpr (PRD) {
         pp = tl.prd_slot >= 0 ? p.lane_prd[pi] : -1;
         rho_lane = pp >= 0 ? prd_rho + (size_t)pp * N : nullptr;
         plain = prd_plain + (size_t)tl.pacc_off * N;
+        hyb = prd_I != nullptr && pp >= 0;
     }
+    (void)prd_q;
 
     // rate contributions of one ray at one depth point (add: accumulate into val)
     auto contrib = [&](const DepthC<R, K> &d, const R (&phi)[K], const R (&chj)[K], const R (&U)[K], R ichi, R wo,
@@ -560,7 +601,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
 
     // contributions of one depth point to the tile's accumulators
     auto emit = [&](int k, const DepthC<R, K> &d, const R (&phi)[K], const R (&chj)[K], const R (&U)[K], R ichi,
-                    R wo, R omwo, R psi, R Ieff, R Ik, R wm2) {
+                    R wo, R omwo, R psi, R Ieff, R Ik, R wm2, int ray) {
         R val[P];
         contrib(d, phi, chj, U, ichi, wo, omwo, psi, Ieff, wm2, val, false);
         if constexpr (PRD) {
@@ -572,14 +613,22 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
             }
             // fire-and-forget reductions (zeroed before the sweep): one lane per
             // location, adding in program order, so the sum is deterministic;
-            // D = dJ/drho through the PRD line's own emission, Psi* n_u U0
+            // D = dJ/drho through the PRD line's own emission, Psi* n_u U0.
+            // Hybrid PRD: the ray's I and dI/drho at the point instead, for
+            // the gas-frame J and D of the rho update
             if (pp >= 0) {
                 R e0 = 0;
 #pragma unroll
                 for (int j = 0; j < K; ++j)
                     if (j == tl.prd_slot) e0 = d.nu_[j] * lc.Uc[j] * phi[j];
-                atomicAdd(prd_J + (size_t)pp * N + k, wm2 * Ik);
-                atomicAdd(prd_D + (size_t)pp * N + k, wm2 * psi * e0);
+                if (hyb) {
+                    const size_t ri = ((size_t)ray * A.npp + pp) * N + k;
+                    prd_I[ri] = Ik;
+                    prd_I[ri + 2 * (size_t)A.nmu * A.npp * N] = psi * e0;
+                } else {
+                    atomicAdd(prd_J + (size_t)pp * N + k, wm2 * Ik);
+                    atomicAdd(prd_D + (size_t)pp * N + k, wm2 * (psi * e0));
+                }
             }
         }
 #pragma unroll
@@ -747,6 +796,9 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
             const R muz = dir == 0 ? -mu : mu;
             const int ray = 2 * m + dir;
             R I, chip = 0, Sp;
+            // rho of the lane's PRD point: the static-frame ratio, or (hybrid)
+            // this ray's interpolated gas-frame ratio
+            const R *rl = hyb ? prd_I + ((4 * (size_t)A.nmu + ray) * A.npp + pp) * N : rho_lane;
             {
                 R pc[K];
                 // boundary point: I = 0 at the top; at the bottom the diffusion
@@ -755,14 +807,14 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 R B2 = 0;
                 if (dir == 1) {
                     DepthC<R, K> d2;
-                    depth_consts<R, K, PRD>(s, lc, N - 2, N, d2, rho_lane ? rho_lane[N - 2] : (R)1, tl.prd_slot);
+                    depth_consts<R, K, PRD>(s, lc, N - 2, N, d2, rl ? rl[N - 2] : (R)1, tl.prd_slot);
                     B2 = d2.B;
                     R phi[K], chj[K], U[K], eta;
                     load_ph(N - 2, ray, pc);
                     angle_vals<R, K, PRD>(lc, d2, pc, chip, eta, phi, chj, U);
                 }
                 DepthC<R, K> d;
-                depth_consts<R, K, PRD>(s, lc, k0, N, d, rho_lane ? rho_lane[k0] : (R)1, tl.prd_slot);
+                depth_consts<R, K, PRD>(s, lc, k0, N, d, rl ? rl[k0] : (R)1, tl.prd_slot);
                 R chi, eta, phi[K], chj[K], U[K];
                 load_ph(k0, ray, pc);
                 angle_vals<R, K, PRD>(lc, d, pc, chi, eta, phi, chj, U);
@@ -775,17 +827,17 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 }
                 chip = chi;
                 Sp = eta * ichi;
-                emit(k0, d, phi, chj, U, ichi, (R)0, (R)1, (R)0, I, I, wm2);
+                emit(k0, d, phi, chj, U, ichi, (R)0, (R)1, (R)0, I, I, wm2, ray);
             }
             // rho of the lane's PRD point (global scratch) loaded one depth step ahead
-            R rho_nx = (PRD && rho_lane) ? rho_lane[dir == 0 ? 1 : N - 2] : (R)1;
+            R rho_nx = (PRD && rl) ? rl[dir == 0 ? 1 : N - 2] : (R)1;
             // cached profiles, like rho, loaded one depth step ahead
             R pa[K];
             load_ph(dir == 0 ? 1 : N - 2, ray, pa);
             for (int step = 1; step < N; ++step) {
                 const int k = dir == 0 ? step : N - 1 - step;
                 const R rho_k = rho_nx;
-                if (PRD && rho_lane && step + 1 < N) rho_nx = rho_lane[dir == 0 ? step + 1 : N - 2 - step];
+                if (PRD && rl && step + 1 < N) rho_nx = rl[dir == 0 ? step + 1 : N - 2 - step];
                 R na[K];
                 load_ph(step + 1 < N ? (dir == 0 ? k + 1 : k - 1) : k, ray, na);
                 DepthC<R, K> d;
@@ -806,7 +858,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 const R psi = wo * ichi;
                 chip = chi;
                 Sp = S;
-                emit(k, d, phi, chj, U, ichi, wo, omwo, psi, Ieff, I, wm2);
+                emit(k, d, phi, chj, U, ichi, wo, omwo, psi, Ieff, I, wm2, ray);
             }
         }
     }
@@ -814,7 +866,8 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
 
 template <typename R, bool PRD, bool CACHE>
 __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane,
-                                           R *prd_rho, R *prd_J, R *prd_D, R *prd_plain, const R *phc)
+                                           R *prd_rho, R *prd_J, R *prd_D, R *prd_plain, R *prd_I,
+                                           const R *prd_q, const R *phc)
 {
     const DevTile &tl = A.tile[b];
     if constexpr (sizeof(R) == 4 && !PRD) {
@@ -823,7 +876,8 @@ __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, c
         // (transitions, lines)
         int nl = 0;
         for (int j = 0; j < tl.K; ++j) nl += A.tr[tl.t[j]].kind == 0;
-#define RH_TILE(K_, NL_) sweep_tile_k<R, K_, NL_, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc)
+#define RH_TILE(K_, NL_) \
+    sweep_tile_k<R, K_, NL_, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc)
         switch (tl.K * 4 + nl) {
         case 4: RH_TILE(1, 0); break;
         case 5: RH_TILE(1, 1); break;
@@ -838,10 +892,113 @@ __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, c
 #undef RH_TILE
     } else {
         switch (tl.K) {
-        case 1: sweep_tile_k<R, 1, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
-        case 2: sweep_tile_k<R, 2, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
-        default: sweep_tile_k<R, 3, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, phc); break;
+        case 1: sweep_tile_k<R, 1, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
+        case 2: sweep_tile_k<R, 2, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
+        default: sweep_tile_k<R, 3, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
         }
+    }
+}
+
+// Hybrid PRD tables.  Interpolation over PRD line [off, last] (points sorted
+// by frequency q, velocity units) at x: the bracket j in [off, last - 1] and
+// weight t on point j + 1, value (1 - t) v_j + t v_{j+1}; beyond the ends
+// the end value, (off, 0) or (last - 1, 1).
+template <typename R>
+__device__ __forceinline__ void prd_bracket(const R *qv, int off, int last, R x, int &j, R &t)
+{
+    if (x <= qv[off]) {
+        j = off;
+        t = 0;
+    } else if (x >= qv[last]) {
+        j = last - 1;
+        t = 1;
+    } else {
+        int lo = off, hi = last;                   // qv[lo] <= x < qv[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (qv[mid] <= x) lo = mid;
+            else hi = mid;
+        }
+        j = lo;
+        t = (x - qv[lo]) / (qv[lo + 1] - qv[lo]);
+    }
+}
+
+// weight of point i in the interpolation at x
+template <typename R>
+__device__ __forceinline__ R prd_weight(const R *qv, int off, int last, int i, R x)
+{
+    int j;
+    R t;
+    prd_bracket<R>(qv, off, last, x, j, t);
+    return (j == i ? (R)1 - t : (R)0) + (j + 1 == i ? t : (R)0);
+}
+
+// the column's tables: threads take (ray, point, depth)
+template <typename R>
+__device__ void build_hybrid_tables(const DevAtom &A, const Smem<R> &s, const PrdScr<R> &ps, int N)
+{
+    const int nw = 2 * A.nmu * A.npp * N;
+    for (int e = threadIdx.x; e < nw; e += blockDim.x) {
+        const int k = e % N, rp = e / N, pt = rp % A.npp, ray = rp / A.npp;
+        int q = 0;
+        while (pt >= A.prd_off[q + 1]) ++q;
+        const int off = A.prd_off[q], last = A.prd_off[q + 1] - 1;
+        const R mu = mu_of<R>(A, ray >> 1), muz = (ray & 1) ? mu : -mu, sh = muz * s.vz[k];
+        int j;
+        R t;
+        prd_bracket<R>(ps.q, off, last, ps.q[pt] + sh, j, t);
+        ps.hj[e] = j;
+        ps.ht[e] = t;
+        ps.he0[e] = prd_weight<R>(ps.q, off, last, pt, ps.q[j] - sh);
+        ps.he1[e] = prd_weight<R>(ps.q, off, last, pt, ps.q[j + 1] - sh);
+        prd_bracket<R>(ps.q, off, last, ps.q[pt] - sh, j, t);
+        ps.rj[e] = j;
+        ps.rt[e] = t;
+    }
+}
+
+// Hybrid PRD: each ray's rho at the PRD points, the gas-frame rho_f at the
+// ray's gas-frame frequency q_p - mu_z v_z, for the sweep to read like the
+// static-frame rho; threads take (ray, point, depth)
+template <typename R>
+__device__ void fill_rho_ray(const DevAtom &A, const PrdScr<R> &ps, int N)
+{
+    const int nw = 2 * A.nmu * A.npp * N;
+    R *out = ps.Iray + 4 * (size_t)A.nmu * A.npp * N;
+    for (int e = threadIdx.x; e < nw; e += blockDim.x) {
+        const int k = e % N, j = ps.rj[e];
+        const R t = ps.rt[e];
+        out[e] = ((R)1 - t) * ps.rho[(size_t)j * N + k] + t * ps.rho[(size_t)(j + 1) * N + k];
+    }
+}
+
+// Hybrid PRD: the gas-frame mean intensity and its local derivative at every
+// PRD point and depth (threads take (point, depth)),
+//   J_f(i) = sum over rays (w_mu/2) [(1 - t) I_j + t I_{j+1}],
+//   D_f(i) = sum over rays (w_mu/2) [(1 - t) dI_j e0 + t dI_{j+1} e1],
+// rays in the order the sweep adds the static-frame J, each product rounded
+// before its sum as the sweep's accumulation does
+template <typename R>
+__device__ void hybrid_JD(const DevAtom &A, const PrdScr<R> &ps, int N)
+{
+    const size_t nt = (size_t)A.npp * N, nr = 2 * (size_t)A.nmu;
+    for (int e = threadIdx.x; e < (int)nt; e += blockDim.x) {
+        const int k = e % N;
+        R J = 0, D = 0;
+        for (int ray = 0; ray < (int)nr; ++ray) {
+            const R w = wm2_of<R>(A, ray >> 1);
+            const size_t x = (size_t)ray * nt + e;
+            const int j = ps.hj[x];
+            const R t = ps.ht[x];
+            const R *Ir = ps.Iray + (size_t)ray * nt + k, *Dr = Ir + nr * nt;
+            const R v = ((R)1 - t) * Ir[(size_t)j * N] + t * Ir[(size_t)(j + 1) * N];
+            const R dv = ((R)1 - t) * Dr[(size_t)j * N] * ps.he0[x] + t * Dr[(size_t)(j + 1) * N] * ps.he1[x];
+            J += mul_rn(w, v);
+            D += mul_rn(w, dv);
+        }
+        ps.J[e] = J;
+        ps.D[e] = D;
     }
 }
 
@@ -1035,6 +1192,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 const double dnuD = tr.nu0 / kC * sqrt(2.0 * kK * p.T[cN + k] / A.mass);
                 ps.x[e] = (R)((p.prd_nu[pp] - tr.nu0) / dnuD);
             }
+            for (int pp = tid; pp < A.npp; pp += blockDim.x) {
+                int q = 0;
+                while (pp >= A.prd_off[q + 1]) ++q;
+                const double nu0 = A.tr[A.prd_t[q]].nu0;
+                ps.q[pp] = (R)(kC * (p.prd_nu[pp] - nu0) / nu0);
+            }
             for (int e = tid; e < A.nprd * N; e += blockDim.x) {
                 const int q = e / N, k = e % N;
                 const DevTrans &tr = A.tr[A.prd_t[q]];
@@ -1042,6 +1205,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 ps.a[e] = (R)exp((1.0 - sk) * tr.ln_atop + sk * tr.ln_abot);
             }
             __syncthreads();
+            if (p.prd_hybrid) build_hybrid_tables<R>(A, s, ps, N);   // read after later barriers
             for (int q = 0; q < A.nprd; ++q) {
                 const int off = A.prd_off[q], np = A.prd_off[q + 1] - off, npair = np * (np + 1) / 2;
                 R *Kq = ps.K + (size_t)A.prd_koff[q] * N;
@@ -1089,8 +1253,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
         int it = 0, status = RH_COL_MAXITER;
         double dmax = 1e300;
       restart:
-        if constexpr (PRD)
+        if constexpr (PRD) {
             for (int i = tid; i < A.npp * N; i += blockDim.x) ps.rho[i] = 1;   // PRD starts as CRD
+            if (p.prd_hybrid) {
+                __syncthreads();
+                fill_rho_ray<R>(A, ps, N);
+            }
+        }
         for (int i = tid; i < LN; i += blockDim.x) {
             double v = start == 0 ? p.nstar[(size_t)col * LN + i] : p.pops[(size_t)col * LN + i];
             s.n[i] = v;
@@ -1118,7 +1287,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 if (lane == 0) q = atomicAdd(&s.ibuf[1], 1);
                 q = __shfl_sync(0xffffffffu, q, 0);
                 if (q >= A.ntile) break;
-                sweep_tile<R, PRD, CACHE>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.D, ps.plain, phc);
+                sweep_tile<R, PRD, CACHE>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.D, ps.plain,
+                                          p.prd_hybrid ? ps.Iray : nullptr, ps.q, phc);
             }
             __syncthreads();
             // ---- rate equations, one thread per depth
@@ -1217,6 +1387,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 // it^2) of the iteration that uses it
                 const double eps =
                     p.prd_eps0 > 0.0 ? fmin(1.0, p.prd_eps0 * (double)(it + 1) * (double)(it + 1)) : 1.0;
+                if (p.prd_hybrid) {
+                    hybrid_JD<R>(A, ps, N);   // the gas-frame J and D in place of the sweep's
+                    __syncthreads();
+                }
                 for (int e = tid; e < A.nprd * N; e += blockDim.x) {
                     const int q = e / N, k = e % N, tq = A.prd_t[q];
                     const int u = A.tr[tq].u, l = A.tr[tq].l;
@@ -1381,6 +1555,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                     }
                 }
                 __syncthreads();
+                if (p.prd_hybrid) fill_rho_ray<R>(A, ps, N);   // read after the next barrier
             }
         }
         if (it > maxiter) it = maxiter;
@@ -1547,6 +1722,7 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
     p.rung_cols = o.rung_cols;
     p.rung_its = o.rung_its;
     p.prd_eps0 = o.prd_eps0;
+    p.prd_hybrid = o.prd_hybrid;
     p.lane_prd = o.lane_prd;
     p.prd_nu = o.prd_nu;
     p.prd_w = o.prd_w;
@@ -1620,6 +1796,7 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     p.rung_cols = o.rung_cols;
     p.rung_its = o.rung_its;
     p.prd_eps0 = o.prd_eps0;
+    p.prd_hybrid = o.prd_hybrid;
     p.lane_prd = o.lane_prd;
     p.prd_nu = o.prd_nu;
     p.prd_w = o.prd_w;
