@@ -145,6 +145,16 @@ typedef struct {
                              mu_z v_z / c); both transfers interpolate linearly in frequency over
                              the line's points, constant beyond its ends.  Without velocities the
                              two are the same scheme */
+    int32_t formal;       /* formal solver of the iteration: 0 linear short characteristics (Olson &
+                             Kunasz 1987); 1 quadratic Bezier short characteristics (the paper names no
+                             scheme): between the upwind point u and the point o the source function
+                             is the Bezier curve with control point C = S_o - (dtau_u/2) S'_o, S'_o the
+                             Fritsch-Butland harmonic mean of the slopes to u and to the downwind
+                             point (0 where they differ in sign), C held between S_u and S_o and the
+                             midpoint without a downwind point; Psi* = w_o + w_c.  Exact for a
+                             source function linear in tau, third order for smooth ones.  Emergent
+                             spectra (rh_emergent_spectrum, rh_emergent_stokes) keep their own
+                             solvers */
 } rh_iter_opts;
 
 typedef struct {

@@ -49,6 +49,10 @@ def lib():
         L.rho_cff.argtypes = []
         L.rho_sc_sweep.restype = None
         L.rho_sc_sweep.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_int, _dp, _dp]
+        L.rho_sc_sweep_bezier.restype = None
+        L.rho_sc_sweep_bezier.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_int, _dp, _dp]
+        L.rho_bez_weights.restype = None
+        L.rho_bez_weights.argtypes = [C.c_double, _dp]
         L.rho_ng2.restype = C.c_int
         L.rho_ng2.argtypes = [C.c_int64, _dp, _dp, _dp, _dp, _dp, C.c_int32]
         L.rho_gauss_legendre01.argtypes = [C.c_int, _dp, _dp]
@@ -122,7 +126,8 @@ class AtomDesc(C.Structure):
 class IterOpts(C.Structure):
     _fields_ = [("maxiter", C.c_int32), ("tol", C.c_double), ("ng_order", C.c_int32),
                 ("ng_delay", C.c_int32), ("ng_period", C.c_int32), ("start", C.c_int32),
-                ("crsw_init", C.c_double), ("prd_eps0", C.c_double), ("prd_hybrid", C.c_int32)]
+                ("crsw_init", C.c_double), ("prd_eps0", C.c_double), ("prd_hybrid", C.c_int32),
+                ("formal", C.c_int32)]
 
 
 class GridOpts(C.Structure):
@@ -197,15 +202,24 @@ def gauss_legendre01(n):
     return x, w
 
 
-def sc_sweep(dtau, S, I0, direction):
-    """Linear short-characteristics sweep; returns (I, dI/dS_local)."""
+def sc_sweep(dtau, S, I0, direction, bezier=False):
+    """Linear (or quadratic Bezier) short-characteristics sweep; returns
+    (I, dI/dS_local)."""
     dtau = np.ascontiguousarray(dtau, dtype=np.float64)
     S = np.ascontiguousarray(S, dtype=np.float64)
     N = S.size
     I = np.zeros(N)
     lam = np.zeros(N)
-    lib().rho_sc_sweep(N, _d(dtau), _d(S), float(I0), int(direction), _d(I), _d(lam))
+    f = lib().rho_sc_sweep_bezier if bezier else lib().rho_sc_sweep
+    f(N, _d(dtau), _d(S), float(I0), int(direction), _d(I), _d(lam))
     return I, lam
+
+
+def bez_weights(d):
+    """Quadratic Bezier step weights (e^-d, w_u, w_o, w_c, 1 - w_o - w_c)."""
+    out = np.zeros(5)
+    lib().rho_bez_weights(float(d), _d(out))
+    return out
 
 
 def ng2(x0, x1, x2, x3, relative=True):
@@ -348,10 +362,10 @@ class Oracle:
         self._check(self._lib.rho_set_populations(self._p, _d(n)))
 
     def iterate(self, maxiter=500, tol=1e-3, ng_order=2, ng_delay=5, ng_period=3, start=0,
-                crsw_init=1.0, nthreads=None, prd_eps0=0.0, prd_hybrid=0):
+                crsw_init=1.0, nthreads=None, prd_eps0=0.0, prd_hybrid=0, formal=0):
         o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
                      ng_period=ng_period, start=start, crsw_init=crsw_init, prd_eps0=prd_eps0,
-                     prd_hybrid=prd_hybrid)
+                     prd_hybrid=prd_hybrid, formal=formal)
         s = IterStats()
         if nthreads is None:
             nthreads = os.cpu_count() or 1

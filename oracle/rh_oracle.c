@@ -89,6 +89,7 @@ typedef struct {
     double prd_eps0;    /* PRD switching (Eq. 1): eps = min(1, eps0 it^2); <= 0: off (eps = 1) */
     int32_t prd_hybrid; /* 0: angle-averaged in the static frame; 1: the hybrid approximation of
                          * angle-dependent PRD in moving atmospheres (Sect. 2.1) */
+    int32_t formal;     /* formal solver: 0 linear short characteristics, 1 quadratic Bezier */
 } rho_iter_opts;
 
 typedef struct {
@@ -492,6 +493,102 @@ static void sc_sweep_full(int N, const double *dtau, const double *S, const doub
 void rho_sc_sweep(int N, const double *dtau, const double *S, double I0, int dir, double *I, double *lam)
 {
     sc_sweep_full(N, dtau, S, NULL, I0, dir, I, lam, NULL, NULL);
+}
+
+/* Quadratic Bezier short characteristics (the higher-order formal solver of
+ * the option formal = 1; the paper names no scheme).  Between the upwind
+ * point u and the point o the source function is the quadratic Bezier curve
+ * S(t) = (1-t)^2 S_u + 2 t (1-t) C + t^2 S_o in t = tau'/d, so
+ *   I_o = I_u e^{-d} + w_u S_u + w_o S_o + w_c C,
+ *   w_u = int_0^1 s^2 e^{-d s} d ds = [2 - e^{-d} (d^2 + 2d + 2)] / d^2,
+ *   w_o = int_0^1 (1-s)^2 e^{-d s} d ds = [d^2 - 2d + 2 - 2 e^{-d}] / d^2,
+ *   w_c = 2 int_0^1 s (1-s) e^{-d s} d ds = [2d - 4 + (2d + 4) e^{-d}] / d^2
+ * (w_u + w_o + w_c = 1 - e^{-d}).  The local operator is Psi* = w_o + w_c
+ * (C follows S_o), and 1 - Psi* = 2 [1 - e^{-d} (1 + d)] / d^2 is formed
+ * directly: at large d it is ~2/d^2 and 1 - (w_o + w_c) would cancel.  For
+ * d < 1 every weight comes from its power series in d (the closed forms
+ * cancel there). */
+static void bez_step_weights(double d, double *ex, double *wu, double *wo, double *wc, double *omp)
+{
+    if (d < 1.0) {
+        double t = 1.0, su = 0.0, so = 0.0, sc = 0.0, sp = 0.0;   /* t = (-d)^n / n! */
+        for (int n = 0; n < 40; ++n) {
+            if (n > 0) t *= -d / n;
+            su += t / (n + 3.0);
+            so += t * 2.0 / ((n + 1.0) * (n + 2.0) * (n + 3.0));
+            sc += t * 2.0 / ((n + 2.0) * (n + 3.0));
+            sp += t * 2.0 / (n + 2.0);
+            if (fabs(t) < 1e-22) break;
+        }
+        *wu = d * su;
+        *wo = d * so;
+        *wc = d * sc;
+        *omp = sp;
+        *ex = exp(-d);
+    } else {
+        double e = exp(-d), d2 = d * d;
+        *ex = e;
+        *wu = (2.0 - e * (d2 + 2.0 * d + 2.0)) / d2;
+        *wo = (d2 - 2.0 * d + 2.0 - 2.0 * e) / d2;
+        *wc = (2.0 * d - 4.0 + (2.0 * d + 4.0) * e) / d2;
+        *omp = 2.0 * (1.0 - e * (1.0 + d)) / d2;
+    }
+}
+
+void rho_bez_weights(double d, double *out5)
+{
+    bez_step_weights(d, out5, out5 + 1, out5 + 2, out5 + 3, out5 + 4);
+}
+
+/* The Bezier control point of the step u -> o: C = S_o - (d_u / 2) S'_o, the
+ * derivative at o the weighted harmonic mean of the two neighbouring slopes
+ * (Fritsch & Butland 1984), 0 where they differ in sign, and C held between
+ * S_u and S_o (no overshoot on the interval); without a downwind point the
+ * midpoint, which makes the step the linear one. */
+static double bez_control(double Su, double So, double Sd, double du, double dd, int has_d)
+{
+    if (!has_d) return 0.5 * (Su + So);
+    double su = (So - Su) / du, sd = (Sd - So) / dd, der = 0.0;
+    if (su * sd > 0.0) {
+        double a = (1.0 + dd / (du + dd)) / 3.0;
+        der = su * sd / (a * sd + (1.0 - a) * su);
+    }
+    double C = So - 0.5 * du * der;
+    double lo = Su < So ? Su : So, hi = Su < So ? So : Su;
+    return C < lo ? lo : (C > hi ? hi : C);
+}
+
+/* One sweep along a ray with the Bezier step (outputs as sc_sweep_full;
+ * lam = Psi* = w_o + w_c, Ieff = I with the local S_o replaced by Sloc_o
+ * through Psi*) */
+static void sc_sweep_bezier(int N, const double *dtau, const double *S, const double *Sloc, double I0, int dir,
+                            double *I, double *lam, double *Ieff, double *omlam)
+{
+    int k0 = dir > 0 ? 0 : N - 1;
+    I[k0] = I0;
+    lam[k0] = 0.0;
+    if (Ieff) Ieff[k0] = I0;
+    if (omlam) omlam[k0] = 1.0;
+    for (int s = 1; s < N; ++s) {
+        int ko = dir > 0 ? s : N - 1 - s;
+        int ku = ko - dir, kd = ko + dir;
+        int has_d = kd >= 0 && kd < N;
+        double du = dtau[dir > 0 ? ku : ko];
+        double dd = has_d ? dtau[dir > 0 ? ko : kd] : 0.0;
+        double ex, wu, wo, wc, omp;
+        bez_step_weights(du, &ex, &wu, &wo, &wc, &omp);
+        double C = bez_control(S[ku], S[ko], has_d ? S[kd] : 0.0, du, dd, has_d);
+        double base = I[ku] * ex + wu * S[ku] + wc * (C - S[ko]);
+        I[ko] = base + (wo + wc) * S[ko];
+        lam[ko] = wo + wc;
+        if (Ieff) Ieff[ko] = base + (wo + wc) * Sloc[ko];
+        if (omlam) omlam[ko] = omp;
+    }
+}
+
+void rho_sc_sweep_bezier(int N, const double *dtau, const double *S, double I0, int dir, double *I, double *lam)
+{
+    sc_sweep_bezier(N, dtau, S, NULL, I0, dir, I, lam, NULL, NULL);
 }
 
 /* ================================================================== */
@@ -1074,6 +1171,7 @@ typedef struct {
     double *Dray;     /* [2 nmu][nlam][N] each ray's dI/drho through the line's own emission */
     const double *vz; /* the column's vertical velocity (hybrid PRD) */
     int hybrid;       /* 1: rho in the fluid frame (hybrid PRD) */
+    int bezier;       /* 1: quadratic Bezier formal solver */
     double *prdK[MAXTR];   /* per PRD line [N][np][np]: normalised redistribution kernel */
     double *prdf[MAXTR];   /* per PRD line [N][np]: weights of J-bar */
 } work_t;
@@ -1668,12 +1766,14 @@ static void formal_ray(const rho_ctx *c, int64_t col, work_t *w, const double *n
     }
     double mu = a->mu[m];
     for (int k = 0; k < N - 1; ++k) w->dtau[k] = 0.5 * (w->chi[k] + w->chi[k + 1]) * w->dz[k] / mu;
+    void (*sweep)(int, const double *, const double *, const double *, double, int, double *, double *, double *,
+                  double *) = w->bezier ? sc_sweep_bezier : sc_sweep_full;
     if (d == 0) {
-        sc_sweep_full(N, w->dtau, w->S, w->Sbg, 0.0, +1, w->I, w->lam, w->Ieff, w->omlam);
+        sweep(N, w->dtau, w->S, w->Sbg, 0.0, +1, w->I, w->lam, w->Ieff, w->omlam);
     } else {
         double dtv = 0.5 * (w->chi[N - 1] + w->chi[N - 2]) * w->dz[N - 2];
         double B1 = w->Bnu[i * N + N - 1], B2 = w->Bnu[i * N + N - 2];
-        sc_sweep_full(N, w->dtau, w->S, w->Sbg, B1 + mu * (B1 - B2) / dtv, -1, w->I, w->lam, w->Ieff, w->omlam);
+        sweep(N, w->dtau, w->S, w->Sbg, B1 + mu * (B1 - B2) / dtv, -1, w->I, w->lam, w->Ieff, w->omlam);
     }
 }
 
@@ -2009,6 +2109,7 @@ static void iterate_column(rho_ctx *c, int64_t col, const rho_iter_opts *o, work
     double *nnew = malloc(nv * 8), *Cbase = malloc(sizeof(double) * N * L * L);
     column_setup(c, col, w);
     w->hybrid = o->prd_hybrid != 0;
+    w->bezier = o->formal == 1;
     w->vz = c->vz + col * N;
     memcpy(Cbase, w->C, sizeof(double) * N * L * L);
     if (o->start == 0)
@@ -2138,6 +2239,7 @@ int rho_iterate(rho_ctx *c, const rho_iter_opts *o, rho_iter_stats *st, int32_t 
     if (o->maxiter < 1 || !(o->tol >= 0)) return fail(c, "invalid iteration options");
     if (o->ng_order != 0 && o->ng_order != 2) return fail(c, "ng_order must be 0 or 2");
     if (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) return fail(c, "invalid Ng schedule");
+    if (o->formal != 0 && o->formal != 1) return fail(c, "formal must be 0 (linear) or 1 (Bezier)");
     if (nthreads < 1) nthreads = 1;
     struct timespec t0, t1;
     clock_gettime(CLOCK_MONOTONIC, &t0);

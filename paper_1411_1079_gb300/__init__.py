@@ -54,7 +54,7 @@ class IterOpts(C.Structure):
                 ("ng_delay", C.c_int32), ("ng_period", C.c_int32), ("start", C.c_int32),
                 ("precision", C.c_int32), ("persistent", C.c_int32), ("block_warps", C.c_int32),
                 ("crsw_init", C.c_double), ("only_unconverged", C.c_int32), ("prd_eps0", C.c_double),
-                ("prd_hybrid", C.c_int32)]
+                ("prd_hybrid", C.c_int32), ("formal", C.c_int32)]
 
 
 class IterStats(C.Structure):
@@ -274,11 +274,11 @@ class Context:
 
     def iterate(self, maxiter=500, tol=1e-3, ng_order=2, ng_delay=5, ng_period=3, start=0,
                 precision=1, persistent=1, block_warps=0, crsw_init=1.0, only_unconverged=0,
-                prd_eps0=0.0, prd_hybrid=0) -> dict:
+                prd_eps0=0.0, prd_hybrid=0, formal=0) -> dict:
         o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
                      ng_period=ng_period, start=start, precision=precision, persistent=persistent,
                      block_warps=block_warps, crsw_init=crsw_init, only_unconverged=only_unconverged,
-                     prd_eps0=prd_eps0, prd_hybrid=prd_hybrid)
+                     prd_eps0=prd_eps0, prd_hybrid=prd_hybrid, formal=formal)
         s = IterStats()
         rc = self._check(self._lib.rh_iterate(self._p, C.byref(o), C.byref(s)), allow=(RH_ENOTCONV,))
         out = {f: getattr(s, f) for f, _ in IterStats._fields_}
@@ -294,7 +294,7 @@ class Context:
 
     def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True, start=0,
               ng_order=2, ng_delay=5, ng_period=3, use_graph=1, autotune=1, fused_rerun=1,
-              prd_eps0=0.0, rungs=None, prd_hybrid=0, rerun_maxiter=None) -> dict:
+              prd_eps0=0.0, rungs=None, prd_hybrid=0, rerun_maxiter=None, formal=0) -> dict:
         """rh_solve: every column from LTE (start=0), the learned guess
         (start=1), the current populations (start=2), zero radiation (3) or
         escape probabilities (4) with Ng acceleration, then the columns that
@@ -312,7 +312,8 @@ class Context:
         o = SolveOpts()
         o.pass1 = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay, ng_period=ng_period,
                            start=start, precision=precision, persistent=persistent, block_warps=block_warps,
-                           crsw_init=1.0, only_unconverged=0, prd_eps0=prd_eps0, prd_hybrid=prd_hybrid)
+                           crsw_init=1.0, only_unconverged=0, prd_eps0=prd_eps0, prd_hybrid=prd_hybrid,
+                           formal=formal)
         # the ladder: from a start other than LTE, first LTE with the same
         # options; then stronger and stronger switching without Ng
         prd = getattr(self, "has_prd", False)
@@ -437,7 +438,7 @@ class Context:
 
     def iterate_noalloc(self, n_out, iters_out, status_out, dmax_out, maxiter=500, tol=1e-3, ng_order=2,
                         ng_delay=5, ng_period=3, start=0, precision=1, persistent=1, block_warps=0,
-                        crsw_init=1.0) -> dict:
+                        crsw_init=1.0, formal=0) -> dict:
         """rh_iterate_noalloc: results into caller-owned CUDA tensors (float64
         [ncol][nlev][ndep], int32 [ncol], uint8 [ncol], float64 [ncol]) on the
         context's device, contiguous; the library allocates nothing during the
@@ -461,7 +462,7 @@ class Context:
                 raise ValueError("%s holds %d elements, needs %d" % (name, t.numel(), numel))
         o = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay,
                      ng_period=ng_period, start=start, precision=precision, persistent=persistent,
-                     block_warps=block_warps, crsw_init=crsw_init, only_unconverged=0)
+                     block_warps=block_warps, crsw_init=crsw_init, only_unconverged=0, formal=formal)
         s = IterStats()
         rc = self._check(self._lib.rh_iterate_noalloc(self._p, C.byref(o), _ptr(n_out), _ptr(iters_out),
                                                       _ptr(status_out), _ptr(dmax_out), C.byref(s)),

@@ -1167,7 +1167,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
         (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) || (o->precision != 0 && o->precision != 1) ||
         (o->start < 0 || o->start > 4) || o->block_warps < 0 || o->block_warps > 8 ||
         (o->only_unconverged != 0 && o->only_unconverged != 1) || !std::isfinite(o->prd_eps0) ||
-        (o->prd_hybrid != 0 && o->prd_hybrid != 1))
+        (o->prd_hybrid != 0 && o->prd_hybrid != 1) || (o->formal != 0 && o->formal != 1))
         return fail(c, RH_EINVAL, "rh_iterate: invalid options");
     cudaSetDevice(c->dev);
     int start = o->start;
@@ -1249,6 +1249,7 @@ int rh_iterate(rh_ctx *c, const rh_iter_opts *o, rh_iter_stats *st)
     }
     IterLaunch il;
     il.precision = o->precision;
+    il.formal = o->formal;
     il.persistent = o->persistent;
     il.block_warps = o->block_warps;
     il.maxiter = o->maxiter;
@@ -1564,7 +1565,8 @@ bool valid_iter_opts(const rh_iter_opts *o)
     return o->maxiter >= 1 && o->tol >= 0 && (o->ng_order == 0 || o->ng_order == 2) &&
            !(o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) && (o->precision == 0 || o->precision == 1) &&
            o->start >= 0 && o->start <= 4 && o->block_warps >= 0 && o->block_warps <= 8 &&
-           std::isfinite(o->prd_eps0) && (o->prd_hybrid == 0 || o->prd_hybrid == 1);
+           std::isfinite(o->prd_eps0) && (o->prd_hybrid == 0 || o->prd_hybrid == 1) &&
+           (o->formal == 0 || o->formal == 1);
 }
 
 // everything the enqueued sequence depends on, compared byte-wise
@@ -1871,6 +1873,7 @@ int rh_solve(rh_ctx *c, const rh_solve_opts *o, rh_solve_stats *st)
 
     IterLaunch base;
     base.precision = prec;
+    base.formal = o->pass1.formal;
     base.persistent = o->pass1.persistent;
     base.block_warps = o->pass1.block_warps;
     base.maxiter = o->pass1.maxiter;
@@ -2055,7 +2058,8 @@ extern "C" int rh_iterate_noalloc(rh_ctx *c, const rh_iter_opts *o, double *n_ou
         return fail(c, RH_EINVAL, "rh_iterate_noalloc: opts and the four output buffers must not be NULL");
     if (o->maxiter < 1 || !(o->tol >= 0) || (o->ng_order != 0 && o->ng_order != 2) ||
         (o->ng_order == 2 && (o->ng_period < 1 || o->ng_delay < 0)) || (o->precision != 0 && o->precision != 1) ||
-        (o->start != 0 && o->start != 2) || o->block_warps < 0 || o->block_warps > 8 || o->only_unconverged != 0)
+        (o->start != 0 && o->start != 2) || o->block_warps < 0 || o->block_warps > 8 || o->only_unconverged != 0 ||
+        (o->formal != 0 && o->formal != 1))
         return fail(c, RH_EINVAL, "rh_iterate_noalloc: invalid options (only_unconverged is not supported here)");
     if (c->da.nprd) return fail(c, RH_EINVAL, "rh_iterate_noalloc: atoms with PRD lines need scratch; use rh_iterate");
     if (c->dev < 0 || c->dev >= kNoallocMaxDev) return fail(c, RH_EINVAL, "rh_iterate_noalloc: device index too large");
@@ -2107,6 +2111,7 @@ extern "C" int rh_iterate_noalloc(rh_ctx *c, const rh_iter_opts *o, double *n_ou
     cc.dmax = dmax_out;
     IterLaunch il{};
     il.precision = o->precision;
+    il.formal = o->formal;
     il.persistent = o->persistent;
     il.block_warps = o->block_warps;
     il.maxiter = o->maxiter;

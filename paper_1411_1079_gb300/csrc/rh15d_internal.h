@@ -584,6 +584,89 @@ __device__ __forceinline__ void sc_weights(float d, float &one_m_e0, float &wu, 
     }
 }
 
+// Quadratic Bezier short-characteristics step over optical path d (the
+// higher-order formal solver option): I_o = I_u ex + wu S_u + wo S_o + wc C
+// with C the Bezier control point of the step, and omp = 1 - wo - wc for the
+// local operator Psi* = wo + wc.  wu = [2 - e^{-d}(d^2 + 2d + 2)]/d^2,
+// wo = [d^2 - 2d + 2 - 2e^{-d}]/d^2, wc = [2d - 4 + (2d + 4)e^{-d}]/d^2,
+// omp = 2[1 - e^{-d}(1 + d)]/d^2; below d = 1 their power series in d
+// (t_n = (-d)^n/n!: wu = d sum t_n/(n+3), wo = d sum 2t_n/((n+1)(n+2)(n+3)),
+// wc = d sum 2t_n/((n+2)(n+3)), omp = sum 2t_n/(n+2)), where the closed
+// forms cancel.
+__device__ __forceinline__ void bez_weights(double d, double &ex, double &wu, double &wo, double &wc, double &omp)
+{
+    if (d < 1.0) {
+        double t = 1.0, su = 0.0, so = 0.0, sc = 0.0, sp = 0.0;   // 22 terms: truncation < 1e-20
+#pragma unroll
+        for (int n = 0; n < 22; ++n) {
+            if (n > 0) t *= -d * (1.0 / n);
+            su += t * (1.0 / (n + 3));
+            so += t * (2.0 / ((n + 1) * (n + 2) * (n + 3)));
+            sc += t * (2.0 / ((n + 2) * (n + 3)));
+            sp += t * (2.0 / (n + 2));
+        }
+        wu = d * su;
+        wo = d * so;
+        wc = d * sc;
+        omp = sp;
+        ex = exp(-d);
+    } else {
+        const double e = exp(-d), d2 = d * d, id2 = 1.0 / d2;
+        ex = e;
+        wu = (2.0 - e * (d2 + 2.0 * d + 2.0)) * id2;
+        wo = (d2 - 2.0 * d + 2.0 - 2.0 * e) * id2;
+        wc = (2.0 * d - 4.0 + (2.0 * d + 4.0) * e) * id2;
+        omp = 2.0 * (1.0 - e * (1.0 + d)) * id2;
+    }
+}
+
+__device__ __forceinline__ void bez_weights(float d, float &ex, float &wu, float &wo, float &wc, float &omp)
+{
+    if (d < 1.0f) {
+        float t = 1.0f, su = 0.0f, so = 0.0f, sc = 0.0f, sp = 0.0f;   // 12 terms: truncation < 3e-9
+#pragma unroll
+        for (int n = 0; n < 12; ++n) {
+            if (n > 0) t *= -d * (1.0f / n);
+            su += t * (1.0f / (n + 3));
+            so += t * (2.0f / ((n + 1) * (n + 2) * (n + 3)));
+            sc += t * (2.0f / ((n + 2) * (n + 3)));
+            sp += t * (2.0f / (n + 2));
+        }
+        wu = d * su;
+        wo = d * so;
+        wc = d * sc;
+        omp = sp;
+        ex = __expf(-d);
+    } else {
+        const float e = __expf(-d), d2 = d * d, id2 = rcp_f32(d2);
+        ex = e;
+        wu = (2.0f - e * (d2 + 2.0f * d + 2.0f)) * id2;
+        wo = (d2 - 2.0f * d + 2.0f - 2.0f * e) * id2;
+        wc = (2.0f * d - 4.0f + (2.0f * d + 4.0f) * e) * id2;
+        omp = 2.0f * (1.0f - e * (1.0f + d)) * id2;
+    }
+}
+
+// The Bezier control point of the step u -> o: C = S_o - (d_u/2) S'_o, S'_o
+// the weighted harmonic mean of the slopes to the upwind and the downwind
+// point (Fritsch & Butland 1984; 0 where they differ in sign), C held
+// between S_u and S_o; without a downwind point the midpoint (the linear
+// step).
+template <typename R>
+__device__ __forceinline__ R bez_control(R Su, R So, R Sd, R du, R dd, bool has_d)
+{
+    if (!has_d) return (R)0.5 * (Su + So);
+    const R su = (So - Su) / du, sd = (Sd - So) / dd;
+    R der = 0;
+    if (su * sd > (R)0) {
+        const R a = ((R)1 + dd / (du + dd)) * (R)(1.0 / 3.0);
+        der = su * sd / (a * sd + ((R)1 - a) * su);
+    }
+    const R C = So - (R)0.5 * du * der;
+    const R lo = Su < So ? Su : So, hi = Su < So ? So : Su;
+    return C < lo ? lo : (C > hi ? hi : C);
+}
+
 // spectrum sweeps need no 1 - w_o
 template <typename R>
 __device__ __forceinline__ void sc_weights(R d, R &one_m_e0, R &wu, R &wo)
@@ -664,6 +747,7 @@ struct IterLaunch {
     // partial redistribution (atoms with PRD lines)
     double prd_eps0 = 0.0;                    // PRD switching eps = min(1, eps0 it^2); <= 0: off
     int prd_hybrid = 0;                       // 1: rho in the frame of the moving gas (hybrid PRD)
+    int formal = 0;                           // formal solver: 0 linear, 1 quadratic Bezier
     const int *lane_prd = nullptr;            // [npad] PRD point of each lane, -1: none
     const double *prd_nu = nullptr, *prd_w = nullptr;   // [npp] frequency, quadrature weight
     void *prd_scr = nullptr;                  // per-block scratch (mali_prd_bytes_per_block)

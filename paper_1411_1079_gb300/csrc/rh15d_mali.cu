@@ -81,6 +81,7 @@ struct KParams {
     // partial redistribution
     double prd_eps0;
     int prd_hybrid;                  // 1: rho in the frame of the moving gas
+    int formal;                      // formal solver: 0 linear, 1 quadratic Bezier short characteristics
     const int *lane_prd;
     const double *prd_nu, *prd_w;
     char *prd_scr;
@@ -256,11 +257,12 @@ __host__ __device__ size_t smem_bytes(int L, int N, int ntr, int ncont, int nlin
     return smem_layout<R>(L, N, ntr, ncont, nline, macc, ring_warps).end;
 }
 
-// kernels whose sweep reads the line profiles through the ring
-template <typename R, bool PRD, bool CACHE>
+// kernels whose sweep reads the line profiles through the ring (the
+// two-angle passes of the linear solver)
+template <typename R, bool PRD, bool CACHE, bool BEZ>
 __host__ __device__ constexpr bool uses_ring()
 {
-    return RH_ANGLE_PAIRS && CACHE && !PRD && sizeof(R) == 4;
+    return RH_ANGLE_PAIRS && CACHE && !PRD && !BEZ && sizeof(R) == 4;
 }
 
 template <typename R>
@@ -495,7 +497,7 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 // prd_I (hybrid PRD only, else nullptr): the rays' intensities at the PRD
 // points and then their dI/drho, written here, and then the rays' rho,
 // read here; prd_q: the points' frequencies in velocity units.
-template <typename R, int K, int NL, bool PRD, bool CACHE>
+template <typename R, int K, int NL, bool PRD, bool CACHE, bool BEZ>
 __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane, R *prd_rho,
                              R *prd_J, R *prd_D, R *prd_plain, R *prd_I, const R *prd_q, const R *phc)
 {
@@ -559,6 +561,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
     int pp = -1;                                   // PRD point of the lane
     const R *rho_lane = nullptr;
     R *plain = nullptr;
+    constexpr bool bez = BEZ;                      // quadratic Bezier formal solver
     bool hyb = false;                              // hybrid PRD at this lane
     if constexpr (PRD) {
         pp = tl.prd_slot >= 0 ? p.lane_prd[pi] : -1;
@@ -641,7 +644,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
     };
 
 #if RH_ANGLE_PAIRS
-    if constexpr (!PRD) {
+    if constexpr (!PRD && !BEZ) {
         // two angles per pass: the depth terms once per depth, the angles'
         // contributions summed in registers, one warp reduction per depth
         for (int m0 = 0; m0 < nmu; m0 += 2) {
@@ -696,7 +699,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
                 }
                 // profiles of the depth being swept: through the warp's ring
                 // (copies issued two steps ahead), else loaded one step ahead
-                constexpr bool RING = uses_ring<R, PRD, CACHE>() && NL > 0;
+                constexpr bool RING = uses_ring<R, PRD, CACHE, BEZ>() && NL > 0;
                 R pa[K], pb[K];
                 float *rw = nullptr;   // the lane's element of the warp's ring
                 int rs = 1;            // ring slot of the current step
@@ -836,26 +839,52 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
             load_ph(dir == 0 ? 1 : N - 2, ray, pa);
             for (int step = 1; step < N; ++step) {
                 const int k = dir == 0 ? step : N - 1 - step;
+                const bool has_d = step + 1 < N;   // a downwind point
                 const R rho_k = rho_nx;
-                if (PRD && rl && step + 1 < N) rho_nx = rl[dir == 0 ? step + 1 : N - 2 - step];
+                if (PRD && rl && has_d) rho_nx = rl[dir == 0 ? step + 1 : N - 2 - step];
                 R na[K];
-                load_ph(step + 1 < N ? (dir == 0 ? k + 1 : k - 1) : k, ray, na);
+                load_ph(has_d ? (dir == 0 ? k + 1 : k - 1) : k, ray, na);
+                // quadratic Bezier step: the downwind point's opacity and source
+                // function first (its profiles and rho are the ones loaded for
+                // the next step), so that its depth terms are dead before the
+                // point's own are formed
+                R chid = 0, Sd = 0;
+                if (bez && has_d) {   // BEZ kernels only
+                    DepthC<R, K> dd;
+                    depth_consts<R, K, PRD>(s, lc, dir == 0 ? k + 1 : k - 1, N, dd, rho_nx, tl.prd_slot);
+                    R etad, phid[K], chjd[K], Ud[K];
+                    angle_vals<R, K, PRD>(lc, dd, na, chid, etad, phid, chjd, Ud);
+                    Sd = etad * rcp<R>(chid);
+                }
                 DepthC<R, K> d;
                 depth_consts<R, K, PRD>(s, lc, k, N, d, rho_k, tl.prd_slot);
                 R chi, eta, phi[K], chj[K], U[K];
                 angle_vals<R, K, PRD>(lc, d, pa, chi, eta, phi, chj, U);
-#pragma unroll
-                for (int j = 0; j < K; ++j) pa[j] = na[j];
                 const R ichi = rcp<R>(chi);
                 const R S = eta * ichi;
                 const R dzk = dir == 0 ? s.dz[k - 1] : s.dz[k];
                 const R dtau = (R)0.5 * (chi + chip) * dzk * imu;
-                R ome, wu, wo, omwo;
-                sc_weights(dtau, ome, wu, wo, omwo);
-                const R base = I * ome + wu * Sp;
-                I = base + wo * S;
-                const R Ieff = base + wo * (d.etabg * ichi);
-                const R psi = wo * ichi;
+                R Ieff, psi, wo, omwo;
+                if (bez) {
+                    const R dtd = has_d ? (R)0.5 * (chid + chi) * (dir == 0 ? s.dz[k] : s.dz[k - 1]) * imu : (R)1;
+                    R ex, wu, wob, wc, omp;
+                    bez_weights(dtau, ex, wu, wob, wc, omp);
+                    const R C = bez_control<R>(Sp, S, Sd, dtau, dtd, has_d);
+                    const R base = I * ex + wu * Sp + wc * (C - S);
+                    wo = wob + wc;                 // Psi* = w_o + w_c
+                    omwo = omp;
+                    I = base + wo * S;
+                    Ieff = base + wo * (d.etabg * ichi);
+                } else {
+                    R ome, wu;
+                    sc_weights(dtau, ome, wu, wo, omwo);
+                    const R base = I * ome + wu * Sp;
+                    I = base + wo * S;
+                    Ieff = base + wo * (d.etabg * ichi);
+                }
+                psi = wo * ichi;
+#pragma unroll
+                for (int j = 0; j < K; ++j) pa[j] = na[j];
                 chip = chi;
                 Sp = S;
                 emit(k, d, phi, chj, U, ichi, wo, omwo, psi, Ieff, I, wm2, ray);
@@ -864,20 +893,20 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
     }
 }
 
-template <typename R, bool PRD, bool CACHE>
+template <typename R, bool PRD, bool CACHE, bool BEZ>
 __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane,
                                            R *prd_rho, R *prd_J, R *prd_D, R *prd_plain, R *prd_I,
                                            const R *prd_q, const R *phc)
 {
     const DevTile &tl = A.tile[b];
-    if constexpr (sizeof(R) == 4 && !PRD) {
+    if constexpr (sizeof(R) == 4 && !PRD && !BEZ) {
         // the FP32 CRD instantiations (with and without the profile cache, so
         // that the two keep the same arithmetic): one tile kernel per
         // (transitions, lines)
         int nl = 0;
         for (int j = 0; j < tl.K; ++j) nl += A.tr[tl.t[j]].kind == 0;
 #define RH_TILE(K_, NL_) \
-    sweep_tile_k<R, K_, NL_, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc)
+    sweep_tile_k<R, K_, NL_, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc)
         switch (tl.K * 4 + nl) {
         case 4: RH_TILE(1, 0); break;
         case 5: RH_TILE(1, 1); break;
@@ -892,9 +921,9 @@ __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, c
 #undef RH_TILE
     } else {
         switch (tl.K) {
-        case 1: sweep_tile_k<R, 1, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
-        case 2: sweep_tile_k<R, 2, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
-        default: sweep_tile_k<R, 3, -1, PRD, CACHE>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
+        case 1: sweep_tile_k<R, 1, -1, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
+        case 2: sweep_tile_k<R, 2, -1, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
+        default: sweep_tile_k<R, 3, -1, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
         }
     }
 }
@@ -1117,14 +1146,16 @@ __device__ int solve_depth(const DevAtom &A, const double *slotd, const float *s
 }
 
 // CACHE: line profiles from the per-block cache (p.phic, nullptr only for an
-// atom without lines); otherwise evaluated in the sweep
-template <typename R, bool PRD, bool CACHE>
+// atom without lines); otherwise evaluated in the sweep.  BEZ: the quadratic
+// Bezier formal solver (its own instantiations, so that the linear kernels
+// keep their registers)
+template <typename R, bool PRD, bool CACHE, bool BEZ>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) mali_kernel(const __grid_constant__ DevAtom A, const KParams p)
 {
     extern __shared__ __align__(16) char smem_raw[];
     const int N = p.N, L = A.nlev;
     Smem<R> s = carve<R>(smem_raw, L, N, A.ntr, A.ncont, A.nline, A.macc,
-                         uses_ring<R, PRD, CACHE>() ? (int)(blockDim.x >> 5) : 0);
+                         uses_ring<R, PRD, CACHE, BEZ>() ? (int)(blockDim.x >> 5) : 0);
     const int tid = threadIdx.x, lane = tid & 31;
     const int LN = L * N;
     double *hist = p.nghist + (size_t)blockIdx.x * 4 * LN;
@@ -1287,7 +1318,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 if (lane == 0) q = atomicAdd(&s.ibuf[1], 1);
                 q = __shfl_sync(0xffffffffu, q, 0);
                 if (q >= A.ntile) break;
-                sweep_tile<R, PRD, CACHE>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.D, ps.plain,
+                sweep_tile<R, PRD, CACHE, BEZ>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.D, ps.plain,
                                           p.prd_hybrid ? ps.Iray : nullptr, ps.q, phc);
             }
             __syncthreads();
@@ -1610,17 +1641,29 @@ size_t mali_prd_bytes_per_block(const DevAtom &A, int ndep, int precision)
     return precision == 1 ? prd_bytes<float>(A, ndep) : prd_bytes<double>(A, ndep);
 }
 
+// the column kernel for (PRD lines, profile cache, Bezier solver); the
+// Bezier kernels exist with the profile cache only (nullptr otherwise)
+template <typename R>
+static void (*pick_kernel(bool prd, bool cache, bool bez))(DevAtom, KParams)
+{
+    if (prd) return bez ? mali_kernel<R, true, true, true> : mali_kernel<R, true, true, false>;
+    if (cache) return bez ? mali_kernel<R, false, true, true> : mali_kernel<R, false, true, false>;
+    return bez ? nullptr : mali_kernel<R, false, false, false>;
+}
+
+// resident blocks per SM of the linear solver's kernel (a launch with the
+// Bezier solver takes its own kernel's occupancy)
 int mali_max_ctas_per_sm(const DevAtom &A, int ndep, int precision, int block_warps)
 {
     size_t sm;
     const void *fn;
     if (precision == 1) {
         sm = smem_bytes<float>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc,
-                               A.nprd ? 0 : (uses_ring<float, false, true>() ? block_warps : 0));
-        fn = A.nprd ? (const void *)mali_kernel<float, true, true> : (const void *)mali_kernel<float, false, true>;
+                               A.nprd ? 0 : (uses_ring<float, false, true, false>() ? block_warps : 0));
+        fn = (const void *)pick_kernel<float>(A.nprd > 0, true, false);
     } else {
         sm = smem_bytes<double>(A.nlev, ndep, A.ntr, A.ncont, A.nline, A.macc, 0);
-        fn = A.nprd ? (const void *)mali_kernel<double, true, true> : (const void *)mali_kernel<double, false, true>;
+        fn = (const void *)pick_kernel<double>(A.nprd > 0, true, false);
     }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
     int per_sm = 0;
@@ -1633,13 +1676,14 @@ static cudaError_t launch_t(const DevAtom &A, const KParams &p, int block_warps,
                             size_t prd_cap, size_t phic_cap, cudaStream_t st, float *ms, char *err, size_t errn,
                             int *grid_out)
 {
-    const int ring_warps = !A.nprd && uses_ring<R, false, true>() ? block_warps : 0;
+    const bool bez = p.formal == 1;
+    const int ring_warps = !A.nprd && !bez && uses_ring<R, false, true, false>() ? block_warps : 0;
     size_t sm = smem_bytes<R>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc, ring_warps);
     if (A.nphi && !p.phic) {
         snprintf(err, errn, "no profile cache");
         return cudaErrorInvalidValue;
     }
-    auto kern = A.nprd ? mali_kernel<R, true, true> : mali_kernel<R, false, true>;
+    auto kern = pick_kernel<R>(A.nprd > 0, true, bez);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int threads = block_warps * 32;
@@ -1723,6 +1767,7 @@ cudaError_t launch_mali(const DevAtom &A, const ColumnArrays &c, const void *lan
     p.rung_its = o.rung_its;
     p.prd_eps0 = o.prd_eps0;
     p.prd_hybrid = o.prd_hybrid;
+    p.formal = o.formal;
     p.lane_prd = o.lane_prd;
     p.prd_nu = o.prd_nu;
     p.prd_w = o.prd_w;
@@ -1797,6 +1842,7 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
     p.rung_its = o.rung_its;
     p.prd_eps0 = o.prd_eps0;
     p.prd_hybrid = o.prd_hybrid;
+    p.formal = o.formal;
     p.lane_prd = o.lane_prd;
     p.prd_nu = o.prd_nu;
     p.prd_w = o.prd_w;
@@ -1815,15 +1861,18 @@ cudaError_t launch_mali_prealloc(const DevAtom &A, const ColumnArrays &c, const 
         snprintf(err, errn, "the partial-redistribution kernel needs the profile cache");
         return cudaErrorInvalidValue;
     }
+    const bool bez = o.formal == 1;
+    if (bez && !cache) {
+        snprintf(err, errn, "the Bezier formal solver needs the profile cache (an earlier rh_iterate or rh_solve)");
+        return cudaErrorInvalidValue;
+    }
     if (o.precision == 1) {
         sm = smem_bytes<float>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc,
-                               (!A.nprd && cache && uses_ring<float, false, true>()) ? bw : 0);
-        fn = A.nprd ? (const void *)mali_kernel<float, true, true>
-                    : (cache ? (const void *)mali_kernel<float, false, true> : (const void *)mali_kernel<float, false, false>);
+                               (!A.nprd && cache && !bez && uses_ring<float, false, true, false>()) ? bw : 0);
+        fn = (const void *)pick_kernel<float>(A.nprd > 0, cache, bez);
     } else {
         sm = smem_bytes<double>(A.nlev, p.N, A.ntr, A.ncont, A.nline, A.macc, 0);
-        fn = A.nprd ? (const void *)mali_kernel<double, true, true>
-                    : (cache ? (const void *)mali_kernel<double, false, true> : (const void *)mali_kernel<double, false, false>);
+        fn = (const void *)pick_kernel<double>(A.nprd > 0, cache, bez);
     }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
