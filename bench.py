@@ -802,7 +802,8 @@ def run_full_compare(args):
 def run_ncu_case(args):
     """Small fixed cases for ncu captures (columns of the 256x256 cube):
     crd -- the column kernel, --ncu-iters iterations from LTE;
-    prd -- the same with Lyman alpha and beta in PRD (64 points each);
+    prd -- the same with Lyman alpha and beta in PRD (64 points each;
+           --ncu-prd-hybrid: the hybrid scheme);
     stokes -- the H alpha Zeeman Stokes spectrum (400 wavelengths) after a
               few iterations;
     mlp -- one training epoch of the learned-guess network (BF16 GEMMs)."""
@@ -817,10 +818,12 @@ def run_ncu_case(args):
         rh_synth.hydrogen_like_atom()
     ctx.setup_atom(atom)
     ctx.load_columns(sub)
-    out = {"ncu_case": kind, "columns": args.ncu_columns, "precision": args.ncu_precision}
+    out = {"ncu_case": kind, "columns": args.ncu_columns, "precision": args.ncu_precision,
+           "prd_hybrid": int(args.ncu_prd_hybrid), "formal": args.ncu_formal}
     if kind in ("crd", "prd"):
         s = ctx.iterate(maxiter=args.ncu_iters, tol=0.0, precision=args.ncu_precision,
-                        prd_eps0=0.05 if kind == "prd" else 0.0)
+                        prd_eps0=0.05 if kind == "prd" else 0.0,
+                        prd_hybrid=int(args.ncu_prd_hybrid) if kind == "prd" else 0, formal=args.ncu_formal)
         out.update(iterations=args.ncu_iters, seconds=s["seconds"], pts=s["pts"])
     elif kind == "stokes":
         ctx.iterate(maxiter=args.ncu_iters, tol=0.0, precision=1)
@@ -874,6 +877,8 @@ def main():
     ap.add_argument("--ncu-kind", default="crd", choices=["crd", "prd", "stokes", "mlp"])
     ap.add_argument("--ncu-precision", type=int, default=1)
     ap.add_argument("--ncu-iters", type=int, default=3)
+    ap.add_argument("--ncu-prd-hybrid", action="store_true")
+    ap.add_argument("--ncu-formal", type=int, default=0, choices=[0, 1])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
