@@ -288,13 +288,15 @@ class Context:
     # Sect. 2.3: run all columns with an aggressive choice of options, then
     # re-run the columns that did not converge with other options.
     RERUN_CRSW = (1e3, 1e5, 1e7)
-    # with PRD lines the rungs keep Ng (its Jacobi step on rho): the damped
-    # rho update without it diverges on strongly moving columns
-    RERUN_CRSW_PRD = (1e3, 1e5)
+    # with PRD lines the rungs keep Ng (its Jacobi step on rho) first -- the
+    # damped rho update without it diverges on strongly moving columns -- and
+    # end with rungs without Ng, which converge columns where Ng's
+    # extrapolation of rho does not
+    RERUN_PRD = ((1e3, 1), (1e5, 1), (1e3, 0), (1e5, 0))
 
     def solve(self, precision=1, maxiter=500, tol=1e-3, persistent=1, block_warps=0, rescue=True, start=0,
               ng_order=2, ng_delay=5, ng_period=3, use_graph=1, autotune=1, fused_rerun=1,
-              prd_eps0=0.0, rungs=None, prd_hybrid=0, rerun_maxiter=None, formal=0) -> dict:
+              prd_eps0=0.0, rungs=None, prd_hybrid=0, rerun_maxiter=None, formal=0, rescue_formal=None) -> dict:
         """rh_solve: every column from LTE (start=0), the learned guess
         (start=1), the current populations (start=2), zero radiation (3) or
         escape probabilities (4) with Ng acceleration, then the columns that
@@ -304,11 +306,17 @@ class Context:
         strategy): by the column kernel itself as
         soon as a column fails (fused_rerun=1) or as separate passes over a
         device-selected list; the sequence is replayed as a CUDA graph.
-        With PRD lines the default ladder keeps Ng in every rung (LTE, then
-        switching x1e3 and x1e5) and re-runs take up to 3 x maxiter
-        iterations.  rungs: the re-run ladder as (collisional-radiative
+        With PRD lines the default ladder is LTE with the same options (when
+        pass 1 started elsewhere), switching x1e3 and x1e5 with Ng, then
+        x1e3 and x1e5 without Ng, at most MAX_RERUN rungs, and re-runs take
+        up to 3 x maxiter iterations.  rungs: the re-run ladder as (collisional-radiative
         factor, Ng on) pairs, at most MAX_RERUN of them, in place of the
-        default; rerun_maxiter: the re-runs' iteration limit."""
+        default; rerun_maxiter: the re-runs' iteration limit.  rescue_formal
+        (default: 1 with PRD lines, none otherwise): after the ladder, one
+        more pass (rh_iterate, only_unconverged) over the columns still not
+        converged, from LTE with Ng and that formal solver -- the Bezier
+        solver converges most PRD columns on which every linear-solver rung
+        diverges; its counts are merged into the result under "rescue"."""
         o = SolveOpts()
         o.pass1 = IterOpts(maxiter=maxiter, tol=tol, ng_order=ng_order, ng_delay=ng_delay, ng_period=ng_period,
                            start=start, precision=precision, persistent=persistent, block_warps=block_warps,
@@ -319,7 +327,7 @@ class Context:
         prd = getattr(self, "has_prd", False)
         if rungs is None:
             if prd:
-                rungs = ([(1.0, 1)] if start != 0 else []) + [(f, 1) for f in self.RERUN_CRSW_PRD]
+                rungs = (([(1.0, 1)] if start != 0 else []) + list(self.RERUN_PRD))[:MAX_RERUN]
             else:
                 rungs = ([(1.0, 1)] if start != 0 else []) + [(f, 0) for f in self.RERUN_CRSW]
         if rerun_maxiter is None:
@@ -340,7 +348,7 @@ class Context:
         if r not in (0, 6):
             self._check(r)
         npass = 1 + o.nrerun
-        return {"n_converged": st.n_converged, "n_maxiter": st.n_maxiter, "n_failed": st.n_failed,
+        out = {"n_converged": st.n_converged, "n_maxiter": st.n_maxiter, "n_failed": st.n_failed,
                 "seconds": st.seconds, "pts": st.pts, "iterations_total": st.iterations_total,
                 "pass_columns": list(st.pass_columns)[:npass], "pass_iterations": list(st.pass_iterations)[:npass],
                 "pass_seconds": list(st.pass_seconds)[:npass],
@@ -348,6 +356,22 @@ class Context:
                 "guess_fallback_depths": st.guess_fallback_depths, "launches": st.kernel_launches,
                 "graph_replayed": bool(st.graph_replayed), "block_warps": st.block_warps,
                 "ctas_per_sm": st.ctas_per_sm}
+        if rescue_formal is None and prd and formal == 0:
+            rescue_formal = 1
+        if rescue and rescue_formal is not None and out["n_converged"] < self.ncol:
+            r2 = self.iterate(maxiter=int(rerun_maxiter), tol=tol, ng_order=ng_order, ng_delay=ng_delay,
+                              ng_period=ng_period, start=0, precision=precision, persistent=persistent,
+                              block_warps=block_warps, only_unconverged=1, prd_eps0=prd_eps0,
+                              prd_hybrid=prd_hybrid, formal=int(rescue_formal))
+            out["rescue"] = {"formal": int(rescue_formal), "columns": r2["n_processed"],
+                             "iterations": r2["iterations_total"], "seconds": r2["seconds"],
+                             "converged_before": out["n_converged"], "converged_after": r2["n_converged"]}
+            for k in ("n_converged", "n_maxiter", "n_failed"):
+                out[k] = r2[k]
+            out["iterations_total"] += r2["iterations_total"]
+            out["seconds"] += r2["seconds"]
+            out["pts"] += r2["pts"]
+        return out
 
     def emergent_stokes(self, line, g_eff, B_T, theta, chi, lam_m, precision=0, out=None):
         """rh_emergent_stokes: (I, Q, U, V) at mu = 1 of line `line` with Zeeman
