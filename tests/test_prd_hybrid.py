@@ -86,3 +86,19 @@ def test_hybrid_at_rest_is_the_static_scheme(rh, cols, precision):
                   prd_hybrid=hyb)
         out.append(g.populations()[0])
     assert np.array_equal(out[0], out[1])
+
+
+def test_solve_rescues_columns_with_the_bezier_solver(rh):
+    """Four columns of the 512x512 x 128-height cube (seed 5678) on which
+    every rung of the re-run ladder diverges with the linear formal solver
+    (hybrid PRD, Lyman alpha and beta at 200 points): the final pass of
+    solve with the Bezier solver converges at least three of them."""
+    atom = rh_synth.hydrogen_like_atom(prd_lines=((1, 2), (1, 3)), prd_nlambda=200)
+    sub = rh_synth.subset(rh_synth.chromosphere_cube(512, 512, 128, seed=5678), [15527, 15528, 28816, 28817])
+    g = rh.Context(0)
+    g.setup_atom(atom)
+    g.load_columns(sub)
+    s = g.solve(maxiter=500, tol=1e-3, precision=1, prd_eps0=0.05, prd_hybrid=1)
+    st = g.populations()[2]
+    assert s["rescue"]["formal"] == 1 and s["rescue"]["converged_before"] == 0
+    assert s["rescue"]["converged_after"] >= 3 and int((st == 0).sum()) == s["n_converged"] >= 3
