@@ -496,10 +496,10 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 // per-slot kind tests fold away; NL < 0: the kinds are read at run time.
 // prd_I (hybrid PRD only, else nullptr): the rays' intensities at the PRD
 // points and then their dI/drho, written here, and then the rays' rho,
-// read here; prd_q: the points' frequencies in velocity units.
+// read here.
 template <typename R, int K, int NL, bool PRD, bool CACHE, bool BEZ>
 __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane, R *prd_rho,
-                             R *prd_J, R *prd_D, R *prd_plain, R *prd_I, const R *prd_q, const R *phc)
+                             R *prd_J, R *prd_D, R *prd_plain, R *prd_I, const R *phc)
 {
     const int N = p.N;
     const DevTile &tl = A.tile[b];
@@ -569,7 +569,6 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
         plain = prd_plain + (size_t)tl.pacc_off * N;
         hyb = prd_I != nullptr && pp >= 0;
     }
-    (void)prd_q;
 
     // rate contributions of one ray at one depth point (add: accumulate into val)
     auto contrib = [&](const DepthC<R, K> &d, const R (&phi)[K], const R (&chj)[K], const R (&U)[K], R ichi, R wo,
@@ -896,7 +895,7 @@ __device__ void sweep_tile_k(const DevAtom &A, const Smem<R> &s, const KParams &
 template <typename R, bool PRD, bool CACHE, bool BEZ>
 __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, const KParams &p, int b, int lane,
                                            R *prd_rho, R *prd_J, R *prd_D, R *prd_plain, R *prd_I,
-                                           const R *prd_q, const R *phc)
+                                           const R *phc)
 {
     const DevTile &tl = A.tile[b];
     if constexpr (sizeof(R) == 4 && !PRD && !BEZ) {
@@ -906,7 +905,7 @@ __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, c
         int nl = 0;
         for (int j = 0; j < tl.K; ++j) nl += A.tr[tl.t[j]].kind == 0;
 #define RH_TILE(K_, NL_) \
-    sweep_tile_k<R, K_, NL_, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc)
+    sweep_tile_k<R, K_, NL_, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, phc)
         switch (tl.K * 4 + nl) {
         case 4: RH_TILE(1, 0); break;
         case 5: RH_TILE(1, 1); break;
@@ -921,9 +920,9 @@ __device__ __forceinline__ void sweep_tile(const DevAtom &A, const Smem<R> &s, c
 #undef RH_TILE
     } else {
         switch (tl.K) {
-        case 1: sweep_tile_k<R, 1, -1, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
-        case 2: sweep_tile_k<R, 2, -1, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
-        default: sweep_tile_k<R, 3, -1, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, prd_q, phc); break;
+        case 1: sweep_tile_k<R, 1, -1, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, phc); break;
+        case 2: sweep_tile_k<R, 2, -1, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, phc); break;
+        default: sweep_tile_k<R, 3, -1, PRD, CACHE, BEZ>(A, s, p, b, lane, prd_rho, prd_J, prd_D, prd_plain, prd_I, phc); break;
         }
     }
 }
@@ -1319,7 +1318,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? RH_FP32_MINBLOCKS : 1) m
                 q = __shfl_sync(0xffffffffu, q, 0);
                 if (q >= A.ntile) break;
                 sweep_tile<R, PRD, CACHE, BEZ>(A, s, p, A.order[q], lane, ps.rho, ps.J, ps.D, ps.plain,
-                                          p.prd_hybrid ? ps.Iray : nullptr, ps.q, phc);
+                                          p.prd_hybrid ? ps.Iray : nullptr, phc);
             }
             __syncthreads();
             // ---- rate equations, one thread per depth
