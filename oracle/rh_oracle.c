@@ -26,7 +26,10 @@
  * iteration; PRD switching eps = min(1, eps0 it^2); Ng and a Jacobi step on
  * the PRD ratio rho; for the hybrid PRD option (Sect. 2.1), the gas-frame
  * mean intensity and ratio transferred between frames by linear
- * interpolation in frequency over the line's points, constant beyond them.
+ * interpolation in frequency over the line's points, constant beyond them;
+ * for the higher-order formal-solver option, quadratic Bezier short
+ * characteristics with a Fritsch-Butland control point held between its
+ * neighbours.
  *
  * Parity status: every function is pinned by a test against closed forms,
  * limits or an independent library routine, except the overall multi-level
