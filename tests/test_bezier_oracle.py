@@ -71,3 +71,20 @@ def test_no_overshoot_at_a_step(orc):
             I, lam = orc.sc_sweep(np.diff(tau) / mu, S, I0, direction, bezier=True)
             assert np.all(I <= S.max() + 1e-12) and np.all(I >= -1e-12)
             assert np.all((lam >= 0) & (lam <= 1))
+
+
+def test_two_point_ray_is_the_linear_step(orc):
+    """Without a downwind point the control point is the midpoint, and the
+    Bezier step is the linear one (w_u + w_c/2 and w_o + w_c/2 are the
+    linear weights): checked on two-point rays across optical thicknesses
+    and with the exact linear-source intensity."""
+    rng = np.random.default_rng(5)
+    for d in (1e-6, 1e-3, 0.2, 0.9, 1.0, 1.5, 7.0, 200.0, 1e6):
+        for _ in range(3):
+            S = rng.uniform(0.1, 5.0, 2)
+            I0 = rng.uniform(0.0, 5.0)
+            for direction in (1, -1):
+                Ib, lb = orc.sc_sweep(np.array([d]), S, I0, direction, bezier=True)
+                Il, ll = orc.sc_sweep(np.array([d]), S, I0, direction, bezier=False)
+                k = 1 if direction > 0 else 0
+                assert abs(Ib[k] - Il[k]) <= 1e-13 * max(1.0, abs(Il[k])), (d, direction)
